@@ -1,0 +1,518 @@
+"""Pins for the FP64 oracle: facts the paper and the mathematics fix, not the oracle's own formulas.
+
+Each test is chosen so that a plausible slip in the oracle (a dropped term, a wrong sign, a
+transposed operand, an off-by-one window) fails at least one of them:
+
+* mesh counts printed in the paper (golden) and vertex valences of the right-cut mesh;
+* Algorithm 1/2 explicit arrays against the vertex lists (twins share an edge, reversed);
+* region growing against an independent union-find over the explicit half-edges;
+* Laplacian: zero motion on affine grids, convexity (no out-of-plane motion), hand cases;
+* normals: the closed form A x B on affine grids, sensor-facing orientation;
+* bilateral: fixed point, the box-filter limit (convolution), the identity limit, a
+  two-triangle closed form, sharp creases preserved;
+* group assignment: thresholds probed from both sides, ties, masks;
+* whole path: noise-free scenes map to their ground-truth groups.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def affine_grid(H, W, o=(0.25, -0.5, 2.0), A=(0.0, 0.0625, 0.0), B=(0.0625, 0.0, 0.0)):
+    """p(u, v) = o + u A + v B with dyadic numbers: exactly representable in FP32."""
+    u, v = np.meshgrid(np.arange(H, dtype=np.float64), np.arange(W, dtype=np.float64), indexing="ij")
+    P = np.asarray(o)[None, None, :] + u[..., None] * np.asarray(A) + v[..., None] * np.asarray(B)
+    return P.astype(np.float32)
+
+
+def plane_grid(H, W, normal, dist, f=50.0, rng=None, nan_frac=0.0):
+    """Pinhole rays (x right, y down, z forward) cut by the plane n . p = dist."""
+    n = np.asarray(normal, np.float64)
+    n = n / np.linalg.norm(n)
+    u, v = np.meshgrid(np.arange(H, dtype=np.float64), np.arange(W, dtype=np.float64), indexing="ij")
+    d = np.stack([(v - (W - 1) / 2) / f, (u - (H - 1) / 2) / f, np.ones_like(u)], -1)
+    t = dist / (d @ n)
+    P = (t[..., None] * d).astype(np.float32)
+    if rng is not None and nan_frac > 0:
+        P[rng.random((H, W)) < nan_frac] = np.nan
+    return P, n
+
+
+# ----------------------------------------------------------------------------- mesh counts
+
+
+def test_paper_triangle_counts():
+    """Full grids keep 2(M-1)(N-1) triangles: the paper's 498,002 and 50,218."""
+    cases = json.load(open(os.path.join(GOLDEN, "paper_triangle_counts.json")))["cases"]
+    for c in cases:
+        P = oracle.widen(affine_grid(c["rows"], c["cols"]))
+        m, _ = oracle.mask(P, P, 0.0)
+        assert int(m.sum()) == c["triangles"]
+        T, Tmap = oracle.extract_triangles(P)
+        assert T.shape[0] == c["triangles"]
+
+
+@pytest.mark.parametrize("pos,lost", [((3, 4), 6), ((0, 0), 2), ((0, 6), 1), ((5, 6), 2), ((5, 0), 1),
+                                      ((0, 3), 3), ((5, 3), 3), ((2, 0), 3), ((2, 6), 3)])
+def test_vertex_valence_of_right_cut_mesh(pos, lost):
+    """A NaN point removes exactly the triangles around it: 6 inside, 3 on an edge, 2 or 1 at corners
+    (the diagonal runs from (u, v) to (u+1, v+1), so corners (0,0) and (M-1,N-1) touch two triangles)."""
+    H, W = 6, 7
+    P = affine_grid(H, W)
+    P[pos] = np.nan
+    m, _ = oracle.mask(oracle.widen(P), oracle.widen(P), 0.0)
+    assert int(m.sum()) == 2 * (H - 1) * (W - 1) - lost
+
+
+def test_edge_length_rule_strict():
+    """Algorithm 4 rejects only when the longest edge is strictly greater than l_max."""
+    P = affine_grid(4, 5, A=(0.0, 0.0625, 0.0), B=(0.0625, 0.0, 0.0))
+    W = oracle.widen(P)
+    diag = np.hypot(0.0625, 0.0625)
+    m, e = oracle.mask(W, W, diag)
+    assert m.all()
+    assert np.allclose(e, diag, rtol=0, atol=1e-15)
+    m, _ = oracle.mask(W, W, np.nextafter(diag, 0))
+    assert not m.any()
+    m, _ = oracle.mask(W, W, 0.0)   # disabled
+    assert m.all()
+
+
+# ----------------------------------------------------------------------------- Algorithms 1 and 2
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_halfedges_are_reversed_shared_edges(seed):
+    """Every twin pair of Algorithm 2 joins two triangles of Algorithm 1 along the same edge, reversed;
+    HE is an involution; and the twins are exactly the implicit neighbour rule."""
+    rng = np.random.default_rng(seed)
+    H, W = int(rng.integers(2, 9)), int(rng.integers(2, 9))
+    P = affine_grid(H, W)
+    P[rng.random((H, W)) < 0.2] = np.nan
+    T, Tmap = oracle.extract_triangles(oracle.widen(P))
+    HE = oracle.extract_halfedges(Tmap, H, W, T.shape[0])
+    # every edge shared by two valid triangles, found by brute force over vertex pairs
+    edges = {}
+    for t in range(T.shape[0]):
+        for e in range(3):
+            a, b = int(T[t, e]), int(T[t, (e + 1) % 3])
+            edges[(a, b)] = 3 * t + e
+    for h in range(HE.shape[0]):
+        t, e = divmod(h, 3)
+        a, b = int(T[t, e]), int(T[t, (e + 1) % 3])
+        twin = edges.get((b, a), -1)
+        assert HE[h] == twin, (h, HE[h], twin)
+        if HE[h] >= 0:
+            assert HE[HE[h]] == h
+    # implicit rule == explicit twins (GID space)
+    inv = {int(i): g for g, i in enumerate(Tmap) if i >= 0}
+    for h in range(HE.shape[0]):
+        if HE[h] < 0:
+            continue
+        g1, g2 = inv[h // 3], inv[int(HE[h]) // 3]
+        assert g2 in oracle.triangle_twins(g1, H, W)
+
+
+def test_first_triangle_vertex_order_and_gid():
+    """Algorithm 1: first = {p3, p2, p1}, second = {p1, p4, p3}; GID = 2 (u (N-1) + v) + k."""
+    H, W = 3, 4
+    T, Tmap = oracle.extract_triangles(oracle.widen(affine_grid(H, W)))
+    u, v = 1, 2
+    p1, p2, p3, p4 = u * W + v, u * W + v + 1, (u + 1) * W + v + 1, (u + 1) * W + v
+    g = 2 * (u * (W - 1) + v)
+    assert list(T[Tmap[g]]) == [p3, p2, p1]
+    assert list(T[Tmap[g + 1]]) == [p1, p4, p3]
+
+
+# ----------------------------------------------------------------------------- region growing
+
+
+class _UF:
+    def __init__(self, n):
+        self.p = list(range(n))
+
+    def find(self, x):
+        while self.p[x] != x:
+            self.p[x] = self.p[self.p[x]]
+            x = self.p[x]
+        return x
+
+    def union(self, a, b):
+        a, b = self.find(a), self.find(b)
+        if a != b:
+            self.p[max(a, b)] = min(a, b)
+
+
+def brute_labels(P, G, tri_min=0, C=None, nd=None, max_offset=0.0):
+    """Components over the explicit half-edges of Algorithms 1-2 with a textbook union-find."""
+    H, W = P.shape[:2]
+    T, Tmap = oracle.extract_triangles(oracle.widen(P))
+    HE = oracle.extract_halfedges(Tmap, H, W, T.shape[0])
+    inv = {int(i): g for g, i in enumerate(Tmap) if i >= 0}
+    n = G.shape[0]
+    uf = _UF(n)
+    for h in range(HE.shape[0]):
+        if HE[h] < 0:
+            continue
+        a, b = inv[h // 3], inv[int(HE[h]) // 3]
+        if G[a] == 255 or G[a] != G[b]:
+            continue
+        if max_offset > 0 and abs(float(nd[G[a]] @ (C[a] - C[b]))) > max_offset:
+            continue
+        uf.union(a, b)
+    lab = np.array([uf.find(i) if G[i] != 255 else -1 for i in range(n)], np.int64)
+    if tri_min > 0:
+        roots, counts = np.unique(lab[lab >= 0], return_counts=True)
+        small = set(int(r) for r, c in zip(roots, counts) if c <= tri_min)
+        lab = np.array([-1 if l in small else l for l in lab])
+    return lab
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_labels_match_union_find_on_tiny_grids(seed):
+    rng = np.random.default_rng(100 + seed)
+    H, W = int(rng.integers(2, 9)), int(rng.integers(2, 9))
+    P = affine_grid(H, W)
+    P[rng.random((H, W)) < 0.15] = np.nan
+    n = 2 * (H - 1) * (W - 1)
+    m, _ = oracle.mask(oracle.widen(P), oracle.widen(P), 0.0)
+    G = rng.integers(0, 3, n).astype(np.uint8)
+    G[rng.random(n) < 0.2] = 255
+    G[m == 0] = 255       # triangles with a NaN vertex have no group (Algorithm 4 runs on T only)
+    tri_min = int(rng.integers(0, 4))
+    got = oracle.label(G, H, W, tri_min=tri_min)
+    want = brute_labels(P, G, tri_min)
+    np.testing.assert_array_equal(got, want)
+
+
+def test_labels_with_offset_test_match_union_find():
+    rng = np.random.default_rng(7)
+    H, W = 7, 8
+    P = affine_grid(H, W)
+    P[..., 2] += rng.normal(0, 0.01, (H, W)).astype(np.float32)
+    Pw = oracle.widen(P)
+    C, _ = oracle.triangle_geometry(Pw)
+    nd = oracle.normalize_dominant(np.array([[0, 0, 1], [1, 0, 0]], np.float32))
+    n = C.shape[0]
+    G = np.zeros(n, np.uint8)
+    G[rng.random(n) < 0.1] = 1
+    got = oracle.label(G, H, W, C, nd, max_offset=0.006)
+    want = brute_labels(P, G, 0, C, nd, 0.006)
+    np.testing.assert_array_equal(got, want)
+
+
+def test_uniform_plane_is_one_component():
+    H, W = 9, 11
+    n = 2 * (H - 1) * (W - 1)
+    lab = oracle.label(np.zeros(n, np.uint8), H, W)
+    assert (lab == 0).all()
+    lab = oracle.label(np.zeros(n, np.uint8), H, W, tri_min=n)      # |T| > tri_min fails
+    assert (lab == -1).all()
+    lab = oracle.label(np.zeros(n, np.uint8), H, W, tri_min=n - 1)
+    assert (lab == 0).all()
+
+
+def test_label_is_min_gid_of_component():
+    rng = np.random.default_rng(3)
+    H, W = 8, 8
+    n = 2 * (H - 1) * (W - 1)
+    G = rng.integers(0, 2, n).astype(np.uint8)
+    lab = oracle.label(G, H, W)
+    for l in np.unique(lab):
+        members = np.nonzero(lab == l)[0]
+        assert members.min() == l
+
+
+# ----------------------------------------------------------------------------- Laplacian (Eq. 1-2)
+
+
+@pytest.mark.parametrize("kernel", [3, 5])
+def test_laplacian_affine_grid_does_not_move(kernel):
+    """Symmetric inverse-distance weights cancel on an affine grid (no NaN)."""
+    P = oracle.widen(affine_grid(12, 13, A=(0.0, 0.0625, 0.125), B=(0.0625, 0.0, -0.03125)))
+    S = oracle.laplacian(P, kernel, 1.0, 4)
+    assert np.abs(S - P).max() < 1e-13
+
+
+def test_laplacian_is_convex_no_out_of_plane_motion():
+    """lambda in [0, 1] makes each update a convex combination, so no point leaves the plane."""
+    rng = np.random.default_rng(5)
+    P, n = plane_grid(20, 24, normal=(0.3, -0.4, -1.0), dist=-2.0, rng=rng, nan_frac=0.1)
+    Pw = oracle.widen(P)
+    d_in = np.nanmax(np.abs(Pw @ n + 2.0))
+    for lam in (0.3, 1.0):
+        S = oracle.laplacian(Pw, 3, lam, 5)
+        d_out = np.nanmax(np.abs(S @ n + 2.0))
+        assert d_out <= d_in + 1e-12
+        np.testing.assert_array_equal(np.isnan(S), np.isnan(Pw))
+
+
+def test_laplacian_lambda_zero_and_border_pinned():
+    rng = np.random.default_rng(6)
+    P = oracle.widen(rng.normal(0, 1, (9, 10, 3)).astype(np.float32))
+    assert np.array_equal(oracle.laplacian(P, 3, 0.0, 3), P)
+    for kernel in (3, 5):
+        r = kernel // 2
+        S = oracle.laplacian(P, kernel, 1.0, 3)
+        border = np.ones((9, 10), bool)
+        border[r:-r, r:-r] = False
+        assert np.array_equal(S[border], P[border])
+        assert not np.array_equal(S[~border], P[~border])
+
+
+def test_laplacian_hand_cases():
+    """3x3 grid, kernel 3: only the centre is filtered (border pinned)."""
+    P = np.full((3, 3, 3), np.nan)
+    P[1, 1] = (0, 0, 0)
+    P[1, 2] = (1, 0, 0)          # distance 1 -> w = 1
+    P[0, 1] = (0, 2, 0)          # distance 2 -> w = 1/2
+    S = oracle.laplacian(P, 3, 1.0, 1)
+    # (1 * (1,0,0) + 1/2 * (0,2,0)) / (1 + 1/2) = (2/3, 2/3, 0)
+    np.testing.assert_allclose(S[1, 1], (2 / 3, 2 / 3, 0), atol=1e-15)
+    S = oracle.laplacian(P, 3, 0.5, 1)
+    np.testing.assert_allclose(S[1, 1], (1 / 3, 1 / 3, 0), atol=1e-15)
+    # a neighbour at distance 0 carries no weight; alone it leaves the point where it is
+    Q = np.full((3, 3, 3), np.nan)
+    Q[1, 1] = (1, 2, 3)
+    Q[2, 2] = (1, 2, 3)
+    assert np.array_equal(oracle.laplacian(Q, 3, 1.0, 2)[1, 1], Q[1, 1])
+    # an isolated point stays put; NaN stays NaN
+    R = np.full((3, 3, 3), np.nan)
+    R[1, 1] = (1, 2, 3)
+    S = oracle.laplacian(R, 3, 1.0, 1)
+    assert np.array_equal(S[1, 1], R[1, 1]) and np.isnan(S[0, 0]).all()
+
+
+def test_laplacian_jacobi_two_iterations_by_hand():
+    """A 1x5 interior row inside a 3x7 grid of NaN: Jacobi reads only the previous iterate."""
+    P = np.full((3, 7, 3), np.nan)
+    xs = [0.0, 1.0, 3.0, 4.0, 8.0]
+    for i, x in enumerate(xs):
+        P[1, 1 + i] = (x, 0, 0)
+    lam = 0.5
+
+    def step(row):
+        # each interior point has its row neighbours v-1, v+1 (border columns and other rows are NaN)
+        out = list(row)
+        for i in range(len(row)):
+            nb = [row[j] for j in (i - 1, i + 1) if 0 <= j < len(row)]
+            w = [1 / abs(x - row[i]) for x in nb]
+            out[i] = row[i] + lam * sum(wi * (x - row[i]) for wi, x in zip(w, nb)) / sum(w)
+        return out
+    r1 = step(xs)
+    np.testing.assert_allclose(oracle.laplacian(P, 3, lam, 1)[1, 1:6, 0], r1, atol=1e-14)
+    np.testing.assert_allclose(oracle.laplacian(P, 3, lam, 2)[1, 1:6, 0], step(r1), atol=1e-14)
+
+
+def test_laplacian_equivariance():
+    """Rigid motions commute with the filter; a sign slip in the update would still pass this, the
+    hand cases above would not."""
+    rng = np.random.default_rng(8)
+    P = oracle.widen(rng.normal(0, 1, (8, 9, 3)).astype(np.float32))
+    P[2, 3] = np.nan
+    q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+    q *= np.sign(np.linalg.det(q))
+    t = np.array([1.0, -2.0, 0.5])
+    S = oracle.laplacian(P, 3, 0.7, 3)
+    S2 = oracle.laplacian(P @ q.T + t, 3, 0.7, 3)
+    np.testing.assert_allclose(S2, S @ q.T + t, atol=1e-12)
+
+
+# ----------------------------------------------------------------------------- normals (Section 5.2)
+
+
+@pytest.mark.parametrize("A,B", [((0.0, 0.0625, 0.0), (0.0625, 0.0, 0.0)),
+                                 ((0.0, 0.0625, 0.03125), (0.0625, 0.0, -0.125)),
+                                 ((0.125, 0.0, 0.0), (0.0, 0.0, 0.0625))])
+def test_normals_on_affine_grid_are_a_cross_b(A, B):
+    """For p = o + u A + v B both triangles of every quad have normal A x B / |A x B|."""
+    P = oracle.widen(affine_grid(5, 6, A=A, B=B))
+    C, N = oracle.triangle_geometry(P)
+    want = np.cross(A, B)
+    want = want / np.linalg.norm(want)
+    np.testing.assert_allclose(N, np.broadcast_to(want, N.shape), atol=1e-14)
+    T, _ = oracle.extract_triangles(P)
+    np.testing.assert_allclose(C, P.reshape(-1, 3)[T].mean(axis=1), atol=1e-14)
+
+
+def test_fronto_parallel_normal_faces_sensor():
+    """Optical frame (x right, y down, z forward): a wall in front of the camera has normal (0, 0, -1)."""
+    P, _ = plane_grid(6, 8, normal=(0, 0, 1), dist=2.0)
+    _, N = oracle.triangle_geometry(oracle.widen(P))
+    np.testing.assert_allclose(N, np.broadcast_to([0, 0, -1.0], N.shape), atol=1e-6)
+
+
+def test_tilted_plane_normals_face_sensor():
+    rng = np.random.default_rng(9)
+    for _ in range(5):
+        n = rng.normal(size=3)
+        n[2] = -abs(n[2]) - 0.5          # plane in front of the camera, facing it
+        P, nu = plane_grid(7, 9, normal=n, dist=-2.0)
+        Pw = oracle.widen(P)
+        C, N = oracle.triangle_geometry(Pw)
+        assert (np.einsum("ij,ij->i", N, C) < 0).all()   # facing the sensor at the origin
+        np.testing.assert_allclose(np.abs(N @ nu), 1.0, atol=1e-5)
+
+
+def test_nan_vertex_gives_nan_triangle():
+    P = affine_grid(4, 4)
+    P[1, 1, 2] = np.inf       # any non-finite coordinate invalidates the point
+    C, N = oracle.triangle_geometry(oracle.widen(P))
+    bad = np.isnan(N[:, 0])
+    assert bad.sum() == 6 and np.isnan(C[bad]).all()
+
+
+# ----------------------------------------------------------------------------- bilateral (Eq. 3-6)
+
+
+def test_bilateral_constant_field_is_fixed_point():
+    P = oracle.widen(affine_grid(9, 10, A=(0.0, 0.0625, 0.03125), B=(0.0625, 0.0, 0.0)))
+    C, N = oracle.triangle_geometry(P)
+    Nf = oracle.bilateral(C, N, 9, 10, 3, 0.1, 0.15, 4)
+    np.testing.assert_allclose(Nf, N, atol=1e-14)
+
+
+def _box_filter_normals(N, H, W, r, iters):
+    """Unweighted window mean via summed shifted copies: the sigma -> infinity limit of Eq. 3."""
+    Hq, Wq = H - 1, W - 1
+    cur = N.reshape(Hq, Wq, 2, 3).copy()
+    for _ in range(iters):
+        valid = ~np.isnan(cur[..., 0])
+        z = np.where(valid[..., None], cur, 0.0).sum(axis=2)           # both triangles of a quad
+        pad = np.pad(z, ((r, r), (r, r), (0, 0)))
+        s = sum(pad[r + du:r + du + Hq, r + dv:r + dv + Wq] for du in range(-r, r + 1) for dv in range(-r, r + 1))
+        s = s / np.linalg.norm(s, axis=-1, keepdims=True)
+        cur = np.where(valid[..., None], s[:, :, None, :], np.nan)
+    return cur.reshape(-1, 3)
+
+
+@pytest.mark.parametrize("kernel,iters", [(3, 1), (3, 2), (5, 1)])
+def test_bilateral_large_sigma_is_box_mean(kernel, iters):
+    rng = np.random.default_rng(10 + kernel)
+    H, W = 8, 11
+    P = oracle.widen(rng.normal(0, 1, (H, W, 3)).astype(np.float32))
+    P[rng.random((H, W)) < 0.1] = np.nan
+    C, N = oracle.triangle_geometry(P)
+    got = oracle.bilateral(C, N, H, W, kernel, 1e9, 1e9, iters)
+    want = _box_filter_normals(N, H, W, kernel // 2, iters)
+    np.testing.assert_array_equal(np.isnan(got), np.isnan(want))
+    ok = ~np.isnan(want[:, 0])
+    np.testing.assert_allclose(got[ok], want[ok], atol=1e-9)
+
+
+def test_bilateral_tiny_sigma_is_identity():
+    rng = np.random.default_rng(11)
+    P = oracle.widen(rng.normal(0, 1, (7, 8, 3)).astype(np.float32))
+    C, N = oracle.triangle_geometry(P)
+    got = oracle.bilateral(C, N, 7, 8, 3, 1e-6, 1e-6, 3)
+    np.testing.assert_allclose(got, N, rtol=0, atol=1e-15)   # self weight 1, every other weight underflows
+
+
+def test_bilateral_two_triangles_closed_form():
+    """A single quad: each triangle sees itself (weight 1) and its partner (weight w), so after one
+    iteration n1' is n1 rotated towards n2 by atan(w sin t / (1 + w cos t))."""
+    P = np.array([[[0, 0, 0], [1, 0, 0]], [[0, 1, 0.4], [1, 1, 0.0]]], np.float32)
+    C, N = oracle.triangle_geometry(oracle.widen(P))
+    sc, ss = 0.8, 0.6
+    cosang = float(N[0] @ N[1])
+    theta = np.arccos(cosang)
+    w = np.exp(-np.sum((C[0] - C[1]) ** 2) / (2 * sc * sc)) * np.exp(-np.sum((N[0] - N[1]) ** 2) / (2 * ss * ss))
+    Nf = oracle.bilateral(C, N, 2, 2, 3, sc, ss, 1)
+    rot = np.arctan2(w * np.sin(theta), 1 + w * cosang)
+    assert np.isclose(np.arccos(np.clip(Nf[0] @ N[0], -1, 1)), rot, atol=1e-7)
+    assert np.isclose(np.arccos(np.clip(Nf[1] @ N[1], -1, 1)), rot, atol=1e-7)
+    # the two rotate towards each other, in the plane they span
+    assert Nf[0] @ N[1] > cosang and Nf[1] @ N[0] > cosang
+    assert abs(np.linalg.det(np.stack([Nf[0], N[0], N[1]]))) < 1e-12
+
+
+def test_bilateral_keeps_sharp_crease():
+    """A 90-degree crease: W_s = exp(-2 / (2 sigma_s^2)) ~ 1e-19 keeps the two sides apart."""
+    H, W = 10, 12
+    u, v = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+    x = v * 0.03125
+    z = np.where(v <= 5, 1.0, 1.0 + (v - 5) * 0.03125)
+    x = np.where(v <= 5, x, 5 * 0.03125)
+    P = np.stack([x, u * 0.03125, z], -1).astype(np.float32)
+    C, N = oracle.triangle_geometry(oracle.widen(P))
+    Nf = oracle.bilateral(C, N, H, W, 3, 0.1, 0.15, 3)
+    q = np.arange(N.shape[0]) // 2
+    col = q % (W - 1)
+    left, right = col < 5, col > 5
+    np.testing.assert_allclose(Nf[left], N[left], atol=1e-6)
+    np.testing.assert_allclose(Nf[right], N[right], atol=1e-6)
+    assert abs(N[left][0] @ N[right][0]) < 1e-12
+
+
+# ----------------------------------------------------------------------------- group assignment (Algorithm 4)
+
+
+def test_classify_thresholds_ties_and_masks():
+    nd = oracle.normalize_dominant(np.array([[0, 0, 2], [0, 0, 1], [1, 0, 0]], np.float32))
+    ang = 0.95
+    th = np.arccos(ang)
+    d = 1e-7
+    normals = np.array([
+        [np.sin(th - d), 0, np.cos(th - d)],      # just inside -> group 0 (tie with group 1, first wins)
+        [np.sin(th + d), 0, np.cos(th + d)],      # just outside -> 255
+        [1, 0, 0],                                # group 2
+        [-1, 0, 0],                               # opposite of group 2: signed dot -> 255
+        [0, 0, 1],                                # masked out -> 255
+        [np.nan, np.nan, np.nan],                 # no normal -> 255
+        [np.cos(0.1), 0, np.sin(0.1)],            # closer to group 2 than 0
+    ])
+    m = np.array([1, 1, 1, 1, 0, 1, 1], np.uint8)
+    G, best, second = oracle.classify(normals, m, nd, ang)
+    assert list(G) == [0, 255, 2, 255, 255, 255, 2]
+    assert best[0] == second[0]                   # the tie is visible to the near-threshold report
+    # exactly at the threshold is kept (reject only when strictly below)
+    G, _, _ = oracle.classify(np.array([[0.0, 0.6, 0.8]]), np.ones(1, np.uint8),
+                              oracle.normalize_dominant(np.array([[0, 0, 1]], np.float32)), 0.8)
+    assert G[0] == 0
+
+
+def test_normalize_dominant_rejects_zero():
+    with pytest.raises(ValueError):
+        oracle.normalize_dominant(np.zeros((1, 3), np.float32))
+    nd = oracle.normalize_dominant(np.array([[3, 4, 0]], np.float32))
+    np.testing.assert_allclose(nd, [[0.6, 0.8, 0.0]])
+
+
+# ----------------------------------------------------------------------------- whole path
+
+
+@pytest.mark.parametrize("scene", ["depth", "lidar"])
+def test_noise_free_scene_maps_to_ground_truth(scene):
+    """On noise-free scenes, triangles well inside a ground-truth planar surface get that surface's group
+    and every segment holds a single group."""
+    if scene == "depth":
+        f = synth.depth_camera_scene(60, 80, seed=1, n_boxes=3, ramp=True, noise_sigma=0.0, nan_frac=0.0)
+    else:
+        f = synth.lidar_scene(32, 512, seed=2, n_cars=8, range_noise=0.0, missing_frac=0.0)
+    p = oracle.OracleParams(**f.params)
+    r = oracle.extract_planes(f.points, p, f.dominant_normals)
+    H, W = f.H, f.W
+    sid = f.surface_id
+    # surface id per quad when all four corners and their 2-ring agree (away from creases)
+    from numpy.lib.stride_tricks import sliding_window_view
+    pad = np.pad(sid, 3, constant_values=-2)
+    win = sliding_window_view(pad, (8, 8))[:H - 1, :W - 1]
+    same = (win == win[..., 3:4, 3:4]).all(axis=(-1, -2)) & (sid[:-1, :-1] >= 0)
+    quad_sid = np.where(same, sid[:-1, :-1], -1)
+    tri_sid = np.repeat(quad_sid.reshape(-1), 2)
+    inside = (tri_sid >= 0) & (r["mask"] == 1)
+    want = f.surface_group[tri_sid[inside]]
+    got = r["groups"][inside].astype(np.int64)
+    got[got == 255] = -1
+    assert inside.sum() > 1000
+    assert (got == want).mean() > 0.999
+    lab = r["labels"]
+    for l in np.unique(lab[lab >= 0]):
+        assert len(np.unique(r["groups"][lab == l])) == 1
