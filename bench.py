@@ -1,0 +1,384 @@
+"""Benchmark: plane extraction on organized point clouds, one frame per step.
+
+Default workload: the 480x640 synthetic depth-camera frame (12 boxes, 15-degree ramp, 5 mm
+noise, 1% outliers, 3% NaN; Laplacian 5 iterations, bilateral 3 iterations, K = 4). A step is
+one pass of the whole path (Laplacian, normals, bilateral, mask, groups, segments) over one
+frame already resident in HBM. The frame (3.7 MB) is smaller than L2, so L2 is flushed by
+writing a 256 MB buffer before every timed step, outside the step's CUDA events.
+
+Prints one JSON line. `value` is Mtri/s over all ranks (triangles = 2(H-1)(W-1) per frame),
+`e2e` repeats the measurement through pl3d_extract_planes_host with pinned host buffers
+(copies inside the timed region), `roofline` describes the kernel with the largest share of
+device time, `cpu_baseline` times the FP64 oracle on the host cores on a bounded sample.
+
+--impl reference times the FP64 oracle itself (the paper has no code to run) on the same
+workload and prints the same line with "impl": "reference".
+
+Multi-GPU (torchrun): frames are independent, so each rank runs its own frame (seeded by rank)
+with no collective on the data path; only the timing uses a barrier and a max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "Mtri/s smoothed+segmented and HBM roofline fraction; served p50/p99 frame latency"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ----------------------------------------------------------------------------- clocks
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 50 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[tuple[float, str]] = []
+        self._t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self._t = threading.Thread(target=self._read, daemon=True)
+        self._t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self, t0: float, t1: float) -> dict:
+        rows = []
+        for t, line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            rows.append((t, parts))
+        inside = [r for r in rows if t0 <= r[0] <= t1] or [r for r in rows if t0 - 0.25 <= r[0] <= t1 + 0.25]
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"], "samples": 0}
+        sm = [float(p[1]) for _, p in inside if p[1].replace(".", "").isdigit()]
+        mx = [float(p[2]) for _, p in inside if p[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, p in inside for i in range(4) if p[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(inside)}
+
+
+# ----------------------------------------------------------------------------- algorithmic work per launch
+
+
+def algorithmic(kernel: str, H: int, W: int, prm: dict, launches_per_step: int) -> tuple[str, float, str]:
+    """(bound, work per launch, unit) for one launch of `kernel` on an H x W frame.
+
+    Bytes: what the launch must move to and from HBM with perfect on-chip reuse. FLOPs (for the
+    ALU-bound bilateral): 20 FP32 operations per (triangle, window triangle) pair and iteration,
+    an FMA counted as 2, an exp2 as 1."""
+    npx = H * W
+    ntri = 2 * (H - 1) * (W - 1)
+    if kernel == "lap_smooth":
+        return "hbm", 24.0 * npx, "B"
+    if kernel == "bilateral":
+        k = prm["bil_kernel"]
+        iters_per_launch = prm["bil_iters"] / max(launches_per_step, 1)
+        return "alu", 20.0 * 2 * k * k * ntri * iters_per_launch, "FLOP"
+    if kernel == "label_union":
+        return "hbm", 5.0 * ntri, "B"
+    if kernel == "label_flatten":
+        return "hbm", 8.0 * ntri, "B"
+    if kernel == "label_filter":
+        return "hbm", 8.0 * ntri, "B"
+    return "hbm", 0.0, "B"
+
+
+def fp32_peak_tflops(sm_count: int, mhz: float) -> float:
+    """FP32 CUDA-core peak: 128 lanes per SM, an FMA = 2 FLOP."""
+    return sm_count * 128 * 2 * mhz * 1e6 / 1e12
+
+
+# ----------------------------------------------------------------------------- oracle timing
+
+
+def time_oracle(frame, seconds_budget: float, threads: int) -> dict:
+    import oracle
+    oracle.set_threads(threads)
+    p = oracle.OracleParams(**frame.params)
+    runs = []
+    t_end = time.perf_counter() + seconds_budget
+    while True:
+        t0 = time.perf_counter()
+        oracle.extract_planes(frame.points, p, frame.dominant_normals)
+        runs.append(time.perf_counter() - t0)
+        if time.perf_counter() >= t_end or len(runs) >= 50:
+            break
+    sec = statistics.median(runs)
+    return {"seconds_per_frame": sec, "frames": len(runs), "threads": threads,
+            "mtri_s": frame.n_triangles / sec / 1e6}
+
+
+# ----------------------------------------------------------------------------- arms
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    frame = synth.WORKLOADS[args.workload]()
+    cores = os.cpu_count() or 1
+    import oracle
+    oracle.set_threads(cores)
+    p = oracle.OracleParams(**frame.params)
+    for _ in range(args.warmup):
+        oracle.extract_planes(frame.points, p, frame.dominant_normals)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.extract_planes(frame.points, p, frame.dominant_normals)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(times) / len(times)
+    value = frame.n_triangles / (ms / 1e3) / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Mtri/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "H": frame.H, "W": frame.W, "triangles": frame.n_triangles},
+        "cpu_baseline": {"value": value, "unit": "Mtri/s", "cores": cores, "kind": "oracle",
+                         "sample": f"whole {frame.H}x{frame.W} frame per step, FP64 C oracle, OpenMP {cores} threads"},
+        "e2e": {"value": value, "unit": "Mtri/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_pl3d(args):
+    import torch
+    import paper_2007_12065_gb300 as pl3d
+    from paper_2007_12065_gb300 import build as pl3d_build
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    pl3d_build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    base = synth.WORKLOADS[args.workload]
+    frame = base() if rank == 0 else base(seed=1000 + rank)
+    H, W, ntri = frame.H, frame.W, frame.n_triangles
+    params = pl3d.make_params(**frame.params)
+    nd = frame.dominant_normals
+    K = nd.shape[0]
+    ctx = pl3d.pl3d_create(local)
+    stream = torch.cuda.current_stream(dev)
+
+    pts = torch.from_numpy(frame.points).to(dev)
+    mask = torch.empty(ntri, dtype=torch.uint8, device=dev)
+    normals = torch.empty((ntri, 3), dtype=torch.float32, device=dev)
+    labels = torch.empty(ntri, dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        pl3d.pl3d_extract_planes(ctx, pts, H, W, params, nd, K, mask, normals, labels, stream)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    for _ in range(max(args.warmup, 3)):
+        flush.fill_(1.0)
+        step()
+    torch.cuda.synchronize()
+    # keep the GPU busy ~0.3 s before timing so that clocks settle and the sampler sees load
+    t_warm = time.perf_counter()
+    while time.perf_counter() - t_warm < 0.3:
+        flush.fill_(0.5)
+        step()
+    torch.cuda.synchronize()
+
+    # ---------------- timed region (device)
+    n0 = pl3d.pl3d_launch_count(ctx)
+    pl3d.pl3d_set_timing(ctx, True)
+    pl3d.pl3d_read_timing(ctx, reset=True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    t1 = time.perf_counter()
+    pl3d.pl3d_set_timing(ctx, False)
+    launches = pl3d.pl3d_launch_count(ctx) - n0
+    per_kernel = pl3d.pl3d_read_timing(ctx, reset=True)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = sum(step_ms) / len(step_ms)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ntri * world / (ms / 1e3) / 1e6
+
+    # ---------------- end to end through the host-buffer entry point
+    h_pts = torch.from_numpy(frame.points).pin_memory()
+    h_mask = torch.empty(ntri, dtype=torch.uint8).pin_memory()
+    h_normals = torch.empty((ntri, 3), dtype=torch.float32).pin_memory()
+    h_labels = torch.empty(ntri, dtype=torch.int32).pin_memory()
+    e2e_steps = max(args.steps // 2, 10)
+    for _ in range(3):
+        pl3d.pl3d_extract_planes_host(ctx, h_pts, H, W, params, nd, K, h_mask, h_normals, h_labels, stream)
+    barrier()
+    torch.cuda.synchronize()
+    e2e_s = []
+    for k in range(e2e_steps):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        t_a = time.perf_counter()
+        pl3d.pl3d_extract_planes_host(ctx, h_pts, H, W, params, nd, K, h_mask, h_normals, h_labels, stream)
+        e2e_s.append(time.perf_counter() - t_a)
+    e2e_ms = 1e3 * sum(e2e_s) / len(e2e_s)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    sampler.stop()
+    clocks = sampler.summary(t0, t1)
+
+    if rank != 0:
+        pl3d.pl3d_destroy(ctx)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
+    # ---------------- roofline of the dominant kernel
+    peaks, peak_src = _peaks()
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    top = max(per_kernel.items(), key=lambda kv: kv[1][0])
+    kname, (kms, kn) = top
+    total_ms = sum(v[0] for v in per_kernel.values())
+    launches_per_step = kn / args.steps
+    bound, work, wunit = algorithmic(kname, H, W, frame.params, launches_per_step)
+    avg_launch_s = kms / kn / 1e3
+    if bound == "hbm":
+        achieved = work / avg_launch_s / 1e9
+        peak, unit = float(peaks["hbm_gbs"]), "GB/s"
+        peak_note = f"{peak_src} hbm_gbs"
+    else:
+        achieved = work / avg_launch_s / 1e12
+        peak = fp32_peak_tflops(sm_count, float(peaks.get("sm_max_mhz", 2070.0)))
+        unit = "TFLOP/s"
+        peak_note = f"FP32 CUDA-core peak: {sm_count} SMs x 128 lanes x 2 FLOP x {peaks.get('sm_max_mhz', 2070.0)} MHz"
+    roofline = {"bound": bound, "kernel": kname, "achieved": achieved, "peak": peak, "unit": unit,
+                "frac": achieved / peak, "traffic": None, "peak_source": peak_note,
+                "avg_launch_us": avg_launch_s * 1e6, "work_per_launch": work, "work_unit": wunit,
+                "share_of_device_time": kms / total_ms if total_ms > 0 else None,
+                "per_kernel_us": {k: (v[0] / v[1] * 1e3 if v[1] else 0.0) for k, v in per_kernel.items()}}
+
+    # ---------------- CPU baseline (oracle on the host cores, bounded sample)
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        r = time_oracle(frame, args.cpu_seconds, cores)
+        cpu = {"value": r["mtri_s"], "unit": "Mtri/s", "cores": cores, "kind": "oracle",
+               "sample": f"{r['frames']} whole {H}x{W} frames, median wall time, FP64 C oracle with OpenMP"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "Mtri/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "H": H, "W": W, "triangles_per_frame": ntri,
+                   "frames_per_step_per_gpu": 1, "lap_iters": frame.params["lap_iters"],
+                   "bil_iters": frame.params["bil_iters"], "K": K,
+                   "l2": f"flushed before every timed step ({L2_FLUSH_BYTES >> 20} MB write, outside the step events)",
+                   "parallelism": f"replicas x{world}"},
+        "clocks": clocks,
+        "e2e": {"value": ntri * world / (e2e_ms / 1e3) / 1e6, "unit": "Mtri/s", "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": int(h_pts.numel() * 4),
+                "d2h_bytes_per_step": int(h_mask.numel() + h_normals.numel() * 4 + h_labels.numel() * 4)},
+        "gpu_launches": int(launches),
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "step_ms_p50": statistics.median(step_ms),
+        "step_ms_min": min(step_ms),
+        "wall_s_timed_region": t1 - t0,
+    }
+    print(json.dumps(line), flush=True)
+    pl3d.pl3d_destroy(ctx)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="pl3d", choices=["pl3d", "reference"])
+    ap.add_argument("--workload", default="rgbd_480x640", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_pl3d(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,176 @@
+/*
+ * pl3d.h -- C ABI of the GB300 (sm_103a) plane-extraction path for organized point
+ * clouds, after Polylidar3D (Castagno & Atkins, arXiv 2007.12065).
+ *
+ * One call runs, on the caller's CUDA stream and entirely in this library's kernels:
+ *
+ *   1. Laplacian vertex smoothing on the implicit image grid       (Eq. 1-2, Section 5.1)
+ *   2. centroids and unit normals of every triangle of T_FC        (Section 4.2, Section 5.2)
+ *   3. bilateral filtering of the triangle normals                 (Eq. 3-6, Section 5.2)
+ *   4. triangle mask: all vertices valid and longest edge <= l_max (Algorithm 1, Algorithm 4)
+ *   5. group assignment against the K dominant normals             (Algorithm 4)
+ *   6. connected planar segments of equal group over twin edges    (Algorithm 5, Algorithm 2)
+ *
+ * Mesh conventions (Section 4.2, Algorithm 1). The cloud is an H x W grid (the paper's
+ * M x N) of FP32 xyz points, row-major, 12 bytes per point; a point with any non-finite
+ * coordinate is invalid. Quad (u, v), 0 <= u < H-1, 0 <= v < W-1, has the points
+ * p1 = (u, v), p2 = (u, v+1), p3 = (u+1, v+1), p4 = (u+1, v) and two triangles,
+ * first = {p3, p2, p1} (k = 0) and second = {p1, p4, p3} (k = 1). Every per-triangle array
+ * has 2 (H-1)(W-1) entries indexed by GID = 2 (u (W-1) + v) + k. Normals follow the
+ * right-hand rule over that vertex order.
+ *
+ * Errors: every entry point returns PL3D_OK (0) or a negative PL3D_ERR_* code and never
+ * aborts the process. Invalid arguments are rejected on the host before anything is
+ * enqueued. Launches are asynchronous: a fault inside a kernel surfaces as
+ * PL3D_ERR_CUDA from a later call or from pl3d_sync.
+ *
+ * Threading: a context is used by one host thread at a time. Calls on one context are
+ * ordered on the stream they are given; calls on different streams with one context
+ * must not overlap because they share the context's scratch memory.
+ */
+#ifndef PL3D_H
+#define PL3D_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PL3D_OK 0
+#define PL3D_ERR_INVALID_ARG (-1)   /* null pointer, bad size, bad parameter */
+#define PL3D_ERR_OUT_OF_MEMORY (-2) /* scratch or staging allocation failed */
+#define PL3D_ERR_CUDA (-3)          /* a CUDA runtime call or a launch failed */
+#define PL3D_ERR_TIMEOUT (-4)       /* a bounded device-side wait gave up */
+#define PL3D_ERR_UNSUPPORTED (-5)   /* device is not sm_103-class, or an unsupported kernel size */
+
+/* Largest number of dominant normals: groups are uint8 with 255 = "no group" (Algorithm 4). */
+#define PL3D_MAX_GROUPS 254
+/* Group value of a triangle that belongs to no dominant normal. */
+#define PL3D_NO_GROUP 255
+
+typedef struct pl3d_ctx pl3d_ctx;
+
+/*
+ * Parameters of one extraction. Paper symbols in brackets.
+ *   lap_iters      Laplacian iterations (>= 0). Eq. 1.
+ *   lap_lambda     [lambda] step in [0, 1]. Eq. 1, used as v' = v + lambda/W sum_j w_j (v_j - v),
+ *                  w_j = 1 / |v - v_j| over the valid points of the lap_kernel x lap_kernel window
+ *                  (the point itself and points at distance 0 excluded); the ring of width
+ *                  lap_kernel/2 at the image border is not filtered (Section 5.1).
+ *   lap_kernel     window size: 3, 5 or 7.
+ *   bil_iters      bilateral iterations (>= 0). Eq. 3.
+ *   bil_sigma_len  [sigma_c] metres, > 0: W_c = exp(-|c_i - c_j|^2 / (2 sigma_c^2)). Eq. 4.
+ *   bil_sigma_ang  [sigma_s] > 0: W_s = exp(-|n_i - n_j|^2 / (2 sigma_s^2)). Eq. 5.
+ *   bil_kernel     quad window size: 3, 5 or 7. The window of a triangle is both triangles of
+ *                  every quad of the bil_kernel x bil_kernel quad block centred on its own quad,
+ *                  itself included; triangles without a normal are skipped; the weighted sum is
+ *                  renormalised to unit length each iteration; centroids stay fixed.
+ *   max_edge       [l_max] metres; a triangle whose longest smoothed edge is > max_edge is
+ *                  rejected. <= 0 disables the test. Algorithm 4.
+ *   min_dot        [ang_min] a triangle joins group argmax_j n . n^d_j (lowest j on ties) unless
+ *                  that dot is < min_dot. Algorithm 4.
+ *   max_offset     if > 0, two adjacent triangles of group g join only when
+ *                  |n^d_g . (c_i - c_j)| <= max_offset (plane-offset test). <= 0 disables.
+ *   min_triangles  [tri_min] if > 0, segments of at most min_triangles triangles are dropped
+ *                  (Algorithm 5 keeps |T^g_i| > tri_min).
+ *   flags          reserved, must be 0.
+ */
+typedef struct pl3d_params {
+    int32_t lap_iters;
+    float lap_lambda;
+    int32_t lap_kernel;
+    int32_t bil_iters;
+    float bil_sigma_len;
+    float bil_sigma_ang;
+    int32_t bil_kernel;
+    float max_edge;
+    float min_dot;
+    float max_offset;
+    int32_t min_triangles;
+    uint32_t flags;
+} pl3d_params;
+
+/* Fills *p with the RGBD settings of the paper's RealSense experiment (Section 9.3.1):
+ * 2 Laplacian iterations (lambda 1, kernel 3), 2 bilateral iterations (sigma_c 0.1,
+ * sigma_s 0.15, kernel 3), l_max 0.05, ang_min 0.96; max_offset and tri_min off.
+ * Returns PL3D_ERR_INVALID_ARG if p is NULL. Host only. */
+int pl3d_default_params(pl3d_params* p);
+
+/* Host-only argument check shared by every entry point: H, W >= 2, 2(H-1)(W-1) < 2^31,
+ * K in [1, 254], finite and non-zero dominant normals (host pointer, may be NULL to skip
+ * that check), parameter ranges as documented above. No CUDA call. */
+int pl3d_validate(const pl3d_params* params, int H, int W, const float* dominant_normals, int K);
+
+/* Creates a context bound to CUDA device `cuda_device` (the device must be sm_103-class,
+ * else PL3D_ERR_UNSUPPORTED). The context owns scratch memory that grows to the largest
+ * frame seen (growth synchronises the stream of the call that grows it). *out receives the
+ * context; on error *out is NULL. */
+int pl3d_create(pl3d_ctx** out, int cuda_device);
+
+/* Releases the context and its scratch memory after synchronising its device.
+ * NULL is ignored. */
+void pl3d_destroy(pl3d_ctx* ctx);
+
+/*
+ * Runs the whole path on one frame, asynchronously on `stream` (a cudaStream_t; NULL =
+ * the legacy default stream).
+ *   points            device, H*W*3 FP32, row-major xyz, not modified.
+ *   dominant_normals  host, K*3 FP32; normalised by the library; read before return.
+ *   out_tri_mask      device, 2(H-1)(W-1) bytes: 1 = triangle kept (all vertices valid and
+ *                     longest edge <= max_edge), else 0.
+ *   out_normals       device, 2(H-1)(W-1)*3 FP32: filtered unit normal; NaN where the
+ *                     triangle has an invalid vertex or a degenerate (zero-area) shape.
+ *   out_labels        device, 2(H-1)(W-1) int32: the smallest GID of the triangle's planar
+ *                     segment, or -1 (no group, or a segment of at most min_triangles).
+ * The caller owns every buffer; the library keeps no pointer after the call returns and
+ * reads/writes them only in work enqueued on `stream`. Outputs are complete when the
+ * stream reaches this call's end. Buffers must not overlap.
+ */
+int pl3d_extract_planes(pl3d_ctx* ctx, const float* points, int H, int W, const pl3d_params* params,
+                        const float* dominant_normals, int K, uint8_t* out_tri_mask, float* out_normals,
+                        int32_t* out_labels, void* stream);
+
+/* As pl3d_extract_planes, plus two optional device outputs (NULL = not written):
+ *   out_points  H*W*3 FP32 smoothed points (invalid points NaN);
+ *   out_groups  2(H-1)(W-1) bytes, the group of Algorithm 4 (255 = none). */
+int pl3d_extract_planes_ex(pl3d_ctx* ctx, const float* points, int H, int W, const pl3d_params* params,
+                           const float* dominant_normals, int K, uint8_t* out_tri_mask, float* out_normals,
+                           int32_t* out_labels, float* out_points, uint8_t* out_groups, void* stream);
+
+/* As pl3d_extract_planes with HOST buffers: copies points to the device, runs the path on
+ * `stream` and copies the three outputs back, then synchronises the stream before
+ * returning. Page-locked host buffers make the copies asynchronous DMA; pageable ones work
+ * but are slower. Device staging buffers are owned by the context. */
+int pl3d_extract_planes_host(pl3d_ctx* ctx, const float* host_points, int H, int W, const pl3d_params* params,
+                             const float* dominant_normals, int K, uint8_t* host_tri_mask, float* host_normals,
+                             int32_t* host_labels, void* stream);
+
+/* Waits for `stream` and reports any pending CUDA error as PL3D_ERR_CUDA. */
+int pl3d_sync(pl3d_ctx* ctx, void* stream);
+
+/* Static, human-readable text for a status code. Never NULL. */
+const char* pl3d_status_string(int status);
+
+/* Per-kernel timing (CUDA events recorded around each launch, on the launch stream).
+ * pl3d_set_timing(ctx, 1) starts recording; pl3d_read_timing waits for the recorded events,
+ * writes per-phase total milliseconds and launch counts for up to n_slots phases
+ * (ms_out, launches_out may be NULL) and returns the number of phases (PL3D_TIMING_SLOTS),
+ * clearing the totals when reset != 0. Phase order: see pl3d_timing_slot_name. */
+#define PL3D_TIMING_SLOTS 6
+int pl3d_set_timing(pl3d_ctx* ctx, int enable);
+int pl3d_read_timing(pl3d_ctx* ctx, double* ms_out, int64_t* launches_out, int n_slots, int reset);
+const char* pl3d_timing_slot_name(int slot);
+
+/* Number of kernels this context has launched since it was created. */
+int64_t pl3d_launch_count(const pl3d_ctx* ctx);
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int pl3d_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PL3D_H */

@@ -1,0 +1,81 @@
+"""Acceptance check of a device result against the FP64 oracle (test infrastructure only).
+
+Bounds: smoothed points within 2e-5 m, normals within 1e-4 rad (angle from atan2(|a x b|, a . b)
+in FP64), masks bit-exact, label partitions bit-exact (both sides label a segment by its
+smallest GID, so equal partitions mean equal arrays).
+
+FP32 and FP64 may take a different side of a threshold when the quantity sits within
+oracle.NEAR of it: the longest edge against l_max, the best dot against ang_min, or the two
+best dots against each other. Such triangles are flagged by the oracle; a mask or group
+mismatch is accepted only on a flagged triangle, and the labels are then checked against the
+oracle's region growing rerun with the device's groups substituted on the flagged triangles
+only. The number of flagged triangles is reported.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import label as _label
+
+POINT_TOL_M = 2e-5
+NORMAL_TOL_RAD = 1e-4
+
+
+def angle_rad(a: np.ndarray, b: np.ndarray) -> np.ndarray:
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    cr = np.linalg.norm(np.cross(a, b), axis=-1)
+    return np.arctan2(cr, np.einsum("ij,ij->i", a, b))
+
+
+def compare(dev: dict, ref: dict, params, H: int, W: int, point_tol=POINT_TOL_M, normal_tol=NORMAL_TOL_RAD) -> dict:
+    """dev: numpy arrays mask [T] u8, normals [T,3] f32, labels [T] i32, optional groups [T] u8 and
+    points [H,W,3] f32. ref: oracle.extract_planes(...). Returns a report; raises AssertionError on a
+    violation of the bounds above."""
+    rep: dict = {}
+    flagged = ref["near_edge"] | ref["near_dot"] | ref["near_tie"]
+    rep["flagged"] = int(flagged.sum())
+
+    if dev.get("points") is not None:
+        P = np.asarray(dev["points"], np.float64).reshape(H, W, 3)
+        S = ref["smoothed"]
+        nan_d, nan_r = np.isnan(P).any(-1), np.isnan(S).any(-1)
+        assert np.array_equal(nan_d, nan_r), f"smoothed NaN pattern differs at {np.argwhere(nan_d != nan_r)[:5]}"
+        err = np.abs(P - S)[~nan_r].max() if (~nan_r).any() else 0.0
+        rep["points_max_err_m"] = float(err)
+        assert err <= point_tol, f"smoothed points off by {err:.3g} m > {point_tol}"
+
+    N = np.asarray(dev["normals"], np.float64).reshape(-1, 3)
+    Nr = ref["normals"]
+    nan_d, nan_r = np.isnan(N).any(-1), np.isnan(Nr).any(-1)
+    assert np.array_equal(nan_d, nan_r), f"normal NaN pattern differs at {np.nonzero(nan_d != nan_r)[0][:5]}"
+    ang = angle_rad(N[~nan_r], Nr[~nan_r]) if (~nan_r).any() else np.zeros(0)
+    rep["normals_max_err_rad"] = float(ang.max()) if ang.size else 0.0
+    rep["normals_over_tol"] = int((ang > normal_tol).sum())
+    assert rep["normals_max_err_rad"] <= normal_tol, (
+        f"normals off by {rep['normals_max_err_rad']:.3g} rad > {normal_tol} on {rep['normals_over_tol']} triangles")
+
+    m = np.asarray(dev["mask"]).reshape(-1)
+    mm = m != ref["mask"]
+    rep["mask_mismatch"] = int(mm.sum())
+    assert not (mm & ~ref["near_edge"]).any(), f"mask differs on unflagged triangles {np.nonzero(mm & ~ref['near_edge'])[0][:5]}"
+
+    lab = np.asarray(dev["labels"]).reshape(-1).astype(np.int64)
+    G_ref = ref["groups"]
+    if dev.get("groups") is not None:
+        G = np.asarray(dev["groups"]).reshape(-1)
+        gm = G != G_ref
+        rep["group_mismatch"] = int(gm.sum())
+        assert not (gm & ~flagged).any(), f"groups differ on unflagged triangles {np.nonzero(gm & ~flagged)[0][:5]}"
+        G_sub = np.where(flagged, G, G_ref).astype(np.uint8)
+    else:
+        G_sub = G_ref
+    if rep["flagged"] and dev.get("groups") is not None:
+        want = _label(G_sub, H, W, ref["centroids"], ref["nd_unit"], params.max_offset, params.min_triangles)
+    else:
+        want = ref["labels"]
+    lm = lab != want
+    rep["label_mismatch"] = int(lm.sum())
+    assert not lm.any(), f"labels differ on {lm.sum()} triangles, first {np.nonzero(lm)[0][:5]}"
+    rep["segments"] = int(len(np.unique(want[want >= 0])))
+    return rep

@@ -1,0 +1,298 @@
+"""pl3d -- GB300 (sm_103a) plane extraction for organized point clouds, after Polylidar3D.
+
+Thin ctypes binding over libpl3d.so (the C ABI in include/pl3d.h). Each function here has the
+name of the C entry point it calls and does argument marshalling only: every step of the path
+runs in the library's CUDA kernels. PyTorch is used for device memory and streams.
+
+The library must have been built (``__graft_entry__.build()`` or
+``python paper_2007_12065_gb300/build.py``); calls fail loudly when it is missing -- there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpl3d.so")
+
+PL3D_OK = 0
+PL3D_ERR_INVALID_ARG = -1
+PL3D_ERR_OUT_OF_MEMORY = -2
+PL3D_ERR_CUDA = -3
+PL3D_ERR_TIMEOUT = -4
+PL3D_ERR_UNSUPPORTED = -5
+PL3D_MAX_GROUPS = 254
+PL3D_NO_GROUP = 255
+PL3D_TIMING_SLOTS = 6
+
+
+class pl3d_params(ctypes.Structure):
+    """Mirror of the C struct pl3d_params (field meaning documented in include/pl3d.h)."""
+    _fields_ = [
+        ("lap_iters", ctypes.c_int32),
+        ("lap_lambda", ctypes.c_float),
+        ("lap_kernel", ctypes.c_int32),
+        ("bil_iters", ctypes.c_int32),
+        ("bil_sigma_len", ctypes.c_float),
+        ("bil_sigma_ang", ctypes.c_float),
+        ("bil_kernel", ctypes.c_int32),
+        ("max_edge", ctypes.c_float),
+        ("min_dot", ctypes.c_float),
+        ("max_offset", ctypes.c_float),
+        ("min_triangles", ctypes.c_int32),
+        ("flags", ctypes.c_uint32),
+    ]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class PL3DError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {pl3d_status_string(status)} ({status})")
+        self.status = status
+
+
+_lib = None
+_vp = ctypes.c_void_p
+
+
+def lib():
+    """The loaded libpl3d.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                           "(the plane-extraction path has no CPU fallback)")
+    L = ctypes.CDLL(LIB_PATH)
+    P = ctypes.POINTER(pl3d_params)
+    L.pl3d_version.restype = ctypes.c_int
+    L.pl3d_status_string.argtypes = [ctypes.c_int]
+    L.pl3d_status_string.restype = ctypes.c_char_p
+    L.pl3d_timing_slot_name.argtypes = [ctypes.c_int]
+    L.pl3d_timing_slot_name.restype = ctypes.c_char_p
+    L.pl3d_default_params.argtypes = [P]
+    L.pl3d_validate.argtypes = [P, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int]
+    L.pl3d_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int]
+    L.pl3d_destroy.argtypes = [_vp]
+    L.pl3d_destroy.restype = None
+    L.pl3d_extract_planes.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, P, _vp, ctypes.c_int, _vp, _vp, _vp, _vp]
+    L.pl3d_extract_planes_ex.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, P, _vp, ctypes.c_int, _vp, _vp, _vp,
+                                         _vp, _vp, _vp]
+    L.pl3d_extract_planes_host.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, P, _vp, ctypes.c_int, _vp, _vp, _vp,
+                                           _vp]
+    L.pl3d_sync.argtypes = [_vp, _vp]
+    L.pl3d_set_timing.argtypes = [_vp, ctypes.c_int]
+    L.pl3d_read_timing.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int]
+    L.pl3d_launch_count.argtypes = [_vp]
+    L.pl3d_launch_count.restype = ctypes.c_int64
+    _lib = L
+    return L
+
+
+# ----------------------------------------------------------------------------- marshalling helpers
+
+
+def _ptr(x) -> Optional[int]:
+    """Address of a torch tensor, a numpy array, an int address, or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)!r}")
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _nd_host(dominant_normals):
+    """Dominant normals as a contiguous host float32 buffer (kept alive by the caller)."""
+    import numpy as np
+    if hasattr(dominant_normals, "detach"):
+        dominant_normals = dominant_normals.detach().cpu().numpy()
+    return np.ascontiguousarray(dominant_normals, dtype=np.float32).reshape(-1, 3)
+
+
+def _check(status: int, what: str) -> int:
+    if status != PL3D_OK:
+        raise PL3DError(status, what)
+    return status
+
+
+def _check_tensor(t, name, dtype, numel, device_kind="cuda"):
+    if t is None:
+        return
+    if hasattr(t, "is_cuda"):
+        if (device_kind == "cuda") != t.is_cuda:
+            raise ValueError(f"{name} must be a {device_kind} tensor")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if str(t.dtype) != dtype:
+            raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+        if t.numel() != numel:
+            raise ValueError(f"{name} must have {numel} elements, got {t.numel()}")
+
+
+# ----------------------------------------------------------------------------- the C ABI, by name
+
+
+def pl3d_version() -> int:
+    return int(lib().pl3d_version())
+
+
+def pl3d_status_string(status: int) -> str:
+    return lib().pl3d_status_string(int(status)).decode()
+
+
+def pl3d_timing_slot_name(slot: int) -> str:
+    return lib().pl3d_timing_slot_name(int(slot)).decode()
+
+
+def pl3d_default_params() -> pl3d_params:
+    p = pl3d_params()
+    _check(lib().pl3d_default_params(ctypes.byref(p)), "pl3d_default_params")
+    return p
+
+
+def make_params(**kw) -> pl3d_params:
+    """pl3d_params from keyword arguments (paper-named fields); unspecified fields take the defaults."""
+    p = pl3d_default_params()
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(f"unknown parameter {k!r}")
+        setattr(p, k, v)
+    return p
+
+
+def pl3d_validate(params: pl3d_params, H: int, W: int, dominant_normals=None, K: Optional[int] = None) -> int:
+    """Host-only argument check; returns the status code (0 = valid)."""
+    nd = _nd_host(dominant_normals) if dominant_normals is not None else None
+    if K is None:
+        K = nd.shape[0] if nd is not None else 1
+    return int(lib().pl3d_validate(ctypes.byref(params), int(H), int(W), _ptr(nd), int(K)))
+
+
+def pl3d_create(device: int = 0) -> int:
+    """Creates a context on `device`; returns its handle (an address)."""
+    h = _vp()
+    _check(lib().pl3d_create(ctypes.byref(h), int(device)), "pl3d_create")
+    return int(h.value)
+
+
+def pl3d_destroy(ctx: int) -> None:
+    lib().pl3d_destroy(ctx)
+
+
+def pl3d_extract_planes(ctx, points, H, W, params, dominant_normals, K, out_tri_mask, out_normals, out_labels,
+                        stream=None) -> int:
+    """Device buffers (torch CUDA tensors or raw addresses); see include/pl3d.h."""
+    return pl3d_extract_planes_ex(ctx, points, H, W, params, dominant_normals, K, out_tri_mask, out_normals,
+                                  out_labels, None, None, stream)
+
+
+def pl3d_extract_planes_ex(ctx, points, H, W, params, dominant_normals, K, out_tri_mask, out_normals, out_labels,
+                           out_points=None, out_groups=None, stream=None) -> int:
+    n_tri = 2 * (H - 1) * (W - 1)
+    _check_tensor(points, "points", "torch.float32", H * W * 3)
+    _check_tensor(out_tri_mask, "out_tri_mask", "torch.uint8", n_tri)
+    _check_tensor(out_normals, "out_normals", "torch.float32", n_tri * 3)
+    _check_tensor(out_labels, "out_labels", "torch.int32", n_tri)
+    _check_tensor(out_points, "out_points", "torch.float32", H * W * 3)
+    _check_tensor(out_groups, "out_groups", "torch.uint8", n_tri)
+    nd = _nd_host(dominant_normals)
+    return _check(lib().pl3d_extract_planes_ex(ctx, _ptr(points), int(H), int(W), ctypes.byref(params), _ptr(nd),
+                                               int(K), _ptr(out_tri_mask), _ptr(out_normals), _ptr(out_labels),
+                                               _ptr(out_points), _ptr(out_groups), _stream(stream)),
+                  "pl3d_extract_planes")
+
+
+def pl3d_extract_planes_host(ctx, points, H, W, params, dominant_normals, K, out_tri_mask, out_normals, out_labels,
+                             stream=None) -> int:
+    """Host buffers (CPU tensors, pinned for async DMA, or numpy arrays); synchronises before returning."""
+    n_tri = 2 * (H - 1) * (W - 1)
+    _check_tensor(points, "points", "torch.float32", H * W * 3, "cpu")
+    _check_tensor(out_tri_mask, "out_tri_mask", "torch.uint8", n_tri, "cpu")
+    _check_tensor(out_normals, "out_normals", "torch.float32", n_tri * 3, "cpu")
+    _check_tensor(out_labels, "out_labels", "torch.int32", n_tri, "cpu")
+    nd = _nd_host(dominant_normals)
+    return _check(lib().pl3d_extract_planes_host(ctx, _ptr(points), int(H), int(W), ctypes.byref(params), _ptr(nd),
+                                                 int(K), _ptr(out_tri_mask), _ptr(out_normals), _ptr(out_labels),
+                                                 _stream(stream)), "pl3d_extract_planes_host")
+
+
+def pl3d_sync(ctx, stream=None) -> int:
+    return _check(lib().pl3d_sync(ctx, _stream(stream)), "pl3d_sync")
+
+
+def pl3d_set_timing(ctx, enable: bool) -> None:
+    _check(lib().pl3d_set_timing(ctx, 1 if enable else 0), "pl3d_set_timing")
+
+
+def pl3d_read_timing(ctx, reset: bool = False) -> dict:
+    """{phase name: (total ms, launches)} for the launches recorded while timing was on."""
+    import numpy as np
+    ms = np.zeros(PL3D_TIMING_SLOTS, np.float64)
+    n = np.zeros(PL3D_TIMING_SLOTS, np.int64)
+    rc = lib().pl3d_read_timing(ctx, ms.ctypes.data, n.ctypes.data, PL3D_TIMING_SLOTS, 1 if reset else 0)
+    if rc < 0:
+        raise PL3DError(rc, "pl3d_read_timing")
+    return {pl3d_timing_slot_name(i): (float(ms[i]), int(n[i])) for i in range(PL3D_TIMING_SLOTS)}
+
+
+def pl3d_launch_count(ctx) -> int:
+    return int(lib().pl3d_launch_count(ctx))
+
+
+# ----------------------------------------------------------------------------- convenience wrapper
+
+
+class PlaneExtractor:
+    """Owns a context and allocates outputs with torch; one call = one frame on the current stream."""
+
+    def __init__(self, device: int = 0):
+        self.device = device
+        self.ctx = pl3d_create(device)
+
+    def close(self):
+        if self.ctx:
+            pl3d_destroy(self.ctx)
+            self.ctx = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __call__(self, points, params: pl3d_params, dominant_normals, want_points=False, want_groups=False,
+                 stream=None):
+        import torch
+        H, W = int(points.shape[0]), int(points.shape[1])
+        n_tri = 2 * (H - 1) * (W - 1)
+        dev = points.device
+        out = dict(
+            mask=torch.empty(n_tri, dtype=torch.uint8, device=dev),
+            normals=torch.empty((n_tri, 3), dtype=torch.float32, device=dev),
+            labels=torch.empty(n_tri, dtype=torch.int32, device=dev),
+        )
+        if want_points:
+            out["points"] = torch.empty((H, W, 3), dtype=torch.float32, device=dev)
+        if want_groups:
+            out["groups"] = torch.empty(n_tri, dtype=torch.uint8, device=dev)
+        nd = _nd_host(dominant_normals)
+        pl3d_extract_planes_ex(self.ctx, points, H, W, params, nd, nd.shape[0], out["mask"], out["normals"],
+                               out["labels"], out.get("points"), out.get("groups"), stream)
+        return out

@@ -1,0 +1,518 @@
+// pl3d_api.cu -- the C ABI declared in include/pl3d.h: argument checks, the context and its
+// scratch memory, the launch sequence of one extraction, per-phase timing, and the
+// host-buffer entry point.
+//
+// Launch sequence of one frame (all on the caller's stream):
+//   lap_smooth_kernel   x ceil(lap_iters / fused)   Eq. 1-2          points -> SoA smoothed
+//   bilateral_kernel    x ceil(bil_iters / fused)   Eq. 3-6, Alg. 1/4 -> mask, normals, groups,
+//                                                                       union-find parents
+//   label_union_kernel                              Alg. 5 / Alg. 2   unions over twin edges
+//   label_flatten_kernel                                              labels = component roots
+//   label_filter_kernel (tri_min > 0 only)                            drop small segments
+#include <float.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "pl3d_internal.cuh"
+
+using namespace pl3d;
+
+namespace {
+
+constexpr int kVersion = 1 * 10000 + 0 * 100 + 0;
+
+enum Slot { kSlotLaplacian = 0, kSlotBilateral, kSlotUnion, kSlotFlatten, kSlotFilter, kSlotCopies };
+const char* const kSlotNames[PL3D_TIMING_SLOTS] = {"lap_smooth", "bilateral", "label_union",
+                                                    "label_flatten", "label_filter", "host_copies"};
+
+struct TimedRange {
+    int slot;
+    cudaEvent_t start, stop;
+};
+
+}  // namespace
+
+struct pl3d_ctx {
+    int device = 0;
+    int sm_count = 0;
+    // scratch (grown to the largest frame)
+    float* points = nullptr;       // 2 x 3 planes of cap_points floats
+    size_t cap_points = 0;
+    float* carry = nullptr;        // 2 x cap_tri x 3 floats (multi-launch bilateral)
+    size_t cap_carry = 0;
+    uint8_t* groups = nullptr;     // cap_tri
+    int32_t* sizes = nullptr;      // cap_tri
+    size_t cap_tri = 0;
+    // device staging for the host-buffer entry point
+    float* st_points = nullptr;
+    size_t st_cap_points = 0;
+    uint8_t* st_mask = nullptr;
+    float* st_normals = nullptr;
+    int32_t* st_labels = nullptr;
+    size_t st_cap_tri = 0;
+    // timing
+    bool timing = false;
+    std::vector<TimedRange> pending;
+    std::vector<cudaEvent_t> free_events;
+    double slot_ms[PL3D_TIMING_SLOTS] = {};
+    int64_t slot_n[PL3D_TIMING_SLOTS] = {};
+    int64_t launches = 0;
+};
+
+namespace {
+
+// Makes the context's device current for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            ok = false;
+            return;
+        }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+bool finite_f(float x) { return isfinite(x) != 0; }
+
+cudaEvent_t take_event(pl3d_ctx* c) {
+    if (!c->free_events.empty()) {
+        cudaEvent_t e = c->free_events.back();
+        c->free_events.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Runs one launch, bracketed by events when timing is on.
+template <class F>
+int launch(pl3d_ctx* c, int slot, cudaStream_t s, F&& fn) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (c->timing) {
+        e0 = take_event(c);
+        e1 = take_event(c);
+        if (e0 && e1) cudaEventRecord(e0, s);
+    }
+    const cudaError_t err = fn();
+    if (e0 && e1) {
+        cudaEventRecord(e1, s);
+        c->pending.push_back({slot, e0, e1});
+    }
+    if (err != cudaSuccess) return PL3D_ERR_CUDA;
+    c->launches += 1;
+    return PL3D_OK;
+}
+
+template <class T>
+int grow(T** ptr, size_t* cap, size_t need, size_t elem_per, cudaStream_t s) {
+    if (*cap >= need) return PL3D_OK;
+    if (*ptr) {
+        if (cudaStreamSynchronize(s) != cudaSuccess) return PL3D_ERR_CUDA;
+        cudaFree(*ptr);
+        *ptr = nullptr;
+        *cap = 0;
+    }
+    const size_t n = need + need / 8;   // headroom so that slightly larger frames do not regrow
+    if (cudaMalloc((void**)ptr, n * elem_per * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        *ptr = nullptr;
+        return PL3D_ERR_OUT_OF_MEMORY;
+    }
+    *cap = n;
+    return PL3D_OK;
+}
+
+// groups and segment sizes share one capacity.
+int grow_tri(pl3d_ctx* ctx, size_t need, cudaStream_t s) {
+    if (ctx->cap_tri >= need) return PL3D_OK;
+    if (ctx->groups && cudaStreamSynchronize(s) != cudaSuccess) return PL3D_ERR_CUDA;
+    cudaFree(ctx->groups);
+    cudaFree(ctx->sizes);
+    ctx->groups = nullptr;
+    ctx->sizes = nullptr;
+    ctx->cap_tri = 0;
+    const size_t n = need + need / 8;
+    if (cudaMalloc((void**)&ctx->groups, n) != cudaSuccess ||
+        cudaMalloc((void**)&ctx->sizes, n * sizeof(int32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        return PL3D_ERR_OUT_OF_MEMORY;
+    }
+    ctx->cap_tri = n;
+    return PL3D_OK;
+}
+
+int run(pl3d_ctx* ctx, const float* points, int H, int W, const pl3d_params* p, const float* nd_host, int K,
+        uint8_t* out_mask, float* out_normals, int32_t* out_labels, float* out_points, uint8_t* out_groups,
+        cudaStream_t s) {
+    const size_t npts = (size_t)H * W;
+    const size_t ntri = 2 * (size_t)(H - 1) * (W - 1);
+    int rc;
+    if ((rc = grow(&ctx->points, &ctx->cap_points, npts, 6, s)) != PL3D_OK) return rc;
+    if ((rc = grow_tri(ctx, ntri, s)) != PL3D_OK) return rc;
+
+    // Dominant normals, normalised in double precision.
+    Dominant nd;
+    nd.K = K;
+    for (int j = 0; j < K; ++j) {
+        const double x = nd_host[3 * j], y = nd_host[3 * j + 1], z = nd_host[3 * j + 2];
+        const double len = sqrt(x * x + y * y + z * z);
+        nd.v[3 * j] = (float)(x / len);
+        nd.v[3 * j + 1] = (float)(y / len);
+        nd.v[3 * j + 2] = (float)(z / len);
+    }
+
+    float* buf[2][3];
+    for (int b = 0; b < 2; ++b)
+        for (int k = 0; k < 3; ++k) buf[b][k] = ctx->points + (size_t)(3 * b + k) * ctx->cap_points;
+
+    // ---- Laplacian (Eq. 1-2)
+    const int lr = p->lap_iters > 0 ? p->lap_kernel / 2 : 1;
+    const int lfuse = kLapMaxHalo / lr;
+    int remaining = p->lap_iters;
+    int cur = 0;
+    bool first = true;
+    do {
+        const int it = remaining < lfuse ? remaining : lfuse;
+        LapArgs la{};
+        la.in_aos = first ? points : nullptr;
+        la.in_x = buf[cur][0];
+        la.in_y = buf[cur][1];
+        la.in_z = buf[cur][2];
+        const int nb = first ? cur : 1 - cur;
+        la.out_x = buf[nb][0];
+        la.out_y = buf[nb][1];
+        la.out_z = buf[nb][2];
+        la.H = H;
+        la.W = W;
+        la.iters = it;
+        la.lambda = p->lap_lambda;
+        remaining -= it;
+        la.out_aos = remaining == 0 ? out_points : nullptr;
+        if ((rc = launch(ctx, kSlotLaplacian, s, [&] { return launch_laplacian(la, lr, s); })) != PL3D_OK) return rc;
+        cur = nb;
+        first = false;
+    } while (remaining > 0);
+    const float* px = buf[cur][0];
+    const float* py = buf[cur][1];
+    const float* pz = buf[cur][2];
+
+    // ---- normals, bilateral (Eq. 3-6), mask and groups (Algorithms 1, 4)
+    uint8_t* groups = out_groups ? out_groups : ctx->groups;
+    const int br = p->bil_iters > 0 ? p->bil_kernel / 2 : 1;
+    const int bfuse = kBilMaxHalo / br;
+    const int nchunks = p->bil_iters <= bfuse ? 1 : (p->bil_iters + bfuse - 1) / bfuse;
+    if (nchunks > 1 && (rc = grow(&ctx->carry, &ctx->cap_carry, ntri, 6, s)) != PL3D_OK) return rc;
+    const double log2e = 1.4426950408889634;
+    double na = -log2e / (2.0 * (double)p->bil_sigma_len * (double)p->bil_sigma_len);
+    double ns = -log2e / (2.0 * (double)p->bil_sigma_ang * (double)p->bil_sigma_ang);
+    // keep the scales finite and non-zero so that 0 * scale and inf * scale stay well defined
+    na = fmin(fmax(na, -(double)FLT_MAX), -(double)FLT_MIN);
+    ns = fmin(fmax(ns, -(double)FLT_MAX), -(double)FLT_MIN);
+    int bremaining = p->bil_iters;
+    for (int c = 0; c < nchunks; ++c) {
+        const int it = bremaining < bfuse ? bremaining : bfuse;
+        bremaining -= it;
+        BilArgs ba;
+        ba.px = px;
+        ba.py = py;
+        ba.pz = pz;
+        ba.carry_in = c > 0 ? ctx->carry + (size_t)((c - 1) % 2) * 3 * ctx->cap_carry : nullptr;
+        ba.carry_out = c + 1 < nchunks ? ctx->carry + (size_t)(c % 2) * 3 * ctx->cap_carry : nullptr;
+        ba.out_mask = out_mask;
+        ba.out_normals = out_normals;
+        ba.out_groups = groups;
+        ba.out_labels = out_labels;
+        ba.H = H;
+        ba.W = W;
+        ba.iters = it;
+        ba.neg_a = (float)na;
+        ba.neg_s = (float)ns;
+        ba.max_edge2 = p->max_edge > 0.f ? p->max_edge * p->max_edge : INFINITY;
+        ba.min_dot = p->min_dot;
+        ba.nd = nd;
+        const bool f = c == 0, l = c + 1 == nchunks;
+        if ((rc = launch(ctx, kSlotBilateral, s, [&] { return launch_bilateral(ba, br, f, l, s); })) != PL3D_OK)
+            return rc;
+    }
+
+    // ---- planar segments (Algorithm 5)
+    LabelArgs lb;
+    lb.groups = groups;
+    lb.labels = out_labels;
+    lb.sizes = p->min_triangles > 0 ? ctx->sizes : nullptr;
+    lb.px = px;
+    lb.py = py;
+    lb.pz = pz;
+    lb.H = H;
+    lb.W = W;
+    lb.max_offset = p->max_offset;
+    lb.min_triangles = p->min_triangles;
+    lb.nd = nd;
+    if ((rc = launch(ctx, kSlotUnion, s, [&] { return launch_label_union(lb, s); })) != PL3D_OK) return rc;
+    if ((rc = launch(ctx, kSlotFlatten, s, [&] { return launch_label_flatten(lb, s); })) != PL3D_OK) return rc;
+    if (p->min_triangles > 0 &&
+        (rc = launch(ctx, kSlotFilter, s, [&] { return launch_label_filter(lb, s); })) != PL3D_OK)
+        return rc;
+    return PL3D_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pl3d_version(void) { return kVersion; }
+
+const char* pl3d_status_string(int status) {
+    switch (status) {
+        case PL3D_OK: return "ok";
+        case PL3D_ERR_INVALID_ARG: return "invalid argument";
+        case PL3D_ERR_OUT_OF_MEMORY: return "out of device memory";
+        case PL3D_ERR_CUDA: return "CUDA error";
+        case PL3D_ERR_TIMEOUT: return "device-side wait timed out";
+        case PL3D_ERR_UNSUPPORTED: return "unsupported device or kernel size";
+        default: return "unknown status";
+    }
+}
+
+const char* pl3d_timing_slot_name(int slot) {
+    if (slot < 0 || slot >= PL3D_TIMING_SLOTS) return "";
+    return kSlotNames[slot];
+}
+
+int pl3d_default_params(pl3d_params* p) {
+    if (!p) return PL3D_ERR_INVALID_ARG;
+    p->lap_iters = 2;
+    p->lap_lambda = 1.0f;
+    p->lap_kernel = 3;
+    p->bil_iters = 2;
+    p->bil_sigma_len = 0.1f;
+    p->bil_sigma_ang = 0.15f;
+    p->bil_kernel = 3;
+    p->max_edge = 0.05f;
+    p->min_dot = 0.96f;
+    p->max_offset = 0.0f;
+    p->min_triangles = 0;
+    p->flags = 0;
+    return PL3D_OK;
+}
+
+int pl3d_validate(const pl3d_params* p, int H, int W, const float* nd, int K) {
+    if (!p) return PL3D_ERR_INVALID_ARG;
+    if (H < 2 || W < 2) return PL3D_ERR_INVALID_ARG;
+    if (2LL * (H - 1) * (long long)(W - 1) >= (1LL << 31) || (long long)H * W >= (1LL << 31))
+        return PL3D_ERR_INVALID_ARG;
+    if (K < 1 || K > PL3D_MAX_GROUPS) return PL3D_ERR_INVALID_ARG;
+    if (p->flags != 0) return PL3D_ERR_INVALID_ARG;
+    if (p->lap_iters < 0 || p->bil_iters < 0 || p->min_triangles < 0) return PL3D_ERR_INVALID_ARG;
+    if (p->lap_iters > 0) {
+        if (p->lap_kernel != 3 && p->lap_kernel != 5 && p->lap_kernel != 7) return PL3D_ERR_UNSUPPORTED;
+        if (!finite_f(p->lap_lambda) || p->lap_lambda < 0.f || p->lap_lambda > 1.f) return PL3D_ERR_INVALID_ARG;
+    }
+    if (p->bil_iters > 0) {
+        if (p->bil_kernel != 3 && p->bil_kernel != 5 && p->bil_kernel != 7) return PL3D_ERR_UNSUPPORTED;
+        if (!finite_f(p->bil_sigma_len) || !(p->bil_sigma_len > 0.f)) return PL3D_ERR_INVALID_ARG;
+        if (!finite_f(p->bil_sigma_ang) || !(p->bil_sigma_ang > 0.f)) return PL3D_ERR_INVALID_ARG;
+    }
+    if (!finite_f(p->max_edge) || !finite_f(p->min_dot) || !finite_f(p->max_offset)) return PL3D_ERR_INVALID_ARG;
+    if (nd) {
+        for (int j = 0; j < K; ++j) {
+            const float x = nd[3 * j], y = nd[3 * j + 1], z = nd[3 * j + 2];
+            if (!finite_f(x) || !finite_f(y) || !finite_f(z)) return PL3D_ERR_INVALID_ARG;
+            if (x == 0.f && y == 0.f && z == 0.f) return PL3D_ERR_INVALID_ARG;
+        }
+    }
+    return PL3D_OK;
+}
+
+int pl3d_create(pl3d_ctx** out, int cuda_device) {
+    if (!out) return PL3D_ERR_INVALID_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess) {
+        cudaGetLastError();
+        return PL3D_ERR_CUDA;
+    }
+    if (cuda_device < 0 || cuda_device >= n) return PL3D_ERR_INVALID_ARG;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, cuda_device) != cudaSuccess) return PL3D_ERR_CUDA;
+    if (prop.major != 10 || prop.minor != 3) return PL3D_ERR_UNSUPPORTED;
+    DeviceGuard g(cuda_device);
+    if (!g.ok) return PL3D_ERR_CUDA;
+    if (laplacian_configure() != cudaSuccess || bilateral_configure() != cudaSuccess) {
+        cudaGetLastError();
+        return PL3D_ERR_CUDA;
+    }
+    pl3d_ctx* c = new (std::nothrow) pl3d_ctx();
+    if (!c) return PL3D_ERR_OUT_OF_MEMORY;
+    c->device = cuda_device;
+    c->sm_count = prop.multiProcessorCount;
+    *out = c;
+    return PL3D_OK;
+}
+
+void pl3d_destroy(pl3d_ctx* c) {
+    if (!c) return;
+    {
+        DeviceGuard g(c->device);
+        cudaDeviceSynchronize();
+        cudaFree(c->points);
+        cudaFree(c->carry);
+        cudaFree(c->groups);
+        cudaFree(c->sizes);
+        cudaFree(c->st_points);
+        cudaFree(c->st_mask);
+        cudaFree(c->st_normals);
+        cudaFree(c->st_labels);
+        for (auto& r : c->pending) {
+            cudaEventDestroy(r.start);
+            cudaEventDestroy(r.stop);
+        }
+        for (auto e : c->free_events) cudaEventDestroy(e);
+        cudaGetLastError();
+    }
+    delete c;
+}
+
+int pl3d_extract_planes_ex(pl3d_ctx* ctx, const float* points, int H, int W, const pl3d_params* params,
+                           const float* dominant_normals, int K, uint8_t* out_tri_mask, float* out_normals,
+                           int32_t* out_labels, float* out_points, uint8_t* out_groups, void* stream) {
+    if (!ctx || !points || !dominant_normals || !out_tri_mask || !out_normals || !out_labels)
+        return PL3D_ERR_INVALID_ARG;
+    int rc = pl3d_validate(params, H, W, dominant_normals, K);
+    if (rc != PL3D_OK) return rc;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return PL3D_ERR_CUDA;
+    return run(ctx, points, H, W, params, dominant_normals, K, out_tri_mask, out_normals, out_labels, out_points,
+               out_groups, (cudaStream_t)stream);
+}
+
+int pl3d_extract_planes(pl3d_ctx* ctx, const float* points, int H, int W, const pl3d_params* params,
+                        const float* dominant_normals, int K, uint8_t* out_tri_mask, float* out_normals,
+                        int32_t* out_labels, void* stream) {
+    return pl3d_extract_planes_ex(ctx, points, H, W, params, dominant_normals, K, out_tri_mask, out_normals,
+                                  out_labels, nullptr, nullptr, stream);
+}
+
+int pl3d_extract_planes_host(pl3d_ctx* ctx, const float* host_points, int H, int W, const pl3d_params* params,
+                             const float* dominant_normals, int K, uint8_t* host_tri_mask, float* host_normals,
+                             int32_t* host_labels, void* stream) {
+    if (!ctx || !host_points || !dominant_normals || !host_tri_mask || !host_normals || !host_labels)
+        return PL3D_ERR_INVALID_ARG;
+    int rc = pl3d_validate(params, H, W, dominant_normals, K);
+    if (rc != PL3D_OK) return rc;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return PL3D_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t npts = (size_t)H * W;
+    const size_t ntri = 2 * (size_t)(H - 1) * (W - 1);
+    if ((rc = grow(&ctx->st_points, &ctx->st_cap_points, npts, 3, s)) != PL3D_OK) return rc;
+    if (ctx->st_cap_tri < ntri) {
+        if (ctx->st_mask && cudaStreamSynchronize(s) != cudaSuccess) return PL3D_ERR_CUDA;
+        cudaFree(ctx->st_mask);
+        cudaFree(ctx->st_normals);
+        cudaFree(ctx->st_labels);
+        ctx->st_mask = nullptr;
+        ctx->st_normals = nullptr;
+        ctx->st_labels = nullptr;
+        ctx->st_cap_tri = 0;
+        const size_t n = ntri + ntri / 8;
+        if (cudaMalloc((void**)&ctx->st_mask, n) != cudaSuccess ||
+            cudaMalloc((void**)&ctx->st_normals, n * 3 * sizeof(float)) != cudaSuccess ||
+            cudaMalloc((void**)&ctx->st_labels, n * sizeof(int32_t)) != cudaSuccess) {
+            cudaGetLastError();
+            return PL3D_ERR_OUT_OF_MEMORY;
+        }
+        ctx->st_cap_tri = n;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (ctx->timing) {
+        e0 = take_event(ctx);
+        e1 = take_event(ctx);
+        if (e0 && e1) cudaEventRecord(e0, s);
+    }
+    if (cudaMemcpyAsync(ctx->st_points, host_points, npts * 3 * sizeof(float), cudaMemcpyHostToDevice, s) !=
+        cudaSuccess)
+        return PL3D_ERR_CUDA;
+    if (e0 && e1) {
+        cudaEventRecord(e1, s);
+        ctx->pending.push_back({kSlotCopies, e0, e1});
+    }
+    rc = run(ctx, ctx->st_points, H, W, params, dominant_normals, K, ctx->st_mask, ctx->st_normals, ctx->st_labels,
+             nullptr, nullptr, s);
+    if (rc != PL3D_OK) return rc;
+    if (ctx->timing) {
+        e0 = take_event(ctx);
+        e1 = take_event(ctx);
+        if (e0 && e1) cudaEventRecord(e0, s);
+    }
+    if (cudaMemcpyAsync(host_tri_mask, ctx->st_mask, ntri, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(host_normals, ctx->st_normals, ntri * 3 * sizeof(float), cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(host_labels, ctx->st_labels, ntri * sizeof(int32_t), cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess)
+        return PL3D_ERR_CUDA;
+    if (e0 && e1) {
+        cudaEventRecord(e1, s);
+        ctx->pending.push_back({kSlotCopies, e0, e1});
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) return PL3D_ERR_CUDA;
+    return PL3D_OK;
+}
+
+int pl3d_sync(pl3d_ctx* ctx, void* stream) {
+    if (!ctx) return PL3D_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return PL3D_ERR_CUDA;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return PL3D_ERR_CUDA;
+    if (cudaGetLastError() != cudaSuccess) return PL3D_ERR_CUDA;
+    return PL3D_OK;
+}
+
+int pl3d_set_timing(pl3d_ctx* ctx, int enable) {
+    if (!ctx) return PL3D_ERR_INVALID_ARG;
+    ctx->timing = enable != 0;
+    return PL3D_OK;
+}
+
+int pl3d_read_timing(pl3d_ctx* ctx, double* ms_out, int64_t* launches_out, int n_slots, int reset) {
+    if (!ctx || n_slots < 0) return PL3D_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return PL3D_ERR_CUDA;
+    for (auto& r : ctx->pending) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(r.stop) != cudaSuccess) return PL3D_ERR_CUDA;
+        if (cudaEventElapsedTime(&ms, r.start, r.stop) == cudaSuccess) {
+            ctx->slot_ms[r.slot] += ms;
+            ctx->slot_n[r.slot] += 1;
+        }
+        ctx->free_events.push_back(r.start);
+        ctx->free_events.push_back(r.stop);
+    }
+    ctx->pending.clear();
+    for (int i = 0; i < n_slots && i < PL3D_TIMING_SLOTS; ++i) {
+        if (ms_out) ms_out[i] = ctx->slot_ms[i];
+        if (launches_out) launches_out[i] = ctx->slot_n[i];
+    }
+    if (reset) {
+        for (int i = 0; i < PL3D_TIMING_SLOTS; ++i) {
+            ctx->slot_ms[i] = 0.0;
+            ctx->slot_n[i] = 0;
+        }
+    }
+    return PL3D_TIMING_SLOTS;
+}
+
+int64_t pl3d_launch_count(const pl3d_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+}  // extern "C"

@@ -1,0 +1,109 @@
+// pl3d_internal.cuh -- declarations shared by the kernels and the C ABI of libpl3d.
+//
+// Data layout in device memory (one frame of H x W points, Q = (H-1)(W-1) quads):
+//   input points     AoS  float [H][W][3]            (caller's buffer)
+//   smoothed points  SoA  float x[H*W], y[H*W], z[H*W] (context scratch, ping-pong pair)
+//   bilateral carry  AoS  float [2Q][3]               (context scratch, only when the
+//                                                      bilateral iterations need more than
+//                                                      one launch)
+//   groups           u8   [2Q]                        (context scratch or caller's buffer)
+//   labels           i32  [2Q]                        (caller's buffer; doubles as the
+//                                                      union-find parent array)
+//   segment sizes    i32  [2Q]                        (context scratch, only when tri_min > 0)
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pl3d.h"
+
+namespace pl3d {
+
+// Largest supported filter radius (kernel size 7).
+constexpr int kMaxRadius = 3;
+
+// Centroid given to a triangle without a normal: its bilateral weight underflows to
+// exactly 0 against any real triangle, so it drops out of every sum without a branch.
+constexpr float kAbsentCentroid = 1.0e30f;
+
+// Squared cross-product length at or below which a triangle has no normal (|n| <= 1e-20).
+constexpr float kDegenerateLen2 = 1.0e-40f;
+
+// Dominant normals, unit length, passed to kernels by value (3 KB, fits the parameter space).
+struct Dominant {
+    int K;
+    float v[PL3D_MAX_GROUPS * 3];
+};
+
+// ---------------------------------------------------------------- Laplacian (Eq. 1-2)
+struct LapArgs {
+    const float* in_aos;                      // AoS input, or nullptr to read in_x/y/z
+    const float* in_x;
+    const float* in_y;
+    const float* in_z;
+    float* out_x;                             // SoA output
+    float* out_y;
+    float* out_z;
+    float* out_aos;                           // optional AoS export of the result
+    int H, W;
+    int iters;                                // iterations fused in this launch (>= 0)
+    float lambda;
+};
+// Tile of output points per CTA.
+constexpr int kLapTileH = 16;
+constexpr int kLapTileW = 32;
+constexpr int kLapThreads = 256;
+// Largest halo (fused iterations x radius) one launch may carry.
+constexpr int kLapMaxHalo = 8;
+cudaError_t launch_laplacian(const LapArgs& a, int radius, cudaStream_t s);
+// Opts the kernels in to their largest shared-memory size on the current device.
+cudaError_t laplacian_configure();
+size_t laplacian_smem_bytes(int radius, int iters);
+
+// ----------------------------------------- normals + bilateral (Eq. 3-6) + Algorithm 4
+struct BilArgs {
+    const float* px;                          // smoothed points, SoA
+    const float* py;
+    const float* pz;
+    const float* carry_in;                    // AoS [2Q][3] normals from the previous launch (non-first)
+    float* carry_out;                         // AoS [2Q][3] normals for the next launch (non-last)
+    uint8_t* out_mask;                        // last launch only
+    float* out_normals;
+    uint8_t* out_groups;
+    int32_t* out_labels;                      // initialised to GID (grouped) or -1
+    int H, W;
+    int iters;                                // iterations fused in this launch (>= 0)
+    float neg_a;                              // -log2(e) / (2 sigma_c^2)
+    float neg_s;                              // -log2(e) / (2 sigma_s^2)
+    float max_edge2;                          // l_max^2, or +inf when disabled
+    float min_dot;
+    Dominant nd;
+};
+constexpr int kBilTileH = 16;                 // quads per CTA tile
+constexpr int kBilTileW = 32;
+constexpr int kBilThreads = 256;
+constexpr int kBilMaxHalo = 6;
+cudaError_t launch_bilateral(const BilArgs& a, int radius, bool first, bool last, cudaStream_t s);
+cudaError_t bilateral_configure();
+size_t bilateral_smem_bytes(int radius, int iters);
+
+// ------------------------------------------------------- connected segments (Algorithm 5)
+struct LabelArgs {
+    const uint8_t* groups;
+    int32_t* labels;                          // parent array in, labels out
+    int32_t* sizes;                           // segment sizes (tri_min > 0) or nullptr
+    const float* px;                          // smoothed points, SoA (offset test only)
+    const float* py;
+    const float* pz;
+    int H, W;
+    float max_offset;                         // <= 0: no offset test
+    int min_triangles;
+    Dominant nd;
+};
+cudaError_t launch_label_union(const LabelArgs& a, cudaStream_t s);
+cudaError_t launch_label_flatten(const LabelArgs& a, cudaStream_t s);
+cudaError_t launch_label_filter(const LabelArgs& a, cudaStream_t s);
+
+inline int div_up(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+}  // namespace pl3d

@@ -1,0 +1,236 @@
+"""GPU vs FP64 oracle parity through the C ABI (needs a GB300 and the built library).
+
+Bounds (oracle.compare): smoothed points <= 2e-5 m, normals <= 1e-4 rad, masks bit-exact,
+labels bit-exact (both sides label a segment by its smallest GID); decisions within 1e-5 of a
+threshold are flagged by the oracle and substituted, and their count is reported.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle.compare import compare
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    import paper_2007_12065_gb300 as pl3d
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    oracle.set_threads(os.cpu_count() or 1)
+    ex = pl3d.PlaneExtractor(0)
+    yield pl3d, ex, torch
+    ex.close()
+
+
+def run_pair(env, points, params: dict, nd, check=True):
+    pl3d, ex, torch = env
+    p = pl3d.make_params(**params)
+    out = ex(torch.from_numpy(np.ascontiguousarray(points)).cuda(), p, nd, want_points=True, want_groups=True)
+    torch.cuda.synchronize()
+    dev = {k: v.cpu().numpy() for k, v in out.items()}
+    op = oracle.OracleParams(**params)
+    ref = oracle.extract_planes(points, op, nd)
+    rep = compare(dev, ref, op, points.shape[0], points.shape[1]) if check else None
+    return dev, ref, rep
+
+
+# ----------------------------------------------------------------------------- the three frame workloads
+
+
+@pytest.mark.parametrize("name", ["rgbd_120x160", "rgbd_480x640", "lidar_64x1024"])
+def test_workload_parity(env, name):
+    f = synth.WORKLOADS[name]()
+    dev, ref, rep = run_pair(env, f.points, f.params, f.dominant_normals)
+    print(name, rep)
+    assert rep["segments"] > 10
+
+
+@pytest.mark.parametrize("H,W", [(720, 1280), (128, 2048), (240, 320)])
+def test_large_and_mixed_sizes(env, H, W):
+    f = synth.mixed_frame(H, W, seed=H * 7 + W)
+    dev, ref, rep = run_pair(env, f.points, f.params, f.dominant_normals)
+    print(H, W, rep)
+
+
+# ----------------------------------------------------------------------------- shapes and edge cases
+
+SMALL = dict(lap_iters=3, lap_lambda=1.0, lap_kernel=3, bil_iters=2, bil_sigma_len=0.1, bil_sigma_ang=0.15,
+             bil_kernel=3, max_edge=0.1, min_dot=0.95, max_offset=0.0, min_triangles=0)
+
+
+@pytest.mark.parametrize("H,W", [(2, 2), (2, 3), (3, 2), (3, 3), (4, 5), (5, 7), (17, 33), (33, 65), (31, 31),
+                                 (16, 32), (18, 34), (49, 97), (1, 5)])
+def test_small_and_ragged_shapes(env, H, W):
+    if H < 2 or W < 2:
+        pl3d, ex, torch = env
+        with pytest.raises(pl3d.PL3DError):
+            ex(torch.zeros((H, W, 3), device="cuda"), pl3d.make_params(**SMALL), np.array([[0, 0, 1]], np.float32))
+        return
+    f = synth.depth_camera_scene(H, W, seed=H * 100 + W, n_boxes=1, noise_sigma=0.003, nan_frac=0.05,
+                                 hfov_deg=10.0)
+    run_pair(env, f.points, SMALL, f.dominant_normals)
+
+
+def test_all_nan_and_no_nan(env):
+    f = synth.rgbd_120x160()
+    pts = np.full_like(f.points, np.nan)
+    dev, ref, rep = run_pair(env, pts, f.params, f.dominant_normals)
+    assert (dev["labels"] == -1).all() and (dev["mask"] == 0).all() and np.isnan(dev["normals"]).all()
+    g = synth.depth_camera_scene(64, 96, seed=3, nan_frac=0.0)
+    dev, ref, rep = run_pair(env, g.points, g.params, g.dominant_normals)
+    assert np.isfinite(dev["normals"]).all()
+
+
+def test_partially_invalid_coordinates(env):
+    """A point with any non-finite coordinate (NaN or inf in one component) is invalid."""
+    f = synth.depth_camera_scene(40, 56, seed=4, nan_frac=0.0)
+    pts = f.points.copy()
+    rng = np.random.default_rng(0)
+    idx = rng.integers(0, 40 * 56, 60)
+    comp = rng.integers(0, 3, 60)
+    vals = rng.choice([np.nan, np.inf, -np.inf], 60)
+    pts.reshape(-1, 3)[idx, comp] = vals
+    run_pair(env, pts, f.params, f.dominant_normals)
+
+
+def test_nan_stripes_cut_segments(env):
+    f = synth.depth_camera_scene(64, 96, seed=5, n_boxes=0, noise_sigma=0.0, nan_frac=0.0)
+    pts = f.points.copy()
+    pts[:, 40] = np.nan        # one-pixel vertical stripe
+    pts[30, :] = np.nan        # one-pixel horizontal stripe
+    dev, ref, rep = run_pair(env, pts, f.params, f.dominant_normals)
+    assert rep["segments"] >= 4
+
+
+@pytest.mark.parametrize("lk,bk", [(5, 3), (7, 3), (3, 5), (3, 7), (5, 5)])
+def test_kernel_sizes(env, lk, bk):
+    f = synth.depth_camera_scene(70, 90, seed=lk * 10 + bk)
+    prm = dict(f.params, lap_kernel=lk, bil_kernel=bk)
+    run_pair(env, f.points, prm, f.dominant_normals)
+
+
+@pytest.mark.parametrize("li,bi", [(0, 0), (0, 3), (4, 0), (1, 1), (8, 6), (9, 7), (20, 13)])
+def test_iteration_counts_including_multi_launch(env, li, bi):
+    """Iteration counts above one launch's halo are split into several launches."""
+    f = synth.depth_camera_scene(60, 100, seed=li * 31 + bi)
+    prm = dict(f.params, lap_iters=li, bil_iters=bi)
+    run_pair(env, f.points, prm, f.dominant_normals)
+
+
+@pytest.mark.parametrize("kw", [dict(lap_lambda=0.5), dict(lap_lambda=0.0), dict(max_edge=0.0), dict(max_edge=0.02),
+                                dict(min_dot=0.99), dict(min_dot=-1.0), dict(bil_sigma_len=0.02, bil_sigma_ang=0.05),
+                                dict(bil_sigma_len=50.0, bil_sigma_ang=50.0), dict(min_triangles=25),
+                                dict(min_triangles=1)])
+def test_parameter_variants(env, kw):
+    f = synth.depth_camera_scene(80, 120, seed=11, n_boxes=3, ramp=True)
+    run_pair(env, f.points, dict(f.params, **kw), f.dominant_normals)
+
+
+def test_offset_test(env):
+    f = synth.depth_camera_scene(60, 80, seed=12, n_boxes=3, noise_sigma=0.002, nan_frac=0.0)
+    prm = dict(f.params, max_offset=0.004)
+    dev, ref, _ = run_pair(env, f.points, prm, f.dominant_normals, check=False)
+    # near-threshold pair decisions would need substitution; this seed must have none
+    C, nd = ref["centroids"], ref["nd_unit"]
+    G = ref["groups"]
+    Wq = f.W - 1
+    near = 0
+    for i in range(0, G.shape[0], 2):
+        if G[i] == 255:
+            continue
+        q = i // 2
+        u, v = divmod(q, Wq)
+        for j in [i + 1] + ([i + 3] if v + 1 < Wq else []) + ([i - 2 * Wq + 1] if u >= 1 else []):
+            if G[j] == G[i]:
+                off = abs(nd[G[i]] @ (C[i] - C[j]))
+                near += abs(off - 0.004) < oracle.NEAR
+    assert near == 0
+    compare(dev, ref, oracle.OracleParams(**prm), f.H, f.W)
+
+
+@pytest.mark.parametrize("K", [1, 2, 254])
+def test_many_dominant_normals(env, K):
+    rng = np.random.default_rng(K)
+    f = synth.depth_camera_scene(48, 64, seed=13)
+    nd = rng.normal(size=(K, 3)).astype(np.float32)
+    nd[0] = (0, 0, 1)
+    run_pair(env, f.points, dict(f.params, min_dot=0.9), nd)
+
+
+def test_lidar_far_range(env):
+    f = synth.lidar_scene(32, 2048, seed=14, n_cars=30)
+    run_pair(env, f.points, f.params, f.dominant_normals)
+
+
+# ----------------------------------------------------------------------------- API behaviour
+
+
+def test_deterministic_and_host_entry_matches(env):
+    pl3d, ex, torch = env
+    f = synth.rgbd_120x160()
+    p = pl3d.make_params(**f.params)
+    pts = torch.from_numpy(f.points).cuda()
+    a = ex(pts, p, f.dominant_normals)
+    b = ex(pts, p, f.dominant_normals)
+    torch.cuda.synchronize()
+    for k in a:
+        assert torch.equal(a[k].nan_to_num(7.0), b[k].nan_to_num(7.0)), k
+    H, W = f.H, f.W
+    n = 2 * (H - 1) * (W - 1)
+    hp = torch.from_numpy(f.points).pin_memory()
+    hm = torch.empty(n, dtype=torch.uint8).pin_memory()
+    hn = torch.empty((n, 3), dtype=torch.float32).pin_memory()
+    hl = torch.empty(n, dtype=torch.int32).pin_memory()
+    pl3d.pl3d_extract_planes_host(ex.ctx, hp, H, W, p, f.dominant_normals, f.dominant_normals.shape[0], hm, hn, hl)
+    assert torch.equal(hm, a["mask"].cpu())
+    assert torch.equal(hn.nan_to_num(7.0), a["normals"].cpu().nan_to_num(7.0))
+    assert torch.equal(hl, a["labels"].cpu())
+
+
+def test_side_stream_and_timing(env):
+    pl3d, ex, torch = env
+    f = synth.rgbd_120x160()
+    p = pl3d.make_params(**f.params)
+    pts = torch.from_numpy(f.points).cuda()
+    s = torch.cuda.Stream()
+    pl3d.pl3d_set_timing(ex.ctx, True)
+    pl3d.pl3d_read_timing(ex.ctx, reset=True)
+    n0 = pl3d.pl3d_launch_count(ex.ctx)
+    with torch.cuda.stream(s):
+        out = ex(pts, p, f.dominant_normals)
+    pl3d.pl3d_sync(ex.ctx, s)
+    t = pl3d.pl3d_read_timing(ex.ctx, reset=True)
+    pl3d.pl3d_set_timing(ex.ctx, False)
+    n1 = pl3d.pl3d_launch_count(ex.ctx)
+    assert sum(v[1] for v in t.values()) == n1 - n0 == 4      # lap, bilateral, union, flatten
+    assert all(v[0] >= 0 for v in t.values())
+    ref = oracle.extract_planes(f.points, oracle.OracleParams(**f.params), f.dominant_normals)
+    assert np.array_equal(out["labels"].cpu().numpy(), ref["labels"])
+
+
+def test_invalid_arguments_raise(env):
+    pl3d, ex, torch = env
+    pts = torch.zeros((8, 8, 3), device="cuda")
+    nd = np.array([[0, 0, 1]], np.float32)
+    with pytest.raises(pl3d.PL3DError):
+        ex(pts, pl3d.make_params(lap_kernel=4), nd)
+    with pytest.raises(pl3d.PL3DError):
+        ex(pts, pl3d.make_params(), np.zeros((0, 3), np.float32))
+    with pytest.raises(ValueError):
+        ex(pts.double(), pl3d.make_params(), nd)
+    # the context stays usable after rejected calls
+    ex(pts, pl3d.make_params(), nd)
+    pl3d.pl3d_sync(ex.ctx)
+
+
+def test_workspace_grows_and_shrinks_back(env):
+    """Frames of different sizes through one context: growth must not disturb later results."""
+    for (H, W) in [(20, 30), (300, 400), (20, 30), (64, 1024)]:
+        f = synth.mixed_frame(H, W, seed=H + W) if (H, W) == (64, 1024) else synth.depth_camera_scene(H, W, seed=H)
+        run_pair(env, f.points, f.params, f.dominant_normals)
