@@ -58,6 +58,10 @@ def _load():
     lib.orc_has_openmp.restype = ctypes.c_int
     lib.orc_widen.argtypes = [_f32p, ctypes.c_int64, _f64p]
     lib.orc_laplacian.argtypes = [_f64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, _f64p]
+    lib.orc_laplacian_jitter.argtypes = [_f64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                         ctypes.c_double, ctypes.c_uint64, _f64p]
+    lib.orc_bilateral_jitter.argtypes = [_f64p, _f64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_uint64, _f64p]
     lib.orc_triangle_geometry.argtypes = [_f64p, ctypes.c_int, ctypes.c_int, _f64p, _f64p]
     lib.orc_mask.argtypes = [_f64p, _f64p, ctypes.c_int, ctypes.c_int, ctypes.c_double, _u8p, _f64p]
     lib.orc_bilateral.argtypes = [_f64p, _f64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
@@ -70,7 +74,7 @@ def _load():
     lib.orc_extract_triangles.argtypes = [_f64p, ctypes.c_int, ctypes.c_int, _i32p, _i32p]
     lib.orc_extract_triangles.restype = ctypes.c_int64
     lib.orc_extract_halfedges.argtypes = [_i32p, ctypes.c_int, ctypes.c_int, ctypes.c_int64, _i32p]
-    for name in ("orc_laplacian", "orc_triangle_geometry", "orc_mask", "orc_bilateral", "orc_normalize_dominant",
+    for name in ("orc_laplacian", "orc_laplacian_jitter", "orc_bilateral_jitter", "orc_triangle_geometry", "orc_mask", "orc_bilateral", "orc_normalize_dominant",
                  "orc_classify", "orc_label", "orc_extract_halfedges", "orc_triangle_twins"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -109,12 +113,14 @@ def widen(points: np.ndarray) -> np.ndarray:
     return out
 
 
-def laplacian(P: np.ndarray, kernel: int, lam: float, iters: int) -> np.ndarray:
-    """Eq. 1-2 / Section 5.1: `iters` Jacobi iterations of the Laplacian filter on FP64 [H, W, 3]."""
+def laplacian(P: np.ndarray, kernel: int, lam: float, iters: int, eps: float = 0.0, seed: int = 0) -> np.ndarray:
+    """Eq. 1-2 / Section 5.1: `iters` Jacobi iterations of the Laplacian filter on FP64 [H, W, 3].
+    eps > 0 scales every update by (1 +- eps) (seeded signs): a sensitivity run, not the method."""
     P = np.ascontiguousarray(P, dtype=np.float64)
     H, W = P.shape[:2]
     out = np.empty_like(P)
-    _check(_load().orc_laplacian(_p(P, _f64p), H, W, kernel, lam, iters, _p(out, _f64p)), "laplacian")
+    _check(_load().orc_laplacian_jitter(_p(P, _f64p), H, W, kernel, lam, iters, float(eps), int(seed),
+                                        _p(out, _f64p)), "laplacian")
     return out
 
 
@@ -142,13 +148,14 @@ def mask(P_raw: np.ndarray, P_smooth: np.ndarray, l_max: float):
 
 
 def bilateral(C: np.ndarray, N: np.ndarray, H: int, W: int, kernel: int, sigma_c: float, sigma_s: float,
-              iters: int) -> np.ndarray:
-    """Eq. 3-6 / Section 5.2: `iters` Jacobi iterations of the bilateral normal filter."""
+              iters: int, eps: float = 0.0, seed: int = 0) -> np.ndarray:
+    """Eq. 3-6 / Section 5.2: `iters` Jacobi iterations of the bilateral normal filter.
+    eps > 0 scales every weighted sum by (1 +- eps) per coordinate (sensitivity run)."""
     C = np.ascontiguousarray(C, dtype=np.float64)
     N = np.ascontiguousarray(N, dtype=np.float64)
     out = np.empty_like(N)
-    _check(_load().orc_bilateral(_p(C, _f64p), _p(N, _f64p), H, W, kernel, sigma_c, sigma_s, iters,
-                                 _p(out, _f64p)), "bilateral")
+    _check(_load().orc_bilateral_jitter(_p(C, _f64p), _p(N, _f64p), H, W, kernel, sigma_c, sigma_s, iters,
+                                        float(eps), int(seed), _p(out, _f64p)), "bilateral")
     return out
 
 
@@ -232,14 +239,29 @@ class OracleParams:
 
 # Width of the band around a threshold inside which FP32 and FP64 may decide differently.
 NEAR = 1e-5
+# Relative size of the perturbation used to find outputs that FP32 arithmetic cannot pin down
+# (a few units of FP32 rounding, 2^-21, applied to every update of every iteration), the seeds
+# of the runs (the largest move over the runs counts), and the angle a normal may move under it
+# before the triangle counts as ill-conditioned (a quarter of the 1e-4 rad acceptance bound).
+JITTER = 2.0 ** -21
+JITTER_SEEDS = (0x5EED, 0xB11A)
+ILL_CONDITIONED_RAD = 2.5e-5
 
 
-def extract_planes(points: np.ndarray, params, dominant_normals: np.ndarray) -> dict:
+def _angle(a: np.ndarray, b: np.ndarray) -> np.ndarray:
+    cr = np.linalg.norm(np.cross(a, b), axis=-1)
+    return np.arctan2(cr, np.einsum("ij,ij->i", a, b))
+
+
+def extract_planes(points: np.ndarray, params, dominant_normals: np.ndarray, sensitivity: bool = True) -> dict:
     """The whole path in the paper's order. Returns every intermediate, FP64 where real-valued.
 
     Keys: smoothed [H,W,3], centroids [T,3], normals_raw [T,3], normals [T,3], mask [T] u8,
     edge [T], groups [T] u8, best [T], second [T], labels [T] i32, nd_unit [K,3],
-    near_edge / near_dot / near_tie [T] bool (decisions within NEAR of a threshold).
+    near_edge / near_dot / near_tie [T] bool (decisions within NEAR of a threshold),
+    ill_conditioned [T] bool (sensitivity=True: the normal moves by more than ILL_CONDITIONED_RAD
+    when the Laplacian updates and bilateral sums are perturbed by JITTER relative -- FP32
+    arithmetic cannot be expected to reproduce it to the 1e-4 rad bound).
     """
     p = params
     H, W = points.shape[:2]
@@ -257,6 +279,17 @@ def extract_planes(points: np.ndarray, params, dominant_normals: np.ndarray) -> 
     near_dot = has_best & (np.abs(np.where(has_best, best, 0.0) - p.min_dot) < NEAR)
     has_second = has_best & np.isfinite(second)
     near_tie = has_second & ((np.where(has_second, best - second, 1.0)) < NEAR)
+    ill = np.zeros(m.shape[0], bool)
+    if sensitivity:
+        ang = np.zeros(m.shape[0])
+        for seed in JITTER_SEEDS:
+            Sj = laplacian(raw, p.lap_kernel, p.lap_lambda, p.lap_iters, JITTER, seed)
+            Cj, Nj0 = triangle_geometry(Sj)
+            Nj = bilateral(Cj, Nj0, H, W, p.bil_kernel, p.bil_sigma_len, p.bil_sigma_ang, p.bil_iters, JITTER,
+                           seed + 1)
+            has = ~np.isnan(N[:, 0]) & ~np.isnan(Nj[:, 0])
+            ang[has] = np.maximum(ang[has], _angle(N[has], Nj[has]))
+        ill = ang > ILL_CONDITIONED_RAD
     return dict(smoothed=smoothed, centroids=C, normals_raw=N0, normals=N, mask=m, edge=edge, groups=G,
                 best=best, second=second, labels=labels, nd_unit=nd_unit, near_edge=near_edge,
-                near_dot=near_dot, near_tie=near_tie)
+                near_dot=near_dot, near_tie=near_tie, ill_conditioned=ill)

@@ -10,6 +10,12 @@ best dots against each other. Such triangles are flagged by the oracle; a mask o
 mismatch is accepted only on a flagged triangle, and the labels are then checked against the
 oracle's region growing rerun with the device's groups substituted on the flagged triangles
 only. The number of flagged triangles is reported.
+
+A normal that the problem itself does not determine to FP32 precision -- the oracle's
+sensitivity runs (every Laplacian update and bilateral sum perturbed by 2^-21 relative, two
+seeds) move it
+by more than a quarter of the bound -- is ill-conditioned: it is reported (count and largest
+error) but not held to the 1e-4 rad bound, and its group counts as flagged.
 """
 from __future__ import annotations
 
@@ -33,8 +39,10 @@ def compare(dev: dict, ref: dict, params, H: int, W: int, point_tol=POINT_TOL_M,
     points [H,W,3] f32. ref: oracle.extract_planes(...). Returns a report; raises AssertionError on a
     violation of the bounds above."""
     rep: dict = {}
-    flagged = ref["near_edge"] | ref["near_dot"] | ref["near_tie"]
+    ill = ref.get("ill_conditioned", np.zeros(ref["mask"].shape[0], bool))
+    flagged = ref["near_edge"] | ref["near_dot"] | ref["near_tie"] | ill
     rep["flagged"] = int(flagged.sum())
+    rep["ill_conditioned"] = int(ill.sum())
 
     if dev.get("points") is not None:
         P = np.asarray(dev["points"], np.float64).reshape(H, W, 3)
@@ -49,9 +57,14 @@ def compare(dev: dict, ref: dict, params, H: int, W: int, point_tol=POINT_TOL_M,
     Nr = ref["normals"]
     nan_d, nan_r = np.isnan(N).any(-1), np.isnan(Nr).any(-1)
     assert np.array_equal(nan_d, nan_r), f"normal NaN pattern differs at {np.nonzero(nan_d != nan_r)[0][:5]}"
-    ang = angle_rad(N[~nan_r], Nr[~nan_r]) if (~nan_r).any() else np.zeros(0)
+    ang_all = np.zeros(N.shape[0])
+    if (~nan_r).any():
+        ang_all[~nan_r] = angle_rad(N[~nan_r], Nr[~nan_r])
+    well = ~nan_r & ~ill
+    ang = ang_all[well]
     rep["normals_max_err_rad"] = float(ang.max()) if ang.size else 0.0
     rep["normals_over_tol"] = int((ang > normal_tol).sum())
+    rep["ill_conditioned_max_err_rad"] = float(ang_all[ill].max()) if ill.any() else 0.0
     assert rep["normals_max_err_rad"] <= normal_tol, (
         f"normals off by {rep['normals_max_err_rad']:.3g} rad > {normal_tol} on {rep['normals_over_tol']} triangles")
 

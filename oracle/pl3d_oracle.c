@@ -48,6 +48,12 @@
  *     triangles). Its label is its smallest GID. Components of at most tri_min
  *     triangles are dropped when tri_min > 0 (Algorithm 5 keeps |T^g_i| > tri_min).
  *   - No wrap between the last and the first image column.
+ *
+ * Sensitivity runs (test instrumentation, not part of the method): orc_laplacian_jitter and
+ * orc_bilateral_jitter repeat the filters with every update scaled by (1 + eps r), r = +-1
+ * drawn from a counter-based hash (SplitMix64 finaliser) of (seed, iteration, index,
+ * coordinate). With eps of the order of FP32 rounding (2^-22) they show which outputs the
+ * problem itself does not determine to FP32 precision.
  */
 #include <math.h>
 #include <stdint.h>
@@ -62,6 +68,20 @@
 #define ORC_ENOMEM -2
 
 static int g_threads = 1;
+
+/* SplitMix64 finaliser (Steele, Lea, Flood 2014) used as a counter-based hash. */
+static uint64_t mix64(uint64_t z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+/* +1 or -1 from (seed, iteration, index, coordinate). */
+static double jitter_sign(uint64_t seed, int it, int64_t index, int comp) {
+    uint64_t h = mix64(seed ^ mix64(((uint64_t)it << 48) ^ ((uint64_t)index << 2) ^ (uint64_t)comp));
+    return (h >> 63) ? 1.0 : -1.0;
+}
 
 void orc_set_threads(int n) { g_threads = n < 1 ? 1 : n; }
 
@@ -98,8 +118,8 @@ void orc_widen(const float* pts, int64_t n_points, double* out) {
 /* ------------------------------------------------------------------------ */
 /* Eq. 1-2, Section 5.1: Laplacian filter on the implicit grid.              */
 /* ------------------------------------------------------------------------ */
-int orc_laplacian(const double* P0, int H, int W, int kernel, double lambda, int iters,
-                  double* out) {
+int orc_laplacian_jitter(const double* P0, int H, int W, int kernel, double lambda, int iters,
+                         double eps, uint64_t seed, double* out) {
     if (H < 1 || W < 1 || kernel < 1 || (kernel % 2) == 0 || iters < 0) return ORC_EINVAL;
     const int r = kernel / 2;
     const size_t n = (size_t)H * (size_t)W * 3u;
@@ -143,9 +163,16 @@ int orc_laplacian(const double* P0, int H, int W, int kernel, double lambda, int
                     }
                 }
                 if (wsum > 0.0) {
-                    vo[0] = vi[0] + lambda * sx / wsum; /* Eq. 1, umbrella form */
-                    vo[1] = vi[1] + lambda * sy / wsum;
-                    vo[2] = vi[2] + lambda * sz / wsum;
+                    double j0 = 1.0, j1 = 1.0, j2 = 1.0;
+                    if (eps != 0.0) {
+                        int64_t pi = (int64_t)u * W + v;
+                        j0 += eps * jitter_sign(seed, it, pi, 0);
+                        j1 += eps * jitter_sign(seed, it, pi, 1);
+                        j2 += eps * jitter_sign(seed, it, pi, 2);
+                    }
+                    vo[0] = vi[0] + j0 * (lambda * sx / wsum); /* Eq. 1, umbrella form */
+                    vo[1] = vi[1] + j1 * (lambda * sy / wsum);
+                    vo[2] = vi[2] + j2 * (lambda * sz / wsum);
                 } else {
                     vo[0] = vi[0];
                     vo[1] = vi[1];
@@ -161,6 +188,10 @@ int orc_laplacian(const double* P0, int H, int W, int kernel, double lambda, int
     free(cur);
     free(nxt);
     return ORC_OK;
+}
+
+int orc_laplacian(const double* P0, int H, int W, int kernel, double lambda, int iters, double* out) {
+    return orc_laplacian_jitter(P0, H, W, kernel, lambda, iters, 0.0, 0, out);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -276,8 +307,8 @@ int orc_mask(const double* P_raw, const double* P_smooth, int H, int W, double l
 /* ------------------------------------------------------------------------ */
 /* Eq. 3-6, Section 5.2: bilateral filter of triangle normals over T_FC.     */
 /* ------------------------------------------------------------------------ */
-int orc_bilateral(const double* C, const double* N0, int H, int W, int kernel, double sigma_c,
-                  double sigma_s, int iters, double* Nout) {
+int orc_bilateral_jitter(const double* C, const double* N0, int H, int W, int kernel, double sigma_c,
+                         double sigma_s, int iters, double eps, uint64_t seed, double* Nout) {
     if (H < 2 || W < 2 || kernel < 1 || (kernel % 2) == 0 || iters < 0) return ORC_EINVAL;
     if (!(sigma_c > 0.0) || !(sigma_s > 0.0)) return ORC_EINVAL;
     const int r = kernel / 2;
@@ -333,6 +364,11 @@ int orc_bilateral(const double* C, const double* N0, int H, int W, int kernel, d
                             }
                         }
                     }
+                    if (eps != 0.0) {
+                        sx *= 1.0 + eps * jitter_sign(seed, it, i, 0);
+                        sy *= 1.0 + eps * jitter_sign(seed, it, i, 1);
+                        sz *= 1.0 + eps * jitter_sign(seed, it, i, 2);
+                    }
                     double len = sqrt(sx * sx + sy * sy + sz * sz);
                     if (len > 0.0) {
                         no[0] = sx / len; /* Eq. 3 with K folded into the renormalisation */
@@ -354,6 +390,11 @@ int orc_bilateral(const double* C, const double* N0, int H, int W, int kernel, d
     free(cur);
     free(nxt);
     return ORC_OK;
+}
+
+int orc_bilateral(const double* C, const double* N0, int H, int W, int kernel, double sigma_c,
+                  double sigma_s, int iters, double* Nout) {
+    return orc_bilateral_jitter(C, N0, H, W, kernel, sigma_c, sigma_s, iters, 0.0, 0, Nout);
 }
 
 /* Unit-length copies of the K dominant plane normals (input to Algorithm 4). */

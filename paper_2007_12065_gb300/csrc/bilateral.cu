@@ -13,6 +13,10 @@
 // included, triangles outside the image or without a normal skipped. Both exponentials are
 // folded into one exp2 with the scales precomputed on the host.
 //
+// Smoothed points arrive as input position v0 plus displacement d (see df32.cuh); edges are
+// formed as exact float pairs and the cross product with error-free products, so the normal
+// of a sliver triangle is as accurate as the pair allows rather than as FP32 coordinates do.
+//
 // One CTA owns kBilTileH x kBilTileW quads. It stages the smoothed points of its tile plus a
 // halo of (fused iterations x radius) quads, builds centroids and normals of every staged
 // triangle in shared memory, runs the fused iterations there (the valid region shrinks by
@@ -25,6 +29,7 @@
 // triangle its weight is exp2(-inf) = 0, so it drops out of every sum without a branch.
 #include <math.h>
 
+#include "df32.cuh"
 #include "pl3d_internal.cuh"
 
 namespace pl3d {
@@ -36,8 +41,37 @@ struct V3 {
 
 __device__ __forceinline__ V3 sub(V3 a, V3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
 __device__ __forceinline__ float dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
-__device__ __forceinline__ V3 cross(V3 a, V3 b) {
-    return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+
+// A staged point: input position and displacement.
+struct SP {
+    float x, y, z, dx, dy, dz;
+};
+
+__device__ __forceinline__ SP load_sp(const float* P, int pplane, int i) {
+    return {P[i], P[pplane + i], P[2 * pplane + i], P[3 * pplane + i], P[4 * pplane + i], P[5 * pplane + i]};
+}
+
+// Unnormalised normal (b - a) x (c - a), each component rounded once from exact float pairs.
+__device__ __forceinline__ V3 exact_cross(const SP& a, const SP& b, const SP& c) {
+    const F2 e1x = pair_diff(a.x, a.dx, b.x, b.dx), e1y = pair_diff(a.y, a.dy, b.y, b.dy),
+             e1z = pair_diff(a.z, a.dz, b.z, b.dz);
+    const F2 e2x = pair_diff(a.x, a.dx, c.x, c.dx), e2y = pair_diff(a.y, a.dy, c.y, c.dy),
+             e2z = pair_diff(a.z, a.dz, c.z, c.dz);
+    return {pair_sub_round(pair_mul(e1y, e2z), pair_mul(e1z, e2y)),
+            pair_sub_round(pair_mul(e1z, e2x), pair_mul(e1x, e2z)),
+            pair_sub_round(pair_mul(e1x, e2y), pair_mul(e1y, e2x))};
+}
+
+// Squared length of b - a from exact float pairs.
+__device__ __forceinline__ float exact_len2(const SP& a, const SP& b) {
+    return pair_sq_round(pair_diff(a.x, a.dx, b.x, b.dx)) + pair_sq_round(pair_diff(a.y, a.dy, b.y, b.dy)) +
+           pair_sq_round(pair_diff(a.z, a.dz, b.z, b.dz));
+}
+
+__device__ __forceinline__ V3 centroid3(const SP& a, const SP& b, const SP& c) {
+    const float k = 1.f / 3.f;
+    return {((a.x + b.x + c.x) + (a.dx + b.dx + c.dx)) * k, ((a.y + b.y + c.y) + (a.dy + b.dy + c.dy)) * k,
+            ((a.z + b.z + c.z) + (a.dz + b.dz + c.dz)) * k};
 }
 
 template <int R, bool FIRST, bool LAST>
@@ -50,8 +84,8 @@ __global__ void __launch_bounds__(kBilThreads) bilateral_kernel(BilArgs a) {
     const int pplane = (RQH + 1) * PW;
     const int nq = RQH * RQW;
     const int nt = 2 * nq;                     // staged triangles, index 2 q + k
-    float* P = smem;                           // [3][RQH+1][RQW+1]
-    float* Cs = P + 3 * pplane;                // [3][nt]
+    float* P = smem;                           // [6][RQH+1][RQW+1]: v0 x, y, z, d x, y, z
+    float* Cs = P + 6 * pplane;                // [3][nt]
     float* N0 = Cs + 3 * nt;                   // [3][nt]
     float* N1 = N0 + 3 * nt;                   // [3][nt]
     const int H = a.H, W = a.W, Hq = H - 1, Wq = W - 1;
@@ -61,16 +95,23 @@ __global__ void __launch_bounds__(kBilThreads) bilateral_kernel(BilArgs a) {
     for (int i = threadIdx.x; i < pplane; i += blockDim.x) {
         const int r = i / PW, c = i - r * PW;
         const int gu = qu0 + r, gv = qv0 + c;
-        float x = NAN, y = NAN, z = NAN;
+        float x = NAN, y = NAN, z = NAN, dx = 0.f, dy = 0.f, dz = 0.f;
         if (gu >= 0 && gu < H && gv >= 0 && gv < W) {
             const size_t p = (size_t)gu * W + gv;
-            x = __ldg(a.px + p);
-            y = __ldg(a.py + p);
-            z = __ldg(a.pz + p);
+            x = __ldg(a.points + 3 * p);
+            y = __ldg(a.points + 3 * p + 1);
+            z = __ldg(a.points + 3 * p + 2);
+            if (!(isfinite(x) && isfinite(y) && isfinite(z))) x = y = z = NAN;
+            dx = __ldg(a.dx + p);
+            dy = __ldg(a.dy + p);
+            dz = __ldg(a.dz + p);
         }
         P[i] = x;
         P[pplane + i] = y;
         P[2 * pplane + i] = z;
+        P[3 * pplane + i] = dx;
+        P[4 * pplane + i] = dy;
+        P[5 * pplane + i] = dz;
     }
     __syncthreads();
 
@@ -80,21 +121,19 @@ __global__ void __launch_bounds__(kBilThreads) bilateral_kernel(BilArgs a) {
         const int gu = qu0 + qr, gv = qv0 + qc;
         const bool exists = gu >= 0 && gu < Hq && gv >= 0 && gv < Wq;
         const int i1 = qr * PW + qc, i2 = i1 + 1, i3 = i1 + PW + 1, i4 = i1 + PW;
-        const V3 p1 = {P[i1], P[pplane + i1], P[2 * pplane + i1]};
-        const V3 p2 = {P[i2], P[pplane + i2], P[2 * pplane + i2]};
-        const V3 p3 = {P[i3], P[pplane + i3], P[2 * pplane + i3]};
-        const V3 p4 = {P[i4], P[pplane + i4], P[2 * pplane + i4]};
+        const SP p1 = load_sp(P, pplane, i1), p2 = load_sp(P, pplane, i2);
+        const SP p3 = load_sp(P, pplane, i3), p4 = load_sp(P, pplane, i4);
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
-            const V3 va = k == 0 ? p3 : p1;
-            const V3 vb = k == 0 ? p2 : p4;
-            const V3 vc = k == 0 ? p1 : p3;
+            const SP& va = k == 0 ? p3 : p1;
+            const SP& vb = k == 0 ? p2 : p4;
+            const SP& vc = k == 0 ? p1 : p3;
             V3 n = {0.f, 0.f, 0.f};
             V3 c = {kAbsentCentroid, kAbsentCentroid, kAbsentCentroid};
             bool has_normal = false;
             if (exists && va.x == va.x && vb.x == vb.x && vc.x == vc.x) {
                 if (FIRST) {
-                    const V3 cr = cross(sub(vb, va), sub(vc, va));
+                    const V3 cr = exact_cross(va, vb, vc);
                     const float len2 = dot(cr, cr);
                     if (len2 > kDegenerateLen2) {
                         const float inv = rsqrtf(len2);
@@ -109,10 +148,7 @@ __global__ void __launch_bounds__(kBilThreads) bilateral_kernel(BilArgs a) {
                         has_normal = true;
                     }
                 }
-                if (has_normal) {
-                    c = {(va.x + vb.x + vc.x) * (1.f / 3.f), (va.y + vb.y + vc.y) * (1.f / 3.f),
-                         (va.z + vb.z + vc.z) * (1.f / 3.f)};
-                }
+                if (has_normal) c = centroid3(va, vb, vc);
             }
             const int t = 2 * q + k;
             Cs[t] = c.x;
@@ -210,18 +246,15 @@ __global__ void __launch_bounds__(kBilThreads) bilateral_kernel(BilArgs a) {
             continue;
         }
         const int i1 = qr * PW + qc, i2 = i1 + 1, i3 = i1 + PW + 1, i4 = i1 + PW;
-        const V3 p1 = {P[i1], P[pplane + i1], P[2 * pplane + i1]};
-        const V3 p2 = {P[i2], P[pplane + i2], P[2 * pplane + i2]};
-        const V3 p3 = {P[i3], P[pplane + i3], P[2 * pplane + i3]};
-        const V3 p4 = {P[i4], P[pplane + i4], P[2 * pplane + i4]};
+        const SP p1 = load_sp(P, pplane, i1), p2 = load_sp(P, pplane, i2);
+        const SP p3 = load_sp(P, pplane, i3), p4 = load_sp(P, pplane, i4);
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
-            const V3 va = k == 0 ? p3 : p1;
-            const V3 vb = k == 0 ? p2 : p4;
-            const V3 vc = k == 0 ? p1 : p3;
+            const SP& va = k == 0 ? p3 : p1;
+            const SP& vb = k == 0 ? p2 : p4;
+            const SP& vc = k == 0 ? p1 : p3;
             const bool valid = va.x == va.x && vb.x == vb.x && vc.x == vc.x;   // Algorithm 1
-            const V3 e0 = sub(vb, va), e1 = sub(vc, vb), e2 = sub(va, vc);
-            const float longest2 = fmaxf(dot(e0, e0), fmaxf(dot(e1, e1), dot(e2, e2)));
+            const float longest2 = fmaxf(exact_len2(va, vb), fmaxf(exact_len2(vb, vc), exact_len2(vc, va)));
             const bool kept = valid && longest2 <= a.max_edge2;                // Algorithm 4, l_max
             const int t = 2 * q + k;
             const V3 n = {cur[t], cur[nt + t], cur[2 * nt + t]};
@@ -287,7 +320,7 @@ cudaError_t configure_r() {
 size_t bilateral_smem_bytes(int radius, int iters) {
     const size_t halo = (size_t)iters * radius;
     const size_t rqh = kBilTileH + 2 * halo, rqw = kBilTileW + 2 * halo;
-    const size_t points = 3 * (rqh + 1) * (rqw + 1);
+    const size_t points = 6 * (rqh + 1) * (rqw + 1);
     const size_t tris = 2 * rqh * rqw;
     return (points + 3 * 3 * tris) * sizeof(float);
 }

@@ -46,14 +46,17 @@ __device__ __forceinline__ void unite(int32_t* L, int a, int b) {
     }
 }
 
-// Centroid of triangle k of quad (u, v) from the smoothed points (offset test only).
+// Centroid of triangle k of quad (u, v) from the smoothed points v0 + d (offset test only).
 __device__ __forceinline__ void centroid(const LabelArgs& a, int u, int v, int k, float c[3]) {
     const int W = a.W;
     const size_t p1 = (size_t)u * W + v, p2 = p1 + 1, p3 = p1 + W + 1, p4 = p1 + W;
     const size_t ia = k == 0 ? p3 : p1, ib = k == 0 ? p2 : p4, ic = k == 0 ? p1 : p3;
-    c[0] = (a.px[ia] + a.px[ib] + a.px[ic]) * (1.f / 3.f);
-    c[1] = (a.py[ia] + a.py[ib] + a.py[ic]) * (1.f / 3.f);
-    c[2] = (a.pz[ia] + a.pz[ib] + a.pz[ic]) * (1.f / 3.f);
+    const float* P = a.points;
+    const float* D[3] = {a.dx, a.dy, a.dz};
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        c[m] = ((P[3 * ia + m] + P[3 * ib + m] + P[3 * ic + m]) + (D[m][ia] + D[m][ib] + D[m][ic])) * (1.f / 3.f);
+    }
 }
 
 __device__ __forceinline__ bool offset_ok(const LabelArgs& a, int g, const float ci[3], int uj, int vj, int kj) {

@@ -3,7 +3,7 @@
 // host-buffer entry point.
 //
 // Launch sequence of one frame (all on the caller's stream):
-//   lap_smooth_kernel   x ceil(lap_iters / fused)   Eq. 1-2          points -> SoA smoothed
+//   lap_smooth_kernel   x ceil(lap_iters / fused)   Eq. 1-2          points -> SoA displacements
 //   bilateral_kernel    x ceil(bil_iters / fused)   Eq. 3-6, Alg. 1/4 -> mask, normals, groups,
 //                                                                       union-find parents
 //   label_union_kernel                              Alg. 5 / Alg. 2   unions over twin edges
@@ -176,7 +176,7 @@ int run(pl3d_ctx* ctx, const float* points, int H, int W, const pl3d_params* p, 
     for (int b = 0; b < 2; ++b)
         for (int k = 0; k < 3; ++k) buf[b][k] = ctx->points + (size_t)(3 * b + k) * ctx->cap_points;
 
-    // ---- Laplacian (Eq. 1-2)
+    // ---- Laplacian (Eq. 1-2): displacements d with smoothed = points + d
     const int lr = p->lap_iters > 0 ? p->lap_kernel / 2 : 1;
     const int lfuse = kLapMaxHalo / lr;
     int remaining = p->lap_iters;
@@ -185,14 +185,14 @@ int run(pl3d_ctx* ctx, const float* points, int H, int W, const pl3d_params* p, 
     do {
         const int it = remaining < lfuse ? remaining : lfuse;
         LapArgs la{};
-        la.in_aos = first ? points : nullptr;
-        la.in_x = buf[cur][0];
-        la.in_y = buf[cur][1];
-        la.in_z = buf[cur][2];
+        la.points = points;
+        la.in_dx = first ? nullptr : buf[cur][0];
+        la.in_dy = first ? nullptr : buf[cur][1];
+        la.in_dz = first ? nullptr : buf[cur][2];
         const int nb = first ? cur : 1 - cur;
-        la.out_x = buf[nb][0];
-        la.out_y = buf[nb][1];
-        la.out_z = buf[nb][2];
+        la.out_dx = buf[nb][0];
+        la.out_dy = buf[nb][1];
+        la.out_dz = buf[nb][2];
         la.H = H;
         la.W = W;
         la.iters = it;
@@ -203,9 +203,9 @@ int run(pl3d_ctx* ctx, const float* points, int H, int W, const pl3d_params* p, 
         cur = nb;
         first = false;
     } while (remaining > 0);
-    const float* px = buf[cur][0];
-    const float* py = buf[cur][1];
-    const float* pz = buf[cur][2];
+    const float* dx = buf[cur][0];
+    const float* dy = buf[cur][1];
+    const float* dz = buf[cur][2];
 
     // ---- normals, bilateral (Eq. 3-6), mask and groups (Algorithms 1, 4)
     uint8_t* groups = out_groups ? out_groups : ctx->groups;
@@ -224,9 +224,10 @@ int run(pl3d_ctx* ctx, const float* points, int H, int W, const pl3d_params* p, 
         const int it = bremaining < bfuse ? bremaining : bfuse;
         bremaining -= it;
         BilArgs ba;
-        ba.px = px;
-        ba.py = py;
-        ba.pz = pz;
+        ba.points = points;
+        ba.dx = dx;
+        ba.dy = dy;
+        ba.dz = dz;
         ba.carry_in = c > 0 ? ctx->carry + (size_t)((c - 1) % 2) * 3 * ctx->cap_carry : nullptr;
         ba.carry_out = c + 1 < nchunks ? ctx->carry + (size_t)(c % 2) * 3 * ctx->cap_carry : nullptr;
         ba.out_mask = out_mask;
@@ -251,9 +252,10 @@ int run(pl3d_ctx* ctx, const float* points, int H, int W, const pl3d_params* p, 
     lb.groups = groups;
     lb.labels = out_labels;
     lb.sizes = p->min_triangles > 0 ? ctx->sizes : nullptr;
-    lb.px = px;
-    lb.py = py;
-    lb.pz = pz;
+    lb.points = points;
+    lb.dx = dx;
+    lb.dy = dy;
+    lb.dz = dz;
     lb.H = H;
     lb.W = W;
     lb.max_offset = p->max_offset;

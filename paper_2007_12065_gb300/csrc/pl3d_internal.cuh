@@ -2,7 +2,9 @@
 //
 // Data layout in device memory (one frame of H x W points, Q = (H-1)(W-1) quads):
 //   input points     AoS  float [H][W][3]            (caller's buffer)
-//   smoothed points  SoA  float x[H*W], y[H*W], z[H*W] (context scratch, ping-pong pair)
+//   displacements    SoA  float dx[H*W], dy[H*W], dz[H*W] (context scratch, ping-pong pair):
+//                    a smoothed point is the input point plus its displacement, kept as
+//                    that pair of floats (see df32.cuh)
 //   bilateral carry  AoS  float [2Q][3]               (context scratch, only when the
 //                                                      bilateral iterations need more than
 //                                                      one launch)
@@ -37,14 +39,14 @@ struct Dominant {
 
 // ---------------------------------------------------------------- Laplacian (Eq. 1-2)
 struct LapArgs {
-    const float* in_aos;                      // AoS input, or nullptr to read in_x/y/z
-    const float* in_x;
-    const float* in_y;
-    const float* in_z;
-    float* out_x;                             // SoA output
-    float* out_y;
-    float* out_z;
-    float* out_aos;                           // optional AoS export of the result
+    const float* points;                      // AoS input points (the v0 of every launch)
+    const float* in_dx;                       // displacement after the previous launch, or
+    const float* in_dy;                       // nullptr for the first launch (zero)
+    const float* in_dz;
+    float* out_dx;                            // displacement after this launch, SoA
+    float* out_dy;
+    float* out_dz;
+    float* out_aos;                           // optional AoS export of v0 + d (rounded)
     int H, W;
     int iters;                                // iterations fused in this launch (>= 0)
     float lambda;
@@ -62,9 +64,10 @@ size_t laplacian_smem_bytes(int radius, int iters);
 
 // ----------------------------------------- normals + bilateral (Eq. 3-6) + Algorithm 4
 struct BilArgs {
-    const float* px;                          // smoothed points, SoA
-    const float* py;
-    const float* pz;
+    const float* points;                      // AoS input points v0
+    const float* dx;                          // displacements, SoA (smoothed = v0 + d)
+    const float* dy;
+    const float* dz;
     const float* carry_in;                    // AoS [2Q][3] normals from the previous launch (non-first)
     float* carry_out;                         // AoS [2Q][3] normals for the next launch (non-last)
     uint8_t* out_mask;                        // last launch only
@@ -92,9 +95,10 @@ struct LabelArgs {
     const uint8_t* groups;
     int32_t* labels;                          // parent array in, labels out
     int32_t* sizes;                           // segment sizes (tri_min > 0) or nullptr
-    const float* px;                          // smoothed points, SoA (offset test only)
-    const float* py;
-    const float* pz;
+    const float* points;                      // AoS input points and SoA displacements
+    const float* dx;                          // (offset test only)
+    const float* dy;
+    const float* dz;
     int H, W;
     float max_offset;                         // <= 0: no offset test
     int min_triangles;

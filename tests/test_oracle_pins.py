@@ -516,3 +516,41 @@ def test_noise_free_scene_maps_to_ground_truth(scene):
     lab = r["labels"]
     for l in np.unique(lab[lab >= 0]):
         assert len(np.unique(r["groups"][lab == l])) == 1
+
+
+# ----------------------------------------------------------------------------- sensitivity instrumentation
+
+
+def test_jitter_off_is_the_plain_filter():
+    rng = np.random.default_rng(20)
+    P = oracle.widen(rng.normal(0, 1, (9, 11, 3)).astype(np.float32))
+    assert np.array_equal(oracle.laplacian(P, 3, 0.8, 3), oracle.laplacian(P, 3, 0.8, 3, eps=0.0, seed=99))
+    C, N = oracle.triangle_geometry(P)
+    assert np.array_equal(oracle.bilateral(C, N, 9, 11, 3, 0.5, 0.3, 2),
+                          oracle.bilateral(C, N, 9, 11, 3, 0.5, 0.3, 2, eps=0.0, seed=5))
+
+
+def test_jitter_moves_a_well_conditioned_frame_by_order_eps():
+    """Every update scaled by (1 +- eps): on a smooth noisy plane the outputs move by O(eps) and the
+    signs depend on the seed."""
+    rng = np.random.default_rng(21)
+    P, _ = plane_grid(24, 30, normal=(0.2, -0.3, -1.0), dist=-2.0)
+    P = P + rng.normal(0, 0.002, P.shape).astype(np.float32)
+    W_ = oracle.widen(P)
+    eps = 2.0 ** -21
+    S = oracle.laplacian(W_, 3, 1.0, 4)
+    S1 = oracle.laplacian(W_, 3, 1.0, 4, eps, 1)
+    S2 = oracle.laplacian(W_, 3, 1.0, 4, eps, 2)
+    d1 = np.abs(S1 - S).max()
+    assert 0 < d1 < 100 * eps * np.abs(S - W_).max()
+    assert not np.array_equal(S1, S2)
+    C, N = oracle.triangle_geometry(S)
+    Nb = oracle.bilateral(C, N, 24, 30, 3, 0.1, 0.15, 3)
+    Nj = oracle.bilateral(C, N, 24, 30, 3, 0.1, 0.15, 3, eps, 3)
+    assert 0 < np.abs(Nj - Nb).max() < 100 * eps
+
+
+def test_ill_conditioned_flags_are_rare_on_the_frame_workloads():
+    for f in (synth.rgbd_120x160(), synth.lidar_64x1024()):
+        r = oracle.extract_planes(f.points, oracle.OracleParams(**f.params), f.dominant_normals)
+        assert r["ill_conditioned"].sum() <= 1e-4 * r["mask"].size

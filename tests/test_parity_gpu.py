@@ -132,26 +132,35 @@ def test_parameter_variants(env, kw):
     run_pair(env, f.points, dict(f.params, **kw), f.dominant_normals)
 
 
-def test_offset_test(env):
-    f = synth.depth_camera_scene(60, 80, seed=12, n_boxes=3, noise_sigma=0.002, nan_frac=0.0)
-    prm = dict(f.params, max_offset=0.004)
-    dev, ref, _ = run_pair(env, f.points, prm, f.dominant_normals, check=False)
-    # near-threshold pair decisions would need substitution; this seed must have none
-    C, nd = ref["centroids"], ref["nd_unit"]
-    G = ref["groups"]
-    Wq = f.W - 1
+def _near_offset_pairs(ref, W, max_offset):
+    """Adjacent same-group pairs whose FP64 plane offset lies within oracle.NEAR of max_offset."""
+    C, nd, G = ref["centroids"], ref["nd_unit"], ref["groups"]
+    Wq = W - 1
     near = 0
     for i in range(0, G.shape[0], 2):
         if G[i] == 255:
             continue
-        q = i // 2
-        u, v = divmod(q, Wq)
+        u, v = divmod(i // 2, Wq)
         for j in [i + 1] + ([i + 3] if v + 1 < Wq else []) + ([i - 2 * Wq + 1] if u >= 1 else []):
             if G[j] == G[i]:
-                off = abs(nd[G[i]] @ (C[i] - C[j]))
-                near += abs(off - 0.004) < oracle.NEAR
-    assert near == 0
-    compare(dev, ref, oracle.OracleParams(**prm), f.H, f.W)
+                near += abs(abs(nd[G[i]] @ (C[i] - C[j])) - max_offset) < oracle.NEAR
+    return near
+
+
+def test_offset_test(env):
+    """Pairwise plane-offset join test. The threshold is chosen, from the oracle alone, so that no
+    adjacent pair sits within 1e-5 of it (those decisions may legitimately differ in FP32)."""
+    f = synth.depth_camera_scene(60, 80, seed=12, n_boxes=3, noise_sigma=0.002, nan_frac=0.0)
+    for max_offset in (0.004, 0.0043, 0.0047, 0.0051, 0.0055, 0.006):
+        prm = dict(f.params, max_offset=max_offset)
+        ref = oracle.extract_planes(f.points, oracle.OracleParams(**prm), f.dominant_normals)
+        if _near_offset_pairs(ref, f.W, max_offset) == 0:
+            break
+    else:
+        pytest.fail("no offset threshold without near pairs")
+    dev, ref, rep = run_pair(env, f.points, prm, f.dominant_normals)
+    base = oracle.extract_planes(f.points, oracle.OracleParams(**f.params), f.dominant_normals)
+    assert rep["segments"] > len(np.unique(base["labels"][base["labels"] >= 0]))   # the test cuts segments
 
 
 @pytest.mark.parametrize("K", [1, 2, 254])
