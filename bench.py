@@ -165,6 +165,29 @@ def dist_env():
     return world, rank, local
 
 
+def rank_frame(workload: str, rank: int):
+    """Rank 0 runs the named workload's own seed; other ranks run the same scene recipe with
+    their own seed (frames are independent units: weak scaling, no data exchange)."""
+    base = synth.WORKLOADS[workload]
+    return base() if rank == 0 else base(seed=1000 + rank)
+
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The slowest rank's time: the job finishes when its last rank does."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_mtri_s(triangles_per_rank: int, world: int, ms_per_step_max: float) -> float:
+    """Whole-job throughput: every rank's triangles over the slowest rank's step time."""
+    return triangles_per_rank * world / (ms_per_step_max / 1e3) / 1e6
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -208,8 +231,7 @@ def run_pl3d(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    base = synth.WORKLOADS[args.workload]
-    frame = base() if rank == 0 else base(seed=1000 + rank)
+    frame = rank_frame(args.workload, rank)
     H, W, ntri = frame.H, frame.W, frame.n_triangles
     params = pl3d.make_params(**frame.params)
     nd = frame.dominant_normals
@@ -264,13 +286,8 @@ def run_pl3d(args):
     launches = pl3d.pl3d_launch_count(ctx) - n0
     per_kernel = pl3d.pl3d_read_timing(ctx, reset=True)
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    ms = sum(step_ms) / len(step_ms)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ntri * world / (ms / 1e3) / 1e6
+    ms = max_over_ranks(sum(step_ms) / len(step_ms), world, dev)
+    value = aggregate_mtri_s(ntri, world, ms)
 
     # ---------------- end to end through the host-buffer entry point
     h_pts = torch.from_numpy(frame.points).pin_memory()
@@ -289,12 +306,7 @@ def run_pl3d(args):
         t_a = time.perf_counter()
         pl3d.pl3d_extract_planes_host(ctx, h_pts, H, W, params, nd, K, h_mask, h_normals, h_labels, stream)
         e2e_s.append(time.perf_counter() - t_a)
-    e2e_ms = 1e3 * sum(e2e_s) / len(e2e_s)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(1e3 * sum(e2e_s) / len(e2e_s), world, dev)
     sampler.stop()
     clocks = sampler.summary(t0, t1)
 
@@ -347,7 +359,7 @@ def run_pl3d(args):
                    "l2": f"flushed before every timed step ({L2_FLUSH_BYTES >> 20} MB write, outside the step events)",
                    "parallelism": f"replicas x{world}"},
         "clocks": clocks,
-        "e2e": {"value": ntri * world / (e2e_ms / 1e3) / 1e6, "unit": "Mtri/s", "ms_per_step": e2e_ms,
+        "e2e": {"value": aggregate_mtri_s(ntri, world, e2e_ms), "unit": "Mtri/s", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": int(h_pts.numel() * 4),
                 "d2h_bytes_per_step": int(h_mask.numel() + h_normals.numel() * 4 + h_labels.numel() * 4)},
         "gpu_launches": int(launches),

@@ -1,0 +1,52 @@
+"""The pins catch plausible mistakes: each case plants one slip in a temporary copy of the oracle's C
+source (on the CPU) and requires the pin suite to fail against it."""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+MUTATIONS = {
+    "laplacian_sign": ("vo[0] = vi[0] + j0 * (lambda * sx / wsum);", "vo[0] = vi[0] - j0 * (lambda * sx / wsum);"),
+    "laplacian_weight": ("double w = 1.0 / d; /* Eq. 2 */", "double w = 1.0 / (d * d);"),
+    "laplacian_border": ("int border = (u < r) || (u >= H - r) || (v < r) || (v >= W - r);",
+                         "int border = (u < r) || (u >= H - r) || (v < r);"),
+    "bilateral_excludes_self": ("if (isnan(nj[0]) || isnan(cj[0])) continue;",
+                                "if (isnan(nj[0]) || isnan(cj[0]) || j == i) continue;"),
+    "bilateral_one_triangle_per_quad": ("for (int kk = 0; kk < 2; ++kk) {", "for (int kk = 0; kk < 1; ++kk) {"),
+    "bilateral_sigma_squared": ("const double two_sc2 = 2.0 * sigma_c * sigma_c;",
+                                "const double two_sc2 = sigma_c * sigma_c;"),
+    "bilateral_no_normal_term": ("double w = wc * ws;", "double w = wc;"),
+    "bilateral_no_renormalisation": ("no[0] = sx / len;", "no[0] = sx;"),
+    "vertex_order": ("        idx[0] = p3;\n        idx[1] = p2;", "        idx[0] = p2;\n        idx[1] = p3;"),
+    "centroid": ("cc[2] = (a[2] + b[2] + c[2]) / 3.0;", "cc[2] = (a[2] + b[2]) / 2.0;"),
+    "classify_last_wins_ties": ("if (s > max_similarity) {", "if (s >= max_similarity) {"),
+    "classify_rejects_equal": ("if (max_similarity < ang_min) g = 255;", "if (max_similarity <= ang_min) g = 255;"),
+    "mask_rejects_equal": ("mask[gid] = (l_max <= 0.0 || !(longest > l_max)) ? 1 : 0;",
+                           "mask[gid] = (l_max <= 0.0 || longest < l_max) ? 1 : 0;"),
+    "twin_top_wrong_triangle": ("if (u - 1 >= 0) out[n++] = 2 * ((int64_t)(u - 1) * Wq + v) + 1;",
+                                "if (u - 1 >= 0) out[n++] = 2 * ((int64_t)(u - 1) * Wq + v);"),
+    "twin_right_wrong_triangle": ("if (v + 1 < Wq) out[n++] = 2 * ((int64_t)u * Wq + v + 1) + 1;",
+                                  "if (v + 1 < Wq) out[n++] = 2 * ((int64_t)u * Wq + v + 1);"),
+    "tri_min_not_strict": ("if (tri_min > 0 && tail <= (int64_t)tri_min) {",
+                           "if (tri_min > 0 && tail < (int64_t)tri_min) {"),
+    "halfedge_top_wrong_edge": ("if (top != -1) HE[3 * (int64_t)first + 1] = 3 * top + 1;",
+                                "if (top != -1) HE[3 * (int64_t)first + 1] = 3 * top;"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_fails_a_pin(name, tmp_path):
+    old, new = MUTATIONS[name]
+    src = open(os.path.join(ROOT, "oracle", "pl3d_oracle.c")).read()
+    assert src.count(old) == 1, f"mutation anchor for {name} not found exactly once"
+    for d in ("oracle", "synth", "tests"):
+        shutil.copytree(os.path.join(ROOT, d), tmp_path / d, ignore=shutil.ignore_patterns("*.so", "__pycache__"))
+    shutil.copy(os.path.join(ROOT, "pytest.ini"), tmp_path / "pytest.ini")
+    (tmp_path / "oracle" / "pl3d_oracle.c").write_text(src.replace(old, new))
+    r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_pins.py", "-q", "-x", "-p", "no:cacheprovider"],
+                       cwd=tmp_path, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 1 and "failed" in r.stdout, r.stdout[-2000:]
