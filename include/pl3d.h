@@ -166,6 +166,31 @@ const char* pl3d_timing_slot_name(int slot);
 /* Number of kernels this context has launched since it was created. */
 int64_t pl3d_launch_count(const pl3d_ctx* ctx);
 
+/*
+ * Allocation-free entry point. The paper has no counterpart: this serves callers that cannot
+ * allocate device memory while they run -- a real-time sensor loop that must avoid the
+ * device-wide synchronisation cudaMalloc/cudaFree can cause, a process whose memory budget
+ * was fixed at start-up, or a plugin that receives a stream and buffers per call and keeps
+ * no context. Same arguments, results and errors as pl3d_extract_planes, without a context:
+ * the scratch comes from one fixed device array inside the library, which every GPU that
+ * loads the library's kernels holds (pl3d_static_scratch_bytes(), about 10.4 MB) until the
+ * process exits.
+ *   - Frames are limited to H*W <= PL3D_STATIC_MAX_POINTS points (640 x 480) and to
+ *     bil_iters <= 6 / (bil_kernel / 2); larger requests return PL3D_ERR_INVALID_ARG before
+ *     anything is enqueued.
+ *   - It never calls cudaMalloc, cudaFree or any allocating routine.
+ *   - The first call on a device (the current device) looks up the array's device address
+ *     and configures the kernels; make that first call before any stream capture.
+ *   - Every call uses the same array: calls whose work overlaps on the GPU race and must be
+ *     serialised by the caller. Nothing needs clearing between calls.
+ */
+#define PL3D_STATIC_MAX_POINTS 307200
+int pl3d_extract_planes_static(const float* points, int H, int W, const pl3d_params* params,
+                               const float* dominant_normals, int K, uint8_t* out_tri_mask, float* out_normals,
+                               int32_t* out_labels, void* stream);
+/* Bytes of device memory the allocation-free entry point reserves on every GPU. */
+size_t pl3d_static_scratch_bytes(void);
+
 /* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
 int pl3d_version(void);
 

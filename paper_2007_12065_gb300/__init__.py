@@ -89,6 +89,8 @@ def lib():
     L.pl3d_read_timing.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int]
     L.pl3d_launch_count.argtypes = [_vp]
     L.pl3d_launch_count.restype = ctypes.c_int64
+    L.pl3d_extract_planes_static.argtypes = [_vp, ctypes.c_int, ctypes.c_int, P, _vp, ctypes.c_int, _vp, _vp, _vp, _vp]
+    L.pl3d_static_scratch_bytes.restype = ctypes.c_size_t
     _lib = L
     return L
 
@@ -231,6 +233,28 @@ def pl3d_extract_planes_host(ctx, points, H, W, params, dominant_normals, K, out
     return _check(lib().pl3d_extract_planes_host(ctx, _ptr(points), int(H), int(W), ctypes.byref(params), _ptr(nd),
                                                  int(K), _ptr(out_tri_mask), _ptr(out_normals), _ptr(out_labels),
                                                  _stream(stream)), "pl3d_extract_planes_host")
+
+
+def pl3d_extract_planes_static(points, H, W, params, dominant_normals, K, out_tri_mask, out_normals, out_labels,
+                               stream=None) -> int:
+    """Allocation-free variant (no context; scratch in a fixed device array, frames up to
+    PL3D_STATIC_MAX_POINTS points); see include/pl3d.h."""
+    n_tri = 2 * (H - 1) * (W - 1)
+    _check_tensor(points, "points", "torch.float32", H * W * 3)
+    _check_tensor(out_tri_mask, "out_tri_mask", "torch.uint8", n_tri)
+    _check_tensor(out_normals, "out_normals", "torch.float32", n_tri * 3)
+    _check_tensor(out_labels, "out_labels", "torch.int32", n_tri)
+    nd = _nd_host(dominant_normals)
+    return _check(lib().pl3d_extract_planes_static(_ptr(points), int(H), int(W), ctypes.byref(params), _ptr(nd),
+                                                   int(K), _ptr(out_tri_mask), _ptr(out_normals), _ptr(out_labels),
+                                                   _stream(stream)), "pl3d_extract_planes_static")
+
+
+def pl3d_static_scratch_bytes() -> int:
+    return int(lib().pl3d_static_scratch_bytes())
+
+
+PL3D_STATIC_MAX_POINTS = 307200
 
 
 def pl3d_sync(ctx, stream=None) -> int:
