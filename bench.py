@@ -121,7 +121,7 @@ def algorithmic(kernel: str, H: int, W: int, prm: dict, launches_per_step: int) 
         k = prm["bil_kernel"]
         iters_per_launch = prm["bil_iters"] / max(launches_per_step, 1)
         return "alu", 20.0 * 2 * k * k * ntri * iters_per_launch, "FLOP"
-    if kernel == "label_union":
+    if kernel == "label_merge":
         return "hbm", 5.0 * ntri, "B"
     if kernel == "label_flatten":
         return "hbm", 8.0 * ntri, "B"

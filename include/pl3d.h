@@ -13,7 +13,8 @@
  *
  * Mesh conventions (Section 4.2, Algorithm 1). The cloud is an H x W grid (the paper's
  * M x N) of FP32 xyz points, row-major, 12 bytes per point; a point with any non-finite
- * coordinate is invalid. Quad (u, v), 0 <= u < H-1, 0 <= v < W-1, has the points
+ * coordinate is invalid. Coordinates must stay below 1e18 in magnitude (squared distances
+ * are formed in FP32); a point beyond that is treated as invalid too. Quad (u, v), 0 <= u < H-1, 0 <= v < W-1, has the points
  * p1 = (u, v), p2 = (u, v+1), p3 = (u+1, v+1), p4 = (u+1, v) and two triangles,
  * first = {p3, p2, p1} (k = 0) and second = {p1, p4, p3} (k = 1). Every per-triangle array
  * has 2 (H-1)(W-1) entries indexed by GID = 2 (u (W-1) + v) + k. Normals follow the

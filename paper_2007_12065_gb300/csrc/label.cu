@@ -1,50 +1,26 @@
-// label.cu -- planar segments: connected components of equal group over twin edges
-// (Algorithm 5, with the twins of Algorithm 2).
+// label.cu -- planar segments across tile borders: connected components of equal group over
+// twin edges (Algorithm 5, with the twins of Algorithm 2).
 //
 // Two triangles are joined when they share an edge, both have the same group g != 255 and,
 // if max_offset > 0, |n^d_g . (c_i - c_j)| <= max_offset. In T_FC the twins of the first
 // triangle of quad (u, v) are the second triangles of quads (u, v), (u, v+1) and (u-1, v);
-// every edge is therefore visited once, from the first triangle that owns it.
+// every edge is visited once, from the first triangle that owns it.
 //
-// Components come from a lock-free union-find over the label array (the caller's output
-// buffer, initialised by the bilateral kernel to GID for grouped triangles and -1
-// otherwise). A root is only ever linked below a smaller root (compare-and-swap on the
-// larger root), so every component ends with its smallest GID as root -- the label the
-// result defines -- whatever order the unions run in. Finding a root halves the path as it
-// walks (each visited node is pointed at its grandparent, an ancestor, so concurrent walks
-// stay valid).
+// The bilateral kernel has already joined every edge inside its tile and left each grouped
+// triangle pointing at the GID of its tile-local root (the smallest GID of its tile-local
+// component). What remains is:
+//   label_merge_kernel    the edges that cross a tile border: the top edge of a tile's first
+//                         quad row and the right edge of its last quad column. Union-find
+//                         with min-index roots (uf.cuh), so labels are component minima
+//                         whatever the order.
+//   label_flatten_kernel  every grouped triangle takes its root; with tri_min > 0 it also
+//                         counts segment sizes, one atomic per run of equal roots in a warp.
+//   label_filter_kernel   (tri_min > 0) drops segments with at most tri_min triangles.
 #include "pl3d_internal.cuh"
+#include "uf.cuh"
 
 namespace pl3d {
 namespace {
-
-__device__ __forceinline__ int find_root_halving(int32_t* L, int x) {
-    volatile int32_t* vl = L;
-    while (true) {
-        const int p = vl[x];
-        if (p == x) return x;
-        const int gp = vl[p];
-        if (gp == p) return p;
-        vl[x] = gp;
-        x = gp;
-    }
-}
-
-__device__ __forceinline__ void unite(int32_t* L, int a, int b) {
-    while (true) {
-        a = find_root_halving(L, a);
-        b = find_root_halving(L, b);
-        if (a == b) return;
-        if (a > b) {
-            const int t = a;
-            a = b;
-            b = t;
-        }
-        const int old = atomicCAS(L + b, b, a);
-        if (old == b) return;
-        b = old;    // b stopped being a root meanwhile; continue from its new parent
-    }
-}
 
 // Centroid of triangle k of quad (u, v) from the smoothed points v0 + d (offset test only).
 __device__ __forceinline__ void centroid(const LabelArgs& a, int u, int v, int k, float c[3]) {
@@ -59,61 +35,65 @@ __device__ __forceinline__ void centroid(const LabelArgs& a, int u, int v, int k
     }
 }
 
-__device__ __forceinline__ bool offset_ok(const LabelArgs& a, int g, const float ci[3], int uj, int vj, int kj) {
-    float cj[3];
-    centroid(a, uj, vj, kj, cj);
+__device__ __forceinline__ bool offset_ok(const LabelArgs& a, int g, int u, int v, int uj, int vj) {
+    if (!(a.max_offset > 0.f)) return true;
+    float ci[3], cj[3];
+    centroid(a, u, v, 0, ci);
+    centroid(a, uj, vj, 1, cj);
     const float* n = a.nd.v + 3 * g;
     const float off = n[0] * (ci[0] - cj[0]) + n[1] * (ci[1] - cj[1]) + n[2] * (ci[2] - cj[2]);
     return fabsf(off) <= a.max_offset;
 }
 
-__global__ void label_union_kernel(LabelArgs a) {
+// Work items: (rows - 1) tile-row borders x Wq quads, then (cols - 1) tile-column borders x Hq.
+__global__ void label_merge_kernel(LabelArgs a) {
     const int Wq = a.W - 1, Hq = a.H - 1;
-    const long long nq = (long long)Hq * Wq;
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nq;
-         q += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(2 * q);
-        if (a.sizes) {
-            a.sizes[i] = 0;
-            a.sizes[i + 1] = 0;
+    const int rb = div_up(Hq, a.tile_h) - 1;
+    const int cb = div_up(Wq, a.tile_w) - 1;
+    const long long n_row_items = (long long)rb * Wq;
+    const long long n = n_row_items + (long long)cb * Hq;
+    for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < n; w += (long long)gridDim.x * blockDim.x) {
+        int u, v, uj, vj;
+        if (w < n_row_items) {           // top edge of the first quad row of a tile
+            u = (int)(w / Wq + 1) * a.tile_h;
+            v = (int)(w % Wq);
+            uj = u - 1;
+            vj = v;
+        } else {                         // right edge of the last quad column of a tile
+            const long long x = w - n_row_items;
+            v = (int)(x / Hq + 1) * a.tile_w - 1;
+            u = (int)(x % Hq);
+            uj = u;
+            vj = v + 1;
         }
+        const int i = 2 * (u * Wq + v);
+        const int j = 2 * (uj * Wq + vj) + 1;
         const int g = a.groups[i];
-        if (g == PL3D_NO_GROUP) continue;
-        const int u = (int)(q / Wq), v = (int)(q % Wq);
-        const bool offs = a.max_offset > 0.f;
-        float ci[3];
-        if (offs) centroid(a, u, v, 0, ci);
-        // diagonal twin: second triangle of the same quad
-        if (a.groups[i + 1] == g && (!offs || offset_ok(a, g, ci, u, v, 1))) unite(a.labels, i, i + 1);
-        // right twin: second triangle of quad (u, v+1)
-        if (v + 1 < Wq) {
-            const int j = i + 3;
-            if (a.groups[j] == g && (!offs || offset_ok(a, g, ci, u, v + 1, 1))) unite(a.labels, i, j);
-        }
-        // top twin: second triangle of quad (u-1, v)
-        if (u >= 1) {
-            const int j = i - 2 * Wq + 1;
-            if (a.groups[j] == g && (!offs || offset_ok(a, g, ci, u - 1, v, 1))) unite(a.labels, i, j);
-        }
+        if (g == PL3D_NO_GROUP || a.groups[j] != g) continue;
+        if (!offset_ok(a, g, u, v, uj, vj)) continue;
+        uf_unite(a.labels, i, j);
     }
 }
 
-// Every grouped triangle takes its root. Walks only read: the single write per entry comes
-// from its own thread, and a walk that reads an entry already rewritten reads its root.
+// Every grouped triangle takes its root (walks only read: the single write per entry comes
+// from its own thread, and a walk that meets an entry already rewritten reads its root).
 __global__ void label_flatten_kernel(LabelArgs a) {
     const long long n = 2LL * (a.H - 1) * (a.W - 1);
-    volatile int32_t* L = a.labels;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        int x = L[i];
-        if (x < 0) continue;
-        while (true) {
-            const int p = L[x];
-            if (p == x) break;
-            x = p;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long n_iter = (n + stride - 1) / stride;
+    const long long base = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    for (long long it = 0; it < n_iter; ++it) {          // uniform trip count: whole warps stay together
+        const long long i = base + it * stride;
+        int root = -1;
+        if (i < n && a.labels[i] >= 0) {
+            root = uf_root(a.labels, (int)i);
+            a.labels[i] = root;
         }
-        L[i] = x;
-        if (a.sizes) atomicAdd(a.sizes + x, 1);
+        if (a.sizes) {
+            const unsigned peers = __match_any_sync(0xffffffffu, root);
+            const int leader = __ffs(peers) - 1;
+            if (root >= 0 && (int)(threadIdx.x & 31) == leader) atomicAdd(a.sizes + root, __popc(peers));
+        }
     }
 }
 
@@ -138,8 +118,10 @@ int grid_for(long long n) {
 
 }  // namespace
 
-cudaError_t launch_label_union(const LabelArgs& a, cudaStream_t s) {
-    label_union_kernel<<<grid_for((long long)(a.H - 1) * (a.W - 1)), kThreads, 0, s>>>(a);
+cudaError_t launch_label_merge(const LabelArgs& a, cudaStream_t s) {
+    const int Wq = a.W - 1, Hq = a.H - 1;
+    const long long n = (long long)(div_up(Hq, a.tile_h) - 1) * Wq + (long long)(div_up(Wq, a.tile_w) - 1) * Hq;
+    label_merge_kernel<<<grid_for(n > 0 ? n : 1), kThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 

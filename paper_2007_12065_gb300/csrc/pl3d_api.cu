@@ -4,9 +4,9 @@
 //
 // Launch sequence of one frame (all on the caller's stream):
 //   lap_smooth_kernel   x ceil(lap_iters / fused)   Eq. 1-2          points -> SoA displacements
-//   bilateral_kernel    x ceil(bil_iters / fused)   Eq. 3-6, Alg. 1/4 -> mask, normals, groups,
-//                                                                       union-find parents
-//   label_union_kernel                              Alg. 5 / Alg. 2   unions over twin edges
+//   bilateral_kernel    x ceil(bil_iters / fused)   Eq. 3-6, Alg. 1/4/5 -> mask, normals, groups,
+//                                                                       tile-local segment roots
+//   label_merge_kernel                              Alg. 5 / Alg. 2   unions over tile-border twins
 //   label_flatten_kernel                                              labels = component roots
 //   label_filter_kernel (tri_min > 0 only)                            drop small segments
 #include <float.h>
@@ -25,8 +25,8 @@ namespace {
 
 constexpr int kVersion = 1 * 10000 + 0 * 100 + 0;
 
-enum Slot { kSlotLaplacian = 0, kSlotBilateral, kSlotUnion, kSlotFlatten, kSlotFilter, kSlotCopies };
-const char* const kSlotNames[PL3D_TIMING_SLOTS] = {"lap_smooth", "bilateral", "label_union",
+enum Slot { kSlotLaplacian = 0, kSlotBilateral, kSlotMerge, kSlotFlatten, kSlotFilter, kSlotCopies };
+const char* const kSlotNames[PL3D_TIMING_SLOTS] = {"lap_smooth", "bilateral", "label_merge",
                                                     "label_flatten", "label_filter", "host_copies"};
 
 struct TimedRange {
@@ -213,12 +213,8 @@ int run(pl3d_ctx* ctx, const float* points, int H, int W, const pl3d_params* p, 
     const int bfuse = kBilMaxHalo / br;
     const int nchunks = p->bil_iters <= bfuse ? 1 : (p->bil_iters + bfuse - 1) / bfuse;
     if (nchunks > 1 && (rc = grow(&ctx->carry, &ctx->cap_carry, ntri, 6, s)) != PL3D_OK) return rc;
-    const double log2e = 1.4426950408889634;
-    double na = -log2e / (2.0 * (double)p->bil_sigma_len * (double)p->bil_sigma_len);
-    double ns = -log2e / (2.0 * (double)p->bil_sigma_ang * (double)p->bil_sigma_ang);
-    // keep the scales finite and non-zero so that 0 * scale and inf * scale stay well defined
-    na = fmin(fmax(na, -(double)FLT_MAX), -(double)FLT_MIN);
-    ns = fmin(fmax(ns, -(double)FLT_MAX), -(double)FLT_MIN);
+    float c_scale = 1.f, a_norm = 0.f;
+    bilateral_scales(p->bil_sigma_len, p->bil_sigma_ang, p->bil_iters, &c_scale, &a_norm);
     int bremaining = p->bil_iters;
     for (int c = 0; c < nchunks; ++c) {
         const int it = bremaining < bfuse ? bremaining : bfuse;
@@ -237,8 +233,10 @@ int run(pl3d_ctx* ctx, const float* points, int H, int W, const pl3d_params* p, 
         ba.H = H;
         ba.W = W;
         ba.iters = it;
-        ba.neg_a = (float)na;
-        ba.neg_s = (float)ns;
+        ba.c_scale = c_scale;
+        ba.a_norm = a_norm;
+        ba.max_offset_scaled = p->max_offset > 0.f ? p->max_offset * c_scale : 0.f;
+        ba.sizes = p->min_triangles > 0 ? ctx->sizes : nullptr;
         ba.max_edge2 = p->max_edge > 0.f ? p->max_edge * p->max_edge : INFINITY;
         ba.min_dot = p->min_dot;
         ba.nd = nd;
@@ -258,10 +256,12 @@ int run(pl3d_ctx* ctx, const float* points, int H, int W, const pl3d_params* p, 
     lb.dz = dz;
     lb.H = H;
     lb.W = W;
+    lb.tile_h = kBilTileH;
+    lb.tile_w = kBilTileW;
     lb.max_offset = p->max_offset;
     lb.min_triangles = p->min_triangles;
     lb.nd = nd;
-    if ((rc = launch(ctx, kSlotUnion, s, [&] { return launch_label_union(lb, s); })) != PL3D_OK) return rc;
+    if ((rc = launch(ctx, kSlotMerge, s, [&] { return launch_label_merge(lb, s); })) != PL3D_OK) return rc;
     if ((rc = launch(ctx, kSlotFlatten, s, [&] { return launch_label_flatten(lb, s); })) != PL3D_OK) return rc;
     if (p->min_triangles > 0 &&
         (rc = launch(ctx, kSlotFilter, s, [&] { return launch_label_filter(lb, s); })) != PL3D_OK)

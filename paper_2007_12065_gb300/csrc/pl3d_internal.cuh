@@ -31,6 +31,16 @@ constexpr float kAbsentCentroid = 1.0e30f;
 // Squared cross-product length at or below which a triangle has no normal (|n| <= 1e-20).
 constexpr float kDegenerateLen2 = 1.0e-40f;
 
+// Coordinates of magnitude 1e18 or more are outside the supported range (their squared
+// distances overflow FP32); such points are treated like non-finite ones: invalid.
+constexpr float kMaxCoord = 1.0e18f;
+__host__ __device__ __forceinline__ bool point_valid(float x, float y, float z) {
+    return fabsf(x) < kMaxCoord && fabsf(y) < kMaxCoord && fabsf(z) < kMaxCoord;   // false for NaN and inf
+}
+
+// Finite stand-in for an invalid point inside the Laplacian's shared-memory tile.
+constexpr float kInvalidCoord = 1.0e30f;
+
 // Dominant normals, unit length, passed to kernels by value (3 KB, fits the parameter space).
 struct Dominant {
     int K;
@@ -52,7 +62,7 @@ struct LapArgs {
     float lambda;
 };
 // Tile of output points per CTA.
-constexpr int kLapTileH = 16;
+constexpr int kLapTileH = 32;
 constexpr int kLapTileW = 32;
 constexpr int kLapThreads = 256;
 // Largest halo (fused iterations x radius) one launch may carry.
@@ -62,7 +72,7 @@ cudaError_t launch_laplacian(const LapArgs& a, int radius, cudaStream_t s);
 cudaError_t laplacian_configure();
 size_t laplacian_smem_bytes(int radius, int iters);
 
-// ----------------------------------------- normals + bilateral (Eq. 3-6) + Algorithm 4
+// ------------------- normals + bilateral (Eq. 3-6) + Algorithm 4 + tile-local Algorithm 5
 struct BilArgs {
     const float* points;                      // AoS input points v0
     const float* dx;                          // displacements, SoA (smoothed = v0 + d)
@@ -73,41 +83,46 @@ struct BilArgs {
     uint8_t* out_mask;                        // last launch only
     float* out_normals;
     uint8_t* out_groups;
-    int32_t* out_labels;                      // initialised to GID (grouped) or -1
+    int32_t* out_labels;                      // GID of the tile-local root, or -1
+    int32_t* sizes;                           // zeroed for the merge/flatten passes, or nullptr
     int H, W;
     int iters;                                // iterations fused in this launch (>= 0)
-    float neg_a;                              // -log2(e) / (2 sigma_c^2)
-    float neg_s;                              // -log2(e) / (2 sigma_s^2)
+    float c_scale;                            // sqrt(log2(e) / (2 sigma_c^2)): centroid pre-scale
+    float a_norm;                             // log2(e) / sigma_s^2
     float max_edge2;                          // l_max^2, or +inf when disabled
     float min_dot;
+    float max_offset_scaled;                  // max_offset * c_scale, <= 0 when disabled
     Dominant nd;
 };
-constexpr int kBilTileH = 16;                 // quads per CTA tile
+constexpr int kBilTileH = 32;                 // quads per CTA tile
 constexpr int kBilTileW = 32;
 constexpr int kBilThreads = 256;
 constexpr int kBilMaxHalo = 6;
 cudaError_t launch_bilateral(const BilArgs& a, int radius, bool first, bool last, cudaStream_t s);
 cudaError_t bilateral_configure();
 size_t bilateral_smem_bytes(int radius, int iters);
+// Host-side scale factors of the bilateral weights, kept finite and non-zero.
+void bilateral_scales(float sigma_c, float sigma_s, int iters, float* c_scale, float* a_norm);
 
-// ------------------------------------------------------- connected segments (Algorithm 5)
+// ------------------------------------------- segments across tile borders (Algorithm 5)
 struct LabelArgs {
     const uint8_t* groups;
-    int32_t* labels;                          // parent array in, labels out
+    int32_t* labels;                          // tile-local roots in, labels out
     int32_t* sizes;                           // segment sizes (tri_min > 0) or nullptr
     const float* points;                      // AoS input points and SoA displacements
     const float* dx;                          // (offset test only)
     const float* dy;
     const float* dz;
     int H, W;
+    int tile_h, tile_w;                       // the bilateral kernel's tile, in quads
     float max_offset;                         // <= 0: no offset test
     int min_triangles;
     Dominant nd;
 };
-cudaError_t launch_label_union(const LabelArgs& a, cudaStream_t s);
+cudaError_t launch_label_merge(const LabelArgs& a, cudaStream_t s);
 cudaError_t launch_label_flatten(const LabelArgs& a, cudaStream_t s);
 cudaError_t launch_label_filter(const LabelArgs& a, cudaStream_t s);
 
-inline int div_up(long long a, long long b) { return (int)((a + b - 1) / b); }
+__host__ __device__ inline int div_up(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 }  // namespace pl3d

@@ -143,10 +143,8 @@ extern "C" int pl3d_extract_planes_static(const float* points, int H, int W, con
     } while (remaining > 0);
 
     // Normals, bilateral, mask and groups in one launch.
-    double na = -1.4426950408889634 / (2.0 * (double)p->bil_sigma_len * (double)p->bil_sigma_len);
-    double ns = -1.4426950408889634 / (2.0 * (double)p->bil_sigma_ang * (double)p->bil_sigma_ang);
-    na = fmin(fmax(na, -(double)FLT_MAX), -(double)FLT_MIN);
-    ns = fmin(fmax(ns, -(double)FLT_MAX), -(double)FLT_MIN);
+    float c_scale = 1.f, a_norm = 0.f;
+    bilateral_scales(p->bil_sigma_len, p->bil_sigma_ang, p->bil_iters, &c_scale, &a_norm);
     BilArgs ba;
     ba.points = points;
     ba.dx = buf[cur][0];
@@ -161,14 +159,16 @@ extern "C" int pl3d_extract_planes_static(const float* points, int H, int W, con
     ba.H = H;
     ba.W = W;
     ba.iters = p->bil_iters;
-    ba.neg_a = (float)na;
-    ba.neg_s = (float)ns;
+    ba.c_scale = c_scale;
+    ba.a_norm = a_norm;
+    ba.max_offset_scaled = p->max_offset > 0.f ? p->max_offset * c_scale : 0.f;
+    ba.sizes = p->min_triangles > 0 ? sizes : nullptr;
     ba.max_edge2 = p->max_edge > 0.f ? p->max_edge * p->max_edge : INFINITY;
     ba.min_dot = p->min_dot;
     ba.nd = nd;
     if (launch_bilateral(ba, br, true, true, s) != cudaSuccess) return PL3D_ERR_CUDA;
 
-    // Planar segments; the union pass zeroes the segment sizes before they are counted.
+    // Planar segments across tile borders; the bilateral pass zeroed the segment sizes.
     LabelArgs lb;
     lb.groups = groups;
     lb.labels = out_labels;
@@ -179,10 +179,12 @@ extern "C" int pl3d_extract_planes_static(const float* points, int H, int W, con
     lb.dz = buf[cur][2];
     lb.H = H;
     lb.W = W;
+    lb.tile_h = kBilTileH;
+    lb.tile_w = kBilTileW;
     lb.max_offset = p->max_offset;
     lb.min_triangles = p->min_triangles;
     lb.nd = nd;
-    if (launch_label_union(lb, s) != cudaSuccess) return PL3D_ERR_CUDA;
+    if (launch_label_merge(lb, s) != cudaSuccess) return PL3D_ERR_CUDA;
     if (launch_label_flatten(lb, s) != cudaSuccess) return PL3D_ERR_CUDA;
     if (p->min_triangles > 0 && launch_label_filter(lb, s) != cudaSuccess) return PL3D_ERR_CUDA;
     return PL3D_OK;
