@@ -107,27 +107,27 @@ class ClockSampler:
 # ----------------------------------------------------------------------------- algorithmic work per launch
 
 
-def algorithmic(kernel: str, H: int, W: int, prm: dict, launches_per_step: int) -> tuple[str, float, str]:
-    """(bound, work per launch, unit) for one launch of `kernel` on an H x W frame.
+def algorithmic_flop(H: int, W: int, prm: dict, K: int) -> dict:
+    """FP32 operations per frame the method defines (an FMA counts 2, an exp or rsqrt 1), phase by phase.
 
-    Bytes: what the launch must move to and from HBM with perfect on-chip reuse. FLOPs (for the
-    ALU-bound bilateral): 20 FP32 operations per (triangle, window triangle) pair and iteration,
-    an FMA counted as 2, an exp2 as 1."""
+    Laplacian (Eq. 1-2), per point, iteration and window neighbour: difference 3, squared norm 5,
+    1/sqrt 1, weighted sum 6, weight sum 1 = 16. Bilateral (Eq. 3-6), per triangle, iteration and
+    window triangle: centroid difference 3 + squared 5, normal difference 3 + squared 5, exponent
+    3, exp 1, weighted sum 6 = 26. Geometry 30 per triangle; group assignment 5 per triangle and
+    dominant normal."""
     npx = H * W
     ntri = 2 * (H - 1) * (W - 1)
-    if kernel == "lap_smooth":
-        return "hbm", 24.0 * npx, "B"
-    if kernel == "bilateral":
-        k = prm["bil_kernel"]
-        iters_per_launch = prm["bil_iters"] / max(launches_per_step, 1)
-        return "alu", 20.0 * 2 * k * k * ntri * iters_per_launch, "FLOP"
-    if kernel == "label_merge":
-        return "hbm", 5.0 * ntri, "B"
-    if kernel == "label_flatten":
-        return "hbm", 8.0 * ntri, "B"
-    if kernel == "label_filter":
-        return "hbm", 8.0 * ntri, "B"
-    return "hbm", 0.0, "B"
+    kl, kb = prm["lap_kernel"], prm["bil_kernel"]
+    lap = 16.0 * (kl * kl - 1) * npx * prm["lap_iters"]
+    bil = 26.0 * 2 * kb * kb * ntri * prm["bil_iters"] + 30.0 * ntri
+    cls = 5.0 * K * ntri
+    return {"laplacian": lap, "bilateral": bil + cls, "total": lap + bil + cls}
+
+
+def algorithmic_bytes(H: int, W: int) -> float:
+    """HBM bytes the fully fused path must move per frame: read points 12 B/px; write normals
+    12 B, mask 1 B and labels 4 B per triangle (about 46 B/px)."""
+    return 12.0 * H * W + 17.0 * 2 * (H - 1) * (W - 1)
 
 
 def fp32_peak_tflops(sm_count: int, mhz: float) -> float:
@@ -317,29 +317,29 @@ def run_pl3d(args):
             dist.destroy_process_group()
         return
 
-    # ---------------- roofline of the dominant kernel
+    # ---------------- roofline of the frame kernel (the only kernel: one launch per frame)
     peaks, peak_src = _peaks()
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-    top = max(per_kernel.items(), key=lambda kv: kv[1][0])
-    kname, (kms, kn) = top
-    total_ms = sum(v[0] for v in per_kernel.values())
-    launches_per_step = kn / args.steps
-    bound, work, wunit = algorithmic(kname, H, W, frame.params, launches_per_step)
-    avg_launch_s = kms / kn / 1e3
-    if bound == "hbm":
-        achieved = work / avg_launch_s / 1e9
-        peak, unit = float(peaks["hbm_gbs"]), "GB/s"
-        peak_note = f"{peak_src} hbm_gbs"
-    else:
-        achieved = work / avg_launch_s / 1e12
-        peak = fp32_peak_tflops(sm_count, float(peaks.get("sm_max_mhz", 2070.0)))
-        unit = "TFLOP/s"
-        peak_note = f"FP32 CUDA-core peak: {sm_count} SMs x 128 lanes x 2 FLOP x {peaks.get('sm_max_mhz', 2070.0)} MHz"
-    roofline = {"bound": bound, "kernel": kname, "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": achieved / peak, "traffic": None, "peak_source": peak_note,
-                "avg_launch_us": avg_launch_s * 1e6, "work_per_launch": work, "work_unit": wunit,
-                "share_of_device_time": kms / total_ms if total_ms > 0 else None,
-                "per_kernel_us": {k: (v[0] / v[1] * 1e3 if v[1] else 0.0) for k, v in per_kernel.items()}}
+    k_ms, k_n = per_kernel["frame_kernel"]
+    avg_launch_s = k_ms / k_n / 1e3
+    flop = algorithmic_flop(H, W, frame.params, K)
+    nbytes = algorithmic_bytes(H, W)
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = fp32_peak_tflops(sm_count, mhz)
+    achieved = flop["total"] / avg_launch_s / 1e12
+    phases = {}
+    for name in ("laplacian", "bilateral", "label_merge", "label_flatten"):
+        p_ms, p_n = per_kernel[name]
+        phases[name] = {"us": p_ms / max(p_n, 1) * 1e3}
+    phases["laplacian"]["tflops"] = flop["laplacian"] / (phases["laplacian"]["us"] * 1e-6) / 1e12
+    phases["bilateral"]["tflops"] = flop["bilateral"] / (phases["bilateral"]["us"] * 1e-6) / 1e12
+    roofline = {"bound": "alu", "kernel": "frame_kernel", "achieved": achieved, "peak": fp32_peak,
+                "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                "peak_source": f"FP32 CUDA-core peak: {sm_count} SMs x 128 lanes x 2 FLOP x {mhz} MHz",
+                "avg_launch_us": avg_launch_s * 1e6, "work_per_launch": flop["total"], "work_unit": "FLOP",
+                "hbm": {"algorithmic_bytes": nbytes, "achieved_gbs": nbytes / avg_launch_s / 1e9,
+                        "peak_gbs": float(peaks["hbm_gbs"]), "peak_source": f"{peak_src} hbm_gbs"},
+                "phases_us": phases}
 
     # ---------------- CPU baseline (oracle on the host cores, bounded sample)
     cpu = None

@@ -1,0 +1,250 @@
+// frame_host.cu -- host side of the frame kernel: pass planning, TMA tensor maps, occupancy and
+// the cooperative launch (which guarantees that every CTA of the grid is resident, as the grid
+// barrier requires).
+#include <float.h>
+#include <math.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "pl3d_internal.cuh"
+
+namespace pl3d {
+
+const void* frame_kernel_rb1(int rl);
+const void* frame_kernel_rb2(int rl);
+const void* frame_kernel_rb3(int rl);
+
+namespace {
+
+const void* kernel_for(int rl, int rb) {
+    switch (rb) {
+        case 1: return frame_kernel_rb1(rl);
+        case 2: return frame_kernel_rb2(rl);
+        case 3: return frame_kernel_rb3(rl);
+        default: return nullptr;
+    }
+}
+
+int round4(int n) { return (n + 3) & ~3; }
+
+BoxGeom lap_box(int halo) { return {kTile + 2 * halo + 1, round4(3 * (kTile + 2 * halo) + 3)}; }
+BoxGeom bil_box(int halo) { return {kTile + 2 * halo + 1, round4(3 * (kTile + 2 * halo + 1) + 3)}; }
+
+size_t lap_smem(int halo) {
+    const BoxGeom b = lap_box(halo);
+    return 128 + 4 * (size_t)(3 * align_floats(b.rows * b.cols));
+}
+
+size_t bil_smem(int halo) {
+    const BoxGeom b = bil_box(halo);
+    const int rq = kTile + 2 * halo;
+    const int quads = align_floats(6 * (rq * rq + rq));
+    const int boxes = 2 * align_floats(b.rows * b.cols);
+    return 128 + 4 * (size_t)(2 * quads + (quads > boxes ? quads : boxes)) + 4 * (size_t)kTile * kTile;
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link against libcuda).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+        cudaGetLastError();
+    });
+    return fn;
+}
+
+// Tensor map of an AoS [H][W][3] float array as H rows of 3W floats; box = b. Out-of-bounds
+// elements read as NaN (nan_fill) or zero.
+bool encode_aos(CUtensorMap* map, const float* base, int H, int W, BoxGeom b, bool nan_fill) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)3 * W, (cuuint64_t)H};
+    const cuuint64_t strides[1] = {(cuuint64_t)12 * W};
+    const cuuint32_t box[2] = {(cuuint32_t)b.cols, (cuuint32_t)b.rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              nan_fill ? CU_TENSOR_MAP_FLOAT_OOB_FILL_NAN_REQUEST_ZERO_FMA : CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+
+// Resident CTAs per SM for a kernel and shared-memory size, and SMs per device (cached).
+struct OccKey {
+    const void* fn;
+    size_t smem;
+    int dev;
+};
+std::mutex g_occ_mutex;
+OccKey g_occ_keys[64];
+int g_occ_vals[64];
+int g_occ_n = 0;
+
+int resident_ctas(const void* fn, size_t smem, int dev) {
+    std::lock_guard<std::mutex> lock(g_occ_mutex);
+    for (int i = 0; i < g_occ_n; ++i)
+        if (g_occ_keys[i].fn == fn && g_occ_keys[i].smem == smem && g_occ_keys[i].dev == dev) return g_occ_vals[i];
+    int per_sm = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    const int v = per_sm * sms;
+    if (g_occ_n < 64) {
+        g_occ_keys[g_occ_n] = {fn, smem, dev};
+        g_occ_vals[g_occ_n] = v;
+        ++g_occ_n;
+    }
+    return v;
+}
+
+void bilateral_scales(float sigma_c, float sigma_s, int iters, float* c_scale, float* a_norm) {
+    const double log2e = 1.4426950408889634;
+    double cs = 1.0, an = 0.0;
+    if (iters > 0) {
+        cs = sqrt(log2e / (2.0 * (double)sigma_c * (double)sigma_c));
+        an = log2e / ((double)sigma_s * (double)sigma_s);
+    }
+    // finite and representable: c' = c * cs must not overflow for coordinates up to ~1e18
+    *c_scale = (float)fmin(fmax(cs, 1e-18), 1e18);
+    *a_norm = (float)fmin(an, 1e30);
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+}  // namespace
+
+int bilateral_passes(const pl3d_params* p) {
+    const int br = p->bil_iters > 0 ? p->bil_kernel / 2 : 1;
+    const int fuse = kBilMaxHalo / br;
+    return p->bil_iters <= fuse ? 1 : (p->bil_iters + fuse - 1) / fuse;
+}
+
+cudaError_t frame_configure() {
+    const size_t need = lap_smem(kLapMaxHalo) > bil_smem(kBilMaxHalo) ? lap_smem(kLapMaxHalo) : bil_smem(kBilMaxHalo);
+    for (int rl = 1; rl <= 3; ++rl)
+        for (int rb = 1; rb <= 3; ++rb) {
+            cudaError_t e = cudaFuncSetAttribute(kernel_for(rl, rb), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)need);
+            if (e != cudaSuccess) return e;
+        }
+    return cudaSuccess;
+}
+
+int frame_launch(const FrameScratch& sc, const float* points, int H, int W, const pl3d_params* p, const float* nd_host,
+                 int K, uint8_t* out_mask, float* out_normals, int32_t* out_labels, float* out_points,
+                 uint8_t* out_groups, cudaStream_t s) {
+    static_assert(sizeof(FrameArgs) < 32000, "kernel parameters must fit the 32 KB parameter space");
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PL3D_ERR_CUDA;
+    FrameArgs a;
+    memset(&a, 0, sizeof(a));
+    a.points = points;
+    a.H = H;
+    a.W = W;
+    a.lambda = p->lap_lambda;
+    const bool tma_ok = (W % 4) == 0 && aligned16(points) && encode_fn() != nullptr;
+
+    // Laplacian passes (Eq. 1-2): displacement ping-pong, the first pass reads no displacement.
+    const int rl = p->lap_iters > 0 ? p->lap_kernel / 2 : 1;
+    const int lfuse = kLapMaxHalo / rl;
+    int remaining = p->lap_iters;
+    size_t smem = 0;
+    do {
+        if (a.n_lap == kMaxPasses) return PL3D_ERR_UNSUPPORTED;
+        LapPhase& ph = a.lap[a.n_lap];
+        ph.iters = remaining < lfuse ? remaining : lfuse;
+        ph.halo = ph.iters * rl;
+        ph.box = lap_box(ph.halo);
+        ph.use_tma = a.n_lap == 0 && tma_ok;
+        ph.d_in = a.n_lap == 0 ? nullptr : sc.disp[(a.n_lap - 1) & 1];
+        ph.d_out = sc.disp[a.n_lap & 1];
+        remaining -= ph.iters;
+        ph.export_points = remaining == 0 ? out_points : nullptr;
+        const size_t m = lap_smem(ph.halo);
+        smem = m > smem ? m : smem;
+        ++a.n_lap;
+    } while (remaining > 0);
+    a.disp = a.lap[a.n_lap - 1].d_out;
+    if (a.lap[0].use_tma && !encode_aos(&a.tm_pts_lap, points, H, W, a.lap[0].box, true)) a.lap[0].use_tma = 0;
+
+    // Bilateral passes (Eq. 3-6) and the quads' finish (Algorithms 1, 4, 5).
+    const int rb = p->bil_iters > 0 ? p->bil_kernel / 2 : 1;
+    const int bfuse = kBilMaxHalo / rb;
+    const int nb = bilateral_passes(p);
+    if (nb > kMaxPasses) return PL3D_ERR_UNSUPPORTED;
+    if (nb > 1 && (!sc.carry[0] || !sc.carry[1])) return PL3D_ERR_INVALID_ARG;
+    int bremaining = p->bil_iters;
+    for (int c = 0; c < nb; ++c) {
+        BilPhase& ph = a.bil[c];
+        ph.iters = bremaining < bfuse ? bremaining : bfuse;
+        bremaining -= ph.iters;
+        ph.halo = ph.iters * rb;
+        ph.box = bil_box(ph.halo);
+        ph.first = c == 0;
+        ph.last = c + 1 == nb;
+        ph.carry_in = c > 0 ? sc.carry[(c - 1) & 1] : nullptr;
+        ph.carry_out = c + 1 < nb ? sc.carry[c & 1] : nullptr;
+        ph.use_tma = c == 0 && tma_ok && aligned16(a.disp);
+        const size_t m = bil_smem(ph.halo);
+        smem = m > smem ? m : smem;
+    }
+    a.n_bil = nb;
+    if (a.bil[0].use_tma && !(encode_aos(&a.tm_pts_bil, points, H, W, a.bil[0].box, true) &&
+                              encode_aos(&a.tm_disp_bil, a.disp, H, W, a.bil[0].box, false)))
+        a.bil[0].use_tma = 0;
+
+    float c_scale = 1.f, a_norm = 0.f;
+    bilateral_scales(p->bil_sigma_len, p->bil_sigma_ang, p->bil_iters, &c_scale, &a_norm);
+    a.out_mask = out_mask;
+    a.out_normals = out_normals;
+    a.groups = out_groups ? out_groups : sc.groups;
+    a.labels = out_labels;
+    a.sizes = p->min_triangles > 0 ? sc.sizes : nullptr;
+    a.c_scale = c_scale;
+    a.a_norm = a_norm;
+    a.max_edge2 = p->max_edge > 0.f ? p->max_edge * p->max_edge : INFINITY;
+    a.min_dot = p->min_dot;
+    a.max_offset = p->max_offset;
+    a.max_offset_scaled = p->max_offset > 0.f ? p->max_offset * c_scale : 0.f;
+    a.min_triangles = p->min_triangles;
+    a.barrier = sc.barrier;
+    a.error = sc.error;
+    a.phase_ns = sc.phase_ns;
+    a.nd.K = K;
+    for (int j = 0; j < K; ++j) {
+        const double x = nd_host[3 * j], y = nd_host[3 * j + 1], z = nd_host[3 * j + 2];
+        const double len = sqrt(x * x + y * y + z * z);
+        a.nd.v[3 * j] = (float)(x / len);
+        a.nd.v[3 * j + 1] = (float)(y / len);
+        a.nd.v[3 * j + 2] = (float)(z / len);
+    }
+
+    const void* fn = kernel_for(rl, rb);
+    if (!fn) return PL3D_ERR_UNSUPPORTED;
+    const int resident = resident_ctas(fn, smem, dev);
+    if (resident <= 0) return PL3D_ERR_CUDA;
+    const int tiles_lap = div_up(H, kTile) * div_up(W, kTile);
+    const int tiles_bil = div_up(H - 1, kTile) * div_up(W - 1, kTile);
+    int grid = tiles_lap > tiles_bil ? tiles_lap : tiles_bil;
+    if (grid > resident) grid = resident;
+    void* args[1] = {&a};
+    if (cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kThreads), args, smem, s) != cudaSuccess) {
+        cudaGetLastError();
+        return PL3D_ERR_CUDA;
+    }
+    return PL3D_OK;
+}
+
+}  // namespace pl3d

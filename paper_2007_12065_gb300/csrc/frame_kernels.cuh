@@ -1,0 +1,770 @@
+// frame_kernels.cuh -- the whole path for one frame in one persistent, cooperatively launched
+// kernel: Laplacian tiles -> grid barrier -> bilateral tiles (normals, filter, mask, groups,
+// tile-local segments) -> grid barrier -> segment merge across tile borders -> grid barrier ->
+// labels (and the tri_min filter). Each CTA loops over the tiles of a phase; the grid barrier
+// (sync.cuh) orders the phases. Included once per (Laplacian radius, bilateral radius).
+//
+// Tiles are staged from HBM with TMA: the input points and the displacements are both AoS
+// [H][W][3] floats, seen as 2-D tensors of H rows x 3W floats, so one box per array covers a
+// tile plus its halo (points outside the image read as NaN, displacements as 0). The box's x
+// coordinate is rounded down to a 16-byte boundary; `delta` is the float offset of the tile's
+// first point inside a box row. When TMA cannot be used (W not a multiple of 4, a misaligned
+// pointer, or a phase split into several launches' worth of iterations), the same box is
+// filled with plain loads, so everything after staging is identical.
+#pragma once
+
+#include <math.h>
+
+#include "df32.cuh"
+#include "pl3d_internal.cuh"
+#include "sync.cuh"
+#include "uf.cuh"
+
+namespace pl3d {
+namespace frame {
+
+constexpr int T = kTile;   // tile edge: points (Laplacian) or quads (bilateral)
+
+struct V3 {
+    float x, y, z;
+};
+
+__device__ __forceinline__ float dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+
+__device__ __forceinline__ V3 cross(V3 a, V3 b) {
+    return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+
+// Hardware approximations from the PTX ISA: base-2 exponential (ex2(-inf) = +0, subnormal
+// results flush to zero) and reciprocal square root (rsqrt(+inf) = 0), both within 2 ulp.
+__device__ __forceinline__ float ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Floor of x to a multiple of 4 (also for negative x).
+__device__ __forceinline__ int floor4(int x) { return x & ~3; }
+
+// ------------------------------------------------------------------------------------ staging
+
+// Fills the box rows x cols (floats) whose top-left element is (x0, y0) of the AoS array
+// `src` seen as H rows of 3W floats: TMA when `map` is given, else plain loads. Elements
+// outside the array read as `fill`. `bar` completes when the TMA bytes have landed.
+__device__ __forceinline__ void stage_box(float* dst, const float* src, const CUtensorMap* map, const BoxGeom& b,
+                                          int x0, int y0, int H, int W, float fill, uint64_t* bar, int n_tma_boxes,
+                                          bool issue_tma) {
+    if (map) {
+        if (issue_tma && threadIdx.x == 0) {
+            if (n_tma_boxes > 0) mbar_arrive_expect_tx(bar, (unsigned)(n_tma_boxes * b.rows * b.cols * 4));
+            tma_load_2d(dst, map, x0, y0, bar);
+        }
+        return;
+    }
+    const int row_floats = 3 * W;
+    for (int e = threadIdx.x; e < b.rows * b.cols; e += blockDim.x) {
+        const int r = e / b.cols, x = e - r * b.cols;
+        const int gy = y0 + r, gx = x0 + x;
+        float v = fill;
+        if (src && gy >= 0 && gy < H && gx >= 0 && gx < row_floats) v = __ldg(src + (size_t)gy * row_floats + gx);
+        dst[e] = v;
+    }
+}
+
+// ------------------------------------------------------------------------------ Laplacian
+
+struct LapAcc {
+    float x, y, z, dx, dy, dz;   // centre: v0 and displacement
+    float sx, sy, sz, ws;        // weighted sums
+};
+
+__device__ __forceinline__ void lap_begin(LapAcc& A, const float* V0, const float* D, int o) {
+    A.x = V0[o];
+    A.y = V0[o + 1];
+    A.z = V0[o + 2];
+    A.dx = D[o];
+    A.dy = D[o + 1];
+    A.dz = D[o + 2];
+    A.sx = A.sy = A.sz = A.ws = 0.f;
+}
+
+// One neighbour (Eq. 2): w = 1 / |v_j - v|; a neighbour at distance 0 is skipped. An invalid
+// neighbour holds kInvalidCoord: the squared distance overflows to +inf, rsqrt(+inf) = 0.
+__device__ __forceinline__ void lap_add(LapAcc& A, const float* V0, const float* D, int o) {
+    const float ex = (V0[o] - A.x) + (D[o] - A.dx);
+    const float ey = (V0[o + 1] - A.y) + (D[o + 1] - A.dy);
+    const float ez = (V0[o + 2] - A.z) + (D[o + 2] - A.dz);
+    const float d2 = ex * ex + ey * ey + ez * ez;
+    const float w = d2 > 0.f ? rsqrt_approx(d2) : 0.f;
+    A.sx = fmaf(w, ex, A.sx);
+    A.sy = fmaf(w, ey, A.sy);
+    A.sz = fmaf(w, ez, A.sz);
+    A.ws += w;
+}
+
+// One Laplacian tile: T x T output points, `ph.iters` fused Jacobi iterations (Eq. 1-2).
+template <int R>
+__device__ void lap_tile(const FrameArgs& a, const LapPhase& ph, const CUtensorMap* map, int tile, float* smem,
+                         uint64_t* bar, unsigned& parity) {
+    const int H = a.H, W = a.W;
+    const int h = ph.halo;
+    const int RH = T + 2 * h, RW = T + 2 * h;
+    const BoxGeom& b = ph.box;                 // rows = RH + 1 (one spare row), cols >= 3 RW + delta
+    const int bsz = b.rows * b.cols;
+    float* V0 = smem;
+    float* Da = smem + align_floats(bsz);
+    float* Db = Da + align_floats(bsz);
+    const int tiles_x = div_up(W, T);
+    const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
+    const int u0 = ty * T - h, c0 = tx * T - h;
+    const int x0 = floor4(3 * c0);
+    const int dlt = 3 * c0 - x0;
+
+    if (map && threadIdx.x == 0) fence_proxy_async_all();
+    stage_box(V0, a.points, map, b, x0, u0, H, W, NAN, bar, 1, true);
+    stage_box(Da, ph.d_in, nullptr, b, x0, u0, H, W, 0.f, bar, 0, false);
+    if (map) {
+        mbar_wait_bounded(bar, parity, a.error);
+        parity ^= 1u;
+    }
+    __syncthreads();
+    // invalid points (non-finite or out of range, including outside the image) become the
+    // finite sentinel with zero displacement
+    for (int i = threadIdx.x; i < RH * RW; i += blockDim.x) {
+        const int r = i / RW, c = i - r * RW;
+        const int o = r * b.cols + dlt + 3 * c;
+        if (!point_valid(V0[o], V0[o + 1], V0[o + 2])) {
+            V0[o] = V0[o + 1] = V0[o + 2] = kInvalidCoord;
+            Da[o] = Da[o + 1] = Da[o + 2] = 0.f;
+        }
+    }
+    __syncthreads();
+
+    float* cur = Da;
+    float* nxt = Db;
+    for (int t = 1; t <= ph.iters; ++t) {
+        const int lo = t * R;
+        const int ch = RH - 2 * lo, cw = RW - 2 * lo;
+        const int strips = (ch + 1) >> 1;
+        for (int i = threadIdx.x; i < strips * cw; i += blockDim.x) {
+            const int sr = i / cw;
+            const int r = lo + 2 * sr, c = lo + (i - sr * cw);
+            const bool two = r + 1 < RH - lo;
+            const int oA = r * b.cols + dlt + 3 * c, oB = oA + b.cols;
+            const int gu = u0 + r, gv = c0 + c;
+            const bool colpin = gv < R || gv >= W - R;
+            // both points are always computed; a missing second point reads the spare row and
+            // is not stored, so the unrolled window has no data-dependent branch
+            LapAcc A, B;
+            lap_begin(A, V0, cur, oA);
+            lap_begin(B, V0, cur, oB);
+#pragma unroll
+            for (int dr = -R; dr <= R + 1; ++dr) {
+#pragma unroll
+                for (int dc = -R; dc <= R; ++dc) {
+                    const int o = oA + dr * b.cols + 3 * dc;
+                    if (dr <= R && !(dr == 0 && dc == 0)) lap_add(A, V0, cur, o);
+                    if (dr >= 1 - R && !(dr == 1 && dc == 0)) lap_add(B, V0, cur, o);
+                }
+            }
+            // Eq. 1 on the displacement; the pinned border ring, invalid points and points
+            // without a usable neighbour keep their displacement
+            const bool keepA = colpin || gu < R || gu >= H - R || A.x == kInvalidCoord || !(A.ws > 0.f);
+            const float sA = keepA ? 0.f : __fdividef(a.lambda, A.ws);
+            nxt[oA] = fmaf(sA, A.sx, A.dx);
+            nxt[oA + 1] = fmaf(sA, A.sy, A.dy);
+            nxt[oA + 2] = fmaf(sA, A.sz, A.dz);
+            if (two) {
+                const bool keepB = colpin || gu + 1 < R || gu + 1 >= H - R || B.x == kInvalidCoord || !(B.ws > 0.f);
+                const float sB = keepB ? 0.f : __fdividef(a.lambda, B.ws);
+                nxt[oB] = fmaf(sB, B.sx, B.dx);
+                nxt[oB + 1] = fmaf(sB, B.sy, B.dy);
+                nxt[oB + 2] = fmaf(sB, B.sz, B.dz);
+            }
+        }
+        __syncthreads();
+        float* tmp = cur;
+        cur = nxt;
+        nxt = tmp;
+    }
+
+    // The tile's own points: displacement out (AoS, row-contiguous), optional export.
+    for (int e = threadIdx.x; e < T * 3 * T; e += blockDim.x) {
+        const int r = e / (3 * T), f = e - r * (3 * T);
+        const int gu = u0 + h + r, gv3 = 3 * (c0 + h) + f;
+        if (gu >= H || gv3 >= 3 * W) continue;
+        const int o = (h + r) * b.cols + dlt + 3 * h + f;
+        const size_t g = (size_t)gu * 3 * W + gv3;
+        const float d = cur[o];
+        ph.d_out[g] = d;
+        if (ph.export_points) {
+            const int pt = o - (f % 3);
+            ph.export_points[g] = V0[pt] != kInvalidCoord ? V0[o] + d : NAN;
+        }
+    }
+    __syncthreads();
+}
+
+// ------------------------------------------------------------------------------ bilateral
+
+// A staged point: input position and displacement.
+struct SP {
+    float x, y, z, dx, dy, dz;
+};
+
+__device__ __forceinline__ SP load_sp(const float* V0, const float* D, int o) {
+    return {V0[o], V0[o + 1], V0[o + 2], D[o], D[o + 1], D[o + 2]};
+}
+
+struct PairEdge {
+    F2 x, y, z;
+};
+
+__device__ __forceinline__ PairEdge pair_edge(const SP& a, const SP& b) {
+    return {pair_diff(a.x, a.dx, b.x, b.dx), pair_diff(a.y, a.dy, b.y, b.dy), pair_diff(a.z, a.dz, b.z, b.dz)};
+}
+
+__device__ __forceinline__ V3 pair_cross(const PairEdge& e1, const PairEdge& e2) {
+    return {pair_sub_round(pair_mul(e1.y, e2.z), pair_mul(e1.z, e2.y)),
+            pair_sub_round(pair_mul(e1.z, e2.x), pair_mul(e1.x, e2.z)),
+            pair_sub_round(pair_mul(e1.x, e2.y), pair_mul(e1.y, e2.x))};
+}
+
+// Edge b - a in FP32 and the size of what was summed to form it (for the error bound).
+struct FastEdge {
+    V3 e;
+    float m;    // sum over coordinates of |v0_b - v0_a| + |d_b - d_a|
+    float l1;   // sum over coordinates of |e|
+};
+
+__device__ __forceinline__ FastEdge fast_edge(const SP& a, const SP& b) {
+    const float ax = b.x - a.x, ay = b.y - a.y, az = b.z - a.z;
+    const float dx = b.dx - a.dx, dy = b.dy - a.dy, dz = b.dz - a.dz;
+    FastEdge f;
+    f.e = {ax + dx, ay + dy, az + dz};
+    f.m = (fabsf(ax) + fabsf(dx)) + (fabsf(ay) + fabsf(dy)) + (fabsf(az) + fabsf(dz));
+    f.l1 = fabsf(f.e.x) + fabsf(f.e.y) + fabsf(f.e.z);
+    return f;
+}
+
+// The FP32 cross product of two FP32 edges is off by at most about
+// 2^-22 sqrt(3) (m1 |e2|_1 + |e1|_1 m2 + |e1|_1 |e2|_1) / |cr|_1 radians; accept it when that
+// is below 2e-6 rad (the factor 8 below), otherwise fall back to exact pairs.
+__device__ __forceinline__ bool fast_cross_ok(const FastEdge& e1, const FastEdge& e2, V3 cr) {
+    const float crl1 = fabsf(cr.x) + fabsf(cr.y) + fabsf(cr.z);
+    return e1.m * e2.l1 + e1.l1 * e2.m + e1.l1 * e2.l1 <= 8.f * crl1;
+}
+
+__device__ __forceinline__ V3 centroid3(const SP& a, const SP& b, const SP& c) {
+    const float k = 1.f / 3.f;
+    return {((a.x + b.x + c.x) + (a.dx + b.dx + c.dx)) * k, ((a.y + b.y + c.y) + (a.dy + b.dy + c.dy)) * k,
+            ((a.z + b.z + c.z) + (a.dz + b.dz + c.dz)) * k};
+}
+
+// Per-quad records in shared memory: 6 floats (triangle 0 xyz, triangle 1 xyz) read and
+// written as three float2.
+__device__ __forceinline__ void load_quad(const float* A, int q, V3& t0, V3& t1) {
+    const float2* p = reinterpret_cast<const float2*>(A) + 3 * q;
+    const float2 u = p[0], v = p[1], w = p[2];
+    t0 = {u.x, u.y, v.x};
+    t1 = {v.y, w.x, w.y};
+}
+
+__device__ __forceinline__ void store_quad(float* A, int q, V3 t0, V3 t1) {
+    float2* p = reinterpret_cast<float2*>(A) + 3 * q;
+    p[0] = make_float2(t0.x, t0.y);
+    p[1] = make_float2(t0.z, t1.x);
+    p[2] = make_float2(t1.y, t1.z);
+}
+
+__device__ __forceinline__ bool has_normal(V3 n) { return n.x != 0.f || n.y != 0.f || n.z != 0.f; }
+
+__device__ __forceinline__ V3 finish_normal(V3 s, V3 own) {
+    const float l2 = dot(s, s);
+    if (!has_normal(own) || !(l2 > 0.f)) return own;
+    const float inv = rsqrtf(l2);
+    return {s.x * inv, s.y * inv, s.z * inv};
+}
+
+// One pair (i, j): s_i += W n_j with W = ex2(-|c'_i - c'_j|^2 + p_i . n_j - a), p_i = a n_i.
+__device__ __forceinline__ void accumulate(V3& s, V3 ci, V3 pi, float a, V3 cj, V3 nj) {
+    const float dx = ci.x - cj.x, dy = ci.y - cj.y, dz = ci.z - cj.z;
+    float e = fmaf(pi.x, nj.x, fmaf(pi.y, nj.y, fmaf(pi.z, nj.z, -a)));
+    e = fmaf(-dx, dx, fmaf(-dy, dy, fmaf(-dz, dz, e)));
+    const float w = ex2(e);
+    s.x = fmaf(w, nj.x, s.x);
+    s.y = fmaf(w, nj.y, s.y);
+    s.z = fmaf(w, nj.z, s.z);
+}
+
+struct QuadAcc {
+    V3 c0, c1;   // scaled centroids
+    V3 n0, n1;   // current normals
+    V3 p0, p1;   // a * normals
+    V3 s0, s1;   // weighted sums
+};
+
+__device__ __forceinline__ void quad_begin(QuadAcc& A, const float* Cq, const float* cur, int q, float a) {
+    load_quad(Cq, q, A.c0, A.c1);
+    load_quad(cur, q, A.n0, A.n1);
+    A.p0 = {a * A.n0.x, a * A.n0.y, a * A.n0.z};
+    A.p1 = {a * A.n1.x, a * A.n1.y, a * A.n1.z};
+    // the triangle itself (weight exactly 1) and its partner in the quad
+    A.s0 = A.n0;
+    A.s1 = A.n1;
+    accumulate(A.s0, A.c0, A.p0, a, A.c1, A.n1);
+    accumulate(A.s1, A.c1, A.p1, a, A.c0, A.n0);
+}
+
+__device__ __forceinline__ void quad_neighbour(QuadAcc& A, float a, V3 cj0, V3 cj1, V3 nj0, V3 nj1) {
+    accumulate(A.s0, A.c0, A.p0, a, cj0, nj0);
+    accumulate(A.s0, A.c0, A.p0, a, cj1, nj1);
+    accumulate(A.s1, A.c1, A.p1, a, cj0, nj0);
+    accumulate(A.s1, A.c1, A.p1, a, cj1, nj1);
+}
+
+// One bilateral tile: T x T quads; geometry, `ph.iters` fused iterations (Eq. 3-6), then either
+// the carry for the next chunk or mask, normals, groups (Algorithm 4) and the tile-local
+// segments (Algorithm 5).
+template <int R>
+__device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float* smem, uint64_t* bar,
+                         unsigned& parity) {
+    const int H = a.H, W = a.W, Hq = H - 1, Wq = W - 1;
+    const int h = ph.halo;
+    const int RQH = T + 2 * h, RQW = T + 2 * h;          // staged quads
+    const int nq = RQH * RQW;
+    const int nqs = nq + RQW;                            // one spare row of quads
+    const BoxGeom& b = ph.box;                           // rows = RQH + 1 points, cols >= 3 (RQW + 1) + delta
+    const int bsz = align_floats(b.rows * b.cols);
+    float* Cq = smem;                                    // [nqs][6] scaled centroids
+    float* Na = Cq + align_floats(6 * nqs);              // [nqs][6] normals
+    float* X = Na + align_floats(6 * nqs);               // Nb, or the two staged boxes before the iterations
+    float* Nb = X;
+    float* V0 = X;
+    float* Dp = X + bsz;
+    const int xw = max(align_floats(6 * nqs), 2 * bsz);
+    uint8_t* Mk = reinterpret_cast<uint8_t*>(X + xw);    // [T*T*2] own masks
+    uint8_t* Gs = Mk + 2 * T * T;                        // [T*T*2] own groups
+    const int tiles_x = div_up(Wq, T);
+    const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
+    const int qu0 = ty * T - h, qv0 = tx * T - h;
+    const int x0 = floor4(3 * qv0);
+    const int dlt = 3 * qv0 - x0;
+    const float cs = a.c_scale;
+
+    const CUtensorMap* mp = ph.use_tma ? &a.tm_pts_bil : nullptr;
+    const CUtensorMap* md = ph.use_tma ? &a.tm_disp_bil : nullptr;
+    if (mp && threadIdx.x == 0) fence_proxy_async_all();
+    stage_box(V0, a.points, mp, b, x0, qu0, H, W, NAN, bar, 2, true);
+    stage_box(Dp, a.disp, md, b, x0, qu0, H, W, 0.f, bar, 0, true);
+    if (mp) {
+        mbar_wait_bounded(bar, parity, a.error);
+        parity ^= 1u;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < (RQH + 1) * (RQW + 1); i += blockDim.x) {
+        const int r = i / (RQW + 1), c = i - r * (RQW + 1);
+        const int o = r * b.cols + dlt + 3 * c;
+        if (!point_valid(V0[o], V0[o + 1], V0[o + 2])) {
+            V0[o] = V0[o + 1] = V0[o + 2] = NAN;
+            Dp[o] = Dp[o + 1] = Dp[o + 2] = 0.f;
+        }
+    }
+    __syncthreads();
+
+    // Centroids and normals of every staged triangle; masks of the tile's own quads.
+    for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+        const int qr = q / RQW, qc = q - qr * RQW;
+        const int gu = qu0 + qr, gv = qv0 + qc;
+        const bool exists = gu >= 0 && gu < Hq && gv >= 0 && gv < Wq;
+        const int o1 = qr * b.cols + dlt + 3 * qc;
+        const SP p1 = load_sp(V0, Dp, o1), p2 = load_sp(V0, Dp, o1 + 3);
+        const SP p3 = load_sp(V0, Dp, o1 + b.cols + 3), p4 = load_sp(V0, Dp, o1 + b.cols);
+        const bool own = ph.last && qr >= h && qr < h + T && qc >= h && qc < h + T;
+        const bool v1 = p1.x == p1.x, v2 = p2.x == p2.x, v3 = p3.x == p3.x, v4 = p4.x == p4.x;
+        const bool valid0 = exists && v1 && v2 && v3;                            // Algorithm 1
+        const bool valid1 = exists && v1 && v3 && v4;
+        V3 nn[2] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+        if (ph.first) {
+            // first = {p3, p2, p1}: (p2 - p3) x (p1 - p3);  second = {p1, p4, p3}: (p4 - p1) x (p3 - p1)
+            const FastEdge er = fast_edge(p3, p2), ed = fast_edge(p3, p1), el = fast_edge(p1, p4);
+            const FastEdge edn = {{-ed.e.x, -ed.e.y, -ed.e.z}, ed.m, ed.l1};
+            V3 cr0 = cross(er.e, ed.e), cr1 = cross(el.e, edn.e);
+            const bool exact0 = valid0 && !fast_cross_ok(er, ed, cr0);
+            const bool exact1 = valid1 && !fast_cross_ok(el, edn, cr1);
+            if (exact0 || exact1) {
+                const PairEdge pd = pair_edge(p3, p1);
+                if (exact0) cr0 = pair_cross(pair_edge(p3, p2), pd);
+                if (exact1) {
+                    const PairEdge pdn = {{-pd.x.h, -pd.x.l}, {-pd.y.h, -pd.y.l}, {-pd.z.h, -pd.z.l}};
+                    cr1 = pair_cross(pair_edge(p1, p4), pdn);
+                }
+            }
+            const V3 cr[2] = {cr0, cr1};
+            const bool vk[2] = {valid0, valid1};
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const float len2 = dot(cr[k], cr[k]);
+                if (vk[k] && len2 > kDegenerateLen2) {
+                    const float inv = rsqrtf(len2);
+                    nn[k] = {cr[k].x * inv, cr[k].y * inv, cr[k].z * inv};
+                }
+            }
+        } else {
+            const bool vk[2] = {valid0, valid1};
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                if (!vk[k]) continue;
+                const size_t gid = 2 * ((size_t)gu * Wq + gv) + k;
+                const float nx = __ldg(ph.carry_in + 3 * gid);
+                if (nx == nx) nn[k] = {nx, __ldg(ph.carry_in + 3 * gid + 1), __ldg(ph.carry_in + 3 * gid + 2)};
+            }
+        }
+        V3 cc[2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const SP& va = k == 0 ? p3 : p1;
+            const SP& vb = k == 0 ? p2 : p4;
+            const SP& vc = k == 0 ? p1 : p3;
+            cc[k] = {kAbsentCentroid, kAbsentCentroid, kAbsentCentroid};
+            if (has_normal(nn[k])) {
+                const V3 c = centroid3(va, vb, vc);
+                cc[k] = {c.x * cs, c.y * cs, c.z * cs};
+            }
+        }
+        if (own) {                                                               // Algorithm 4, l_max
+            // FP32 edges: ~1e-7 relative error, far inside the 1e-5 m band where FP32 and FP64
+            // may disagree
+            const V3 er = fast_edge(p3, p2).e, et = fast_edge(p2, p1).e, ed = fast_edge(p3, p1).e;
+            const V3 el = fast_edge(p1, p4).e, eb = fast_edge(p4, p3).e;
+            const float d2 = dot(ed, ed);
+            const float l0 = fmaxf(d2, fmaxf(dot(er, er), dot(et, et)));
+            const float l1 = fmaxf(d2, fmaxf(dot(el, el), dot(eb, eb)));
+            const int t = 2 * ((qr - h) * T + (qc - h));
+            Mk[t] = (valid0 && l0 <= a.max_edge2) ? 1 : 0;
+            Mk[t + 1] = (valid1 && l1 <= a.max_edge2) ? 1 : 0;
+        }
+        store_quad(Cq, q, cc[0], cc[1]);
+        store_quad(Na, q, nn[0], nn[1]);
+    }
+    __syncthreads();   // the staged boxes are dead from here on; Nb reuses their space
+
+    // Fused bilateral iterations: each work item is a vertical pair of quads.
+    float* cur = Na;
+    float* nxt = Nb;
+    const float an = a.a_norm;
+    for (int it = 1; it <= ph.iters; ++it) {
+        const int lo = it * R;
+        const int ch = RQH - 2 * lo, cw = RQW - 2 * lo;
+        const int strips = (ch + 1) >> 1;
+        for (int i = threadIdx.x; i < strips * cw; i += blockDim.x) {
+            const int sr = i / cw;
+            const int qr = lo + 2 * sr, qc = lo + (i - sr * cw);
+            const bool two = qr + 1 < RQH - lo;
+            const int qA = qr * RQW + qc, qB = qA + RQW;
+            QuadAcc A, B;
+            quad_begin(A, Cq, cur, qA, an);
+            quad_begin(B, Cq, cur, qB, an);
+#pragma unroll
+            for (int dr = -R; dr <= R + 1; ++dr) {
+#pragma unroll
+                for (int dc = -R; dc <= R; ++dc) {
+                    const bool forA = dr <= R && !(dr == 0 && dc == 0);
+                    const bool forB = dr >= 1 - R && !(dr == 1 && dc == 0);
+                    const int qj = qA + dr * RQW + dc;
+                    V3 cj0, cj1, nj0, nj1;
+                    load_quad(Cq, qj, cj0, cj1);
+                    load_quad(cur, qj, nj0, nj1);
+                    if (forA) quad_neighbour(A, an, cj0, cj1, nj0, nj1);
+                    if (forB) quad_neighbour(B, an, cj0, cj1, nj0, nj1);
+                }
+            }
+            store_quad(nxt, qA, finish_normal(A.s0, A.n0), finish_normal(A.s1, A.n1));
+            if (two) store_quad(nxt, qB, finish_normal(B.s0, B.n0), finish_normal(B.s1, B.n1));
+        }
+        __syncthreads();
+        float* tmp = cur;
+        cur = nxt;
+        nxt = tmp;
+    }
+
+    if (!ph.last) {
+        for (int i = threadIdx.x; i < T * T; i += blockDim.x) {
+            const int r = i / T, c = i - r * T;
+            const int gu = ty * T + r, gv = tx * T + c;
+            if (gu >= Hq || gv >= Wq) continue;
+            V3 n[2];
+            load_quad(cur, (r + h) * RQW + (c + h), n[0], n[1]);
+            const size_t gid0 = 2 * ((size_t)gu * Wq + gv);
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const bool has = has_normal(n[k]);
+                float* o = ph.carry_out + 3 * (gid0 + k);
+                o[0] = has ? n[k].x : NAN;
+                o[1] = has ? n[k].y : NAN;
+                o[2] = has ? n[k].z : NAN;
+            }
+        }
+        __syncthreads();
+        return;
+    }
+
+    int32_t* Lp = reinterpret_cast<int32_t*>(nxt);   // free after the last iteration: [T*T*2] parents
+    for (int i = threadIdx.x; i < T * T; i += blockDim.x) {
+        const int r = i / T, c = i - r * T;
+        const int gu = ty * T + r, gv = tx * T + c;
+        const bool exists = gu < Hq && gv < Wq;
+        V3 n[2];
+        load_quad(cur, (r + h) * RQW + (c + h), n[0], n[1]);
+        const size_t gid0 = exists ? 2 * ((size_t)gu * Wq + gv) : 0;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int t = 2 * i + k;
+            const bool kept = Mk[t] != 0;
+            const bool has = has_normal(n[k]);
+            int g = PL3D_NO_GROUP;
+            if (exists && kept && has) {                                         // Algorithm 4, ang_min
+                float best = -1.0f;
+                for (int j = 0; j < a.nd.K; ++j) {
+                    const float s = n[k].x * a.nd.v[3 * j] + n[k].y * a.nd.v[3 * j + 1] + n[k].z * a.nd.v[3 * j + 2];
+                    if (s > best) {
+                        best = s;
+                        g = j;
+                    }
+                }
+                if (best < a.min_dot) g = PL3D_NO_GROUP;
+            }
+            if (exists) {
+                const size_t gid = gid0 + k;
+                a.out_mask[gid] = kept ? 1 : 0;
+                float* o = a.out_normals + 3 * gid;
+                o[0] = has ? n[k].x : NAN;
+                o[1] = has ? n[k].y : NAN;
+                o[2] = has ? n[k].z : NAN;
+                a.groups[gid] = (uint8_t)g;
+                if (a.sizes) a.sizes[gid] = 0;
+            }
+            Gs[t] = exists ? (uint8_t)g : (uint8_t)PL3D_NO_GROUP;
+        }
+    }
+    __syncthreads();
+
+    // Connected components inside the tile (twins of Algorithm 2 that stay in the tile).
+    const bool offs = a.max_offset_scaled > 0.f;
+    const float lim = a.max_offset_scaled;
+    auto offset_ok = [&](int g, V3 ci, V3 cj) {
+        const float* nd = a.nd.v + 3 * g;
+        return !offs || fabsf(nd[0] * (ci.x - cj.x) + nd[1] * (ci.y - cj.y) + nd[2] * (ci.z - cj.z)) <= lim;
+    };
+    constexpr unsigned kFull = 0xffffffffu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // (1) Runs along each quad row. Chain position 2v is second(v), 2v+1 is first(v).
+    for (int r = warp; r < T; r += kThreads / 32) {
+        const int tf = 2 * (r * T + lane), ts = tf + 1;
+        const int gf = Gs[tf], gs = Gs[ts];
+        V3 cf = {0.f, 0.f, 0.f}, cs2 = cf;
+        if (offs) load_quad(Cq, (r + h) * RQW + (lane + h), cf, cs2);
+        const int gs_next = __shfl_down_sync(kFull, gs, 1);
+        const V3 cs_next = {__shfl_down_sync(kFull, cs2.x, 1), __shfl_down_sync(kFull, cs2.y, 1),
+                            __shfl_down_sync(kFull, cs2.z, 1)};
+        const bool diag = gf != PL3D_NO_GROUP && gs == gf && offset_ok(gf, cf, cs2);
+        const bool right = lane < 31 && gf != PL3D_NO_GROUP && gs_next == gf && offset_ok(gf, cf, cs_next);
+        const bool right_prev = __shfl_up_sync(kFull, right, 1);
+        const bool brk_s = lane == 0 || !right_prev;                 // a run starts at second(v)
+        const bool brk_f = !diag;                                    // a run starts at first(v)
+        int pm = brk_f ? 2 * lane + 1 : (brk_s ? 2 * lane : -1);      // last run start up to this lane
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(kFull, pm, o);
+            if (lane >= o) pm = max(pm, v);
+        }
+        const int before = __shfl_up_sync(kFull, pm, 1);
+        const int start_s = brk_s ? 2 * lane : before;
+        const int start_f = pm;
+        const unsigned brk_f_mask = __ballot_sync(kFull, brk_f);
+        // smallest GID of a run starting at chain position p: first(p/2), unless the run is
+        // second(p/2) alone
+        auto root_of = [&](int p) {
+            const int l0 = p >> 1;
+            const int t0 = 2 * (r * T + l0);
+            return ((p & 1) || !((brk_f_mask >> l0) & 1u)) ? t0 : t0 + 1;
+        };
+        Lp[ts] = gs != PL3D_NO_GROUP ? root_of(start_s) : -1;
+        Lp[tf] = gf != PL3D_NO_GROUP ? root_of(start_f) : -1;
+    }
+    __syncthreads();
+    // (2) Rows joined across horizontal edges: first(r, v) with second(r-1, v); one union per
+    // run pair (a lane skips the pair its left neighbour already joined).
+    for (int r = 1 + warp; r < T; r += kThreads / 32) {
+        const int tf = 2 * (r * T + lane), tu = 2 * ((r - 1) * T + lane) + 1;
+        const int gf = Gs[tf];
+        bool link = gf != PL3D_NO_GROUP && Gs[tu] == gf;
+        if (offs && link) {
+            V3 cf, c1, c0u, cu;
+            load_quad(Cq, (r + h) * RQW + (lane + h), cf, c1);
+            load_quad(Cq, (r - 1 + h) * RQW + (lane + h), c0u, cu);
+            link = offset_ok(gf, cf, cu);
+        }
+        const int ra = link ? Lp[tf] : -1, rb = link ? Lp[tu] : -1;
+        const int pa = __shfl_up_sync(kFull, ra, 1), pb = __shfl_up_sync(kFull, rb, 1);
+        const bool dup = lane > 0 && pa == ra && pb == rb;
+        if (link && !dup) uf_unite(Lp, ra, rb);
+    }
+    __syncthreads();
+    // (3) Each triangle leaves with the GID of its tile-local root (-1 without a group).
+    for (int i = threadIdx.x; i < T * T; i += blockDim.x) {
+        const int r = i / T, c = i - r * T;
+        const int gu = ty * T + r, gv = tx * T + c;
+        if (gu >= Hq || gv >= Wq) continue;
+        const size_t gid0 = 2 * ((size_t)gu * Wq + gv);
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int t = 2 * i + k;
+            int lab = -1;
+            if (Lp[t] >= 0) {
+                const int root = uf_root(Lp, t);
+                const int rq = root >> 1, rr = rq / T, rc = rq - rr * T;
+                lab = (int)(2 * ((size_t)(ty * T + rr) * Wq + (tx * T + rc)) + (root & 1));
+            }
+            a.labels[gid0 + k] = lab;
+        }
+    }
+    __syncthreads();
+}
+
+// ------------------------------------------------------------------------- segments (Alg. 5)
+
+// Centroid of triangle k of quad (u, v) from the smoothed points v0 + d (offset test only).
+__device__ __forceinline__ V3 centroid_global(const FrameArgs& a, int u, int v, int k) {
+    const int W = a.W;
+    const size_t p1 = (size_t)u * W + v, p2 = p1 + 1, p3 = p1 + W + 1, p4 = p1 + W;
+    const size_t ia = 3 * (k == 0 ? p3 : p1), ib = 3 * (k == 0 ? p2 : p4), ic = 3 * (k == 0 ? p1 : p3);
+    const float* P = a.points;
+    const float* D = a.disp;
+    const float kk = 1.f / 3.f;
+    return {((P[ia] + P[ib] + P[ic]) + (D[ia] + D[ib] + D[ic])) * kk,
+            ((P[ia + 1] + P[ib + 1] + P[ic + 1]) + (D[ia + 1] + D[ib + 1] + D[ic + 1])) * kk,
+            ((P[ia + 2] + P[ib + 2] + P[ic + 2]) + (D[ia + 2] + D[ib + 2] + D[ic + 2])) * kk};
+}
+
+// Twins that cross a tile border: the top edge of a tile's first quad row and the right edge of
+// its last quad column. Work items: (row borders) x Wq, then (column borders) x Hq.
+__device__ __forceinline__ void merge_phase(const FrameArgs& a) {
+    const int Wq = a.W - 1, Hq = a.H - 1;
+    const int rb = div_up(Hq, T) - 1;
+    const int cb = div_up(Wq, T) - 1;
+    const long long n_row_items = (long long)rb * Wq;
+    const long long n = n_row_items + (long long)cb * Hq;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < n; w += stride) {
+        int u, v, uj, vj;
+        if (w < n_row_items) {
+            u = (int)(w / Wq + 1) * T;
+            v = (int)(w % Wq);
+            uj = u - 1;
+            vj = v;
+        } else {
+            const long long x = w - n_row_items;
+            v = (int)(x / Hq + 1) * T - 1;
+            u = (int)(x % Hq);
+            uj = u;
+            vj = v + 1;
+        }
+        const int i = 2 * (u * Wq + v);
+        const int j = 2 * (uj * Wq + vj) + 1;
+        const int g = a.groups[i];
+        if (g == PL3D_NO_GROUP || a.groups[j] != g) continue;
+        if (a.max_offset > 0.f) {
+            const V3 ci = centroid_global(a, u, v, 0), cj = centroid_global(a, uj, vj, 1);
+            const float* nd = a.nd.v + 3 * g;
+            if (fabsf(nd[0] * (ci.x - cj.x) + nd[1] * (ci.y - cj.y) + nd[2] * (ci.z - cj.z)) > a.max_offset) continue;
+        }
+        uf_unite(a.labels, i, j);
+    }
+}
+
+// Every grouped triangle takes its root; with tri_min > 0 the segment sizes are counted, one
+// atomic per run of equal roots in a warp.
+__device__ __forceinline__ void flatten_phase(const FrameArgs& a) {
+    const long long n = 2LL * (a.H - 1) * (a.W - 1);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long n_iter = (n + stride - 1) / stride;
+    const long long base = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    for (long long it = 0; it < n_iter; ++it) {          // uniform trip count: whole warps stay together
+        const long long i = base + it * stride;
+        int root = -1;
+        if (i < n && a.labels[i] >= 0) {
+            root = uf_root(a.labels, (int)i);
+            a.labels[i] = root;
+        }
+        if (a.sizes) {
+            const unsigned peers = __match_any_sync(0xffffffffu, root);
+            const int leader = __ffs(peers) - 1;
+            if (root >= 0 && (int)(threadIdx.x & 31) == leader) atomicAdd(a.sizes + root, __popc(peers));
+        }
+    }
+}
+
+// Algorithm 5 keeps a segment only when it has more than tri_min triangles.
+__device__ __forceinline__ void filter_phase(const FrameArgs& a) {
+    const long long n = 2LL * (a.H - 1) * (a.W - 1);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int l = a.labels[i];
+        if (l >= 0 && a.sizes[l] <= a.min_triangles) a.labels[i] = -1;
+    }
+}
+
+__device__ __forceinline__ void phase_mark(const FrameArgs& a, int slot, uint64_t& t_prev) {
+    if (a.phase_ns && blockIdx.x == 0 && threadIdx.x == 0) {
+        const uint64_t t = global_ns();
+        atomicAdd(a.phase_ns + slot, (unsigned long long)(t - t_prev));
+        t_prev = t;
+    }
+}
+
+}  // namespace frame
+
+template <int RL, int RB>
+__global__ void __launch_bounds__(kThreads) frame_kernel(const __grid_constant__ FrameArgs a) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+    float* smem = reinterpret_cast<float*>(smem_raw + 128);
+    if (threadIdx.x == 0) mbar_init(bar, 1);
+    __syncthreads();
+    unsigned parity = 0;
+    uint64_t t_prev = 0;
+    if (a.phase_ns && blockIdx.x == 0 && threadIdx.x == 0) t_prev = global_ns();
+
+    const int tiles_lap = div_up(a.H, kTile) * div_up(a.W, kTile);
+    for (int c = 0; c < a.n_lap; ++c) {
+        const CUtensorMap* map = a.lap[c].use_tma ? &a.tm_pts_lap : nullptr;
+        for (int t = blockIdx.x; t < tiles_lap; t += gridDim.x)
+            frame::lap_tile<RL>(a, a.lap[c], map, t, smem, bar, parity);
+        grid_barrier(a.barrier, a.error);
+    }
+    frame::phase_mark(a, 0, t_prev);
+    const int tiles_bil = div_up(a.H - 1, kTile) * div_up(a.W - 1, kTile);
+    for (int c = 0; c < a.n_bil; ++c) {
+        for (int t = blockIdx.x; t < tiles_bil; t += gridDim.x) frame::bil_tile<RB>(a, a.bil[c], t, smem, bar, parity);
+        grid_barrier(a.barrier, a.error);
+    }
+    frame::phase_mark(a, 1, t_prev);
+    frame::merge_phase(a);
+    grid_barrier(a.barrier, a.error);
+    frame::phase_mark(a, 2, t_prev);
+    frame::flatten_phase(a);
+    if (a.min_triangles > 0) {
+        grid_barrier(a.barrier, a.error);
+        frame::filter_phase(a);
+    }
+    frame::phase_mark(a, 3, t_prev);
+}
+
+}  // namespace pl3d

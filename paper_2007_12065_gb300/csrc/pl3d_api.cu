@@ -1,15 +1,8 @@
 // pl3d_api.cu -- the C ABI declared in include/pl3d.h: argument checks, the context and its
-// scratch memory, the launch sequence of one extraction, per-phase timing, and the
-// host-buffer entry point.
-//
-// Launch sequence of one frame (all on the caller's stream):
-//   lap_smooth_kernel   x ceil(lap_iters / fused)   Eq. 1-2          points -> SoA displacements
-//   bilateral_kernel    x ceil(bil_iters / fused)   Eq. 3-6, Alg. 1/4/5 -> mask, normals, groups,
-//                                                                       tile-local segment roots
-//   label_merge_kernel                              Alg. 5 / Alg. 2   unions over tile-border twins
-//   label_flatten_kernel                                              labels = component roots
-//   label_filter_kernel (tri_min > 0 only)                            drop small segments
-#include <float.h>
+// scratch memory, per-phase timing, the device error word, and the host-buffer entry point.
+// The path itself is one cooperative launch of the frame kernel per call (frame_host.cu,
+// frame_kernels.cuh): Laplacian passes, bilateral passes with the quads' finish and the
+// tile-local segments, the segment merge across tiles, and the labels.
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -23,11 +16,13 @@ using namespace pl3d;
 
 namespace {
 
-constexpr int kVersion = 1 * 10000 + 0 * 100 + 0;
+constexpr int kVersion = 2 * 10000 + 0 * 100 + 0;
 
-enum Slot { kSlotLaplacian = 0, kSlotBilateral, kSlotMerge, kSlotFlatten, kSlotFilter, kSlotCopies };
-const char* const kSlotNames[PL3D_TIMING_SLOTS] = {"lap_smooth", "bilateral", "label_merge",
-                                                    "label_flatten", "label_filter", "host_copies"};
+// Timing slots: four phases of the frame kernel (device %globaltimer, accumulated by the
+// kernel), the kernel as a whole and the host copies (CUDA events on the call's stream).
+enum Slot { kSlotLap = 0, kSlotBil, kSlotMerge, kSlotLabels, kSlotKernel, kSlotCopies };
+const char* const kSlotNames[PL3D_TIMING_SLOTS] = {"laplacian", "bilateral", "label_merge",
+                                                    "label_flatten", "frame_kernel", "host_copies"};
 
 struct TimedRange {
     int slot;
@@ -38,15 +33,15 @@ struct TimedRange {
 
 struct pl3d_ctx {
     int device = 0;
-    int sm_count = 0;
     // scratch (grown to the largest frame)
-    float* points = nullptr;       // 2 x 3 planes of cap_points floats
+    float* disp = nullptr;          // 2 x 3 cap_points floats (AoS displacement ping-pong)
     size_t cap_points = 0;
-    float* carry = nullptr;        // 2 x cap_tri x 3 floats (multi-launch bilateral)
+    float* carry = nullptr;         // 2 x 3 cap_carry floats (multi-pass bilateral)
     size_t cap_carry = 0;
-    uint8_t* groups = nullptr;     // cap_tri
-    int32_t* sizes = nullptr;      // cap_tri
+    uint8_t* groups = nullptr;      // cap_tri
+    int32_t* sizes = nullptr;       // cap_tri
     size_t cap_tri = 0;
+    unsigned* ctl = nullptr;        // barrier [2], error word, pad, phase totals [4] (u64)
     // device staging for the host-buffer entry point
     float* st_points = nullptr;
     size_t st_cap_points = 0;
@@ -56,14 +51,21 @@ struct pl3d_ctx {
     size_t st_cap_tri = 0;
     // timing
     bool timing = false;
+    int64_t timed_frames = 0;
     std::vector<TimedRange> pending;
     std::vector<cudaEvent_t> free_events;
     double slot_ms[PL3D_TIMING_SLOTS] = {};
     int64_t slot_n[PL3D_TIMING_SLOTS] = {};
     int64_t launches = 0;
+
+    unsigned* barrier() const { return ctl; }
+    int* error() const { return reinterpret_cast<int*>(ctl + 2); }
+    unsigned long long* phase_ns() const { return reinterpret_cast<unsigned long long*>(ctl + 4); }
 };
 
 namespace {
+
+constexpr size_t kCtlBytes = 4 * sizeof(unsigned) + 4 * sizeof(unsigned long long);
 
 // Makes the context's device current for the duration of a call.
 struct DeviceGuard {
@@ -95,25 +97,22 @@ cudaEvent_t take_event(pl3d_ctx* c) {
     return e;
 }
 
-// Runs one launch, bracketed by events when timing is on.
-template <class F>
-int launch(pl3d_ctx* c, int slot, cudaStream_t s, F&& fn) {
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (c->timing) {
-        e0 = take_event(c);
-        e1 = take_event(c);
-        if (e0 && e1) cudaEventRecord(e0, s);
-    }
-    const cudaError_t err = fn();
-    if (e0 && e1) {
-        cudaEventRecord(e1, s);
-        c->pending.push_back({slot, e0, e1});
-    }
-    if (err != cudaSuccess) return PL3D_ERR_CUDA;
-    c->launches += 1;
-    return PL3D_OK;
+void record_start(pl3d_ctx* c, cudaStream_t s, cudaEvent_t* e0, cudaEvent_t* e1) {
+    *e0 = *e1 = nullptr;
+    if (!c->timing) return;
+    *e0 = take_event(c);
+    *e1 = take_event(c);
+    if (*e0 && *e1) cudaEventRecord(*e0, s);
 }
 
+void record_stop(pl3d_ctx* c, cudaStream_t s, int slot, cudaEvent_t e0, cudaEvent_t e1) {
+    if (!e0 || !e1) return;
+    cudaEventRecord(e1, s);
+    c->pending.push_back({slot, e0, e1});
+}
+
+// Frees and reallocates `*ptr` to hold `need` units of `elem_per` elements (plus headroom).
+// Waits for the stream first, since work in flight may still use the old buffer.
 template <class T>
 int grow(T** ptr, size_t* cap, size_t need, size_t elem_per, cudaStream_t s) {
     if (*cap >= need) return PL3D_OK;
@@ -123,7 +122,7 @@ int grow(T** ptr, size_t* cap, size_t need, size_t elem_per, cudaStream_t s) {
         *ptr = nullptr;
         *cap = 0;
     }
-    const size_t n = need + need / 8;   // headroom so that slightly larger frames do not regrow
+    const size_t n = need + need / 8;
     if (cudaMalloc((void**)ptr, n * elem_per * sizeof(T)) != cudaSuccess) {
         cudaGetLastError();
         *ptr = nullptr;
@@ -158,114 +157,28 @@ int run(pl3d_ctx* ctx, const float* points, int H, int W, const pl3d_params* p, 
     const size_t npts = (size_t)H * W;
     const size_t ntri = 2 * (size_t)(H - 1) * (W - 1);
     int rc;
-    if ((rc = grow(&ctx->points, &ctx->cap_points, npts, 6, s)) != PL3D_OK) return rc;
+    if ((rc = grow(&ctx->disp, &ctx->cap_points, npts, 6, s)) != PL3D_OK) return rc;
     if ((rc = grow_tri(ctx, ntri, s)) != PL3D_OK) return rc;
+    if (bilateral_passes(p) > 1 && (rc = grow(&ctx->carry, &ctx->cap_carry, ntri, 6, s)) != PL3D_OK) return rc;
 
-    // Dominant normals, normalised in double precision.
-    Dominant nd;
-    nd.K = K;
-    for (int j = 0; j < K; ++j) {
-        const double x = nd_host[3 * j], y = nd_host[3 * j + 1], z = nd_host[3 * j + 2];
-        const double len = sqrt(x * x + y * y + z * z);
-        nd.v[3 * j] = (float)(x / len);
-        nd.v[3 * j + 1] = (float)(y / len);
-        nd.v[3 * j + 2] = (float)(z / len);
-    }
+    FrameScratch sc;
+    sc.disp[0] = ctx->disp;
+    sc.disp[1] = ctx->disp + 3 * ctx->cap_points;
+    sc.carry[0] = ctx->carry;
+    sc.carry[1] = ctx->carry ? ctx->carry + 3 * ctx->cap_carry : nullptr;
+    sc.groups = ctx->groups;
+    sc.sizes = ctx->sizes;
+    sc.barrier = ctx->barrier();
+    sc.error = ctx->error();
+    sc.phase_ns = ctx->timing ? ctx->phase_ns() : nullptr;
 
-    float* buf[2][3];
-    for (int b = 0; b < 2; ++b)
-        for (int k = 0; k < 3; ++k) buf[b][k] = ctx->points + (size_t)(3 * b + k) * ctx->cap_points;
-
-    // ---- Laplacian (Eq. 1-2): displacements d with smoothed = points + d
-    const int lr = p->lap_iters > 0 ? p->lap_kernel / 2 : 1;
-    const int lfuse = kLapMaxHalo / lr;
-    int remaining = p->lap_iters;
-    int cur = 0;
-    bool first = true;
-    do {
-        const int it = remaining < lfuse ? remaining : lfuse;
-        LapArgs la{};
-        la.points = points;
-        la.in_dx = first ? nullptr : buf[cur][0];
-        la.in_dy = first ? nullptr : buf[cur][1];
-        la.in_dz = first ? nullptr : buf[cur][2];
-        const int nb = first ? cur : 1 - cur;
-        la.out_dx = buf[nb][0];
-        la.out_dy = buf[nb][1];
-        la.out_dz = buf[nb][2];
-        la.H = H;
-        la.W = W;
-        la.iters = it;
-        la.lambda = p->lap_lambda;
-        remaining -= it;
-        la.out_aos = remaining == 0 ? out_points : nullptr;
-        if ((rc = launch(ctx, kSlotLaplacian, s, [&] { return launch_laplacian(la, lr, s); })) != PL3D_OK) return rc;
-        cur = nb;
-        first = false;
-    } while (remaining > 0);
-    const float* dx = buf[cur][0];
-    const float* dy = buf[cur][1];
-    const float* dz = buf[cur][2];
-
-    // ---- normals, bilateral (Eq. 3-6), mask and groups (Algorithms 1, 4)
-    uint8_t* groups = out_groups ? out_groups : ctx->groups;
-    const int br = p->bil_iters > 0 ? p->bil_kernel / 2 : 1;
-    const int bfuse = kBilMaxHalo / br;
-    const int nchunks = p->bil_iters <= bfuse ? 1 : (p->bil_iters + bfuse - 1) / bfuse;
-    if (nchunks > 1 && (rc = grow(&ctx->carry, &ctx->cap_carry, ntri, 6, s)) != PL3D_OK) return rc;
-    float c_scale = 1.f, a_norm = 0.f;
-    bilateral_scales(p->bil_sigma_len, p->bil_sigma_ang, p->bil_iters, &c_scale, &a_norm);
-    int bremaining = p->bil_iters;
-    for (int c = 0; c < nchunks; ++c) {
-        const int it = bremaining < bfuse ? bremaining : bfuse;
-        bremaining -= it;
-        BilArgs ba;
-        ba.points = points;
-        ba.dx = dx;
-        ba.dy = dy;
-        ba.dz = dz;
-        ba.carry_in = c > 0 ? ctx->carry + (size_t)((c - 1) % 2) * 3 * ctx->cap_carry : nullptr;
-        ba.carry_out = c + 1 < nchunks ? ctx->carry + (size_t)(c % 2) * 3 * ctx->cap_carry : nullptr;
-        ba.out_mask = out_mask;
-        ba.out_normals = out_normals;
-        ba.out_groups = groups;
-        ba.out_labels = out_labels;
-        ba.H = H;
-        ba.W = W;
-        ba.iters = it;
-        ba.c_scale = c_scale;
-        ba.a_norm = a_norm;
-        ba.max_offset_scaled = p->max_offset > 0.f ? p->max_offset * c_scale : 0.f;
-        ba.sizes = p->min_triangles > 0 ? ctx->sizes : nullptr;
-        ba.max_edge2 = p->max_edge > 0.f ? p->max_edge * p->max_edge : INFINITY;
-        ba.min_dot = p->min_dot;
-        ba.nd = nd;
-        const bool f = c == 0, l = c + 1 == nchunks;
-        if ((rc = launch(ctx, kSlotBilateral, s, [&] { return launch_bilateral(ba, br, f, l, s); })) != PL3D_OK)
-            return rc;
-    }
-
-    // ---- planar segments (Algorithm 5)
-    LabelArgs lb;
-    lb.groups = groups;
-    lb.labels = out_labels;
-    lb.sizes = p->min_triangles > 0 ? ctx->sizes : nullptr;
-    lb.points = points;
-    lb.dx = dx;
-    lb.dy = dy;
-    lb.dz = dz;
-    lb.H = H;
-    lb.W = W;
-    lb.tile_h = kBilTileH;
-    lb.tile_w = kBilTileW;
-    lb.max_offset = p->max_offset;
-    lb.min_triangles = p->min_triangles;
-    lb.nd = nd;
-    if ((rc = launch(ctx, kSlotMerge, s, [&] { return launch_label_merge(lb, s); })) != PL3D_OK) return rc;
-    if ((rc = launch(ctx, kSlotFlatten, s, [&] { return launch_label_flatten(lb, s); })) != PL3D_OK) return rc;
-    if (p->min_triangles > 0 &&
-        (rc = launch(ctx, kSlotFilter, s, [&] { return launch_label_filter(lb, s); })) != PL3D_OK)
-        return rc;
+    cudaEvent_t e0, e1;
+    record_start(ctx, s, &e0, &e1);
+    rc = frame_launch(sc, points, H, W, p, nd_host, K, out_mask, out_normals, out_labels, out_points, out_groups, s);
+    record_stop(ctx, s, kSlotKernel, e0, e1);
+    if (rc != PL3D_OK) return rc;
+    ctx->launches += 1;
+    if (ctx->timing) ctx->timed_frames += 1;
     return PL3D_OK;
 }
 
@@ -312,19 +225,20 @@ int pl3d_default_params(pl3d_params* p) {
 int pl3d_validate(const pl3d_params* p, int H, int W, const float* nd, int K) {
     if (!p) return PL3D_ERR_INVALID_ARG;
     if (H < 2 || W < 2) return PL3D_ERR_INVALID_ARG;
-    if (2LL * (H - 1) * (long long)(W - 1) >= (1LL << 31) || (long long)H * W >= (1LL << 31))
-        return PL3D_ERR_INVALID_ARG;
+    if (2LL * (H - 1) * (long long)(W - 1) >= (1LL << 31) || 3LL * H * W >= (1LL << 31)) return PL3D_ERR_INVALID_ARG;
     if (K < 1 || K > PL3D_MAX_GROUPS) return PL3D_ERR_INVALID_ARG;
     if (p->flags != 0) return PL3D_ERR_INVALID_ARG;
     if (p->lap_iters < 0 || p->bil_iters < 0 || p->min_triangles < 0) return PL3D_ERR_INVALID_ARG;
     if (p->lap_iters > 0) {
         if (p->lap_kernel != 3 && p->lap_kernel != 5 && p->lap_kernel != 7) return PL3D_ERR_UNSUPPORTED;
         if (!finite_f(p->lap_lambda) || p->lap_lambda < 0.f || p->lap_lambda > 1.f) return PL3D_ERR_INVALID_ARG;
+        if (p->lap_iters > kMaxPasses * (kLapMaxHalo / (p->lap_kernel / 2))) return PL3D_ERR_UNSUPPORTED;
     }
     if (p->bil_iters > 0) {
         if (p->bil_kernel != 3 && p->bil_kernel != 5 && p->bil_kernel != 7) return PL3D_ERR_UNSUPPORTED;
         if (!finite_f(p->bil_sigma_len) || !(p->bil_sigma_len > 0.f)) return PL3D_ERR_INVALID_ARG;
         if (!finite_f(p->bil_sigma_ang) || !(p->bil_sigma_ang > 0.f)) return PL3D_ERR_INVALID_ARG;
+        if (p->bil_iters > kMaxPasses * (kBilMaxHalo / (p->bil_kernel / 2))) return PL3D_ERR_UNSUPPORTED;
     }
     if (!finite_f(p->max_edge) || !finite_f(p->min_dot) || !finite_f(p->max_offset)) return PL3D_ERR_INVALID_ARG;
     if (nd) {
@@ -349,16 +263,22 @@ int pl3d_create(pl3d_ctx** out, int cuda_device) {
     cudaDeviceProp prop;
     if (cudaGetDeviceProperties(&prop, cuda_device) != cudaSuccess) return PL3D_ERR_CUDA;
     if (prop.major != 10 || prop.minor != 3) return PL3D_ERR_UNSUPPORTED;
+    if (!prop.cooperativeLaunch) return PL3D_ERR_UNSUPPORTED;
     DeviceGuard g(cuda_device);
     if (!g.ok) return PL3D_ERR_CUDA;
-    if (laplacian_configure() != cudaSuccess || bilateral_configure() != cudaSuccess) {
+    if (frame_configure() != cudaSuccess) {
         cudaGetLastError();
         return PL3D_ERR_CUDA;
     }
     pl3d_ctx* c = new (std::nothrow) pl3d_ctx();
     if (!c) return PL3D_ERR_OUT_OF_MEMORY;
     c->device = cuda_device;
-    c->sm_count = prop.multiProcessorCount;
+    if (cudaMalloc((void**)&c->ctl, kCtlBytes) != cudaSuccess || cudaMemset(c->ctl, 0, kCtlBytes) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(c->ctl);
+        delete c;
+        return PL3D_ERR_OUT_OF_MEMORY;
+    }
     *out = c;
     return PL3D_OK;
 }
@@ -368,10 +288,11 @@ void pl3d_destroy(pl3d_ctx* c) {
     {
         DeviceGuard g(c->device);
         cudaDeviceSynchronize();
-        cudaFree(c->points);
+        cudaFree(c->disp);
         cudaFree(c->carry);
         cudaFree(c->groups);
         cudaFree(c->sizes);
+        cudaFree(c->ctl);
         cudaFree(c->st_points);
         cudaFree(c->st_mask);
         cudaFree(c->st_normals);
@@ -437,37 +358,23 @@ int pl3d_extract_planes_host(pl3d_ctx* ctx, const float* host_points, int H, int
         }
         ctx->st_cap_tri = n;
     }
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (ctx->timing) {
-        e0 = take_event(ctx);
-        e1 = take_event(ctx);
-        if (e0 && e1) cudaEventRecord(e0, s);
-    }
+    cudaEvent_t e0, e1;
+    record_start(ctx, s, &e0, &e1);
     if (cudaMemcpyAsync(ctx->st_points, host_points, npts * 3 * sizeof(float), cudaMemcpyHostToDevice, s) !=
         cudaSuccess)
         return PL3D_ERR_CUDA;
-    if (e0 && e1) {
-        cudaEventRecord(e1, s);
-        ctx->pending.push_back({kSlotCopies, e0, e1});
-    }
+    record_stop(ctx, s, kSlotCopies, e0, e1);
     rc = run(ctx, ctx->st_points, H, W, params, dominant_normals, K, ctx->st_mask, ctx->st_normals, ctx->st_labels,
              nullptr, nullptr, s);
     if (rc != PL3D_OK) return rc;
-    if (ctx->timing) {
-        e0 = take_event(ctx);
-        e1 = take_event(ctx);
-        if (e0 && e1) cudaEventRecord(e0, s);
-    }
+    record_start(ctx, s, &e0, &e1);
     if (cudaMemcpyAsync(host_tri_mask, ctx->st_mask, ntri, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaMemcpyAsync(host_normals, ctx->st_normals, ntri * 3 * sizeof(float), cudaMemcpyDeviceToHost, s) !=
             cudaSuccess ||
         cudaMemcpyAsync(host_labels, ctx->st_labels, ntri * sizeof(int32_t), cudaMemcpyDeviceToHost, s) !=
             cudaSuccess)
         return PL3D_ERR_CUDA;
-    if (e0 && e1) {
-        cudaEventRecord(e1, s);
-        ctx->pending.push_back({kSlotCopies, e0, e1});
-    }
+    record_stop(ctx, s, kSlotCopies, e0, e1);
     if (cudaStreamSynchronize(s) != cudaSuccess) return PL3D_ERR_CUDA;
     return PL3D_OK;
 }
@@ -478,6 +385,13 @@ int pl3d_sync(pl3d_ctx* ctx, void* stream) {
     if (!g.ok) return PL3D_ERR_CUDA;
     if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return PL3D_ERR_CUDA;
     if (cudaGetLastError() != cudaSuccess) return PL3D_ERR_CUDA;
+    int err = 0;
+    if (cudaMemcpy(&err, ctx->error(), sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return PL3D_ERR_CUDA;
+    if (err != 0) {
+        // a wait gave up: results of the affected calls are void; reset the barrier state
+        cudaMemset(ctx->ctl, 0, 4 * sizeof(unsigned));
+        return PL3D_ERR_TIMEOUT;
+    }
     return PL3D_OK;
 }
 
@@ -502,15 +416,31 @@ int pl3d_read_timing(pl3d_ctx* ctx, double* ms_out, int64_t* launches_out, int n
         ctx->free_events.push_back(r.stop);
     }
     ctx->pending.clear();
+    if (cudaDeviceSynchronize() != cudaSuccess) return PL3D_ERR_CUDA;
+    unsigned long long ns[4] = {0, 0, 0, 0};
+    if (cudaMemcpy(ns, ctx->phase_ns(), sizeof(ns), cudaMemcpyDeviceToHost) != cudaSuccess) return PL3D_ERR_CUDA;
+    double ms_all[PL3D_TIMING_SLOTS];
+    int64_t n_all[PL3D_TIMING_SLOTS];
+    for (int i = 0; i < PL3D_TIMING_SLOTS; ++i) {
+        ms_all[i] = ctx->slot_ms[i];
+        n_all[i] = ctx->slot_n[i];
+    }
+    for (int i = 0; i < 4; ++i) {
+        ms_all[i] = (double)ns[i] * 1e-6;
+        n_all[i] = ctx->timed_frames;
+    }
     for (int i = 0; i < n_slots && i < PL3D_TIMING_SLOTS; ++i) {
-        if (ms_out) ms_out[i] = ctx->slot_ms[i];
-        if (launches_out) launches_out[i] = ctx->slot_n[i];
+        if (ms_out) ms_out[i] = ms_all[i];
+        if (launches_out) launches_out[i] = n_all[i];
     }
     if (reset) {
         for (int i = 0; i < PL3D_TIMING_SLOTS; ++i) {
             ctx->slot_ms[i] = 0.0;
             ctx->slot_n[i] = 0;
         }
+        ctx->timed_frames = 0;
+        if (cudaMemset(ctx->phase_ns(), 0, sizeof(ns)) != cudaSuccess) return PL3D_ERR_CUDA;
+        if (cudaDeviceSynchronize() != cudaSuccess) return PL3D_ERR_CUDA;
     }
     return PL3D_TIMING_SLOTS;
 }

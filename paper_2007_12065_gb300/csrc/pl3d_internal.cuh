@@ -1,19 +1,19 @@
-// pl3d_internal.cuh -- declarations shared by the kernels and the C ABI of libpl3d.
+// pl3d_internal.cuh -- declarations shared by the frame kernel and the C ABI of libpl3d.
 //
 // Data layout in device memory (one frame of H x W points, Q = (H-1)(W-1) quads):
-//   input points     AoS  float [H][W][3]            (caller's buffer)
-//   displacements    SoA  float dx[H*W], dy[H*W], dz[H*W] (context scratch, ping-pong pair):
-//                    a smoothed point is the input point plus its displacement, kept as
-//                    that pair of floats (see df32.cuh)
-//   bilateral carry  AoS  float [2Q][3]               (context scratch, only when the
-//                                                      bilateral iterations need more than
-//                                                      one launch)
-//   groups           u8   [2Q]                        (context scratch or caller's buffer)
-//   labels           i32  [2Q]                        (caller's buffer; doubles as the
-//                                                      union-find parent array)
-//   segment sizes    i32  [2Q]                        (context scratch, only when tri_min > 0)
+//   input points     AoS  float [H][W][3]     (caller's buffer)
+//   displacements    AoS  float [H][W][3]     (scratch, ping-pong pair): a smoothed point is the
+//                                              input point plus its displacement, kept as that
+//                                              pair of floats (see df32.cuh)
+//   bilateral carry  AoS  float [2Q][3]       (scratch, only when the bilateral iterations need
+//                                              more than one tile pass)
+//   groups           u8   [2Q]                (scratch or the caller's buffer)
+//   labels           i32  [2Q]                (caller's buffer; doubles as the union-find parents)
+//   segment sizes    i32  [2Q]                (scratch, only when tri_min > 0)
+//   barrier, error   u32 [2], i32             (scratch: grid barrier state, device error word)
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -21,8 +21,10 @@
 
 namespace pl3d {
 
-// Largest supported filter radius (kernel size 7).
-constexpr int kMaxRadius = 3;
+constexpr int kThreads = 256;    // threads per CTA
+constexpr int kTile = 32;        // tile edge: 32 x 32 points (Laplacian) or quads (bilateral)
+constexpr int kLapMaxHalo = 8;   // largest halo (fused iterations x radius) of one Laplacian pass
+constexpr int kBilMaxHalo = 6;   // same for the bilateral
 
 // Centroid given to a triangle without a normal: its bilateral weight underflows to
 // exactly 0 against any real triangle, so it drops out of every sum without a branch.
@@ -41,88 +43,101 @@ __host__ __device__ __forceinline__ bool point_valid(float x, float y, float z) 
 // Finite stand-in for an invalid point inside the Laplacian's shared-memory tile.
 constexpr float kInvalidCoord = 1.0e30f;
 
+__host__ __device__ inline int div_up(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// Shared-memory buffers start on 128-byte boundaries (TMA destinations).
+__host__ __device__ inline int align_floats(int n) { return (n + 31) & ~31; }
+
 // Dominant normals, unit length, passed to kernels by value (3 KB, fits the parameter space).
 struct Dominant {
     int K;
     float v[PL3D_MAX_GROUPS * 3];
 };
 
-// ---------------------------------------------------------------- Laplacian (Eq. 1-2)
-struct LapArgs {
-    const float* points;                      // AoS input points (the v0 of every launch)
-    const float* in_dx;                       // displacement after the previous launch, or
-    const float* in_dy;                       // nullptr for the first launch (zero)
-    const float* in_dz;
-    float* out_dx;                            // displacement after this launch, SoA
-    float* out_dy;
-    float* out_dz;
-    float* out_aos;                           // optional AoS export of v0 + d (rounded)
+// A staged box: rows x cols floats of an AoS array seen as H rows of 3W floats. cols is a
+// multiple of 4 (16 bytes) and covers the tile's points plus up to 3 floats of alignment slack.
+struct BoxGeom {
+    int rows;
+    int cols;
+};
+
+struct LapPhase {
+    int iters;                     // Jacobi iterations fused in this pass
+    int halo;                      // iters * radius
+    int use_tma;                   // points staged by TMA (tm_pts_lap), else plain loads
+    BoxGeom box;                   // rows = 32 + 2 halo + 1 (a spare row), cols >= 3 (32 + 2 halo) + 3
+    const float* d_in;             // displacement after the previous pass, or nullptr (zero)
+    float* d_out;                  // displacement after this pass
+    float* export_points;          // optional AoS export of v0 + d (last pass only)
+};
+
+struct BilPhase {
+    int iters;
+    int halo;
+    int use_tma;                   // points and displacement staged by TMA (tm_pts_bil, tm_disp_bil)
+    BoxGeom box;                   // rows = 32 + 2 halo + 1, cols >= 3 (32 + 2 halo + 1) + 3
+    int first, last;               // first pass builds the normals; last pass finishes the quads
+    const float* carry_in;         // AoS [2Q][3] normals from the previous pass (not first)
+    float* carry_out;              // AoS [2Q][3] normals for the next pass (not last)
+};
+
+constexpr int kMaxPasses = 8;
+
+struct FrameArgs {
+    CUtensorMap tm_pts_lap;        // points, Laplacian box (first pass)
+    CUtensorMap tm_pts_bil;        // points, bilateral box
+    CUtensorMap tm_disp_bil;       // final displacement, bilateral box
+    const float* points;
+    const float* disp;             // final displacement, read by the bilateral and the merge
     int H, W;
-    int iters;                                // iterations fused in this launch (>= 0)
     float lambda;
-};
-// Tile of output points per CTA.
-constexpr int kLapTileH = 32;
-constexpr int kLapTileW = 32;
-constexpr int kLapThreads = 256;
-// Largest halo (fused iterations x radius) one launch may carry.
-constexpr int kLapMaxHalo = 8;
-cudaError_t launch_laplacian(const LapArgs& a, int radius, cudaStream_t s);
-// Opts the kernels in to their largest shared-memory size on the current device.
-cudaError_t laplacian_configure();
-size_t laplacian_smem_bytes(int radius, int iters);
-
-// ------------------- normals + bilateral (Eq. 3-6) + Algorithm 4 + tile-local Algorithm 5
-struct BilArgs {
-    const float* points;                      // AoS input points v0
-    const float* dx;                          // displacements, SoA (smoothed = v0 + d)
-    const float* dy;
-    const float* dz;
-    const float* carry_in;                    // AoS [2Q][3] normals from the previous launch (non-first)
-    float* carry_out;                         // AoS [2Q][3] normals for the next launch (non-last)
-    uint8_t* out_mask;                        // last launch only
+    int n_lap;
+    LapPhase lap[kMaxPasses];
+    int n_bil;
+    BilPhase bil[kMaxPasses];
+    uint8_t* out_mask;
     float* out_normals;
-    uint8_t* out_groups;
-    int32_t* out_labels;                      // GID of the tile-local root, or -1
-    int32_t* sizes;                           // zeroed for the merge/flatten passes, or nullptr
-    int H, W;
-    int iters;                                // iterations fused in this launch (>= 0)
-    float c_scale;                            // sqrt(log2(e) / (2 sigma_c^2)): centroid pre-scale
-    float a_norm;                             // log2(e) / sigma_s^2
-    float max_edge2;                          // l_max^2, or +inf when disabled
+    uint8_t* groups;
+    int32_t* labels;
+    int32_t* sizes;                // zeroed in the bilateral pass when tri_min > 0, else nullptr
+    float c_scale;                 // sqrt(log2(e) / (2 sigma_c^2)): centroid pre-scale
+    float a_norm;                  // log2(e) / sigma_s^2
+    float max_edge2;               // l_max^2, or +inf when disabled
     float min_dot;
-    float max_offset_scaled;                  // max_offset * c_scale, <= 0 when disabled
-    Dominant nd;
-};
-constexpr int kBilTileH = 32;                 // quads per CTA tile
-constexpr int kBilTileW = 32;
-constexpr int kBilThreads = 256;
-constexpr int kBilMaxHalo = 6;
-cudaError_t launch_bilateral(const BilArgs& a, int radius, bool first, bool last, cudaStream_t s);
-cudaError_t bilateral_configure();
-size_t bilateral_smem_bytes(int radius, int iters);
-// Host-side scale factors of the bilateral weights, kept finite and non-zero.
-void bilateral_scales(float sigma_c, float sigma_s, int iters, float* c_scale, float* a_norm);
-
-// ------------------------------------------- segments across tile borders (Algorithm 5)
-struct LabelArgs {
-    const uint8_t* groups;
-    int32_t* labels;                          // tile-local roots in, labels out
-    int32_t* sizes;                           // segment sizes (tri_min > 0) or nullptr
-    const float* points;                      // AoS input points and SoA displacements
-    const float* dx;                          // (offset test only)
-    const float* dy;
-    const float* dz;
-    int H, W;
-    int tile_h, tile_w;                       // the bilateral kernel's tile, in quads
-    float max_offset;                         // <= 0: no offset test
+    float max_offset;              // <= 0 when disabled
+    float max_offset_scaled;       // max_offset * c_scale
     int min_triangles;
+    unsigned* barrier;             // [2] grid barrier state
+    int* error;                    // device error word (sync.cuh bits)
+    unsigned long long* phase_ns;  // [4] accumulated phase times, or nullptr
     Dominant nd;
 };
-cudaError_t launch_label_merge(const LabelArgs& a, cudaStream_t s);
-cudaError_t launch_label_flatten(const LabelArgs& a, cudaStream_t s);
-cudaError_t launch_label_filter(const LabelArgs& a, cudaStream_t s);
 
-__host__ __device__ inline int div_up(long long a, long long b) { return (int)((a + b - 1) / b); }
+template <int RL, int RB>
+__global__ void frame_kernel(const __grid_constant__ FrameArgs a);
+
+// --------------------------------------------------------------------------- host side
+
+// Device buffers one frame needs besides its inputs and outputs.
+struct FrameScratch {
+    float* disp[2];                // >= 3 H W floats each, 16-byte aligned
+    float* carry[2];               // >= 6 Q floats each when the bilateral needs several passes
+    uint8_t* groups;               // >= 2 Q
+    int32_t* sizes;                // >= 2 Q
+    unsigned* barrier;             // [2], zero before the first use
+    int* error;                    // [1]
+    unsigned long long* phase_ns;  // [4] or nullptr
+};
+
+// Number of bilateral passes the parameters need (> 1 needs the carry buffers).
+int bilateral_passes(const pl3d_params* p);
+
+// Sets the shared-memory opt-in of every frame kernel on the current device.
+cudaError_t frame_configure();
+
+// Enqueues the whole path for one frame on `s` (one cooperative launch). Returns a PL3D status.
+int frame_launch(const FrameScratch& sc, const float* points, int H, int W, const pl3d_params* p, const float* nd_host,
+                 int K, uint8_t* out_mask, float* out_normals, int32_t* out_labels, float* out_points,
+                 uint8_t* out_groups, cudaStream_t s);
 
 }  // namespace pl3d

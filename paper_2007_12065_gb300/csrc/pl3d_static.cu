@@ -5,7 +5,8 @@
 // cause, a process whose memory budget was fixed when it started, or a caller with no
 // context object to keep (plugins that get a stream and buffers per call). Such a caller
 // passes its inputs and outputs; the scratch the path needs (point displacements, groups,
-// segment sizes) lives in the file-scope device array below instead of in a context.
+// segment sizes, the grid-barrier and error words) lives in the file-scope device array below
+// instead of in a context.
 //
 // The array is part of the library's device code, so every GPU on which the library's
 // kernels load holds it (static_scratch_bytes(), about 10.4 MB) until the process exits.
@@ -16,8 +17,9 @@
 //
 // All calls share the one array: calls whose work overlaps on the GPU (different streams,
 // or host threads that do not order their streams) race on it and must be serialised by
-// the caller. Nothing in it needs clearing between calls -- every scratch value is written
-// before it is read within a call.
+// the caller. Nothing in it needs clearing between calls: every scratch value is written before
+// it is read within a call, and the barrier words return to their starting state at the end of
+// each call (the array starts zeroed when the library's device code loads).
 #include <float.h>
 #include <math.h>
 
@@ -31,10 +33,11 @@ namespace {
 
 constexpr size_t kMaxPoints = PL3D_STATIC_MAX_POINTS;
 constexpr size_t kMaxTri = 2 * kMaxPoints;                       // 2(H-1)(W-1) < 2 H W
-constexpr size_t kDispBytes = 6 * kMaxPoints * sizeof(float);    // displacement ping-pong, SoA
+constexpr size_t kDispBytes = 6 * kMaxPoints * sizeof(float);    // displacement ping-pong, AoS
 constexpr size_t kGroupBytes = (kMaxTri + 255) / 256 * 256;
 constexpr size_t kSizeBytes = kMaxTri * sizeof(int32_t);
-constexpr size_t kScratchBytes = kDispBytes + kGroupBytes + kSizeBytes;
+constexpr size_t kCtlBytes = 256;                                // barrier [2], error word
+constexpr size_t kScratchBytes = kDispBytes + kGroupBytes + kSizeBytes + kCtlBytes;
 
 static __device__ __align__(256) unsigned char g_static_scratch[kScratchBytes];
 
@@ -58,12 +61,12 @@ int setup_device(int dev, unsigned char** scratch) {
             cudaGetLastError();
             return PL3D_ERR_CUDA;   // not cached: a later call may succeed
         }
-        if (prop.major != 10 || prop.minor != 3) {
+        if (prop.major != 10 || prop.minor != 3 || !prop.cooperativeLaunch) {
             s.status = PL3D_ERR_UNSUPPORTED;
         } else if (cudaGetSymbolAddress((void**)&s.scratch, g_static_scratch) != cudaSuccess) {
             cudaGetLastError();
             return PL3D_ERR_CUDA;
-        } else if (laplacian_configure() != cudaSuccess || bilateral_configure() != cudaSuccess) {
+        } else if (frame_configure() != cudaSuccess) {
             cudaGetLastError();
             return PL3D_ERR_CUDA;
         } else {
@@ -86,8 +89,7 @@ extern "C" int pl3d_extract_planes_static(const float* points, int H, int W, con
     int rc = pl3d_validate(p, H, W, nd_host, K);
     if (rc != PL3D_OK) return rc;
     if ((size_t)H * (size_t)W > kMaxPoints) return PL3D_ERR_INVALID_ARG;
-    const int br = p->bil_iters > 0 ? p->bil_kernel / 2 : 1;
-    if (p->bil_iters > kBilMaxHalo / br) return PL3D_ERR_INVALID_ARG;   // would need the carry buffers
+    if (bilateral_passes(p) > 1) return PL3D_ERR_INVALID_ARG;   // would need the carry buffers
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();
@@ -95,97 +97,17 @@ extern "C" int pl3d_extract_planes_static(const float* points, int H, int W, con
     }
     unsigned char* scratch = nullptr;
     if ((rc = setup_device(dev, &scratch)) != PL3D_OK) return rc;
-    cudaStream_t s = (cudaStream_t)stream;
 
-    float* disp = (float*)scratch;
-    uint8_t* groups = scratch + kDispBytes;
-    int32_t* sizes = (int32_t*)(scratch + kDispBytes + kGroupBytes);
-    const size_t npts = (size_t)H * W;
-    float* buf[2][3];
-    for (int b = 0; b < 2; ++b)
-        for (int k = 0; k < 3; ++k) buf[b][k] = disp + (size_t)(3 * b + k) * npts;
-
-    Dominant nd;
-    nd.K = K;
-    for (int j = 0; j < K; ++j) {
-        const double x = nd_host[3 * j], y = nd_host[3 * j + 1], z = nd_host[3 * j + 2];
-        const double len = sqrt(x * x + y * y + z * z);
-        nd.v[3 * j] = (float)(x / len);
-        nd.v[3 * j + 1] = (float)(y / len);
-        nd.v[3 * j + 2] = (float)(z / len);
-    }
-
-    // Laplacian launches (displacement ping-pong in the static array).
-    const int lr = p->lap_iters > 0 ? p->lap_kernel / 2 : 1;
-    const int lfuse = kLapMaxHalo / lr;
-    int remaining = p->lap_iters, cur = 0;
-    bool first = true;
-    do {
-        const int it = remaining < lfuse ? remaining : lfuse;
-        LapArgs la{};
-        la.points = points;
-        la.in_dx = first ? nullptr : buf[cur][0];
-        la.in_dy = first ? nullptr : buf[cur][1];
-        la.in_dz = first ? nullptr : buf[cur][2];
-        const int nb = first ? cur : 1 - cur;
-        la.out_dx = buf[nb][0];
-        la.out_dy = buf[nb][1];
-        la.out_dz = buf[nb][2];
-        la.H = H;
-        la.W = W;
-        la.iters = it;
-        la.lambda = p->lap_lambda;
-        la.out_aos = nullptr;
-        remaining -= it;
-        if (launch_laplacian(la, lr, s) != cudaSuccess) return PL3D_ERR_CUDA;
-        cur = nb;
-        first = false;
-    } while (remaining > 0);
-
-    // Normals, bilateral, mask and groups in one launch.
-    float c_scale = 1.f, a_norm = 0.f;
-    bilateral_scales(p->bil_sigma_len, p->bil_sigma_ang, p->bil_iters, &c_scale, &a_norm);
-    BilArgs ba;
-    ba.points = points;
-    ba.dx = buf[cur][0];
-    ba.dy = buf[cur][1];
-    ba.dz = buf[cur][2];
-    ba.carry_in = nullptr;
-    ba.carry_out = nullptr;
-    ba.out_mask = out_mask;
-    ba.out_normals = out_normals;
-    ba.out_groups = groups;
-    ba.out_labels = out_labels;
-    ba.H = H;
-    ba.W = W;
-    ba.iters = p->bil_iters;
-    ba.c_scale = c_scale;
-    ba.a_norm = a_norm;
-    ba.max_offset_scaled = p->max_offset > 0.f ? p->max_offset * c_scale : 0.f;
-    ba.sizes = p->min_triangles > 0 ? sizes : nullptr;
-    ba.max_edge2 = p->max_edge > 0.f ? p->max_edge * p->max_edge : INFINITY;
-    ba.min_dot = p->min_dot;
-    ba.nd = nd;
-    if (launch_bilateral(ba, br, true, true, s) != cudaSuccess) return PL3D_ERR_CUDA;
-
-    // Planar segments across tile borders; the bilateral pass zeroed the segment sizes.
-    LabelArgs lb;
-    lb.groups = groups;
-    lb.labels = out_labels;
-    lb.sizes = p->min_triangles > 0 ? sizes : nullptr;
-    lb.points = points;
-    lb.dx = buf[cur][0];
-    lb.dy = buf[cur][1];
-    lb.dz = buf[cur][2];
-    lb.H = H;
-    lb.W = W;
-    lb.tile_h = kBilTileH;
-    lb.tile_w = kBilTileW;
-    lb.max_offset = p->max_offset;
-    lb.min_triangles = p->min_triangles;
-    lb.nd = nd;
-    if (launch_label_merge(lb, s) != cudaSuccess) return PL3D_ERR_CUDA;
-    if (launch_label_flatten(lb, s) != cudaSuccess) return PL3D_ERR_CUDA;
-    if (p->min_triangles > 0 && launch_label_filter(lb, s) != cudaSuccess) return PL3D_ERR_CUDA;
-    return PL3D_OK;
+    FrameScratch sc;
+    sc.disp[0] = reinterpret_cast<float*>(scratch);
+    sc.disp[1] = sc.disp[0] + 3 * kMaxPoints;
+    sc.carry[0] = sc.carry[1] = nullptr;
+    sc.groups = scratch + kDispBytes;
+    sc.sizes = reinterpret_cast<int32_t*>(scratch + kDispBytes + kGroupBytes);
+    unsigned* ctl = reinterpret_cast<unsigned*>(scratch + kDispBytes + kGroupBytes + kSizeBytes);
+    sc.barrier = ctl;
+    sc.error = reinterpret_cast<int*>(ctl + 2);
+    sc.phase_ns = nullptr;
+    return frame_launch(sc, points, H, W, p, nd_host, K, out_mask, out_normals, out_labels, nullptr, nullptr,
+                        (cudaStream_t)stream);
 }

@@ -1,0 +1,105 @@
+// sync.cuh -- TMA tile loads, mbarriers and a grid-wide barrier, all with bounded waits.
+//
+// Every wait here gives up after kWaitLimitNs of %globaltimer time (and an iteration cap),
+// records the reason in the frame's device error word and returns, so a fault elsewhere
+// surfaces as PL3D_ERR_TIMEOUT on the host instead of a hung GPU.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pl3d {
+
+constexpr uint64_t kWaitLimitNs = 1000000000ull;   // 1 s
+constexpr int kErrTmaTimeout = 1;                  // bits of the device error word
+constexpr int kErrBarrierTimeout = 2;
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Orders earlier generic-proxy accesses (this CTA's shared memory; global memory written by
+// any CTA before a grid barrier) before later async-proxy (TMA) accesses.
+__device__ __forceinline__ void fence_proxy_async_all() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// 2-D tiled TMA load of a box at element coordinates (x, y) into shared memory; completion is
+// counted in bytes on `bar`. x * element size must be a multiple of 16 bytes.
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Waits for the phase `parity` of `bar` to complete. On timeout it records the error, waits
+// once more (bounded) for the copies still in flight, and returns false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, int* err) {
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        const uint64_t t0 = global_ns();
+        for (uint32_t i = 0; i < (1u << 28); ++i) {
+            if (mbar_try_wait(bar, parity)) return attempt == 0;
+            if ((i & 63u) == 63u && global_ns() - t0 > kWaitLimitNs) break;
+        }
+        if (attempt == 0) atomicOr(err, kErrTmaTimeout);
+    }
+    return false;
+}
+
+// Grid-wide barrier for a co-resident (cooperatively launched) grid. bar[0] counts arrivals,
+// bar[1] is the generation; the last CTA to arrive resets the count and advances the
+// generation. Global writes made before the barrier are visible to every CTA after it.
+__device__ __forceinline__ void grid_barrier(unsigned* bar, int* err) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* vgen = bar + 1;
+        const unsigned nblocks = gridDim.x * gridDim.y * gridDim.z;
+        const unsigned g = *vgen;
+        __threadfence();
+        if (atomicAdd(bar, 1u) + 1u == nblocks) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            const uint64_t t0 = global_ns();
+            for (uint32_t i = 1; *vgen == g; ++i) {
+                if ((i & 63u) == 0u && global_ns() - t0 > kWaitLimitNs) {
+                    atomicOr(err, kErrBarrierTimeout);
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+}  // namespace pl3d
