@@ -137,6 +137,10 @@ cudaError_t frame_configure() {
         for (int rb = 1; rb <= 3; ++rb) {
             cudaError_t e = cudaFuncSetAttribute(kernel_for(rl, rb), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)need);
+            // all of the unified L1 / shared storage as shared memory, so that two CTAs fit per SM
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(kernel_for(rl, rb), cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         cudaSharedmemCarveoutMaxShared);
             if (e != cudaSuccess) return e;
         }
     return cudaSuccess;

@@ -4,6 +4,11 @@
 // labels (and the tri_min filter). Each CTA loops over the tiles of a phase; the grid barrier
 // (sync.cuh) orders the phases. Included once per (Laplacian radius, bilateral radius).
 //
+// Bilateral arithmetic (Eq. 3-6): centroids are stored pre-scaled by sqrt(log2(e) / (2 sigma_c^2))
+// and, for unit normals, |n_i - n_j|^2 = 2 - 2 n_i . n_j, so W_c W_s for a pair is one base-2
+// exponential of -(|c'_i - c'_j|^2 + a - a n_i . n_j), a = log2(e) / sigma_s^2; a triangle is
+// filtered against both triangles of a neighbour quad at once with paired FP32 instructions.
+//
 // Tiles are staged from HBM with TMA: the input points and the displacements are both AoS
 // [H][W][3] floats, seen as 2-D tensors of H rows x 3W floats, so one box per array covers a
 // tile plus its halo (points outside the image read as NaN, displacements as 0). The box's x
@@ -16,6 +21,7 @@
 #include <math.h>
 
 #include "df32.cuh"
+#include "f32x2.cuh"
 #include "pl3d_internal.cuh"
 #include "sync.cuh"
 #include "uf.cuh"
@@ -267,20 +273,28 @@ __device__ __forceinline__ V3 centroid3(const SP& a, const SP& b, const SP& c) {
             ((a.z + b.z + c.z) + (a.dz + b.dz + c.dz)) * k};
 }
 
-// Per-quad records in shared memory: 6 floats (triangle 0 xyz, triangle 1 xyz) read and
-// written as three float2.
+// Per-quad records in shared memory: 6 floats interleaving the quad's two triangles,
+// {x0, x1, y0, y1, z0, z1}, so that each 64-bit load yields one coordinate of both triangles as
+// a packed pair (f32x2.cuh).
 __device__ __forceinline__ void load_quad(const float* A, int q, V3& t0, V3& t1) {
     const float2* p = reinterpret_cast<const float2*>(A) + 3 * q;
-    const float2 u = p[0], v = p[1], w = p[2];
-    t0 = {u.x, u.y, v.x};
-    t1 = {v.y, w.x, w.y};
+    const float2 x = p[0], y = p[1], z = p[2];
+    t0 = {x.x, y.x, z.x};
+    t1 = {x.y, y.y, z.y};
+}
+
+__device__ __forceinline__ void load_quad2(const float* A, int q, f2& x, f2& y, f2& z) {
+    const f2* p = reinterpret_cast<const f2*>(A) + 3 * q;
+    x = p[0];
+    y = p[1];
+    z = p[2];
 }
 
 __device__ __forceinline__ void store_quad(float* A, int q, V3 t0, V3 t1) {
     float2* p = reinterpret_cast<float2*>(A) + 3 * q;
-    p[0] = make_float2(t0.x, t0.y);
-    p[1] = make_float2(t0.z, t1.x);
-    p[2] = make_float2(t1.y, t1.z);
+    p[0] = make_float2(t0.x, t1.x);
+    p[1] = make_float2(t0.y, t1.y);
+    p[2] = make_float2(t0.z, t1.z);
 }
 
 __device__ __forceinline__ bool has_normal(V3 n) { return n.x != 0.f || n.y != 0.f || n.z != 0.f; }
@@ -292,41 +306,83 @@ __device__ __forceinline__ V3 finish_normal(V3 s, V3 own) {
     return {s.x * inv, s.y * inv, s.z * inv};
 }
 
-// One pair (i, j): s_i += W n_j with W = ex2(-|c'_i - c'_j|^2 + p_i . n_j - a), p_i = a n_i.
-__device__ __forceinline__ void accumulate(V3& s, V3 ci, V3 pi, float a, V3 cj, V3 nj) {
-    const float dx = ci.x - cj.x, dy = ci.y - cj.y, dz = ci.z - cj.z;
-    float e = fmaf(pi.x, nj.x, fmaf(pi.y, nj.y, fmaf(pi.z, nj.z, -a)));
-    e = fmaf(-dx, dx, fmaf(-dy, dy, fmaf(-dz, dz, e)));
-    const float w = ex2(e);
-    s.x = fmaf(w, nj.x, s.x);
-    s.y = fmaf(w, nj.y, s.y);
-    s.z = fmaf(w, nj.z, s.z);
-}
-
-struct QuadAcc {
-    V3 c0, c1;   // scaled centroids
-    V3 n0, n1;   // current normals
-    V3 p0, p1;   // a * normals
-    V3 s0, s1;   // weighted sums
+// One own triangle i against the two triangles of a neighbour quad at once, in packed pairs:
+//   W_j = ex2(-(|c'_i - c'_j|^2 + a - a n_i . n_j)),   s_i += W_j n_j   (j = both triangles)
+// The state holds i's centroid and -a n_i broadcast to both halves, and the two halves of the
+// running sum (added together at the end).
+struct OwnTri {
+    f2 cx, cy, cz;
+    f2 px, py, pz;
+    f2 sx, sy, sz;
 };
 
-__device__ __forceinline__ void quad_begin(QuadAcc& A, const float* Cq, const float* cur, int q, float a) {
-    load_quad(Cq, q, A.c0, A.c1);
-    load_quad(cur, q, A.n0, A.n1);
-    A.p0 = {a * A.n0.x, a * A.n0.y, a * A.n0.z};
-    A.p1 = {a * A.n1.x, a * A.n1.y, a * A.n1.z};
-    // the triangle itself (weight exactly 1) and its partner in the quad
-    A.s0 = A.n0;
-    A.s1 = A.n1;
-    accumulate(A.s0, A.c0, A.p0, a, A.c1, A.n1);
-    accumulate(A.s1, A.c1, A.p1, a, A.c0, A.n0);
+__device__ __forceinline__ void own_begin(OwnTri& o, V3 c, V3 n, float a) {
+    o.cx = bc(c.x);
+    o.cy = bc(c.y);
+    o.cz = bc(c.z);
+    o.px = bc(-a * n.x);
+    o.py = bc(-a * n.y);
+    o.pz = bc(-a * n.z);
+    o.sx = o.sy = o.sz = 0ull;
 }
 
-__device__ __forceinline__ void quad_neighbour(QuadAcc& A, float a, V3 cj0, V3 cj1, V3 nj0, V3 nj1) {
-    accumulate(A.s0, A.c0, A.p0, a, cj0, nj0);
-    accumulate(A.s0, A.c0, A.p0, a, cj1, nj1);
-    accumulate(A.s1, A.c1, A.p1, a, cj0, nj0);
-    accumulate(A.s1, A.c1, A.p1, a, cj1, nj1);
+__device__ __forceinline__ f2 own_weights(const OwnTri& o, f2 a2, f2 cx, f2 cy, f2 cz, f2 nx, f2 ny, f2 nz) {
+    const f2 dx = sub2(o.cx, cx), dy = sub2(o.cy, cy), dz = sub2(o.cz, cz);
+    f2 ne = fma2(o.px, nx, a2);
+    ne = fma2(o.py, ny, ne);
+    ne = fma2(o.pz, nz, ne);
+    ne = fma2(dz, dz, ne);
+    ne = fma2(dy, dy, ne);
+    ne = fma2(dx, dx, ne);
+    float e0, e1;
+    upk(ne, e0, e1);
+    return pk(ex2(-e0), ex2(-e1));
+}
+
+__device__ __forceinline__ void own_add(OwnTri& o, f2 w, f2 nx, f2 ny, f2 nz) {
+    o.sx = fma2(w, nx, o.sx);
+    o.sy = fma2(w, ny, o.sy);
+    o.sz = fma2(w, nz, o.sz);
+}
+
+__device__ __forceinline__ V3 own_sum(const OwnTri& o) {
+    float a, b, c, d, e, f;
+    upk(o.sx, a, b);
+    upk(o.sy, c, d);
+    upk(o.sz, e, f);
+    return {a + b, c + d, e + f};
+}
+
+// A quad's two triangles: their own quad first (each triangle's weight with itself is exactly 1).
+struct QuadAcc {
+    OwnTri t0, t1;
+    V3 n0, n1;   // current normals (a triangle without a normal keeps n = 0)
+};
+
+__device__ __forceinline__ void quad_begin(QuadAcc& A, const float* Cq, const float* cur, int q, float a, f2 a2) {
+    f2 cx, cy, cz, nx, ny, nz;
+    load_quad2(Cq, q, cx, cy, cz);
+    load_quad2(cur, q, nx, ny, nz);
+    float c0x, c1x, c0y, c1y, c0z, c1z, n0x, n1x, n0y, n1y, n0z, n1z;
+    upk(cx, c0x, c1x);
+    upk(cy, c0y, c1y);
+    upk(cz, c0z, c1z);
+    upk(nx, n0x, n1x);
+    upk(ny, n0y, n1y);
+    upk(nz, n0z, n1z);
+    A.n0 = {n0x, n0y, n0z};
+    A.n1 = {n1x, n1y, n1z};
+    own_begin(A.t0, {c0x, c0y, c0z}, A.n0, a);
+    own_begin(A.t1, {c1x, c1y, c1z}, A.n1, a);
+    const f2 w0 = own_weights(A.t0, a2, cx, cy, cz, nx, ny, nz);
+    own_add(A.t0, pk(1.f, hi_of(w0)), nx, ny, nz);
+    const f2 w1 = own_weights(A.t1, a2, cx, cy, cz, nx, ny, nz);
+    own_add(A.t1, pk(lo_of(w1), 1.f), nx, ny, nz);
+}
+
+__device__ __forceinline__ void quad_neighbour(QuadAcc& A, f2 a2, f2 cx, f2 cy, f2 cz, f2 nx, f2 ny, f2 nz) {
+    own_add(A.t0, own_weights(A.t0, a2, cx, cy, cz, nx, ny, nz), nx, ny, nz);
+    own_add(A.t1, own_weights(A.t1, a2, cx, cy, cz, nx, ny, nz), nx, ny, nz);
 }
 
 // One bilateral tile: T x T quads; geometry, `ph.iters` fused iterations (Eq. 3-6), then either
@@ -459,6 +515,7 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
     float* cur = Na;
     float* nxt = Nb;
     const float an = a.a_norm;
+    const f2 a2 = bc(an);
     for (int it = 1; it <= ph.iters; ++it) {
         const int lo = it * R;
         const int ch = RQH - 2 * lo, cw = RQW - 2 * lo;
@@ -469,8 +526,8 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
             const bool two = qr + 1 < RQH - lo;
             const int qA = qr * RQW + qc, qB = qA + RQW;
             QuadAcc A, B;
-            quad_begin(A, Cq, cur, qA, an);
-            quad_begin(B, Cq, cur, qB, an);
+            quad_begin(A, Cq, cur, qA, an, a2);
+            quad_begin(B, Cq, cur, qB, an, a2);
 #pragma unroll
             for (int dr = -R; dr <= R + 1; ++dr) {
 #pragma unroll
@@ -478,15 +535,15 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
                     const bool forA = dr <= R && !(dr == 0 && dc == 0);
                     const bool forB = dr >= 1 - R && !(dr == 1 && dc == 0);
                     const int qj = qA + dr * RQW + dc;
-                    V3 cj0, cj1, nj0, nj1;
-                    load_quad(Cq, qj, cj0, cj1);
-                    load_quad(cur, qj, nj0, nj1);
-                    if (forA) quad_neighbour(A, an, cj0, cj1, nj0, nj1);
-                    if (forB) quad_neighbour(B, an, cj0, cj1, nj0, nj1);
+                    f2 cx, cy, cz, nx, ny, nz;
+                    load_quad2(Cq, qj, cx, cy, cz);
+                    load_quad2(cur, qj, nx, ny, nz);
+                    if (forA) quad_neighbour(A, a2, cx, cy, cz, nx, ny, nz);
+                    if (forB) quad_neighbour(B, a2, cx, cy, cz, nx, ny, nz);
                 }
             }
-            store_quad(nxt, qA, finish_normal(A.s0, A.n0), finish_normal(A.s1, A.n1));
-            if (two) store_quad(nxt, qB, finish_normal(B.s0, B.n0), finish_normal(B.s1, B.n1));
+            store_quad(nxt, qA, finish_normal(own_sum(A.t0), A.n0), finish_normal(own_sum(A.t1), A.n1));
+            if (two) store_quad(nxt, qB, finish_normal(own_sum(B.t0), B.n0), finish_normal(own_sum(B.t1), B.n1));
         }
         __syncthreads();
         float* tmp = cur;
@@ -628,7 +685,9 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
             const int t = 2 * i + k;
             int lab = -1;
             if (Lp[t] >= 0) {
-                const int root = uf_root(Lp, t);
+                // no union runs any more: halving the path while walking only ever points a
+                // node at one of its ancestors, and shortens the walks of the other threads
+                const int root = uf_find(Lp, t);
                 const int rq = root >> 1, rr = rq / T, rc = rq - rr * T;
                 lab = (int)(2 * ((size_t)(ty * T + rr) * Wq + (tx * T + rc)) + (root & 1));
             }
@@ -732,7 +791,7 @@ __device__ __forceinline__ void phase_mark(const FrameArgs& a, int slot, uint64_
 }  // namespace frame
 
 template <int RL, int RB>
-__global__ void __launch_bounds__(kThreads) frame_kernel(const __grid_constant__ FrameArgs a) {
+__global__ void __launch_bounds__(kThreads, 2) frame_kernel(const __grid_constant__ FrameArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
     float* smem = reinterpret_cast<float*>(smem_raw + 128);
