@@ -192,6 +192,148 @@ int pl3d_extract_planes_static(const float* points, int H, int W, const pl3d_par
 /* Bytes of device memory the allocation-free entry point reserves on every GPU. */
 size_t pl3d_static_scratch_bytes(void);
 
+/*
+ * Batches. The paper runs its pipeline one frame at a time; a batch runs the whole path of
+ * pl3d_extract_planes_ex (same arguments per frame, same results bit for bit) on many frames
+ * of any sizes in ONE persistent cooperative launch, replayed from a CUDA graph. Each phase
+ * (Laplacian tiles, bilateral tiles, tile-border merge, labels) spans the work of all frames,
+ * so small frames no longer leave most of the GPU idle.
+ *
+ * pl3d_frame describes one frame; pointers and sizes as in pl3d_extract_planes_ex (points and
+ * outputs on the device, params and dominant_normals on the host; out_points and out_groups
+ * may be NULL). Frames of one batch may differ in size, iteration counts and thresholds, but
+ * every frame with lap_iters > 0 must use one lap_kernel and every frame with bil_iters > 0 one
+ * bil_kernel (else PL3D_ERR_UNSUPPORTED). Output buffers of different frames must not overlap.
+ *
+ * pl3d_extract_planes_batched enqueues the batch on `stream`. Host work: it validates every
+ * frame (any invalid frame rejects the whole batch before anything is enqueued), fills a
+ * descriptor block in page-locked memory and copies it to the device unless it is identical to
+ * the last one, then launches the graph for the batch's launch shape (built on first use).
+ * Scratch for all frames of the batch comes from one slab of the context that grows to the
+ * largest batch (growth synchronises the stream). n == 0 does nothing. Calls are ordered on
+ * the stream like every other call on the context.
+ */
+typedef struct pl3d_frame {
+    const float* points;
+    int32_t H;
+    int32_t W;
+    const pl3d_params* params;
+    const float* dominant_normals;
+    int32_t K;
+    uint8_t* out_tri_mask;
+    float* out_normals;
+    int32_t* out_labels;
+    float* out_points;
+    uint8_t* out_groups;
+} pl3d_frame;
+
+int pl3d_extract_planes_batched(pl3d_ctx* ctx, const pl3d_frame* frames, int n, void* stream);
+
+/*
+ * Launch shape of every later call on the context (single frames and batches). None of these
+ * changes a result bit: iterations split over more passes go through global memory as the same
+ * FP32 values the fused form keeps in shared memory.
+ *   lap_fuse     most Laplacian iterations fused into one tile pass (0 = as many as the tile's
+ *                halo of 8 points allows); fewer means smaller halos but more passes.
+ *   bil_fuse     the same for the bilateral (halo of 6 quads).
+ *                Either depth is raised where needed so that a filter takes at most 8 passes.
+ *   ctas_per_sm  resident CTAs per SM of the persistent launch (0 = as many as fit, at most 2).
+ * pl3d_set_tuning(ctx, NULL) restores the defaults {0, 0, 0}. Negative fields are rejected.
+ */
+typedef struct pl3d_tuning {
+    int32_t lap_fuse;
+    int32_t bil_fuse;
+    int32_t ctas_per_sm;
+} pl3d_tuning;
+
+int pl3d_set_tuning(pl3d_ctx* ctx, const pl3d_tuning* tuning);
+int pl3d_get_tuning(const pl3d_ctx* ctx, pl3d_tuning* tuning);
+
+/*
+ * Autotuner: times the batch under every launch shape of a small candidate set (fused depths
+ * of 1, 2 or 3 passes per filter, 1 or 2 CTAs per SM), `reps` timed runs each after one
+ * untimed run, on `stream` with CUDA events, and keeps the fastest median as the context's
+ * tuning. Writes the choice to *best and its median milliseconds to *best_ms (either may be
+ * NULL). Runs the batch (1 + reps) times per candidate and once more under the choice, so the
+ * outputs hold that run's (identical) results. Synchronises the stream. reps in [1, 50].
+ */
+int pl3d_autotune_batched(pl3d_ctx* ctx, const pl3d_frame* frames, int n, void* stream, int reps,
+                          pl3d_tuning* best, double* best_ms);
+
+/* Counters of the batch machinery: graph launches, descriptor uploads (a batch identical to
+ * the previous one skips its upload) and graphs instantiated. Any pointer may be NULL. */
+int pl3d_batch_stats(const pl3d_ctx* ctx, int64_t* graph_launches, int64_t* desc_uploads, int64_t* graphs);
+
+/*
+ * Serving (no counterpart in the paper). A server takes frames from any number of sensors as
+ * they arrive and runs them with continuous batching: a worker thread owns `max_inflight`
+ * slots, each with its own stream, context and device arena; whenever a slot is free it takes
+ * the waiting requests in arrival order, as many as its arena has room for (admission by free
+ * HBM) up to `max_batch_frames`, copies their points in, runs them as one batch
+ * (pl3d_extract_planes_batched) and copies the outputs back, while the other slot's batch is
+ * still on the GPU. Two batches in flight run side by side, one CTA per SM each.
+ *
+ *   device            CUDA device (sm_103-class).
+ *   max_inflight      1 or 2 batches on the GPU at once.
+ *   max_batch_frames  1..4096 frames per launch; 1 = one plain single-frame launch per request
+ *                     (with max_inflight 1: the plain sequential path).
+ *   hbm_bytes         device memory for request buffers and scratch over all slots; 0 = half of
+ *                     the free memory at creation. A slot holds hbm_bytes / max_inflight.
+ *
+ * pl3d_server_submit enqueues one frame and returns at once with a ticket (1, 2, 3, ... in
+ * submission order). Host buffers as in pl3d_extract_planes_host (page-locked ones give
+ * asynchronous copies); they stay the caller's and must stay valid and untouched until the
+ * ticket completes. params and dominant_normals are copied. A frame that does not fit an empty
+ * slot is rejected with PL3D_ERR_OUT_OF_MEMORY; invalid arguments with their error; nothing is
+ * enqueued then. Results are bit-identical to pl3d_extract_planes on the same frame.
+ *
+ * pl3d_server_poll moves up to `max` completions to `out` (oldest first), waiting up to
+ * wait_ms milliseconds for the first one (0 = do not wait, < 0 = until one arrives or nothing
+ * is outstanding), and returns how many it wrote, or a negative error. A completion gives the
+ * ticket, the status of its batch, the frames of that batch, the latency from submission to
+ * the end of the batch's last copy (measured on the host when the stream reaches it) and the
+ * time the request waited before its batch was enqueued.
+ * pl3d_server_drain waits until every submitted request has completed.
+ * pl3d_server_destroy drains, stops the worker and frees everything.
+ */
+typedef struct pl3d_server pl3d_server;
+
+typedef struct pl3d_server_config {
+    int32_t device;
+    int32_t max_inflight;
+    int32_t max_batch_frames;
+    int32_t reserved;     /* must be 0 */
+    int64_t hbm_bytes;
+} pl3d_server_config;
+
+typedef struct pl3d_completion {
+    uint64_t ticket;
+    int32_t status;
+    int32_t batch_frames;
+    double latency_ms;
+    double queue_ms;
+} pl3d_completion;
+
+typedef struct pl3d_server_stats {
+    int64_t submitted;
+    int64_t completed;
+    int64_t rejected;
+    int64_t batches;
+    int64_t triangles;            /* of completed requests */
+    int64_t max_batch_frames;     /* largest batch launched */
+    int64_t max_inflight;         /* most batches seen in flight at once */
+    int64_t slot_bytes;           /* device bytes per slot (arena + scratch) */
+} pl3d_server_stats;
+
+int pl3d_server_create(pl3d_server** out, const pl3d_server_config* cfg);
+int pl3d_server_submit(pl3d_server* srv, const float* host_points, int H, int W, const pl3d_params* params,
+                       const float* dominant_normals, int K, uint8_t* host_tri_mask, float* host_normals,
+                       int32_t* host_labels, uint64_t* ticket);
+int pl3d_server_poll(pl3d_server* srv, pl3d_completion* out, int max, int wait_ms);
+int pl3d_server_drain(pl3d_server* srv);
+int pl3d_server_get_stats(const pl3d_server* srv, pl3d_server_stats* out);
+void pl3d_server_destroy(pl3d_server* srv);
+
 /* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
 int pl3d_version(void);
 

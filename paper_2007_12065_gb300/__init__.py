@@ -49,6 +49,35 @@ class pl3d_params(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class pl3d_frame(ctypes.Structure):
+    """Mirror of the C struct pl3d_frame: one frame of a batch."""
+    _fields_ = [
+        ("points", ctypes.c_void_p),
+        ("H", ctypes.c_int32),
+        ("W", ctypes.c_int32),
+        ("params", ctypes.POINTER(pl3d_params)),
+        ("dominant_normals", ctypes.c_void_p),
+        ("K", ctypes.c_int32),
+        ("out_tri_mask", ctypes.c_void_p),
+        ("out_normals", ctypes.c_void_p),
+        ("out_labels", ctypes.c_void_p),
+        ("out_points", ctypes.c_void_p),
+        ("out_groups", ctypes.c_void_p),
+    ]
+
+
+class pl3d_tuning(ctypes.Structure):
+    """Mirror of the C struct pl3d_tuning (launch shape; never changes a result)."""
+    _fields_ = [
+        ("lap_fuse", ctypes.c_int32),
+        ("bil_fuse", ctypes.c_int32),
+        ("ctas_per_sm", ctypes.c_int32),
+    ]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 class PL3DError(RuntimeError):
     def __init__(self, status: int, what: str):
         super().__init__(f"{what}: {pl3d_status_string(status)} ({status})")
@@ -91,6 +120,14 @@ def lib():
     L.pl3d_launch_count.restype = ctypes.c_int64
     L.pl3d_extract_planes_static.argtypes = [_vp, ctypes.c_int, ctypes.c_int, P, _vp, ctypes.c_int, _vp, _vp, _vp, _vp]
     L.pl3d_static_scratch_bytes.restype = ctypes.c_size_t
+    F = ctypes.POINTER(pl3d_frame)
+    T = ctypes.POINTER(pl3d_tuning)
+    L.pl3d_extract_planes_batched.argtypes = [_vp, F, ctypes.c_int, _vp]
+    L.pl3d_set_tuning.argtypes = [_vp, T]
+    L.pl3d_get_tuning.argtypes = [_vp, T]
+    L.pl3d_autotune_batched.argtypes = [_vp, F, ctypes.c_int, _vp, ctypes.c_int, T, ctypes.POINTER(ctypes.c_double)]
+    L.pl3d_batch_stats.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                   ctypes.POINTER(ctypes.c_int64)]
     _lib = L
     return L
 
@@ -255,6 +292,75 @@ def pl3d_static_scratch_bytes() -> int:
 
 
 PL3D_STATIC_MAX_POINTS = 307200
+
+
+class Batch:
+    """A list of frames marshalled into a C array of pl3d_frame. Keeps every buffer it points at
+    (torch tensors, parameter structs, host normals) alive for as long as the batch lives."""
+
+    def __init__(self):
+        self._keep = []
+        self._frames = []
+        self._array = None
+
+    def add(self, points, H, W, params, dominant_normals, out_tri_mask, out_normals, out_labels, out_points=None,
+            out_groups=None):
+        n_tri = 2 * (H - 1) * (W - 1)
+        _check_tensor(points, "points", "torch.float32", H * W * 3)
+        _check_tensor(out_tri_mask, "out_tri_mask", "torch.uint8", n_tri)
+        _check_tensor(out_normals, "out_normals", "torch.float32", n_tri * 3)
+        _check_tensor(out_labels, "out_labels", "torch.int32", n_tri)
+        _check_tensor(out_points, "out_points", "torch.float32", H * W * 3)
+        _check_tensor(out_groups, "out_groups", "torch.uint8", n_tri)
+        nd = _nd_host(dominant_normals)
+        p = pl3d_params(**params.as_dict()) if isinstance(params, pl3d_params) else make_params(**params)
+        self._keep += [points, out_tri_mask, out_normals, out_labels, out_points, out_groups, nd, p]
+        f = pl3d_frame(_ptr(points), int(H), int(W), ctypes.pointer(p), _ptr(nd), int(nd.shape[0]),
+                       _ptr(out_tri_mask), _ptr(out_normals), _ptr(out_labels), _ptr(out_points), _ptr(out_groups))
+        self._frames.append(f)
+        self._array = None
+        return len(self._frames) - 1
+
+    def __len__(self):
+        return len(self._frames)
+
+    def array(self):
+        if self._array is None:
+            self._array = (pl3d_frame * max(1, len(self._frames)))(*self._frames)
+        return self._array
+
+
+def pl3d_extract_planes_batched(ctx, batch: Batch, stream=None) -> int:
+    """All frames of `batch` in one persistent launch (a CUDA graph); see include/pl3d.h."""
+    return _check(lib().pl3d_extract_planes_batched(ctx, batch.array(), len(batch), _stream(stream)),
+                  "pl3d_extract_planes_batched")
+
+
+def pl3d_set_tuning(ctx, tuning: Optional[pl3d_tuning] = None, **kw) -> None:
+    if tuning is None and kw:
+        tuning = pl3d_tuning(**kw)
+    _check(lib().pl3d_set_tuning(ctx, ctypes.byref(tuning) if tuning is not None else None), "pl3d_set_tuning")
+
+
+def pl3d_get_tuning(ctx) -> pl3d_tuning:
+    t = pl3d_tuning()
+    _check(lib().pl3d_get_tuning(ctx, ctypes.byref(t)), "pl3d_get_tuning")
+    return t
+
+
+def pl3d_autotune_batched(ctx, batch: Batch, stream=None, reps: int = 3):
+    """Times the batch under each candidate launch shape, keeps the fastest; returns (tuning, ms)."""
+    t = pl3d_tuning()
+    ms = ctypes.c_double()
+    _check(lib().pl3d_autotune_batched(ctx, batch.array(), len(batch), _stream(stream), int(reps), ctypes.byref(t),
+                                       ctypes.byref(ms)), "pl3d_autotune_batched")
+    return t, float(ms.value)
+
+
+def pl3d_batch_stats(ctx) -> dict:
+    a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().pl3d_batch_stats(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "pl3d_batch_stats")
+    return {"graph_launches": a.value, "desc_uploads": b.value, "graphs": c.value}
 
 
 def pl3d_sync(ctx, stream=None) -> int:

@@ -14,6 +14,9 @@ namespace pl3d {
 const void* frame_kernel_rb1(int rl);
 const void* frame_kernel_rb2(int rl);
 const void* frame_kernel_rb3(int rl);
+const void* batch_kernel_rb1(int rl);
+const void* batch_kernel_rb2(int rl);
+const void* batch_kernel_rb3(int rl);
 
 namespace {
 
@@ -22,6 +25,15 @@ const void* kernel_for(int rl, int rb) {
         case 1: return frame_kernel_rb1(rl);
         case 2: return frame_kernel_rb2(rl);
         case 3: return frame_kernel_rb3(rl);
+        default: return nullptr;
+    }
+}
+
+const void* batch_kernel_for(int rl, int rb) {
+    switch (rb) {
+        case 1: return batch_kernel_rb1(rl);
+        case 2: return batch_kernel_rb2(rl);
+        case 3: return batch_kernel_rb3(rl);
         default: return nullptr;
     }
 }
@@ -79,7 +91,24 @@ bool encode_aos(CUtensorMap* map, const float* base, int H, int W, BoxGeom b, bo
            CUDA_SUCCESS;
 }
 
-// Resident CTAs per SM for a kernel and shared-memory size, and SMs per device (cached).
+void bilateral_scales(float sigma_c, float sigma_s, int iters, float* c_scale, float* a_norm) {
+    const double log2e = 1.4426950408889634;
+    double cs = 1.0, an = 0.0;
+    if (iters > 0) {
+        cs = sqrt(log2e / (2.0 * (double)sigma_c * (double)sigma_c));
+        an = log2e / ((double)sigma_s * (double)sigma_s);
+    }
+    // finite and representable: c' = c * cs must not overflow for coordinates up to ~1e18
+    *c_scale = (float)fmin(fmax(cs, 1e-18), 1e18);
+    *a_norm = (float)fmin(an, 1e30);
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+}  // namespace
+
+// Resident CTAs per device for a kernel and shared-memory size (cached).
+namespace {
 struct OccKey {
     const void* fn;
     size_t smem;
@@ -89,6 +118,7 @@ std::mutex g_occ_mutex;
 OccKey g_occ_keys[64];
 int g_occ_vals[64];
 int g_occ_n = 0;
+}  // namespace
 
 int resident_ctas(const void* fn, size_t smem, int dev) {
     std::lock_guard<std::mutex> lock(g_occ_mutex);
@@ -109,50 +139,52 @@ int resident_ctas(const void* fn, size_t smem, int dev) {
     return v;
 }
 
-void bilateral_scales(float sigma_c, float sigma_s, int iters, float* c_scale, float* a_norm) {
-    const double log2e = 1.4426950408889634;
-    double cs = 1.0, an = 0.0;
-    if (iters > 0) {
-        cs = sqrt(log2e / (2.0 * (double)sigma_c * (double)sigma_c));
-        an = log2e / ((double)sigma_s * (double)sigma_s);
-    }
-    // finite and representable: c' = c * cs must not overflow for coordinates up to ~1e18
-    *c_scale = (float)fmin(fmax(cs, 1e-18), 1e18);
-    *a_norm = (float)fmin(an, 1e30);
+const void* batch_kernel_for_radii(int rl, int rb) { return batch_kernel_for(rl, rb); }
+
+// Iterations per pass: as many as the halo allows, or fewer on request, but never so few that
+// the passes outnumber kMaxPasses (a tuning must not turn a valid frame into an error).
+static int fused_iters(int iters, int max_fuse, int requested) {
+    int fuse = max_fuse;
+    if (requested > 0 && requested < fuse) fuse = requested;
+    const int least = (iters + kMaxPasses - 1) / kMaxPasses;
+    return fuse < least ? least : fuse;
 }
 
-bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+size_t frame_smem_bytes(const pl3d_params* p, const Tuning& t) {
+    const int rl = p->lap_iters > 0 ? p->lap_kernel / 2 : 1;
+    const int rb = p->bil_iters > 0 ? p->bil_kernel / 2 : 1;
+    const int lf = fused_iters(p->lap_iters, kLapMaxHalo / rl, t.lap_fuse);
+    const int bf = fused_iters(p->bil_iters, kBilMaxHalo / rb, t.bil_fuse);
+    // the first pass of each filter fuses the most iterations, so it has the largest halo
+    const size_t l = lap_smem((p->lap_iters < lf ? p->lap_iters : lf) * rl);
+    const size_t b = bil_smem((p->bil_iters < bf ? p->bil_iters : bf) * rb);
+    return l > b ? l : b;
+}
 
-}  // namespace
-
-int bilateral_passes(const pl3d_params* p) {
+int bilateral_passes(const pl3d_params* p, const Tuning& t) {
     const int br = p->bil_iters > 0 ? p->bil_kernel / 2 : 1;
-    const int fuse = kBilMaxHalo / br;
+    const int fuse = fused_iters(p->bil_iters, kBilMaxHalo / br, t.bil_fuse);
     return p->bil_iters <= fuse ? 1 : (p->bil_iters + fuse - 1) / fuse;
 }
 
 cudaError_t frame_configure() {
     const size_t need = lap_smem(kLapMaxHalo) > bil_smem(kBilMaxHalo) ? lap_smem(kLapMaxHalo) : bil_smem(kBilMaxHalo);
     for (int rl = 1; rl <= 3; ++rl)
-        for (int rb = 1; rb <= 3; ++rb) {
-            cudaError_t e = cudaFuncSetAttribute(kernel_for(rl, rb), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)need);
-            // all of the unified L1 / shared storage as shared memory, so that two CTAs fit per SM
-            if (e == cudaSuccess)
-                e = cudaFuncSetAttribute(kernel_for(rl, rb), cudaFuncAttributePreferredSharedMemoryCarveout,
-                                         cudaSharedmemCarveoutMaxShared);
-            if (e != cudaSuccess) return e;
-        }
+        for (int rb = 1; rb <= 3; ++rb)
+            for (const void* fn : {kernel_for(rl, rb), batch_kernel_for(rl, rb)}) {
+                cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+                // all of the unified L1 / shared storage as shared memory, so that two CTAs fit per SM
+                if (e == cudaSuccess)
+                    e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                             cudaSharedmemCarveoutMaxShared);
+                if (e != cudaSuccess) return e;
+            }
     return cudaSuccess;
 }
 
-int frame_launch(const FrameScratch& sc, const float* points, int H, int W, const pl3d_params* p, const float* nd_host,
-                 int K, uint8_t* out_mask, float* out_normals, int32_t* out_labels, float* out_points,
-                 uint8_t* out_groups, cudaStream_t s) {
-    static_assert(sizeof(FrameArgs) < 32000, "kernel parameters must fit the 32 KB parameter space");
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return PL3D_ERR_CUDA;
-    FrameArgs a;
+int frame_build(FrameArgs& a, FramePlan& plan, const FrameScratch& sc, const float* points, int H, int W,
+                const pl3d_params* p, const float* nd_host, int K, uint8_t* out_mask, float* out_normals,
+                int32_t* out_labels, float* out_points, uint8_t* out_groups, const Tuning& t) {
     memset(&a, 0, sizeof(a));
     a.points = points;
     a.H = H;
@@ -162,7 +194,7 @@ int frame_launch(const FrameScratch& sc, const float* points, int H, int W, cons
 
     // Laplacian passes (Eq. 1-2): displacement ping-pong, the first pass reads no displacement.
     const int rl = p->lap_iters > 0 ? p->lap_kernel / 2 : 1;
-    const int lfuse = kLapMaxHalo / rl;
+    const int lfuse = fused_iters(p->lap_iters, kLapMaxHalo / rl, t.lap_fuse);
     int remaining = p->lap_iters;
     size_t smem = 0;
     do {
@@ -185,8 +217,8 @@ int frame_launch(const FrameScratch& sc, const float* points, int H, int W, cons
 
     // Bilateral passes (Eq. 3-6) and the quads' finish (Algorithms 1, 4, 5).
     const int rb = p->bil_iters > 0 ? p->bil_kernel / 2 : 1;
-    const int bfuse = kBilMaxHalo / rb;
-    const int nb = bilateral_passes(p);
+    const int bfuse = fused_iters(p->bil_iters, kBilMaxHalo / rb, t.bil_fuse);
+    const int nb = bilateral_passes(p, t);
     if (nb > kMaxPasses) return PL3D_ERR_UNSUPPORTED;
     if (nb > 1 && (!sc.carry[0] || !sc.carry[1])) return PL3D_ERR_INVALID_ARG;
     int bremaining = p->bil_iters;
@@ -235,16 +267,48 @@ int frame_launch(const FrameScratch& sc, const float* points, int H, int W, cons
         a.nd.v[3 * j + 2] = (float)(z / len);
     }
 
-    const void* fn = kernel_for(rl, rb);
-    if (!fn) return PL3D_ERR_UNSUPPORTED;
-    const int resident = resident_ctas(fn, smem, dev);
-    if (resident <= 0) return PL3D_ERR_CUDA;
-    const int tiles_lap = div_up(H, kTile) * div_up(W, kTile);
-    const int tiles_bil = div_up(H - 1, kTile) * div_up(W - 1, kTile);
-    int grid = tiles_lap > tiles_bil ? tiles_lap : tiles_bil;
-    if (grid > resident) grid = resident;
+    plan.frame_fn = kernel_for(rl, rb);
+    plan.batch_fn = batch_kernel_for(rl, rb);
+    if (!plan.frame_fn || !plan.batch_fn) return PL3D_ERR_UNSUPPORTED;
+    plan.rl = rl;
+    plan.rb = rb;
+    plan.smem = smem;
+    plan.tiles_lap = div_up(H, kTile) * div_up(W, kTile);
+    plan.tiles_bil = div_up(H - 1, kTile) * div_up(W - 1, kTile);
+    const int Hq = H - 1, Wq = W - 1;
+    plan.merge_items = (long long)(div_up(Hq, kTile) - 1) * Wq + (long long)(div_up(Wq, kTile) - 1) * Hq;
+    plan.tris = 2LL * Hq * Wq;
+    return PL3D_OK;
+}
+
+int persistent_grid(const void* fn, size_t smem, int dev, const Tuning& t, long long work) {
+    int resident = resident_ctas(fn, smem, dev);
+    if (resident <= 0) return 0;
+    if (t.ctas_per_sm > 0) {
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+        const long long want = (long long)t.ctas_per_sm * sms;
+        if (want < resident) resident = (int)want;
+    }
+    return work < resident ? (int)(work > 0 ? work : 1) : resident;
+}
+
+int frame_launch(const FrameScratch& sc, const float* points, int H, int W, const pl3d_params* p, const float* nd_host,
+                 int K, uint8_t* out_mask, float* out_normals, int32_t* out_labels, float* out_points,
+                 uint8_t* out_groups, const Tuning& t, cudaStream_t s) {
+    static_assert(sizeof(FrameArgs) < 32000, "kernel parameters must fit the 32 KB parameter space");
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PL3D_ERR_CUDA;
+    FrameArgs a;
+    FramePlan plan;
+    int rc = frame_build(a, plan, sc, points, H, W, p, nd_host, K, out_mask, out_normals, out_labels, out_points,
+                         out_groups, t);
+    if (rc != PL3D_OK) return rc;
+    const int work = plan.tiles_lap > plan.tiles_bil ? plan.tiles_lap : plan.tiles_bil;
+    const int grid = persistent_grid(plan.frame_fn, plan.smem, dev, t, work);
+    if (grid <= 0) return PL3D_ERR_CUDA;
     void* args[1] = {&a};
-    if (cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kThreads), args, smem, s) != cudaSuccess) {
+    if (cudaLaunchCooperativeKernel(plan.frame_fn, dim3(grid), dim3(kThreads), args, plan.smem, s) != cudaSuccess) {
         cudaGetLastError();
         return PL3D_ERR_CUDA;
     }

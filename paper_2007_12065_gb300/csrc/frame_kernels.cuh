@@ -714,38 +714,39 @@ __device__ __forceinline__ V3 centroid_global(const FrameArgs& a, int u, int v, 
 
 // Twins that cross a tile border: the top edge of a tile's first quad row and the right edge of
 // its last quad column. Work items: (row borders) x Wq, then (column borders) x Hq.
+__device__ __forceinline__ void merge_item(const FrameArgs& a, long long w) {
+    const int Wq = a.W - 1, Hq = a.H - 1;
+    const long long n_row_items = (long long)(div_up(Hq, T) - 1) * Wq;
+    int u, v, uj, vj;
+    if (w < n_row_items) {
+        u = (int)(w / Wq + 1) * T;
+        v = (int)(w % Wq);
+        uj = u - 1;
+        vj = v;
+    } else {
+        const long long x = w - n_row_items;
+        v = (int)(x / Hq + 1) * T - 1;
+        u = (int)(x % Hq);
+        uj = u;
+        vj = v + 1;
+    }
+    const int i = 2 * (u * Wq + v);
+    const int j = 2 * (uj * Wq + vj) + 1;
+    const int g = a.groups[i];
+    if (g == PL3D_NO_GROUP || a.groups[j] != g) return;
+    if (a.max_offset > 0.f) {
+        const V3 ci = centroid_global(a, u, v, 0), cj = centroid_global(a, uj, vj, 1);
+        const float* nd = a.nd.v + 3 * g;
+        if (fabsf(nd[0] * (ci.x - cj.x) + nd[1] * (ci.y - cj.y) + nd[2] * (ci.z - cj.z)) > a.max_offset) return;
+    }
+    uf_unite(a.labels, i, j);
+}
+
 __device__ __forceinline__ void merge_phase(const FrameArgs& a) {
     const int Wq = a.W - 1, Hq = a.H - 1;
-    const int rb = div_up(Hq, T) - 1;
-    const int cb = div_up(Wq, T) - 1;
-    const long long n_row_items = (long long)rb * Wq;
-    const long long n = n_row_items + (long long)cb * Hq;
+    const long long n = (long long)(div_up(Hq, T) - 1) * Wq + (long long)(div_up(Wq, T) - 1) * Hq;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < n; w += stride) {
-        int u, v, uj, vj;
-        if (w < n_row_items) {
-            u = (int)(w / Wq + 1) * T;
-            v = (int)(w % Wq);
-            uj = u - 1;
-            vj = v;
-        } else {
-            const long long x = w - n_row_items;
-            v = (int)(x / Hq + 1) * T - 1;
-            u = (int)(x % Hq);
-            uj = u;
-            vj = v + 1;
-        }
-        const int i = 2 * (u * Wq + v);
-        const int j = 2 * (uj * Wq + vj) + 1;
-        const int g = a.groups[i];
-        if (g == PL3D_NO_GROUP || a.groups[j] != g) continue;
-        if (a.max_offset > 0.f) {
-            const V3 ci = centroid_global(a, u, v, 0), cj = centroid_global(a, uj, vj, 1);
-            const float* nd = a.nd.v + 3 * g;
-            if (fabsf(nd[0] * (ci.x - cj.x) + nd[1] * (ci.y - cj.y) + nd[2] * (ci.z - cj.z)) > a.max_offset) continue;
-        }
-        uf_unite(a.labels, i, j);
-    }
+    for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < n; w += stride) merge_item(a, w);
 }
 
 // Every grouped triangle takes its root; with tri_min > 0 the segment sizes are counted, one
@@ -824,6 +825,137 @@ __global__ void __launch_bounds__(kThreads, 2) frame_kernel(const __grid_constan
         frame::filter_phase(a);
     }
     frame::phase_mark(a, 3, t_prev);
+}
+
+namespace frame {
+
+// Frame of work item t: the largest f < n with pre[f] <= t (pre[0] = 0 <= t < pre[n]).
+__device__ __forceinline__ int find_frame(const int* pre, int n, int t) {
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(pre + mid) <= t) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Advances f (never backwards) to the frame whose range of pre holds item i.
+__device__ __forceinline__ int advance_frame(const long long* pre, int f, long long i) {
+    while (__ldg(pre + f + 1) <= i) ++f;
+    return f;
+}
+
+}  // namespace frame
+
+// Many frames in one persistent launch: each phase runs over the concatenated work of all
+// frames (tiles, tile-border twins, triangles), with one grid barrier between phases, so the
+// small frames of a batch share the GPU instead of leaving most of it idle.
+template <int RL, int RB>
+__global__ void __launch_bounds__(kThreads, 2) batch_kernel(const __grid_constant__ BatchArgs b) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+    float* smem = reinterpret_cast<float*>(smem_raw + 128);
+    if (threadIdx.x == 0) mbar_init(bar, 1);
+    __syncthreads();
+    unsigned parity = 0;
+    const int n = b.hdr->n, n_lap = b.hdr->n_lap, n_bil = b.hdr->n_bil;
+    const bool any_filter = b.hdr->any_filter != 0;
+    unsigned long long* pns = b.hdr->timing ? b.phase_ns : nullptr;
+    uint64_t t_prev = 0;
+    const bool stamp = pns && blockIdx.x == 0 && threadIdx.x == 0;
+    auto mark = [&](int slot) {
+        if (stamp) {
+            const uint64_t t = global_ns();
+            atomicAdd(pns + slot, (unsigned long long)(t - t_prev));
+            t_prev = t;
+        }
+    };
+    if (stamp) t_prev = global_ns();
+
+    for (int c = 0; c < n_lap; ++c) {
+        const int* pre = b.lap_tiles + c * b.stride;
+        const int total = __ldg(pre + n);
+        for (int t = blockIdx.x; t < total; t += gridDim.x) {
+            const int f = frame::find_frame(pre, n, t);
+            const FrameArgs& a = b.frames[f];
+            const CUtensorMap* map = a.lap[c].use_tma ? &a.tm_pts_lap : nullptr;
+            if (map && threadIdx.x == 0) tensormap_acquire(map);
+            frame::lap_tile<RL>(a, a.lap[c], map, t - __ldg(pre + f), smem, bar, parity);
+        }
+        grid_barrier(b.barrier, b.error);
+    }
+    mark(0);
+    for (int c = 0; c < n_bil; ++c) {
+        const int* pre = b.bil_tiles + c * b.stride;
+        const int total = __ldg(pre + n);
+        for (int t = blockIdx.x; t < total; t += gridDim.x) {
+            const int f = frame::find_frame(pre, n, t);
+            const FrameArgs& a = b.frames[f];
+            if (a.bil[c].use_tma && threadIdx.x == 0) {
+                tensormap_acquire(&a.tm_pts_bil);
+                tensormap_acquire(&a.tm_disp_bil);
+            }
+            frame::bil_tile<RB>(a, a.bil[c], t - __ldg(pre + f), smem, bar, parity);
+        }
+        grid_barrier(b.barrier, b.error);
+    }
+    mark(1);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long base = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    {
+        const long long total = __ldg(b.merge_items + n);
+        int f = 0;
+        for (long long w = base; w < total; w += stride) {
+            f = frame::advance_frame(b.merge_items, f, w);
+            frame::merge_item(b.frames[f], w - __ldg(b.merge_items + f));
+        }
+    }
+    grid_barrier(b.barrier, b.error);
+    mark(2);
+    {
+        // every grouped triangle takes its root; segment sizes are counted per (frame, root)
+        const long long total = __ldg(b.tris + n);
+        const long long n_iter = (total + stride - 1) / stride;   // uniform: whole warps stay together
+        int f = 0;
+        for (long long it = 0; it < n_iter; ++it) {
+            const long long i = base + it * stride;
+            int root = -1;
+            long long key = -1;
+            int32_t* sizes = nullptr;
+            if (i < total) {
+                f = frame::advance_frame(b.tris, f, i);
+                const FrameArgs& a = b.frames[f];
+                const int li = (int)(i - __ldg(b.tris + f));
+                if (a.labels[li] >= 0) {
+                    root = uf_root(a.labels, li);
+                    a.labels[li] = root;
+                    key = ((long long)f << 32) | (unsigned)root;
+                    sizes = a.sizes;
+                }
+            }
+            if (any_filter) {
+                const unsigned peers = __match_any_sync(0xffffffffu, key);
+                const int leader = __ffs(peers) - 1;
+                if (sizes && (int)(threadIdx.x & 31) == leader) atomicAdd(sizes + root, __popc(peers));
+            }
+        }
+    }
+    if (any_filter) {
+        grid_barrier(b.barrier, b.error);
+        // Algorithm 5 keeps a segment only when it has more than tri_min triangles
+        const long long total = __ldg(b.tris + n);
+        int f = 0;
+        for (long long i = base; i < total; i += stride) {
+            f = frame::advance_frame(b.tris, f, i);
+            const FrameArgs& a = b.frames[f];
+            if (!a.sizes) continue;
+            const int li = (int)(i - __ldg(b.tris + f));
+            const int l = a.labels[li];
+            if (l >= 0 && a.sizes[l] <= a.min_triangles) a.labels[li] = -1;
+        }
+    }
+    mark(3);
 }
 
 }  // namespace pl3d

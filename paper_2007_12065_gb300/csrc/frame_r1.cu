@@ -1,4 +1,4 @@
-// frame_r1.cu -- frame kernels for a bilateral window of 3 x 3 quads (radius 1), one per
+// frame_r1.cu -- frame and batch kernels for a bilateral window of 3 x 3 quads (radius 1), one per
 // Laplacian radius; split by bilateral radius so the three translation units compile in parallel.
 #include "frame_kernels.cuh"
 
@@ -9,6 +9,15 @@ const void* frame_kernel_rb1(int rl) {
         case 1: return reinterpret_cast<const void*>(&frame_kernel<1, 1>);
         case 2: return reinterpret_cast<const void*>(&frame_kernel<2, 1>);
         case 3: return reinterpret_cast<const void*>(&frame_kernel<3, 1>);
+        default: return nullptr;
+    }
+}
+
+const void* batch_kernel_rb1(int rl) {
+    switch (rl) {
+        case 1: return reinterpret_cast<const void*>(&batch_kernel<1, 1>);
+        case 2: return reinterpret_cast<const void*>(&batch_kernel<2, 1>);
+        case 3: return reinterpret_cast<const void*>(&batch_kernel<3, 1>);
         default: return nullptr;
     }
 }

@@ -2,7 +2,8 @@
 // scratch memory, per-phase timing, the device error word, and the host-buffer entry point.
 // The path itself is one cooperative launch of the frame kernel per call (frame_host.cu,
 // frame_kernels.cuh): Laplacian passes, bilateral passes with the quads' finish and the
-// tile-local segments, the segment merge across tiles, and the labels.
+// tile-local segments, the segment merge across tiles, and the labels. Batches of frames
+// (one launch for many frames) are in pl3d_batch.cu.
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -10,127 +11,19 @@
 #include <new>
 #include <vector>
 
-#include "pl3d_internal.cuh"
+#include "pl3d_ctx.cuh"
 
 using namespace pl3d;
+using namespace pl3d::ctxutil;
 
 namespace {
 
-constexpr int kVersion = 2 * 10000 + 0 * 100 + 0;
+constexpr int kVersion = 2 * 10000 + 1 * 100 + 0;
 
-// Timing slots: four phases of the frame kernel (device %globaltimer, accumulated by the
-// kernel), the kernel as a whole and the host copies (CUDA events on the call's stream).
-enum Slot { kSlotLap = 0, kSlotBil, kSlotMerge, kSlotLabels, kSlotKernel, kSlotCopies };
 const char* const kSlotNames[PL3D_TIMING_SLOTS] = {"laplacian", "bilateral", "label_merge",
                                                     "label_flatten", "frame_kernel", "host_copies"};
 
-struct TimedRange {
-    int slot;
-    cudaEvent_t start, stop;
-};
-
-}  // namespace
-
-struct pl3d_ctx {
-    int device = 0;
-    // scratch (grown to the largest frame)
-    float* disp = nullptr;          // 2 x 3 cap_points floats (AoS displacement ping-pong)
-    size_t cap_points = 0;
-    float* carry = nullptr;         // 2 x 3 cap_carry floats (multi-pass bilateral)
-    size_t cap_carry = 0;
-    uint8_t* groups = nullptr;      // cap_tri
-    int32_t* sizes = nullptr;       // cap_tri
-    size_t cap_tri = 0;
-    unsigned* ctl = nullptr;        // barrier [2], error word, pad, phase totals [4] (u64)
-    // device staging for the host-buffer entry point
-    float* st_points = nullptr;
-    size_t st_cap_points = 0;
-    uint8_t* st_mask = nullptr;
-    float* st_normals = nullptr;
-    int32_t* st_labels = nullptr;
-    size_t st_cap_tri = 0;
-    // timing
-    bool timing = false;
-    int64_t timed_frames = 0;
-    std::vector<TimedRange> pending;
-    std::vector<cudaEvent_t> free_events;
-    double slot_ms[PL3D_TIMING_SLOTS] = {};
-    int64_t slot_n[PL3D_TIMING_SLOTS] = {};
-    int64_t launches = 0;
-
-    unsigned* barrier() const { return ctl; }
-    int* error() const { return reinterpret_cast<int*>(ctl + 2); }
-    unsigned long long* phase_ns() const { return reinterpret_cast<unsigned long long*>(ctl + 4); }
-};
-
-namespace {
-
-constexpr size_t kCtlBytes = 4 * sizeof(unsigned) + 4 * sizeof(unsigned long long);
-
-// Makes the context's device current for the duration of a call.
-struct DeviceGuard {
-    int prev = -1;
-    bool ok = true;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess) {
-            ok = false;
-            return;
-        }
-        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
-    }
-    ~DeviceGuard() {
-        int cur = -1;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
-
 bool finite_f(float x) { return isfinite(x) != 0; }
-
-cudaEvent_t take_event(pl3d_ctx* c) {
-    if (!c->free_events.empty()) {
-        cudaEvent_t e = c->free_events.back();
-        c->free_events.pop_back();
-        return e;
-    }
-    cudaEvent_t e = nullptr;
-    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
-    return e;
-}
-
-void record_start(pl3d_ctx* c, cudaStream_t s, cudaEvent_t* e0, cudaEvent_t* e1) {
-    *e0 = *e1 = nullptr;
-    if (!c->timing) return;
-    *e0 = take_event(c);
-    *e1 = take_event(c);
-    if (*e0 && *e1) cudaEventRecord(*e0, s);
-}
-
-void record_stop(pl3d_ctx* c, cudaStream_t s, int slot, cudaEvent_t e0, cudaEvent_t e1) {
-    if (!e0 || !e1) return;
-    cudaEventRecord(e1, s);
-    c->pending.push_back({slot, e0, e1});
-}
-
-// Frees and reallocates `*ptr` to hold `need` units of `elem_per` elements (plus headroom).
-// Waits for the stream first, since work in flight may still use the old buffer.
-template <class T>
-int grow(T** ptr, size_t* cap, size_t need, size_t elem_per, cudaStream_t s) {
-    if (*cap >= need) return PL3D_OK;
-    if (*ptr) {
-        if (cudaStreamSynchronize(s) != cudaSuccess) return PL3D_ERR_CUDA;
-        cudaFree(*ptr);
-        *ptr = nullptr;
-        *cap = 0;
-    }
-    const size_t n = need + need / 8;
-    if (cudaMalloc((void**)ptr, n * elem_per * sizeof(T)) != cudaSuccess) {
-        cudaGetLastError();
-        *ptr = nullptr;
-        return PL3D_ERR_OUT_OF_MEMORY;
-    }
-    *cap = n;
-    return PL3D_OK;
-}
 
 // groups and segment sizes share one capacity.
 int grow_tri(pl3d_ctx* ctx, size_t need, cudaStream_t s) {
@@ -159,7 +52,7 @@ int run(pl3d_ctx* ctx, const float* points, int H, int W, const pl3d_params* p, 
     int rc;
     if ((rc = grow(&ctx->disp, &ctx->cap_points, npts, 6, s)) != PL3D_OK) return rc;
     if ((rc = grow_tri(ctx, ntri, s)) != PL3D_OK) return rc;
-    if (bilateral_passes(p) > 1 && (rc = grow(&ctx->carry, &ctx->cap_carry, ntri, 6, s)) != PL3D_OK) return rc;
+    if (bilateral_passes(p, ctx->tuning) > 1 && (rc = grow(&ctx->carry, &ctx->cap_carry, ntri, 6, s)) != PL3D_OK) return rc;
 
     FrameScratch sc;
     sc.disp[0] = ctx->disp;
@@ -174,7 +67,8 @@ int run(pl3d_ctx* ctx, const float* points, int H, int W, const pl3d_params* p, 
 
     cudaEvent_t e0, e1;
     record_start(ctx, s, &e0, &e1);
-    rc = frame_launch(sc, points, H, W, p, nd_host, K, out_mask, out_normals, out_labels, out_points, out_groups, s);
+    rc = frame_launch(sc, points, H, W, p, nd_host, K, out_mask, out_normals, out_labels, out_points, out_groups,
+                      ctx->tuning, s);
     record_stop(ctx, s, kSlotKernel, e0, e1);
     if (rc != PL3D_OK) return rc;
     ctx->launches += 1;
@@ -297,6 +191,11 @@ void pl3d_destroy(pl3d_ctx* c) {
         cudaFree(c->st_mask);
         cudaFree(c->st_normals);
         cudaFree(c->st_labels);
+        drop_graphs(c);
+        cudaFree(c->bslab);
+        cudaFree(c->bdesc);
+        cudaFreeHost(c->bstage);
+        if (c->bupload) cudaEventDestroy(c->bupload);
         for (auto& r : c->pending) {
             cudaEventDestroy(r.start);
             cudaEventDestroy(r.stop);

@@ -116,6 +116,34 @@ struct FrameArgs {
 template <int RL, int RB>
 __global__ void frame_kernel(const __grid_constant__ FrameArgs a);
 
+// A batch of frames in one persistent launch. Everything the kernel reads lives in one device
+// block laid out for `cap` frames: a header, per-pass prefix sums of the frames' tile counts,
+// prefix sums of their merge items and triangles, and one FrameArgs per frame (whose tensor
+// maps are then read from global memory).
+struct BatchHeader {
+    int n;                         // frames in this batch
+    int n_lap, n_bil;              // most Laplacian / bilateral passes of any frame
+    int any_filter;                // some frame has tri_min > 0
+    int timing;                    // accumulate phase times into BatchArgs::phase_ns
+    int pad[11];
+};
+
+struct BatchArgs {
+    const BatchHeader* hdr;
+    const int* lap_tiles;          // [kMaxPasses][cap + 1]: pass c, frames before f -> tiles
+    const int* bil_tiles;          // [kMaxPasses][cap + 1]
+    const long long* merge_items;  // [cap + 1]
+    const long long* tris;         // [cap + 1]
+    const FrameArgs* frames;       // [cap], 64-byte aligned
+    int stride;                    // cap + 1
+    unsigned* barrier;
+    int* error;
+    unsigned long long* phase_ns;
+};
+
+template <int RL, int RB>
+__global__ void batch_kernel(const __grid_constant__ BatchArgs b);
+
 // --------------------------------------------------------------------------- host side
 
 // Device buffers one frame needs besides its inputs and outputs.
@@ -129,8 +157,41 @@ struct FrameScratch {
     unsigned long long* phase_ns;  // [4] or nullptr
 };
 
+// Launch-shape choices that leave every result bit-identical (Jacobi iterations split over
+// more passes go through global memory as the same FP32 values).
+struct Tuning {
+    int lap_fuse;                  // most Laplacian iterations per pass, 0 = as many as fit the halo
+    int bil_fuse;                  // same for the bilateral
+    int ctas_per_sm;               // 0 = as many as fit
+};
+
 // Number of bilateral passes the parameters need (> 1 needs the carry buffers).
-int bilateral_passes(const pl3d_params* p);
+int bilateral_passes(const pl3d_params* p, const Tuning& t);
+
+// Dynamic shared memory the persistent kernels need for this frame under tuning t.
+size_t frame_smem_bytes(const pl3d_params* p, const Tuning& t);
+
+// Everything a launch needs besides the frame's arguments.
+struct FramePlan {
+    const void* frame_fn;          // frame_kernel<RL, RB>
+    const void* batch_fn;          // batch_kernel<RL, RB>
+    int rl, rb;
+    size_t smem;                   // dynamic shared memory
+    int tiles_lap, tiles_bil;      // tiles per pass
+    long long merge_items;         // tile-border twins
+    long long tris;                // 2 (H-1)(W-1)
+};
+
+// Fills the arguments of one frame (no CUDA call besides tensor-map encoding).
+int frame_build(FrameArgs& a, FramePlan& plan, const FrameScratch& sc, const float* points, int H, int W,
+                const pl3d_params* p, const float* nd_host, int K, uint8_t* out_mask, float* out_normals,
+                int32_t* out_labels, float* out_points, uint8_t* out_groups, const Tuning& t);
+
+// batch_kernel<rl, rb>, or nullptr outside radii 1..3.
+const void* batch_kernel_for_radii(int rl, int rb);
+
+// Resident CTAs of a kernel over the whole device for a shared-memory size (cached).
+int resident_ctas(const void* fn, size_t smem, int dev);
 
 // Sets the shared-memory opt-in of every frame kernel on the current device.
 cudaError_t frame_configure();
@@ -138,6 +199,9 @@ cudaError_t frame_configure();
 // Enqueues the whole path for one frame on `s` (one cooperative launch). Returns a PL3D status.
 int frame_launch(const FrameScratch& sc, const float* points, int H, int W, const pl3d_params* p, const float* nd_host,
                  int K, uint8_t* out_mask, float* out_normals, int32_t* out_labels, float* out_points,
-                 uint8_t* out_groups, cudaStream_t s);
+                 uint8_t* out_groups, const Tuning& t, cudaStream_t s);
+
+// Grid size of a persistent launch: all resident CTAs (or ctas_per_sm per SM), at most `work`.
+int persistent_grid(const void* fn, size_t smem, int dev, const Tuning& t, long long work);
 
 }  // namespace pl3d

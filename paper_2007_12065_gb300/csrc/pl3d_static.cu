@@ -89,7 +89,7 @@ extern "C" int pl3d_extract_planes_static(const float* points, int H, int W, con
     int rc = pl3d_validate(p, H, W, nd_host, K);
     if (rc != PL3D_OK) return rc;
     if ((size_t)H * (size_t)W > kMaxPoints) return PL3D_ERR_INVALID_ARG;
-    if (bilateral_passes(p) > 1) return PL3D_ERR_INVALID_ARG;   // would need the carry buffers
+    if (bilateral_passes(p, Tuning{0, 0, 0}) > 1) return PL3D_ERR_INVALID_ARG;   // would need the carry buffers
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();
@@ -109,5 +109,5 @@ extern "C" int pl3d_extract_planes_static(const float* points, int H, int W, con
     sc.error = reinterpret_cast<int*>(ctl + 2);
     sc.phase_ns = nullptr;
     return frame_launch(sc, points, H, W, p, nd_host, K, out_mask, out_normals, out_labels, nullptr, nullptr,
-                        (cudaStream_t)stream);
+                        Tuning{0, 0, 0}, (cudaStream_t)stream);
 }

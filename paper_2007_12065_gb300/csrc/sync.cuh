@@ -35,6 +35,12 @@ __device__ __forceinline__ void fence_proxy_async_all() {
     asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
+// Makes a tensor map that the host copied into global memory before the launch visible to the
+// tensor-map proxy of this thread (issued before the thread's first TMA through that map).
+__device__ __forceinline__ void tensormap_acquire(const void* map) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(map) : "memory");
+}
+
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }

@@ -116,3 +116,20 @@ def test_product_path_does_not_touch_the_oracle():
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "import synth" not in text and "from synth" not in text, f
                 assert "pl3d_oracle" not in text and "liborc" not in text, f
+
+
+def test_batch_and_tuning_structs(pl3d):
+    assert ctypes.sizeof(pl3d.pl3d_frame) == 80
+    assert pl3d.pl3d_frame.params.offset == 16 and pl3d.pl3d_frame.K.offset == 32
+    assert pl3d.pl3d_frame.out_groups.offset == 72
+    assert ctypes.sizeof(pl3d.pl3d_tuning) == 12
+
+
+def test_batch_and_tuning_null_arguments(pl3d):
+    L = pl3d.lib()
+    t = pl3d.pl3d_tuning(1, 1, 1)
+    assert L.pl3d_extract_planes_batched(None, None, 0, None) == pl3d.PL3D_ERR_INVALID_ARG
+    assert L.pl3d_set_tuning(None, ctypes.byref(t)) == pl3d.PL3D_ERR_INVALID_ARG
+    assert L.pl3d_get_tuning(None, ctypes.byref(t)) == pl3d.PL3D_ERR_INVALID_ARG
+    assert L.pl3d_autotune_batched(None, None, 1, None, 3, None, None) == pl3d.PL3D_ERR_INVALID_ARG
+    assert L.pl3d_batch_stats(None, None, None, None) == pl3d.PL3D_ERR_INVALID_ARG
