@@ -130,6 +130,40 @@ def algorithmic_bytes(H: int, W: int) -> float:
     return 12.0 * H * W + 17.0 * 2 * (H - 1) * (W - 1)
 
 
+KERNEL_SOURCES = ["frame_kernels.cuh", "pl3d_internal.cuh", "sync.cuh", "df32.cuh", "uf.cuh", "f32x2.cuh"]
+
+
+def kernel_source_hash() -> str:
+    """sha256 over the sources the persistent kernels are compiled from."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2007_12065_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary of this kernel and workload, or None
+    when the kernel sources changed since that capture (the summary records their hash)."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        for key in ("traffic_bytes_per_launch:", "kernel_sources_sha256:"):
+            if line.strip().startswith(key):
+                vals[key] = line.strip()[len(key):].strip()
+    if vals.get("kernel_sources_sha256:") != kernel_source_hash():
+        return None
+    try:
+        return float(vals["traffic_bytes_per_launch:"])
+    except (KeyError, ValueError):
+        return None
+
+
 def fp32_peak_tflops(sm_count: int, mhz: float) -> float:
     """FP32 CUDA-core peak: 128 lanes per SM, an FMA = 2 FLOP."""
     return sm_count * 128 * 2 * mhz * 1e6 / 1e12
@@ -153,6 +187,188 @@ def time_oracle(frame, seconds_budget: float, threads: int) -> dict:
     sec = statistics.median(runs)
     return {"seconds_per_frame": sec, "frames": len(runs), "threads": threads,
             "mtri_s": frame.n_triangles / sec / 1e6}
+
+
+# ----------------------------------------------------------------------------- batched and served workloads
+
+SERVED_SENSORS = [(240, 320)] * 3 + [(480, 640)] * 2 + [(720, 1280)] + [(128, 2048)] * 2
+
+
+def _gen_frame(task):
+    H, W, seed = task
+    return synth.mixed_frame(H, W, seed=seed)
+
+
+def generate_frames(tasks, procs: int):
+    """Synthetic frames (H, W, seed) from the scene generators, made in a spawn pool (safe with
+    CUDA initialised in this process)."""
+    if procs <= 1 or len(tasks) <= 1:
+        return [_gen_frame(t) for t in tasks]
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(min(procs, len(tasks))) as pool:
+        return pool.map(_gen_frame, tasks)
+
+
+def batch_frames(bases: dict, n: int, seed: int):
+    """n frames with sizes drawn uniformly from synth.MIXED_SIZES; each is one of the generated
+    scenes of its size seen with fresh range noise (1e-3 relative, per pixel)."""
+    rng = np.random.default_rng(seed)
+    picks = rng.integers(0, len(synth.MIXED_SIZES), n)
+    out = []
+    for i, k in enumerate(picks):
+        variants = bases[synth.MIXED_SIZES[int(k)]]
+        base = variants[i % len(variants)]
+        r = np.random.default_rng(seed * 7919 + i)
+        pts = base.points * (1.0 + r.normal(0.0, 1e-3, base.points.shape[:2] + (1,))).astype(np.float32)
+        out.append((np.ascontiguousarray(pts, dtype=np.float32), base))
+    return out
+
+
+def run_batched(pl3d, torch, dev, frames, reps: int) -> dict:
+    """One batch of all frames (one persistent launch from a CUDA graph, autotuned launch shape)
+    against one plain launch per frame, both timed with CUDA events on one stream."""
+    stream = torch.cuda.current_stream(dev)
+    ctx = pl3d.pl3d_create(dev.index or 0)
+    b = pl3d.Batch()
+    keep = []
+    tris = 0
+    for pts, base in frames:
+        H, W = pts.shape[:2]
+        n = 2 * (H - 1) * (W - 1)
+        tris += n
+        d = torch.from_numpy(pts).to(dev)
+        o = (torch.empty(n, dtype=torch.uint8, device=dev), torch.empty((n, 3), device=dev),
+             torch.empty(n, dtype=torch.int32, device=dev))
+        p = pl3d.make_params(**base.params)
+        keep.append((d, o, p, base.dominant_normals))
+        b.add(d, H, W, p, base.dominant_normals, *o)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, n_rep):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(n_rep):
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    batched = lambda: pl3d.pl3d_extract_planes_batched(ctx, b, stream)  # noqa: E731
+
+    def per_frame():
+        for (d, o, p, nd), (pts, base) in zip(keep, frames):
+            pl3d.pl3d_extract_planes(ctx, d, pts.shape[0], pts.shape[1], p, nd, nd.shape[0], *o, stream)
+
+    ms_default = timed(batched, reps)
+    tun, tune_ms = pl3d.pl3d_autotune_batched(ctx, b, stream, reps=2)
+    ms_batched = timed(batched, reps)
+    pl3d.pl3d_set_tuning(ctx, None)
+    ms_loop = timed(per_frame, reps)
+    stats = pl3d.pl3d_batch_stats(ctx)
+    pl3d.pl3d_destroy(ctx)
+    sizes = {}
+    for pts, _ in frames:
+        k = f"{pts.shape[0]}x{pts.shape[1]}"
+        sizes[k] = sizes.get(k, 0) + 1
+    return {"frames": len(frames), "sizes": sizes, "triangles": tris, "inputs_mb": sum(p.nbytes for p, _ in frames) / 1e6,
+            "ms_batched": ms_batched, "mtri_s_batched": tris / ms_batched / 1e3,
+            "ms_batched_default_tuning": ms_default, "tuning": tun.as_dict(),
+            "ms_per_frame_launches": ms_loop, "mtri_s_per_frame_launches": tris / ms_loop / 1e3,
+            "speedup_vs_per_frame": ms_loop / ms_batched, "graph_launches": stats["graph_launches"],
+            "l2": "inputs (about 450 MB) larger than L2; no flush"}
+
+
+def run_served(pl3d, torch, sensor_frames, rate: float, seconds: float, max_inflight: int, max_batch: int,
+               seed: int) -> dict:
+    """Replays a Poisson trace (total `rate` frames/s over the sensors, sensor of each arrival
+    uniform) against a server; latency = completion - scheduled arrival (the driver's own lag
+    included)."""
+    ring = 8
+    srv = pl3d.pl3d_server_create(0, max_inflight=max_inflight, max_batch_frames=max_batch, hbm_bytes=24 << 30)
+    host_pts = [[torch.from_numpy(f.points).pin_memory() for f in fs] for fs in sensor_frames]
+    params = [pl3d.make_params(**fs[0].params) for fs in sensor_frames]
+    outs = []
+    for fs in sensor_frames:
+        H, W = fs[0].points.shape[:2]
+        n = 2 * (H - 1) * (W - 1)
+        outs.append([(torch.empty(n, dtype=torch.uint8).pin_memory(), torch.empty((n, 3)).pin_memory(),
+                      torch.empty(n, dtype=torch.int32).pin_memory()) for _ in range(ring)])
+    tri = [2 * (fs[0].points.shape[0] - 1) * (fs[0].points.shape[1] - 1) for fs in sensor_frames]
+
+    def submit(s, k):
+        f = sensor_frames[s][k % len(sensor_frames[s])]
+        H, W = f.points.shape[:2]
+        return pl3d.pl3d_server_submit(srv, host_pts[s][k % len(host_pts[s])], H, W, params[s], f.dominant_normals,
+                                       f.dominant_normals.shape[0], *outs[s][k % ring])
+
+    done = {}
+
+    def collect(wait_ms=0):
+        for c in pl3d.pl3d_server_poll(srv, max_n=4096, wait_ms=wait_ms):
+            done[c["ticket"]] = c
+
+    try:
+        for s in range(len(sensor_frames)):              # warm-up: every sensor once
+            submit(s, 0)
+        pl3d.pl3d_server_drain(srv)
+        collect()
+        done.clear()
+        base_stats = pl3d.pl3d_server_get_stats(srv)
+        rng = np.random.default_rng(seed)
+        n = max(1, int(rate * seconds))
+        t_arr = np.cumsum(rng.exponential(1.0 / rate, n))
+        which = rng.integers(0, len(sensor_frames), n)
+        count = [0] * len(sensor_frames)
+        ring_ticket = [[0] * ring for _ in sensor_frames]
+        lag, sensor_of = {}, {}
+        t0 = time.perf_counter()
+        for i in range(n):
+            target = t0 + t_arr[i]
+            while True:
+                now = time.perf_counter()
+                if now >= target:
+                    break
+                if target - now > 0.0015:
+                    time.sleep(0.0005)
+            s = int(which[i])
+            k = count[s]
+            count[s] += 1
+            prev = ring_ticket[s][k % ring]
+            while prev and prev not in done:            # the output buffers are still in use
+                collect(wait_ms=1)
+            t_sub = time.perf_counter()
+            tk = submit(s, k)
+            lag[tk] = t_sub - target
+            sensor_of[tk] = s
+            ring_ticket[s][k % ring] = tk
+            if i % 16 == 0:
+                collect()
+        pl3d.pl3d_server_drain(srv)
+        t_end = time.perf_counter()
+        collect()
+        stats = pl3d.pl3d_server_get_stats(srv)
+    finally:
+        pl3d.pl3d_server_destroy(srv)
+    lat = np.array([done[t]["latency_ms"] + 1e3 * lag[t] for t in lag])
+    lags = np.array(list(lag.values())) * 1e3
+    tris = sum(tri[sensor_of[t]] for t in lag)
+    bf = np.array([done[t]["batch_frames"] for t in lag])
+    return {"rate_fps": rate, "seconds": seconds, "requests": n, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+            "mtri_s": tris / (t_end - t0) / 1e6, "achieved_fps": n / (t_end - t0),
+            "mean_batch_frames": float(bf.mean()), "max_batch_frames": int(bf.max()),
+            "batches": stats["batches"] - base_stats["batches"], "max_inflight": stats["max_inflight"],
+            "driver_lag_p99_ms": float(np.percentile(lags, 99)),
+            "all_ok": all(done[t]["status"] == 0 for t in lag)}
+
+
+def served_sensor_frames(procs: int, seed: int = 105):
+    tasks = [(H, W, seed * 100 + 10 * i + j) for i, (H, W) in enumerate(SERVED_SENSORS) for j in range(2)]
+    fr = generate_frames(tasks, procs)
+    return [fr[2 * i:2 * i + 2] for i in range(len(SERVED_SENSORS))]
 
 
 # ----------------------------------------------------------------------------- arms
@@ -317,6 +533,25 @@ def run_pl3d(args):
             dist.destroy_process_group()
         return
 
+    # ---------------- batched (256 mixed frames, one launch) and served (Poisson trace) workloads
+    batched = served = None
+    if world == 1 and not args.no_batched:
+        tasks = [(H_, W_, 104_000 + 10 * i + j) for i, (H_, W_) in enumerate(synth.MIXED_SIZES) for j in range(2)]
+        gen = generate_frames(tasks, os.cpu_count() or 1)
+        bases = {hw: gen[2 * i:2 * i + 2] for i, hw in enumerate(synth.MIXED_SIZES)}
+        batched = run_batched(pl3d, torch, dev, batch_frames(bases, 256, 104), reps=5)
+        batched["config"] = "256 frames, sizes uniform over " + ", ".join(f"{a}x{b}" for a, b in synth.MIXED_SIZES)
+    if world == 1 and not args.no_served:
+        sf = served_sensor_frames(os.cpu_count() or 1)
+        served = {"sensors": ", ".join(f"{a}x{b}" for a, b in SERVED_SENSORS),
+                  "continuous_batching": run_served(pl3d, torch, sf, args.served_rate, args.served_seconds, 2, 64,
+                                                    105),
+                  "sequential_fifo": run_served(pl3d, torch, sf, args.served_rate, args.served_seconds, 1, 1, 105)}
+        if args.served_sweep:
+            served["sweep"] = [{"mode": mode, **run_served(pl3d, torch, sf, r, 10.0, mi, mb, 105)}
+                               for r in (200, 500, 1000, 2000, 5000)
+                               for mode, mi, mb in (("continuous_batching", 2, 64), ("sequential_fifo", 1, 1))]
+
     # ---------------- roofline of the frame kernel (the only kernel: one launch per frame)
     peaks, peak_src = _peaks()
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -334,7 +569,8 @@ def run_pl3d(args):
     phases["laplacian"]["tflops"] = flop["laplacian"] / (phases["laplacian"]["us"] * 1e-6) / 1e12
     phases["bilateral"]["tflops"] = flop["bilateral"] / (phases["bilateral"]["us"] * 1e-6) / 1e12
     roofline = {"bound": "alu", "kernel": "frame_kernel", "achieved": achieved, "peak": fp32_peak,
-                "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                "traffic": recorded_traffic("frame_kernel", args.workload),
                 "peak_source": f"FP32 CUDA-core peak: {sm_count} SMs x 128 lanes x 2 FLOP x {mhz} MHz",
                 "avg_launch_us": avg_launch_s * 1e6, "work_per_launch": flop["total"], "work_unit": "FLOP",
                 "hbm": {"algorithmic_bytes": nbytes, "achieved_gbs": nbytes / avg_launch_s / 1e9,
@@ -365,6 +601,8 @@ def run_pl3d(args):
         "gpu_launches": int(launches),
         "roofline": roofline,
         "cpu_baseline": cpu,
+        "batched": batched,
+        "served": served,
         "step_ms_p50": statistics.median(step_ms),
         "step_ms_min": min(step_ms),
         "wall_s_timed_region": t1 - t0,
@@ -385,6 +623,11 @@ def main():
     ap.add_argument("--workload", default="rgbd_480x640", choices=sorted(synth.WORKLOADS))
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 256-frame batched workload")
+    ap.add_argument("--no-served", action="store_true", help="skip the served (Poisson trace) workload")
+    ap.add_argument("--served-rate", type=float, default=2000.0, help="frames/s of the served trace")
+    ap.add_argument("--served-seconds", type=float, default=2.0)
+    ap.add_argument("--served-sweep", action="store_true", help="also sweep 200..5000 frames/s, 10 s each")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

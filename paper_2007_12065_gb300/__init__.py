@@ -78,6 +78,34 @@ class pl3d_tuning(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class pl3d_server_config(ctypes.Structure):
+    _fields_ = [
+        ("device", ctypes.c_int32),
+        ("max_inflight", ctypes.c_int32),
+        ("max_batch_frames", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("hbm_bytes", ctypes.c_int64),
+    ]
+
+
+class pl3d_completion(ctypes.Structure):
+    _fields_ = [
+        ("ticket", ctypes.c_uint64),
+        ("status", ctypes.c_int32),
+        ("batch_frames", ctypes.c_int32),
+        ("latency_ms", ctypes.c_double),
+        ("queue_ms", ctypes.c_double),
+    ]
+
+
+class pl3d_server_stats(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_int64) for name in ("submitted", "completed", "rejected", "batches", "triangles",
+                                                   "max_batch_frames", "max_inflight", "slot_bytes")]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 class PL3DError(RuntimeError):
     def __init__(self, status: int, what: str):
         super().__init__(f"{what}: {pl3d_status_string(status)} ({status})")
@@ -128,6 +156,14 @@ def lib():
     L.pl3d_autotune_batched.argtypes = [_vp, F, ctypes.c_int, _vp, ctypes.c_int, T, ctypes.POINTER(ctypes.c_double)]
     L.pl3d_batch_stats.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                    ctypes.POINTER(ctypes.c_int64)]
+    L.pl3d_server_create.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(pl3d_server_config)]
+    L.pl3d_server_submit.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, P, _vp, ctypes.c_int, _vp, _vp, _vp,
+                                     ctypes.POINTER(ctypes.c_uint64)]
+    L.pl3d_server_poll.argtypes = [_vp, ctypes.POINTER(pl3d_completion), ctypes.c_int, ctypes.c_int]
+    L.pl3d_server_drain.argtypes = [_vp]
+    L.pl3d_server_get_stats.argtypes = [_vp, ctypes.POINTER(pl3d_server_stats)]
+    L.pl3d_server_destroy.argtypes = [_vp]
+    L.pl3d_server_destroy.restype = None
     _lib = L
     return L
 
@@ -361,6 +397,52 @@ def pl3d_batch_stats(ctx) -> dict:
     a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
     _check(lib().pl3d_batch_stats(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "pl3d_batch_stats")
     return {"graph_launches": a.value, "desc_uploads": b.value, "graphs": c.value}
+
+
+def pl3d_server_create(device: int = 0, max_inflight: int = 2, max_batch_frames: int = 64, hbm_bytes: int = 0) -> int:
+    """A frame server with continuous batching; returns its handle (see include/pl3d.h)."""
+    cfg = pl3d_server_config(int(device), int(max_inflight), int(max_batch_frames), 0, int(hbm_bytes))
+    h = _vp()
+    _check(lib().pl3d_server_create(ctypes.byref(h), ctypes.byref(cfg)), "pl3d_server_create")
+    return int(h.value)
+
+
+def pl3d_server_submit(srv, points, H, W, params, dominant_normals, K, out_tri_mask, out_normals, out_labels) -> int:
+    """Host buffers (pinned CPU tensors or numpy arrays) that must stay alive until the ticket completes."""
+    n_tri = 2 * (H - 1) * (W - 1)
+    _check_tensor(points, "points", "torch.float32", H * W * 3, "cpu")
+    _check_tensor(out_tri_mask, "out_tri_mask", "torch.uint8", n_tri, "cpu")
+    _check_tensor(out_normals, "out_normals", "torch.float32", n_tri * 3, "cpu")
+    _check_tensor(out_labels, "out_labels", "torch.int32", n_tri, "cpu")
+    nd = _nd_host(dominant_normals)
+    t = ctypes.c_uint64()
+    _check(lib().pl3d_server_submit(srv, _ptr(points), int(H), int(W), ctypes.byref(params), _ptr(nd), int(K),
+                                    _ptr(out_tri_mask), _ptr(out_normals), _ptr(out_labels), ctypes.byref(t)),
+           "pl3d_server_submit")
+    return int(t.value)
+
+
+def pl3d_server_poll(srv, max_n: int = 1024, wait_ms: int = 0) -> list:
+    buf = (pl3d_completion * max(1, max_n))()
+    n = lib().pl3d_server_poll(srv, buf, int(max_n), int(wait_ms))
+    if n < 0:
+        raise PL3DError(n, "pl3d_server_poll")
+    return [dict(ticket=int(c.ticket), status=int(c.status), batch_frames=int(c.batch_frames),
+                 latency_ms=float(c.latency_ms), queue_ms=float(c.queue_ms)) for c in buf[:n]]
+
+
+def pl3d_server_drain(srv) -> None:
+    _check(lib().pl3d_server_drain(srv), "pl3d_server_drain")
+
+
+def pl3d_server_get_stats(srv) -> dict:
+    st = pl3d_server_stats()
+    _check(lib().pl3d_server_get_stats(srv, ctypes.byref(st)), "pl3d_server_get_stats")
+    return st.as_dict()
+
+
+def pl3d_server_destroy(srv) -> None:
+    lib().pl3d_server_destroy(srv)
 
 
 def pl3d_sync(ctx, stream=None) -> int:

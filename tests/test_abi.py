@@ -133,3 +133,21 @@ def test_batch_and_tuning_null_arguments(pl3d):
     assert L.pl3d_get_tuning(None, ctypes.byref(t)) == pl3d.PL3D_ERR_INVALID_ARG
     assert L.pl3d_autotune_batched(None, None, 1, None, 3, None, None) == pl3d.PL3D_ERR_INVALID_ARG
     assert L.pl3d_batch_stats(None, None, None, None) == pl3d.PL3D_ERR_INVALID_ARG
+
+
+def test_server_structs_and_config_checks(pl3d):
+    assert ctypes.sizeof(pl3d.pl3d_server_config) == 24
+    assert ctypes.sizeof(pl3d.pl3d_completion) == 32
+    assert ctypes.sizeof(pl3d.pl3d_server_stats) == 64
+    L = pl3d.lib()
+    h = ctypes.c_void_p()
+    for cfg in [(0, 0, 8, 0, 0), (0, 3, 8, 0, 0), (0, 1, 0, 0, 0), (0, 1, 5000, 0, 0), (0, 1, 8, 1, 0),
+                (0, 1, 8, 0, -1)]:
+        c = pl3d.pl3d_server_config(*cfg)
+        assert L.pl3d_server_create(ctypes.byref(h), ctypes.byref(c)) == pl3d.PL3D_ERR_INVALID_ARG, cfg
+    assert L.pl3d_server_create(None, None) == pl3d.PL3D_ERR_INVALID_ARG
+    assert L.pl3d_server_submit(None, None, 4, 4, None, None, 1, None, None, None, None) == pl3d.PL3D_ERR_INVALID_ARG
+    assert L.pl3d_server_poll(None, None, 0, 0) == pl3d.PL3D_ERR_INVALID_ARG
+    assert L.pl3d_server_drain(None) == pl3d.PL3D_ERR_INVALID_ARG
+    assert L.pl3d_server_get_stats(None, None) == pl3d.PL3D_ERR_INVALID_ARG
+    L.pl3d_server_destroy(None)
