@@ -53,7 +53,8 @@ size_t bil_smem(int halo) {
     const int rq = kTile + 2 * halo;
     const int quads = align_floats(6 * (rq * rq + rq));
     const int boxes = 2 * align_floats(b.rows * b.cols);
-    return 128 + 4 * (size_t)(2 * quads + (quads > boxes ? quads : boxes)) + 4 * (size_t)kTile * kTile;
+    return 128 + 4 * (size_t)(2 * quads + (quads > boxes ? quads : boxes)) + 4 * (size_t)kTile * kTile +
+           4 * (size_t)kExactCap;
 }
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link against libcuda).

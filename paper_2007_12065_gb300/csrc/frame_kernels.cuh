@@ -245,26 +245,39 @@ __device__ __forceinline__ V3 pair_cross(const PairEdge& e1, const PairEdge& e2)
 // Edge b - a in FP32 and the size of what was summed to form it (for the error bound).
 struct FastEdge {
     V3 e;
-    float m;    // sum over coordinates of |v0_b - v0_a| + |d_b - d_a|
+    float m;    // sum over coordinates of the differences |v0_b - v0_a|, |d_b - d_a| that were rounded
     float l1;   // sum over coordinates of |e|
 };
+
+// |q - p| where the difference q - p was rounded, 0 where it is exact: a computed difference
+// below both operands in magnitude proves that q lies within a factor 2 of p (rounding is
+// monotonic, so the exact difference is below them too), and then q - p is exact (Sterbenz).
+__device__ __forceinline__ float rounded_part(float diff, float p, float q) {
+    const float ad = fabsf(diff);
+    return ad < fminf(fabsf(p), fabsf(q)) ? 0.f : ad;
+}
 
 __device__ __forceinline__ FastEdge fast_edge(const SP& a, const SP& b) {
     const float ax = b.x - a.x, ay = b.y - a.y, az = b.z - a.z;
     const float dx = b.dx - a.dx, dy = b.dy - a.dy, dz = b.dz - a.dz;
     FastEdge f;
     f.e = {ax + dx, ay + dy, az + dz};
-    f.m = (fabsf(ax) + fabsf(dx)) + (fabsf(ay) + fabsf(dy)) + (fabsf(az) + fabsf(dz));
+    f.m = (rounded_part(ax, a.x, b.x) + rounded_part(dx, a.dx, b.dx)) +
+          (rounded_part(ay, a.y, b.y) + rounded_part(dy, a.dy, b.dy)) +
+          (rounded_part(az, a.z, b.z) + rounded_part(dz, a.dz, b.dz));
     f.l1 = fabsf(f.e.x) + fabsf(f.e.y) + fabsf(f.e.z);
     return f;
 }
 
-// The FP32 cross product of two FP32 edges is off by at most about
-// 2^-22 sqrt(3) (m1 |e2|_1 + |e1|_1 m2 + |e1|_1 |e2|_1) / |cr|_1 radians; accept it when that
-// is below 2e-6 rad (the factor 8 below), otherwise fall back to exact pairs.
+// Error of the FP32 normal. Each edge coordinate is off by at most u (m_c + |e_c|), u = 2^-24,
+// m_c the rounded differences summed into it; the cross product adds u per product and u for
+// the difference. So |d cr|_1 <= u (m1 |e2|_1 + |e1|_1 m2 + 4 |e1|_1 |e2|_1), and the angle is
+// off by at most sqrt(3) |d cr|_1 / |cr|_1. Accept the FP32 normal when that bound is below
+// sqrt(3) 64 u = 6.6e-6 rad (15 times inside the 1e-4 rad tolerance), otherwise recompute it
+// from exact pairs.
 __device__ __forceinline__ bool fast_cross_ok(const FastEdge& e1, const FastEdge& e2, V3 cr) {
     const float crl1 = fabsf(cr.x) + fabsf(cr.y) + fabsf(cr.z);
-    return e1.m * e2.l1 + e1.l1 * e2.m + e1.l1 * e2.l1 <= 8.f * crl1;
+    return e1.m * e2.l1 + e1.l1 * e2.m + 4.f * (e1.l1 * e2.l1) <= 64.f * crl1;
 }
 
 __device__ __forceinline__ V3 centroid3(const SP& a, const SP& b, const SP& c) {
@@ -407,6 +420,7 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
     const int xw = max(align_floats(6 * nqs), 2 * bsz);
     uint8_t* Mk = reinterpret_cast<uint8_t*>(X + xw);    // [T*T*2] own masks
     uint8_t* Gs = Mk + 2 * T * T;                        // [T*T*2] own groups
+    int* ex_list = reinterpret_cast<int*>(Gs + 2 * T * T);   // [kExactCap] deferred exact normals
     const int tiles_x = div_up(Wq, T);
     const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
     const int qu0 = ty * T - h, qv0 = tx * T - h;
@@ -424,6 +438,8 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
         parity ^= 1u;
     }
     __syncthreads();
+    int* n_exact = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(bar) + 64);   // in the smem header
+    if (threadIdx.x == 0) *n_exact = 0;
     for (int i = threadIdx.x; i < (RQH + 1) * (RQW + 1); i += blockDim.x) {
         const int r = i / (RQW + 1), c = i - r * (RQW + 1);
         const int o = r * b.cols + dlt + 3 * c;
@@ -434,7 +450,36 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
     }
     __syncthreads();
 
-    // Centroids and normals of every staged triangle; masks of the tile's own quads.
+    // Centroids and normals of every staged triangle; masks of the tile's own quads. A normal
+    // whose FP32 error bound fails is deferred: its quad goes on a short list that a second
+    // loop recomputes from exact pairs with every lane busy (inline, divergent, only when the
+    // list is full).
+    auto exact_normals = [&](const SP& p1, const SP& p2, const SP& p3, const SP& p4, bool do0, bool do1, V3& n0,
+                             V3& n1) {
+        const PairEdge pd = pair_edge(p3, p1);
+        if (do0) n0 = pair_cross(pair_edge(p3, p2), pd);
+        if (do1) {
+            const PairEdge pdn = {{-pd.x.h, -pd.x.l}, {-pd.y.h, -pd.y.l}, {-pd.z.h, -pd.z.l}};
+            n1 = pair_cross(pair_edge(p1, p4), pdn);
+        }
+    };
+    auto unit_or_none = [](V3 cr, bool valid) {
+        const float len2 = dot(cr, cr);
+        V3 n = {0.f, 0.f, 0.f};
+        if (valid && len2 > kDegenerateLen2) {
+            const float inv = rsqrtf(len2);
+            n = {cr.x * inv, cr.y * inv, cr.z * inv};
+        }
+        return n;
+    };
+    auto scaled_centroid = [&](const SP& va, const SP& vb, const SP& vc, V3 n) {
+        V3 c = {kAbsentCentroid, kAbsentCentroid, kAbsentCentroid};
+        if (has_normal(n)) {
+            const V3 m = centroid3(va, vb, vc);
+            c = {m.x * cs, m.y * cs, m.z * cs};
+        }
+        return c;
+    };
     for (int q = threadIdx.x; q < nq; q += blockDim.x) {
         const int qr = q / RQW, qc = q - qr * RQW;
         const int gu = qu0 + qr, gv = qv0 + qc;
@@ -454,24 +499,19 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
             V3 cr0 = cross(er.e, ed.e), cr1 = cross(el.e, edn.e);
             const bool exact0 = valid0 && !fast_cross_ok(er, ed, cr0);
             const bool exact1 = valid1 && !fast_cross_ok(el, edn, cr1);
+            bool defer = false;
             if (exact0 || exact1) {
-                const PairEdge pd = pair_edge(p3, p1);
-                if (exact0) cr0 = pair_cross(pair_edge(p3, p2), pd);
-                if (exact1) {
-                    const PairEdge pdn = {{-pd.x.h, -pd.x.l}, {-pd.y.h, -pd.y.l}, {-pd.z.h, -pd.z.l}};
-                    cr1 = pair_cross(pair_edge(p1, p4), pdn);
+                const int slot = atomicAdd(n_exact, 1);
+                if (slot < kExactCap) {
+                    ex_list[slot] = q | (exact0 ? 1 << 29 : 0) | (exact1 ? 1 << 30 : 0);
+                    defer = true;
+                } else {
+                    exact_normals(p1, p2, p3, p4, exact0, exact1, cr0, cr1);
                 }
             }
-            const V3 cr[2] = {cr0, cr1};
-            const bool vk[2] = {valid0, valid1};
-#pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                const float len2 = dot(cr[k], cr[k]);
-                if (vk[k] && len2 > kDegenerateLen2) {
-                    const float inv = rsqrtf(len2);
-                    nn[k] = {cr[k].x * inv, cr[k].y * inv, cr[k].z * inv};
-                }
-            }
+            // a deferred quad's records are written again by the second loop
+            nn[0] = unit_or_none(cr0, valid0 && !(defer && exact0));
+            nn[1] = unit_or_none(cr1, valid1 && !(defer && exact1));
         } else {
             const bool vk[2] = {valid0, valid1};
 #pragma unroll
@@ -482,18 +522,7 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
                 if (nx == nx) nn[k] = {nx, __ldg(ph.carry_in + 3 * gid + 1), __ldg(ph.carry_in + 3 * gid + 2)};
             }
         }
-        V3 cc[2];
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const SP& va = k == 0 ? p3 : p1;
-            const SP& vb = k == 0 ? p2 : p4;
-            const SP& vc = k == 0 ? p1 : p3;
-            cc[k] = {kAbsentCentroid, kAbsentCentroid, kAbsentCentroid};
-            if (has_normal(nn[k])) {
-                const V3 c = centroid3(va, vb, vc);
-                cc[k] = {c.x * cs, c.y * cs, c.z * cs};
-            }
-        }
+        const V3 cc0 = scaled_centroid(p3, p2, p1, nn[0]), cc1 = scaled_centroid(p1, p4, p3, nn[1]);
         if (own) {                                                               // Algorithm 4, l_max
             // FP32 edges: ~1e-7 relative error, far inside the 1e-5 m band where FP32 and FP64
             // may disagree
@@ -506,8 +535,35 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
             Mk[t] = (valid0 && l0 <= a.max_edge2) ? 1 : 0;
             Mk[t + 1] = (valid1 && l1 <= a.max_edge2) ? 1 : 0;
         }
-        store_quad(Cq, q, cc[0], cc[1]);
+        store_quad(Cq, q, cc0, cc1);
         store_quad(Na, q, nn[0], nn[1]);
+    }
+    __syncthreads();
+    // the deferred normals (and their centroids), one quad per lane
+    const int n_ex = min(*n_exact, kExactCap);
+    for (int i = threadIdx.x; i < n_ex; i += blockDim.x) {
+        const int e = ex_list[i];
+        const int q = e & ((1 << 29) - 1);
+        const bool do0 = (e >> 29) & 1, do1 = (e >> 30) & 1;
+        const int qr = q / RQW, qc = q - qr * RQW;
+        const int o1 = qr * b.cols + dlt + 3 * qc;
+        const SP p1 = load_sp(V0, Dp, o1), p2 = load_sp(V0, Dp, o1 + 3);
+        const SP p3 = load_sp(V0, Dp, o1 + b.cols + 3), p4 = load_sp(V0, Dp, o1 + b.cols);
+        V3 cr0 = {0.f, 0.f, 0.f}, cr1 = cr0;
+        exact_normals(p1, p2, p3, p4, do0, do1, cr0, cr1);
+        // the flagged triangles are valid (the flag requires it); write only their slots
+        float* cq = Cq + 6 * q;
+        float* na = Na + 6 * q;
+        if (do0) {
+            const V3 n = unit_or_none(cr0, true), c = scaled_centroid(p3, p2, p1, n);
+            na[0] = n.x, na[2] = n.y, na[4] = n.z;
+            cq[0] = c.x, cq[2] = c.y, cq[4] = c.z;
+        }
+        if (do1) {
+            const V3 n = unit_or_none(cr1, true), c = scaled_centroid(p1, p4, p3, n);
+            na[1] = n.x, na[3] = n.y, na[5] = n.z;
+            cq[1] = c.x, cq[3] = c.y, cq[5] = c.z;
+        }
     }
     __syncthreads();   // the staged boxes are dead from here on; Nb reuses their space
 
@@ -572,7 +628,11 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
         return;
     }
 
-    int32_t* Lp = reinterpret_cast<int32_t*>(nxt);   // free after the last iteration: [T*T*2] parents
+    // free after the last iteration (>= 6 * 1056 floats): union-find parents, the run
+    // representative of each triangle, and the tile root of each representative [T*T*2] each
+    int32_t* Lp = reinterpret_cast<int32_t*>(nxt);
+    int32_t* RunOf = Lp + 2 * T * T;
+    int32_t* RootOf = RunOf + 2 * T * T;
     for (int i = threadIdx.x; i < T * T; i += blockDim.x) {
         const int r = i / T, c = i - r * T;
         const int gu = ty * T + r, gv = tx * T + c;
@@ -652,8 +712,12 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
             const int t0 = 2 * (r * T + l0);
             return ((p & 1) || !((brk_f_mask >> l0) & 1u)) ? t0 : t0 + 1;
         };
-        Lp[ts] = gs != PL3D_NO_GROUP ? root_of(start_s) : -1;
-        Lp[tf] = gf != PL3D_NO_GROUP ? root_of(start_f) : -1;
+        const int rep_s = gs != PL3D_NO_GROUP ? root_of(start_s) : -1;
+        const int rep_f = gf != PL3D_NO_GROUP ? root_of(start_f) : -1;
+        Lp[ts] = rep_s;
+        Lp[tf] = rep_f;
+        RunOf[ts] = rep_s;
+        RunOf[tf] = rep_f;
     }
     __syncthreads();
     // (2) Rows joined across horizontal edges: first(r, v) with second(r-1, v); one union per
@@ -668,13 +732,19 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
             load_quad(Cq, (r - 1 + h) * RQW + (lane + h), c0u, cu);
             link = offset_ok(gf, cf, cu);
         }
-        const int ra = link ? Lp[tf] : -1, rb = link ? Lp[tu] : -1;
+        const int ra = link ? RunOf[tf] : -1, rb = link ? RunOf[tu] : -1;
         const int pa = __shfl_up_sync(kFull, ra, 1), pb = __shfl_up_sync(kFull, rb, 1);
         const bool dup = lane > 0 && pa == ra && pb == rb;
         if (link && !dup) uf_unite(Lp, ra, rb);
     }
     __syncthreads();
-    // (3) Each triangle leaves with the GID of its tile-local root (-1 without a group).
+    // (3) Only the run representatives walk to their tile root (the unions linked nothing
+    // else); no union runs any more, so halving the path while walking only ever points a node
+    // at one of its ancestors, and shortens the walks of the other threads.
+    for (int t = threadIdx.x; t < 2 * T * T; t += blockDim.x)
+        if (RunOf[t] == t) RootOf[t] = uf_find(Lp, t);
+    __syncthreads();
+    // (4) Each triangle leaves with the GID of its tile-local root (-1 without a group).
     for (int i = threadIdx.x; i < T * T; i += blockDim.x) {
         const int r = i / T, c = i - r * T;
         const int gu = ty * T + r, gv = tx * T + c;
@@ -682,12 +752,10 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
         const size_t gid0 = 2 * ((size_t)gu * Wq + gv);
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
-            const int t = 2 * i + k;
+            const int rep = RunOf[2 * i + k];
             int lab = -1;
-            if (Lp[t] >= 0) {
-                // no union runs any more: halving the path while walking only ever points a
-                // node at one of its ancestors, and shortens the walks of the other threads
-                const int root = uf_find(Lp, t);
+            if (rep >= 0) {
+                const int root = RootOf[rep];
                 const int rq = root >> 1, rr = rq / T, rc = rq - rr * T;
                 lab = (int)(2 * ((size_t)(ty * T + rr) * Wq + (tx * T + rc)) + (root & 1));
             }
@@ -713,8 +781,10 @@ __device__ __forceinline__ V3 centroid_global(const FrameArgs& a, int u, int v, 
 }
 
 // Twins that cross a tile border: the top edge of a tile's first quad row and the right edge of
-// its last quad column. Work items: (row borders) x Wq, then (column borders) x Hq.
-__device__ __forceinline__ void merge_item(const FrameArgs& a, long long w) {
+// its last quad column. Work items: (row borders) x Wq, then (column borders) x Hq. Returns
+// whether item w joins two triangles, and then their current labels (each in its triangle's
+// set: the tile root, or an ancestor of it once a union has linked that root).
+__device__ __forceinline__ bool merge_pair(const FrameArgs& a, long long w, int& ra, int& rb) {
     const int Wq = a.W - 1, Hq = a.H - 1;
     const long long n_row_items = (long long)(div_up(Hq, T) - 1) * Wq;
     int u, v, uj, vj;
@@ -733,40 +803,84 @@ __device__ __forceinline__ void merge_item(const FrameArgs& a, long long w) {
     const int i = 2 * (u * Wq + v);
     const int j = 2 * (uj * Wq + vj) + 1;
     const int g = a.groups[i];
-    if (g == PL3D_NO_GROUP || a.groups[j] != g) return;
+    if (g == PL3D_NO_GROUP || a.groups[j] != g) return false;
     if (a.max_offset > 0.f) {
         const V3 ci = centroid_global(a, u, v, 0), cj = centroid_global(a, uj, vj, 1);
         const float* nd = a.nd.v + 3 * g;
-        if (fabsf(nd[0] * (ci.x - cj.x) + nd[1] * (ci.y - cj.y) + nd[2] * (ci.z - cj.z)) > a.max_offset) return;
+        if (fabsf(nd[0] * (ci.x - cj.x) + nd[1] * (ci.y - cj.y) + nd[2] * (ci.z - cj.z)) > a.max_offset) return false;
     }
-    uf_unite(a.labels, i, j);
+    ra = __ldcg(a.labels + i);
+    rb = __ldcg(a.labels + j);
+    return true;
+}
+
+// One union per distinct pair in a warp: consecutive lanes walk one border, where long runs
+// of twins join the same two tile segments; a lane whose pair (and frame) equals its left
+// neighbour's leaves the union to that lane. Called by whole warps.
+__device__ __forceinline__ void merge_unite(int32_t* labels, bool link, int ra, int rb, int frame) {
+    if (!link) ra = rb = -1;
+    const int pa = __shfl_up_sync(0xffffffffu, ra, 1), pb = __shfl_up_sync(0xffffffffu, rb, 1);
+    const int pf = __shfl_up_sync(0xffffffffu, frame, 1);
+    const bool dup = (threadIdx.x & 31) > 0 && pa == ra && pb == rb && pf == frame;
+    if (link && !dup) uf_unite(labels, ra, rb);
 }
 
 __device__ __forceinline__ void merge_phase(const FrameArgs& a) {
     const int Wq = a.W - 1, Hq = a.H - 1;
     const long long n = (long long)(div_up(Hq, T) - 1) * Wq + (long long)(div_up(Wq, T) - 1) * Hq;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < n; w += stride) merge_item(a, w);
+    const long long n_iter = (n + stride - 1) / stride;   // uniform: whole warps stay together
+    const long long base = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    for (long long it = 0; it < n_iter; ++it) {
+        const long long w = base + it * stride;
+        int ra = -1, rb = -1;
+        const bool link = w < n && merge_pair(a, w, ra, rb);
+        merge_unite(a.labels, link, ra, rb, 0);
+    }
+}
+
+// Root of a label whose parent has already been loaded (no union runs any more; L2 loads, as
+// other threads overwrite labels with roots meanwhile -- an ancestor either way).
+__device__ __forceinline__ int root_from(const int32_t* L, int x, int p) {
+    while (p != x) {
+        x = p;
+        p = __ldcg(L + x);
+    }
+    return x;
 }
 
 // Every grouped triangle takes its root; with tri_min > 0 the segment sizes are counted, one
-// atomic per run of equal roots in a warp.
+// atomic per run of equal roots in a warp. Four triangles per thread are in flight at once:
+// their labels, then their parents, are loaded together before any walk continues.
 __device__ __forceinline__ void flatten_phase(const FrameArgs& a) {
+    constexpr int U = 4;
     const long long n = 2LL * (a.H - 1) * (a.W - 1);
     const long long stride = (long long)gridDim.x * blockDim.x;
-    const long long n_iter = (n + stride - 1) / stride;
+    const long long n_iter = (n + stride - 1) / stride;   // uniform: whole warps stay together
     const long long base = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    for (long long it = 0; it < n_iter; ++it) {          // uniform trip count: whole warps stay together
-        const long long i = base + it * stride;
-        int root = -1;
-        if (i < n && a.labels[i] >= 0) {
-            root = uf_root(a.labels, (int)i);
-            a.labels[i] = root;
+    int32_t* L = a.labels;
+    for (long long it0 = 0; it0 < n_iter; it0 += U) {
+        int lab[U], par[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const long long i = base + (it0 + u) * stride;
+            lab[u] = (it0 + u < n_iter && i < n) ? __ldcg(L + i) : -1;
         }
-        if (a.sizes) {
-            const unsigned peers = __match_any_sync(0xffffffffu, root);
-            const int leader = __ffs(peers) - 1;
-            if (root >= 0 && (int)(threadIdx.x & 31) == leader) atomicAdd(a.sizes + root, __popc(peers));
+#pragma unroll
+        for (int u = 0; u < U; ++u) par[u] = lab[u] >= 0 ? __ldcg(L + lab[u]) : -1;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const long long i = base + (it0 + u) * stride;
+            int root = -1;
+            if (lab[u] >= 0) {
+                root = root_from(L, lab[u], par[u]);
+                L[i] = root;
+            }
+            if (a.sizes) {
+                const unsigned peers = __match_any_sync(0xffffffffu, root);
+                const int leader = __ffs(peers) - 1;
+                if (root >= 0 && (int)(threadIdx.x & 31) == leader) atomicAdd(a.sizes + root, __popc(peers));
+            }
         }
     }
 }
@@ -905,39 +1019,67 @@ __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const __grid_constan
     const long long base = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     {
         const long long total = __ldg(b.merge_items + n);
+        const long long n_iter = (total + stride - 1) / stride;   // uniform: whole warps stay together
         int f = 0;
-        for (long long w = base; w < total; w += stride) {
-            f = frame::advance_frame(b.merge_items, f, w);
-            frame::merge_item(b.frames[f], w - __ldg(b.merge_items + f));
+        for (long long it = 0; it < n_iter; ++it) {
+            const long long w = base + it * stride;
+            int ra = -1, rb = -1;
+            bool link = false;
+            int32_t* labels = nullptr;
+            if (w < total) {
+                f = frame::advance_frame(b.merge_items, f, w);
+                const FrameArgs& a = b.frames[f];
+                labels = a.labels;
+                link = frame::merge_pair(a, w - __ldg(b.merge_items + f), ra, rb);
+            }
+            frame::merge_unite(labels, link, ra, rb, f);
         }
     }
     grid_barrier(b.barrier, b.error);
     mark(2);
     {
-        // every grouped triangle takes its root; segment sizes are counted per (frame, root)
+        // every grouped triangle takes its root; segment sizes are counted per (frame, root);
+        // four triangles per thread in flight at once, as in the single-frame flatten
+        constexpr int U = 4;
         const long long total = __ldg(b.tris + n);
         const long long n_iter = (total + stride - 1) / stride;   // uniform: whole warps stay together
         int f = 0;
-        for (long long it = 0; it < n_iter; ++it) {
-            const long long i = base + it * stride;
-            int root = -1;
-            long long key = -1;
-            int32_t* sizes = nullptr;
-            if (i < total) {
-                f = frame::advance_frame(b.tris, f, i);
-                const FrameArgs& a = b.frames[f];
-                const int li = (int)(i - __ldg(b.tris + f));
-                if (a.labels[li] >= 0) {
-                    root = uf_root(a.labels, li);
-                    a.labels[li] = root;
-                    key = ((long long)f << 32) | (unsigned)root;
-                    sizes = a.sizes;
+        for (long long it0 = 0; it0 < n_iter; it0 += U) {
+            int lab[U], par[U], fr[U];
+            int32_t* lp[U];
+            long long li[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const long long i = base + (it0 + u) * stride;
+                lab[u] = -1;
+                fr[u] = 0;
+                lp[u] = nullptr;
+                li[u] = 0;
+                if (it0 + u < n_iter && i < total) {
+                    f = frame::advance_frame(b.tris, f, i);
+                    fr[u] = f;
+                    lp[u] = b.frames[f].labels;
+                    li[u] = i - __ldg(b.tris + f);
+                    lab[u] = __ldcg(lp[u] + li[u]);
                 }
             }
-            if (any_filter) {
-                const unsigned peers = __match_any_sync(0xffffffffu, key);
-                const int leader = __ffs(peers) - 1;
-                if (sizes && (int)(threadIdx.x & 31) == leader) atomicAdd(sizes + root, __popc(peers));
+#pragma unroll
+            for (int u = 0; u < U; ++u) par[u] = lab[u] >= 0 ? __ldcg(lp[u] + lab[u]) : -1;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                int root = -1;
+                long long key = -1;
+                if (lab[u] >= 0) {
+                    root = frame::root_from(lp[u], lab[u], par[u]);
+                    lp[u][li[u]] = root;
+                    key = ((long long)fr[u] << 32) | (unsigned)root;
+                }
+                if (any_filter) {
+                    const unsigned peers = __match_any_sync(0xffffffffu, key);
+                    const int leader = __ffs(peers) - 1;
+                    int32_t* sizes = root >= 0 ? b.frames[fr[u]].sizes : nullptr;
+                    if (sizes && (int)(threadIdx.x & 31) == leader) atomicAdd(sizes + root, __popc(peers));
+                }
             }
         }
     }

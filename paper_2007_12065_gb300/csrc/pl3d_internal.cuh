@@ -25,6 +25,7 @@ constexpr int kThreads = 256;    // threads per CTA
 constexpr int kTile = 32;        // tile edge: 32 x 32 points (Laplacian) or quads (bilateral)
 constexpr int kLapMaxHalo = 8;   // largest halo (fused iterations x radius) of one Laplacian pass
 constexpr int kBilMaxHalo = 6;   // same for the bilateral
+constexpr int kExactCap = 256;   // deferred exact-normal quads a bilateral tile lists (then inline)
 
 // Centroid given to a triangle without a normal: its bilateral weight underflows to
 // exactly 0 against any real triangle, so it drops out of every sum without a branch.
