@@ -218,6 +218,49 @@ def extract_halfedges(Tmap: np.ndarray, H: int, W: int, ntri: int) -> np.ndarray
     return HE[:3 * ntri].copy()
 
 
+def segment_lists(labels: np.ndarray, Tmap: np.ndarray):
+    """Planar segments as triangle sets (Algorithm 5's output T^g_i, the input of polygon
+    extraction, Section 7.2). Segments are ordered by label (their smallest GID); each holds the
+    T indices (Algorithm 1) of its triangles in ascending order.
+    -> (seg_labels int32 [S], offsets int32 [S + 1], tris int32 [offsets[S]])."""
+    labels = np.asarray(labels, np.int64)
+    Tmap = np.asarray(Tmap, np.int64)
+    gids = np.nonzero(labels >= 0)[0]                    # ascending GID
+    lab = labels[gids]
+    order = np.argsort(lab, kind="stable")               # by label, ties kept in GID order
+    seg_labels, counts = np.unique(lab, return_counts=True)
+    offsets = np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)
+    return seg_labels.astype(np.int32), offsets, Tmap[gids[order]].astype(np.int32)
+
+
+def segment_border(T_labels: np.ndarray, HE: np.ndarray) -> np.ndarray:
+    """Boundary half-edges of the segments (the set BE of Section 7.2): bit e of entry t is set when
+    triangle t belongs to a segment and its half-edge 3t + e has no twin (HE = -1) or a twin whose
+    triangle carries another label. -> uint8 [len(T_labels)]."""
+    T_labels = np.asarray(T_labels, np.int64)
+    HE = np.asarray(HE, np.int64).reshape(-1, 3)
+    out = np.zeros(len(T_labels), np.uint8)
+    for e in range(3):
+        tw = HE[:, e]
+        other = np.where(tw >= 0, T_labels[np.maximum(tw, 0) // 3], -2)
+        border = (T_labels >= 0) & ((tw < 0) | (other != T_labels))
+        out |= (border.astype(np.uint8) << e)
+    return out
+
+
+def mesh_outputs(points: np.ndarray, labels: np.ndarray) -> dict:
+    """Explicit mesh (Algorithm 1: T, T_map; Algorithm 2: HE) of a frame and its segments' triangle
+    lists and boundary half-edges, given the frame's labels."""
+    H, W = points.shape[:2]
+    T, Tmap = extract_triangles(widen(points))
+    HE = extract_halfedges(Tmap, H, W, len(T))
+    seg_labels, offsets, tris = segment_lists(labels, Tmap)
+    gid_of = np.nonzero(np.asarray(Tmap) >= 0)[0]      # T index -> GID (T keeps GID order)
+    T_labels = np.asarray(labels)[gid_of]
+    return dict(T=T, Tmap=Tmap, HE=HE, seg_labels=seg_labels, seg_offsets=offsets, seg_tris=tris,
+                border=segment_border(T_labels, HE))
+
+
 # --------------------------------------------------------------------------- pipeline
 
 

@@ -554,3 +554,73 @@ def test_ill_conditioned_flags_are_rare_on_the_frame_workloads():
     for f in (synth.rgbd_120x160(), synth.lidar_64x1024()):
         r = oracle.extract_planes(f.points, oracle.OracleParams(**f.params), f.dominant_normals)
         assert r["ill_conditioned"].sum() <= 1e-4 * r["mask"].size
+
+
+# ----------------------------------------------------------------------------- segment triangle lists
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_segment_lists_match_bucketing_by_hand(seed):
+    """Section 7.2 takes each segment T^g_i as a triangle set: bucketing the labels GID by GID
+    into a dict must give the same lists, segment order by label, triangles by T index."""
+    rng = np.random.default_rng(seed)
+    H, W = 9, 13
+    pts = rng.normal(size=(H, W, 3)).astype(np.float32)
+    pts[rng.random((H, W)) < 0.15] = np.nan
+    T, Tmap = oracle.extract_triangles(oracle.widen(pts))
+    n = 2 * (H - 1) * (W - 1)
+    labels = np.full(n, -1, np.int32)
+    valid = np.nonzero(Tmap >= 0)[0]
+    roots = rng.choice(valid, size=5, replace=False)
+    for g in valid:
+        if rng.random() < 0.7:
+            r = roots[rng.integers(0, 5)]
+            labels[g] = min(r, g) if g < r else r   # any label; lists are defined for any values
+    buckets = {}
+    for g in range(n):
+        if labels[g] >= 0:
+            buckets.setdefault(int(labels[g]), []).append(int(Tmap[g]))
+    seg_labels, offsets, tris = oracle.segment_lists(labels, Tmap)
+    assert list(seg_labels) == sorted(buckets)
+    assert offsets[0] == 0 and offsets[-1] == len(tris) == sum(len(v) for v in buckets.values())
+    for k, lab in enumerate(seg_labels):
+        assert list(tris[offsets[k]:offsets[k + 1]]) == buckets[int(lab)]
+        assert np.all(np.diff(tris[offsets[k]:offsets[k + 1]]) > 0)
+
+
+def test_segment_border_of_full_grid_is_its_perimeter():
+    """One segment over a fully valid grid: its boundary half-edges are exactly the grid's
+    perimeter edges, 2 (H-1) + 2 (W-1) of them, one per border half-edge of Algorithm 2."""
+    H, W = 6, 9
+    pts = np.zeros((H, W, 3), np.float32)
+    pts[..., 0], pts[..., 1] = np.meshgrid(np.arange(W), np.arange(H))
+    out = oracle.mesh_outputs(pts, np.zeros(2 * (H - 1) * (W - 1), np.int32))
+    assert len(out["T"]) == 2 * (H - 1) * (W - 1)
+    bits = np.unpackbits(out["border"][:, None], axis=1, bitorder="little")[:, :3]
+    assert bits.sum() == 2 * (H - 1) + 2 * (W - 1)
+    assert np.array_equal(bits.astype(bool), out["HE"].reshape(-1, 3) < 0)
+    assert list(out["seg_labels"]) == [0] and list(out["seg_offsets"]) == [0, len(out["T"])]
+
+
+def test_segment_border_between_two_segments():
+    """Two segments split at a quad column: every half-edge of the dividing line is a boundary
+    half-edge on both sides (2 per quad row), on top of the perimeter; unlabelled triangles have no
+    boundary bits."""
+    H, W = 5, 8
+    pts = np.zeros((H, W, 3), np.float32)
+    pts[..., 0], pts[..., 1] = np.meshgrid(np.arange(W), np.arange(H))
+    Hq, Wq = H - 1, W - 1
+    gid = np.arange(2 * Hq * Wq)
+    v = (gid // 2) % Wq
+    labels = np.where(v < 3, 0, 6).astype(np.int32)
+    out = oracle.mesh_outputs(pts, labels)
+    bits = np.unpackbits(out["border"][:, None], axis=1, bitorder="little")[:, :3]
+    assert bits.sum() == 2 * Hq + 2 * Wq + 2 * Hq
+    labels[v == Wq - 1] = -1                           # the last quad column belongs to no segment
+    out = oracle.mesh_outputs(pts, labels)
+    bits = np.unpackbits(out["border"][:, None], axis=1, bitorder="little")[:, :3]
+    unl = np.nonzero(labels[np.nonzero(out["Tmap"] >= 0)[0]] < 0)[0]
+    assert bits[unl].sum() == 0
+    # the labelled region's perimeter (its right side now faces the unlabelled column) plus the
+    # dividing line counted on both sides
+    assert bits.sum() == (2 * Hq + 2 * (Wq - 1)) + 2 * Hq
