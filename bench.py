@@ -533,6 +533,34 @@ def run_pl3d(args):
             dist.destroy_process_group()
         return
 
+    # ---------------- explicit mesh and segment lists of the frame (pl3d_extract_mesh)
+    mesh = None
+    if world == 1:
+        i32 = dict(dtype=torch.int32, device=dev)
+        mo = [torch.empty(3 * ntri, **i32), torch.empty(ntri, **i32), torch.empty(3 * ntri, **i32),
+              torch.zeros(3, dtype=torch.int64, device=dev), torch.empty(ntri, **i32), torch.empty(ntri + 1, **i32),
+              torch.empty(ntri, **i32), torch.empty(ntri, dtype=torch.uint8, device=dev)]
+        step()                                           # labels of this frame
+        for _ in range(3):
+            pl3d.pl3d_extract_mesh(ctx, pts, labels, H, W, *mo, stream=stream)
+        m_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(50)]
+        for e_a, e_b in m_ev:
+            flush.fill_(0.25)
+            e_a.record(stream)
+            pl3d.pl3d_extract_mesh(ctx, pts, labels, H, W, *mo, stream=stream)
+            e_b.record(stream)
+        torch.cuda.synchronize()
+        m_us = statistics.median(a.elapsed_time(b) for a, b in m_ev) * 1e3
+        nT, nS, nL = (int(x) for x in mo[3].cpu())
+        # algorithmic bytes: read points 12 B/px and labels 4 B/tri; write T_map 4 B/tri, T and HE
+        # 12 B per kept triangle each, border 1 B per kept triangle, segment lists 4 B per listed one
+        m_bytes = 12.0 * H * W + 8.0 * ntri + 25.0 * nT + 4.0 * nL + 8.0 * nS
+        peaks_m, src_m = _peaks()
+        mesh = {"us": m_us, "triangles": nT, "segments": nS, "in_segments": nL, "algorithmic_bytes": m_bytes,
+                "achieved_gbs": m_bytes / (m_us * 1e-6) / 1e9, "peak_gbs": float(peaks_m["hbm_gbs"]),
+                "frac": m_bytes / (m_us * 1e-6) / 1e9 / float(peaks_m["hbm_gbs"]),
+                "peak_source": f"{src_m} hbm_gbs", "l2": "flushed before every launch"}
+
     # ---------------- batched (256 mixed frames, one launch) and served (Poisson trace) workloads
     batched = served = None
     if world == 1 and not args.no_batched:
@@ -601,6 +629,7 @@ def run_pl3d(args):
         "gpu_launches": int(launches),
         "roofline": roofline,
         "cpu_baseline": cpu,
+        "mesh": mesh,
         "batched": batched,
         "served": served,
         "step_ms_p50": statistics.median(step_ms),

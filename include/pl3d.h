@@ -159,7 +159,7 @@ const char* pl3d_status_string(int status);
  * writes per-phase total milliseconds and launch counts for up to n_slots phases
  * (ms_out, launches_out may be NULL) and returns the number of phases (PL3D_TIMING_SLOTS),
  * clearing the totals when reset != 0. Phase order: see pl3d_timing_slot_name. */
-#define PL3D_TIMING_SLOTS 6
+#define PL3D_TIMING_SLOTS 7
 int pl3d_set_timing(pl3d_ctx* ctx, int enable);
 int pl3d_read_timing(pl3d_ctx* ctx, double* ms_out, int64_t* launches_out, int n_slots, int reset);
 const char* pl3d_timing_slot_name(int slot);
@@ -333,6 +333,36 @@ int pl3d_server_poll(pl3d_server* srv, pl3d_completion* out, int max, int wait_m
 int pl3d_server_drain(pl3d_server* srv);
 int pl3d_server_get_stats(const pl3d_server* srv, pl3d_server_stats* out);
 void pl3d_server_destroy(pl3d_server* srv);
+
+/*
+ * Explicit half-edge mesh and segment lists of one frame, the inputs of polygon extraction
+ * (Section 7.2), in one launch on `stream`:
+ *   Algorithm 1: T, the triangles of T_FC whose three points are valid, in GID order, each as
+ *                its three point indices (first = {p3, p2, p1}, second = {p1, p4, p3}), and
+ *                T_map, the index into T of every GID (-1 for a triangle with an invalid point);
+ *   Algorithm 2: HE, the twin of every half-edge 3 t + e of T (e-th edge of triangle t in the
+ *                order above), -1 on a border;
+ *   segments:    for the labels of pl3d_extract_planes (each label is the smallest GID of its
+ *                segment), the segments in ascending label order (seg_labels), CSR offsets
+ *                into seg_tris, and seg_tris, the T indices of each segment's triangles in
+ *                ascending order;
+ *   boundary:    border[t], bit e set when triangle t is in a segment and its half-edge 3 t + e
+ *                has no twin or a twin in another segment (or in none): the boundary half-edges
+ *                polygon extraction follows.
+ * All buffers are on the device and owned by the caller (Q = (H-1)(W-1)):
+ *   points [H W 3] FP32 (the frame's input: validity as everywhere in this library);
+ *   labels [2Q] int32, or NULL (then only T, T_map, HE and counts[0] are produced, and the
+ *          segment buffers may be NULL);
+ *   out_T [3 * 2Q], out_Tmap [2Q], out_HE [3 * 2Q] int32; out_counts int64 [3] = {|T|,
+ *   segments, triangles in segments}; out_seg_labels [2Q], out_seg_offsets [2Q + 1],
+ *   out_seg_tris [2Q] int32; out_border [2Q] uint8 or NULL.
+ * Only the first counts[...] entries of each output are written. Sizes need 6 Q < 2^31 (half-edge
+ * ids are int32), else PL3D_ERR_INVALID_ARG. The context's mesh scratch (about 28 bytes per
+ * triangle) grows to the largest frame seen. Results are exact: no floating-point arithmetic.
+ */
+int pl3d_extract_mesh(pl3d_ctx* ctx, const float* points, const int32_t* labels, int H, int W, int32_t* out_T,
+                      int32_t* out_Tmap, int32_t* out_HE, int64_t* out_counts, int32_t* out_seg_labels,
+                      int32_t* out_seg_offsets, int32_t* out_seg_tris, uint8_t* out_border, void* stream);
 
 /* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
 int pl3d_version(void);

@@ -25,7 +25,7 @@ PL3D_ERR_TIMEOUT = -4
 PL3D_ERR_UNSUPPORTED = -5
 PL3D_MAX_GROUPS = 254
 PL3D_NO_GROUP = 255
-PL3D_TIMING_SLOTS = 6
+PL3D_TIMING_SLOTS = 7
 
 
 class pl3d_params(ctypes.Structure):
@@ -156,6 +156,8 @@ def lib():
     L.pl3d_autotune_batched.argtypes = [_vp, F, ctypes.c_int, _vp, ctypes.c_int, T, ctypes.POINTER(ctypes.c_double)]
     L.pl3d_batch_stats.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                    ctypes.POINTER(ctypes.c_int64)]
+    L.pl3d_extract_mesh.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                    _vp]
     L.pl3d_server_create.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(pl3d_server_config)]
     L.pl3d_server_submit.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, P, _vp, ctypes.c_int, _vp, _vp, _vp,
                                      ctypes.POINTER(ctypes.c_uint64)]
@@ -397,6 +399,49 @@ def pl3d_batch_stats(ctx) -> dict:
     a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
     _check(lib().pl3d_batch_stats(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "pl3d_batch_stats")
     return {"graph_launches": a.value, "desc_uploads": b.value, "graphs": c.value}
+
+
+def pl3d_extract_mesh(ctx, points, labels, H, W, out_T, out_Tmap, out_HE, out_counts, out_seg_labels=None,
+                      out_seg_offsets=None, out_seg_tris=None, out_border=None, stream=None) -> int:
+    """Explicit mesh (Algorithms 1-2) and segment lists of one frame; device buffers, see include/pl3d.h."""
+    n_tri = 2 * (H - 1) * (W - 1)
+    _check_tensor(points, "points", "torch.float32", H * W * 3)
+    _check_tensor(labels, "labels", "torch.int32", n_tri)
+    _check_tensor(out_T, "out_T", "torch.int32", 3 * n_tri)
+    _check_tensor(out_Tmap, "out_Tmap", "torch.int32", n_tri)
+    _check_tensor(out_HE, "out_HE", "torch.int32", 3 * n_tri)
+    _check_tensor(out_counts, "out_counts", "torch.int64", 3)
+    _check_tensor(out_seg_labels, "out_seg_labels", "torch.int32", n_tri)
+    _check_tensor(out_seg_offsets, "out_seg_offsets", "torch.int32", n_tri + 1)
+    _check_tensor(out_seg_tris, "out_seg_tris", "torch.int32", n_tri)
+    _check_tensor(out_border, "out_border", "torch.uint8", n_tri)
+    return _check(lib().pl3d_extract_mesh(ctx, _ptr(points), _ptr(labels), int(H), int(W), _ptr(out_T), _ptr(out_Tmap),
+                                          _ptr(out_HE), _ptr(out_counts), _ptr(out_seg_labels), _ptr(out_seg_offsets),
+                                          _ptr(out_seg_tris), _ptr(out_border), _stream(stream)), "pl3d_extract_mesh")
+
+
+def extract_mesh(ctx, points, labels, stream=None) -> dict:
+    """Allocates the outputs with torch, runs pl3d_extract_mesh, waits, and returns them cut to
+    their counts: T [|T|, 3], Tmap, HE [3 |T|], seg_labels, seg_offsets, seg_tris, border."""
+    import torch
+    H, W = int(points.shape[0]), int(points.shape[1])
+    n = 2 * (H - 1) * (W - 1)
+    dev = points.device
+    i32 = dict(dtype=torch.int32, device=dev)
+    o = dict(T=torch.empty(3 * n, **i32), Tmap=torch.empty(n, **i32), HE=torch.empty(3 * n, **i32),
+             counts=torch.zeros(3, dtype=torch.int64, device=dev))
+    if labels is not None:
+        o.update(seg_labels=torch.empty(n, **i32), seg_offsets=torch.empty(n + 1, **i32), seg_tris=torch.empty(n, **i32),
+                 border=torch.empty(n, dtype=torch.uint8, device=dev))
+    pl3d_extract_mesh(ctx, points, labels, H, W, o["T"], o["Tmap"], o["HE"], o["counts"], o.get("seg_labels"),
+                      o.get("seg_offsets"), o.get("seg_tris"), o.get("border"), stream)
+    (torch.cuda.current_stream(dev) if stream is None else stream).synchronize()
+    nT, nS, nL = (int(x) for x in o["counts"].cpu())
+    out = dict(T=o["T"][:3 * nT].view(nT, 3), Tmap=o["Tmap"], HE=o["HE"][:3 * nT], counts=(nT, nS, nL))
+    if labels is not None:
+        out.update(seg_labels=o["seg_labels"][:nS], seg_offsets=o["seg_offsets"][:nS + 1], seg_tris=o["seg_tris"][:nL],
+                   border=o["border"][:nT])
+    return out
 
 
 def pl3d_server_create(device: int = 0, max_inflight: int = 2, max_batch_frames: int = 64, hbm_bytes: int = 0) -> int:

@@ -78,7 +78,9 @@ __device__ __forceinline__ void stage_box(float* dst, const float* src, const CU
         const int r = e / b.cols, x = e - r * b.cols;
         const int gy = y0 + r, gx = x0 + x;
         float v = fill;
-        if (src && gy >= 0 && gy < H && gx >= 0 && gx < row_floats) v = __ldg(src + (size_t)gy * row_floats + gx);
+        // L2-coherent loads: displacements were written earlier in this launch by other CTAs,
+        // and a non-coherent (read-only) cache line from an earlier pass could be stale
+        if (src && gy >= 0 && gy < H && gx >= 0 && gx < row_floats) v = __ldcg(src + (size_t)gy * row_floats + gx);
         dst[e] = v;
     }
 }
@@ -262,9 +264,9 @@ __device__ __forceinline__ FastEdge fast_edge(const SP& a, const SP& b) {
     const float dx = b.dx - a.dx, dy = b.dy - a.dy, dz = b.dz - a.dz;
     FastEdge f;
     f.e = {ax + dx, ay + dy, az + dz};
-    f.m = (rounded_part(ax, a.x, b.x) + rounded_part(dx, a.dx, b.dx)) +
-          (rounded_part(ay, a.y, b.y) + rounded_part(dy, a.dy, b.dy)) +
-          (rounded_part(az, a.z, b.z) + rounded_part(dz, a.dz, b.dz));
+    // (the displacements' differences are counted as rounded: they are rarely within a factor 2)
+    f.m = (rounded_part(ax, a.x, b.x) + fabsf(dx)) + (rounded_part(ay, a.y, b.y) + fabsf(dy)) +
+          (rounded_part(az, a.z, b.z) + fabsf(dz));
     f.l1 = fabsf(f.e.x) + fabsf(f.e.y) + fabsf(f.e.z);
     return f;
 }
@@ -518,8 +520,8 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
             for (int k = 0; k < 2; ++k) {
                 if (!vk[k]) continue;
                 const size_t gid = 2 * ((size_t)gu * Wq + gv) + k;
-                const float nx = __ldg(ph.carry_in + 3 * gid);
-                if (nx == nx) nn[k] = {nx, __ldg(ph.carry_in + 3 * gid + 1), __ldg(ph.carry_in + 3 * gid + 2)};
+                const float nx = __ldcg(ph.carry_in + 3 * gid);   // written by the previous pass
+                if (nx == nx) nn[k] = {nx, __ldcg(ph.carry_in + 3 * gid + 1), __ldcg(ph.carry_in + 3 * gid + 2)};
             }
         }
         const V3 cc0 = scaled_centroid(p3, p2, p1, nn[0]), cc1 = scaled_centroid(p1, p4, p3, nn[1]);
@@ -738,11 +740,26 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
         if (link && !dup) uf_unite(Lp, ra, rb);
     }
     __syncthreads();
-    // (3) Only the run representatives walk to their tile root (the unions linked nothing
-    // else); no union runs any more, so halving the path while walking only ever points a node
-    // at one of its ancestors, and shortens the walks of the other threads.
-    for (int t = threadIdx.x; t < 2 * T * T; t += blockDim.x)
-        if (RunOf[t] == t) RootOf[t] = uf_find(Lp, t);
+    // (3) Only the run representatives were linked by the unions. Synchronous pointer jumping
+    // over them: every round points each representative at its grandparent (an ancestor), so the
+    // depth halves per round, however deep the concurrent unions left the forest.
+    {
+        bool changed = true;
+        while (__syncthreads_or(changed)) {
+            changed = false;
+            for (int t = threadIdx.x; t < 2 * T * T; t += blockDim.x) {
+                if (RunOf[t] != t) continue;
+                volatile int32_t* vl = Lp;
+                const int p = vl[t], gp = vl[p];
+                if (gp != p) {
+                    vl[t] = gp;
+                    changed = true;
+                }
+            }
+        }
+        for (int t = threadIdx.x; t < 2 * T * T; t += blockDim.x)
+            if (RunOf[t] == t) RootOf[t] = Lp[t];
+    }
     __syncthreads();
     // (4) Each triangle leaves with the GID of its tile-local root (-1 without a group).
     for (int i = threadIdx.x; i < T * T; i += blockDim.x) {
@@ -773,11 +790,11 @@ __device__ __forceinline__ V3 centroid_global(const FrameArgs& a, int u, int v, 
     const size_t p1 = (size_t)u * W + v, p2 = p1 + 1, p3 = p1 + W + 1, p4 = p1 + W;
     const size_t ia = 3 * (k == 0 ? p3 : p1), ib = 3 * (k == 0 ? p2 : p4), ic = 3 * (k == 0 ? p1 : p3);
     const float* P = a.points;
-    const float* D = a.disp;
+    const float* D = a.disp;   // written earlier in this launch: L2-coherent loads
     const float kk = 1.f / 3.f;
-    return {((P[ia] + P[ib] + P[ic]) + (D[ia] + D[ib] + D[ic])) * kk,
-            ((P[ia + 1] + P[ib + 1] + P[ic + 1]) + (D[ia + 1] + D[ib + 1] + D[ic + 1])) * kk,
-            ((P[ia + 2] + P[ib + 2] + P[ic + 2]) + (D[ia + 2] + D[ib + 2] + D[ic + 2])) * kk};
+    return {((P[ia] + P[ib] + P[ic]) + (__ldcg(D + ia) + __ldcg(D + ib) + __ldcg(D + ic))) * kk,
+            ((P[ia + 1] + P[ib + 1] + P[ic + 1]) + (__ldcg(D + ia + 1) + __ldcg(D + ib + 1) + __ldcg(D + ic + 1))) * kk,
+            ((P[ia + 2] + P[ib + 2] + P[ic + 2]) + (__ldcg(D + ia + 2) + __ldcg(D + ib + 2) + __ldcg(D + ic + 2))) * kk};
 }
 
 // Twins that cross a tile border: the top edge of a tile's first quad row and the right edge of
@@ -802,8 +819,8 @@ __device__ __forceinline__ bool merge_pair(const FrameArgs& a, long long w, int&
     }
     const int i = 2 * (u * Wq + v);
     const int j = 2 * (uj * Wq + vj) + 1;
-    const int g = a.groups[i];
-    if (g == PL3D_NO_GROUP || a.groups[j] != g) return false;
+    const int g = __ldcg(a.groups + i);   // written by the bilateral pass of this launch
+    if (g == PL3D_NO_GROUP || __ldcg(a.groups + j) != g) return false;
     if (a.max_offset > 0.f) {
         const V3 ci = centroid_global(a, u, v, 0), cj = centroid_global(a, uj, vj, 1);
         const float* nd = a.nd.v + 3 * g;
@@ -890,8 +907,8 @@ __device__ __forceinline__ void filter_phase(const FrameArgs& a) {
     const long long n = 2LL * (a.H - 1) * (a.W - 1);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-        const int l = a.labels[i];
-        if (l >= 0 && a.sizes[l] <= a.min_triangles) a.labels[i] = -1;
+        const int l = __ldcg(a.labels + i);
+        if (l >= 0 && __ldcg(a.sizes + l) <= a.min_triangles) a.labels[i] = -1;   // sizes: other CTAs' atomics
     }
 }
 
@@ -1093,8 +1110,8 @@ __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const __grid_constan
             const FrameArgs& a = b.frames[f];
             if (!a.sizes) continue;
             const int li = (int)(i - __ldg(b.tris + f));
-            const int l = a.labels[li];
-            if (l >= 0 && a.sizes[l] <= a.min_triangles) a.labels[li] = -1;
+            const int l = __ldcg(a.labels + li);
+            if (l >= 0 && __ldcg(a.sizes + l) <= a.min_triangles) a.labels[li] = -1;
         }
     }
     mark(3);

@@ -20,8 +20,8 @@ namespace {
 
 constexpr int kVersion = 2 * 10000 + 1 * 100 + 0;
 
-const char* const kSlotNames[PL3D_TIMING_SLOTS] = {"laplacian", "bilateral", "label_merge",
-                                                    "label_flatten", "frame_kernel", "host_copies"};
+const char* const kSlotNames[PL3D_TIMING_SLOTS] = {"laplacian",    "bilateral",   "label_merge", "label_flatten",
+                                                    "frame_kernel", "host_copies", "mesh_kernel"};
 
 bool finite_f(float x) { return isfinite(x) != 0; }
 
@@ -193,6 +193,7 @@ void pl3d_destroy(pl3d_ctx* c) {
         cudaFree(c->st_labels);
         drop_graphs(c);
         cudaFree(c->bslab);
+        cudaFree(c->mslab);
         cudaFree(c->bdesc);
         cudaFreeHost(c->bstage);
         if (c->bupload) cudaEventDestroy(c->bupload);

@@ -13,8 +13,9 @@ namespace pl3d {
 namespace ctxutil {
 
 // Timing slots: four phases of the persistent kernels (device %globaltimer, accumulated by the
-// kernel), the kernel as a whole and the host copies (CUDA events on the call's stream).
-enum Slot { kSlotLap = 0, kSlotBil, kSlotMerge, kSlotLabels, kSlotKernel, kSlotCopies };
+// kernel), the kernel as a whole, the host copies and the explicit-mesh launch (CUDA events on
+// the call's stream).
+enum Slot { kSlotLap = 0, kSlotBil, kSlotMerge, kSlotLabels, kSlotKernel, kSlotCopies, kSlotMesh };
 
 struct TimedRange {
     int slot;
@@ -66,6 +67,9 @@ struct pl3d_ctx {
     std::vector<pl3d::ctxutil::BatchGraph> graphs;
     int64_t graph_launches = 0;
     int64_t desc_uploads = 0;
+    // scratch of the explicit-mesh launch (pl3d_mesh.cu)
+    unsigned char* mslab = nullptr;
+    size_t mslab_cap = 0;
     // timing
     bool timing = false;
     int64_t timed_frames = 0;       // timed persistent launches

@@ -1,0 +1,466 @@
+// pl3d_mesh.cu -- the explicit half-edge mesh of a frame (Algorithm 1: T and T_map; Algorithm 2:
+// HE) and the triangle lists and boundary half-edges of its planar segments (the inputs of the
+// polygon extraction of Section 7.2), in one cooperative launch (pl3d_extract_mesh).
+//
+// Phases, one grid barrier apart, all over chunks of 2048 consecutive entries (8 per thread):
+//   A  per chunk of GIDs: valid triangles (all three points valid, Algorithm 1) and segment
+//      roots (a label is the smallest GID of its segment, so a root is labelled with itself)
+//   B  one CTA turns the chunk counts into exclusive offsets (and the totals)
+//   C  T, T_map, the label of each T entry, and the segment index of each root, in GID order
+//   D  HE from the neighbours' T_map (the twin rules of Algorithm 2); sort keys: the segment
+//      index of each T entry (the segment count for an unlabelled one, so it sorts last)
+//   R  a stable LSD radix sort of (segment index, T index), 8 bits per pass: per-chunk digit
+//      histograms; per-digit exclusive scans over the chunks; a stable scatter that ranks equal
+//      digits inside a warp with __match_any_sync and across warps with per-warp counters
+//   G  the segments' CSR (offsets where the key changes) and the boundary half-edges
+// Data written by one CTA and read by another after a barrier is loaded with __ldcg (L2), never
+// through the non-coherent read-only path.
+// Everything in T order keeps GID order, so the lists come out sorted by (label, T index).
+#include <string.h>
+
+#include "pl3d_ctx.cuh"
+#include "sync.cuh"
+
+namespace pl3d {
+namespace mesh {
+
+constexpr int kChunk = 2048;
+constexpr int kPer = kChunk / kThreads;   // 8 consecutive entries per thread
+constexpr int kBins = 256;
+constexpr int kWarps = kThreads / 32;
+
+struct MeshArgs {
+    const float* points;
+    const int32_t* labels;       // nullptr: no segment outputs
+    int H, W;
+    int32_t* T;                  // [3 |T|]
+    int32_t* Tmap;               // [2Q]
+    int32_t* HE;                 // [3 |T|]
+    long long* counts;           // [3]: |T|, segments, triangles in segments
+    int32_t* seg_labels;         // [segments]
+    int32_t* seg_offsets;        // [segments + 1]
+    int32_t* seg_tris;           // [triangles in segments]
+    uint8_t* border;             // [|T|]
+    int n_chunks;                // chunks of GIDs
+    int32_t* cnt;                // [2][n_chunks]: T entries and roots per chunk -> exclusive offsets
+    int32_t* root_idx;           // [2Q]
+    int32_t* tlab;               // [2Q] label of each T entry
+    int32_t* keys[2];            // [2Q]
+    int32_t* vals[2];            // [2Q]
+    int32_t* hist;               // [kBins][n_chunks]
+    int32_t* bin_tot;            // [kBins]
+    unsigned* barrier;
+    int* error;
+};
+
+__device__ __forceinline__ bool vertex_valid(const float* P, long long i) {
+    return point_valid(__ldg(P + 3 * i), __ldg(P + 3 * i + 1), __ldg(P + 3 * i + 2));
+}
+
+// Vertex (point) indices of triangle gid in the order of Algorithm 1:
+// first = {p3, p2, p1}, second = {p1, p4, p3}.
+__device__ __forceinline__ void tri_vertices(long long gid, int W, int Wq, long long v[3]) {
+    const long long q = gid >> 1;
+    const long long u = q / Wq, c = q - u * Wq;
+    const long long p1 = u * W + c, p2 = p1 + 1, p3 = p1 + W + 1, p4 = p1 + W;
+    if ((gid & 1) == 0) {
+        v[0] = p3, v[1] = p2, v[2] = p1;
+    } else {
+        v[0] = p1, v[1] = p4, v[2] = p3;
+    }
+}
+
+// Exclusive prefix of v over the CTA (thread order); *total receives the sum. Uses sh[kWarps + 1].
+__device__ __forceinline__ int block_exclusive(int v, int* sh, int* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[warp] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int w = 0; w < kWarps; ++w) {
+            const int t = sh[w];
+            sh[w] = run;
+            run += t;
+        }
+        sh[kWarps] = run;
+    }
+    __syncthreads();
+    const int r = sh[warp] + x - v;
+    *total = sh[kWarps];
+    __syncthreads();
+    return r;
+}
+
+struct Flags {
+    bool valid, root;
+};
+
+__device__ __forceinline__ Flags gid_flags(const MeshArgs& a, long long g, long long n) {
+    Flags f = {false, false};
+    if (g >= n) return f;
+    long long v[3];
+    tri_vertices(g, a.W, a.W - 1, v);
+    f.valid = vertex_valid(a.points, v[0]) && vertex_valid(a.points, v[1]) && vertex_valid(a.points, v[2]);
+    if (f.valid && a.labels) f.root = __ldg(a.labels + g) == (int)g;
+    return f;
+}
+
+__global__ void __launch_bounds__(kThreads, 4) mesh_kernel(const __grid_constant__ MeshArgs a) {
+    __shared__ int sh_scan[kWarps + 1];
+    __shared__ int sh_bins[kBins];
+    __shared__ int sh_base[kBins];
+    __shared__ int sh_wc[kWarps][kBins];
+    const int Wq = a.W - 1, Hq = a.H - 1;
+    const long long n = 2LL * Hq * Wq;
+    const int C = a.n_chunks;
+    int32_t* cT = a.cnt;
+    int32_t* cR = a.cnt + C;
+
+    // A: counts per chunk; every GID's root index starts undefined
+    for (int c = blockIdx.x; c < C; c += gridDim.x) {
+        const long long g0 = (long long)c * kChunk + threadIdx.x * kPer;
+        int nt = 0, nr = 0;
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            const Flags f = gid_flags(a, g0 + j, n);
+            nt += f.valid;
+            nr += f.root;
+            if (a.labels && g0 + j < n) a.root_idx[g0 + j] = -1;
+        }
+        int tt, tr;
+        block_exclusive(nt, sh_scan, &tt);
+        block_exclusive(nr, sh_scan, &tr);
+        if (threadIdx.x == 0) {
+            cT[c] = tt;
+            cR[c] = tr;
+        }
+    }
+    grid_barrier(a.barrier, a.error);
+
+    // B: exclusive offsets of the chunks, and the totals
+    if (blockIdx.x == 0) {
+        for (int arr = 0; arr < 2; ++arr) {
+            int32_t* x = a.cnt + arr * C;
+            long long carry = 0;
+            for (int base = 0; base < C; base += kThreads) {
+                const int i = base + threadIdx.x;
+                const int v = i < C ? __ldcg(x + i) : 0;
+                int tot;
+                const int e = block_exclusive(v, sh_scan, &tot);
+                if (i < C) x[i] = (int)(carry + e);
+                carry += tot;
+            }
+            if (threadIdx.x == 0) a.counts[arr] = carry;
+        }
+        if (threadIdx.x == 0) a.counts[2] = 0;
+    }
+    grid_barrier(a.barrier, a.error);
+    const long long nT = __ldcg(a.counts);
+    const int nS = (int)__ldcg(a.counts + 1);
+
+    // C: T, T_map, T labels, segment roots (GID order)
+    for (int c = blockIdx.x; c < C; c += gridDim.x) {
+        const long long g0 = (long long)c * kChunk + threadIdx.x * kPer;
+        Flags f[kPer];
+        int nt = 0, nr = 0;
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            f[j] = gid_flags(a, g0 + j, n);
+            nt += f[j].valid;
+            nr += f[j].root;
+        }
+        int tt, tr;
+        int pt = __ldcg(cT + c) + block_exclusive(nt, sh_scan, &tt);
+        int pr = __ldcg(cR + c) + block_exclusive(nr, sh_scan, &tr);
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            const long long g = g0 + j;
+            if (g >= n) break;
+            if (f[j].valid) {
+                long long v[3];
+                tri_vertices(g, a.W, Wq, v);
+                a.T[3LL * pt] = (int32_t)v[0];
+                a.T[3LL * pt + 1] = (int32_t)v[1];
+                a.T[3LL * pt + 2] = (int32_t)v[2];
+                a.tlab[pt] = a.labels ? __ldg(a.labels + g) : -1;
+                a.Tmap[g] = pt++;
+            } else {
+                a.Tmap[g] = -1;
+            }
+            if (f[j].root) {
+                a.seg_labels[pr] = (int32_t)g;
+                a.root_idx[g] = pr++;
+            }
+        }
+    }
+    grid_barrier(a.barrier, a.error);
+
+    // D: HE (Algorithm 2) and the sort keys
+    {
+        const long long stride = (long long)gridDim.x * blockDim.x;
+        for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < (long long)Hq * Wq; q += stride) {
+            const int u = (int)(q / Wq), v = (int)(q - (long long)u * Wq);
+            const int32_t* tm = a.Tmap;
+            const int first = __ldcg(tm + 2 * q), second = __ldcg(tm + 2 * q + 1);
+            if (first >= 0) {
+                const int right = v + 1 < Wq ? __ldcg(tm + 2 * (q + 1) + 1) : -1;
+                const int top = u > 0 ? __ldcg(tm + 2 * (q - Wq) + 1) : -1;
+                a.HE[3LL * first] = right >= 0 ? 3 * right : -1;
+                a.HE[3LL * first + 1] = top >= 0 ? 3 * top + 1 : -1;
+                a.HE[3LL * first + 2] = second >= 0 ? 3 * second + 2 : -1;
+            }
+            if (second >= 0) {
+                const int left = v > 0 ? __ldcg(tm + 2 * (q - 1)) : -1;
+                const int bottom = u + 1 < Hq ? __ldcg(tm + 2 * (q + Wq)) : -1;
+                a.HE[3LL * second] = left >= 0 ? 3 * left : -1;
+                a.HE[3LL * second + 1] = bottom >= 0 ? 3 * bottom + 1 : -1;
+                a.HE[3LL * second + 2] = first >= 0 ? 3 * first + 2 : -1;
+            }
+            if (a.labels && nS > 0) {
+                for (int side = 0; side < 2; ++side) {
+                    const int t = side == 0 ? first : second;
+                    if (t < 0) continue;
+                    // the segment index of the label's root; a label that names no root (only
+                    // possible for labels not made by pl3d_extract_planes) sorts with the rest
+                    const int l = __ldcg(a.tlab + t);
+                    const int k = (l >= 0 && l < n) ? __ldcg(a.root_idx + l) : -1;
+                    a.keys[0][t] = k >= 0 ? k : nS;
+                    a.vals[0][t] = t;
+                }
+            }
+        }
+    }
+    if (!a.labels || nS == 0) {
+        // no segments: no lists; every boundary flag is 0
+        const long long stride = (long long)gridDim.x * blockDim.x;
+        for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nT; t += stride)
+            if (a.border) a.border[t] = 0;
+        if (a.labels && blockIdx.x == 0 && threadIdx.x == 0) a.seg_offsets[0] = 0;
+        return;
+    }
+    grid_barrier(a.barrier, a.error);
+
+    // R: stable LSD radix sort of (segment index, T index) over the T entries
+    const int Ct = (int)((nT + kChunk - 1) / kChunk);
+    const int key_bits = 32 - __clz(nS);   // keys run over 0..nS
+    const int passes = (key_bits + 7) / 8;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int pass = 0; pass < passes; ++pass) {
+        const int shift = 8 * pass;
+        const int32_t* ks = a.keys[pass & 1];
+        const int32_t* vs = a.vals[pass & 1];
+        int32_t* kd = a.keys[(pass + 1) & 1];
+        int32_t* vd = a.vals[(pass + 1) & 1];
+        // R1: digit histogram of every chunk
+        for (int c = blockIdx.x; c < Ct; c += gridDim.x) {
+            sh_bins[threadIdx.x] = 0;
+            __syncthreads();
+            const long long i0 = (long long)c * kChunk + threadIdx.x * kPer;
+#pragma unroll
+            for (int j = 0; j < kPer; ++j)
+                if (i0 + j < nT) atomicAdd(&sh_bins[(__ldcg(ks + i0 + j) >> shift) & (kBins - 1)], 1);
+            __syncthreads();
+            a.hist[(long long)threadIdx.x * Ct + c] = sh_bins[threadIdx.x];
+            __syncthreads();
+        }
+        grid_barrier(a.barrier, a.error);
+        // R2: per digit, exclusive offsets over the chunks, and the digit's total
+        for (int d = blockIdx.x; d < kBins; d += gridDim.x) {
+            int32_t* h = a.hist + (long long)d * Ct;
+            long long carry = 0;
+            for (int base = 0; base < Ct; base += kThreads) {
+                const int i = base + threadIdx.x;
+                const int v = i < Ct ? __ldcg(h + i) : 0;
+                int tot;
+                const int e = block_exclusive(v, sh_scan, &tot);
+                if (i < Ct) h[i] = (int)(carry + e);
+                carry += tot;
+            }
+            if (threadIdx.x == 0) a.bin_tot[d] = (int)carry;
+        }
+        grid_barrier(a.barrier, a.error);
+        // R3: stable scatter
+        {
+            int tot;
+            sh_base[threadIdx.x] = block_exclusive(__ldcg(a.bin_tot + threadIdx.x), sh_scan, &tot);
+        }
+        for (int c = blockIdx.x; c < Ct; c += gridDim.x) {
+            for (int d = threadIdx.x; d < kWarps * kBins; d += kThreads) (&sh_wc[0][0])[d] = 0;
+            __syncthreads();
+            // warp w owns the 256 consecutive entries [c kChunk + 256 w, + 256), in 8 rounds of 32
+            const long long w0 = (long long)c * kChunk + warp * (kChunk / kWarps);
+            int rank[kPer], dig[kPer];
+#pragma unroll
+            for (int r = 0; r < kPer; ++r) {
+                const long long i = w0 + r * 32 + lane;
+                const int d = i < nT ? (__ldcg(ks + i) >> shift) & (kBins - 1) : -1;
+                const unsigned peers = __match_any_sync(0xffffffffu, d);
+                const unsigned lower = peers & ((1u << lane) - 1u);
+                int base = 0;
+                if (d >= 0) base = sh_wc[warp][d];
+                __syncwarp();
+                if (d >= 0 && lower == 0) sh_wc[warp][d] = base + __popc(peers);
+                __syncwarp();
+                rank[r] = base + __popc(lower);
+                dig[r] = d;
+            }
+            __syncthreads();
+            // per digit: offsets of the warps (warp order = entry order)
+            {
+                const int d = threadIdx.x;
+                int run = 0;
+                for (int w = 0; w < kWarps; ++w) {
+                    const int t = sh_wc[w][d];
+                    sh_wc[w][d] = run;
+                    run += t;
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < kPer; ++r) {
+                const int d = dig[r];
+                if (d < 0) continue;
+                const long long i = w0 + r * 32 + lane;
+                const long long pos =
+                    (long long)sh_base[d] + __ldcg(a.hist + (long long)d * Ct + c) + sh_wc[warp][d] + rank[r];
+                kd[pos] = __ldcg(ks + i);
+                vd[pos] = __ldcg(vs + i);
+            }
+            __syncthreads();
+        }
+        grid_barrier(a.barrier, a.error);
+    }
+
+    // G: CSR of the segments and their boundary half-edges
+    // keys below nS are the triangles in segments, sorted first
+    const int32_t* K = a.keys[passes & 1];
+    const int32_t* V = a.vals[passes & 1];
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < nT; p += stride) {
+        const int k = __ldcg(K + p);
+        if (k >= nS) continue;
+        a.seg_tris[p] = __ldcg(V + p);
+        if (p == 0 || __ldcg(K + p - 1) != k) a.seg_offsets[k] = (int32_t)p;
+        if (p + 1 == nT || __ldcg(K + p + 1) >= nS) {   // the last triangle in a segment
+            a.seg_offsets[nS] = (int32_t)(p + 1);
+            a.counts[2] = p + 1;
+        }
+    }
+    if (a.border) {
+        for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nT; t += stride) {
+            const int l = __ldcg(a.tlab + t);
+            unsigned bits = 0;
+            if (l >= 0) {
+#pragma unroll
+                for (int e = 0; e < 3; ++e) {
+                    const int tw = __ldcg(a.HE + 3 * t + e);
+                    if (tw < 0 || __ldcg(a.tlab + tw / 3) != l) bits |= 1u << e;
+                }
+            }
+            a.border[t] = (uint8_t)bits;
+        }
+    }
+}
+
+}  // namespace mesh
+}  // namespace pl3d
+
+using namespace pl3d;
+using namespace pl3d::ctxutil;
+
+namespace {
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+int grow_mesh(pl3d_ctx* c, size_t need, cudaStream_t s) {
+    if (c->mslab_cap >= need) return PL3D_OK;
+    if (c->mslab && cudaStreamSynchronize(s) != cudaSuccess) return PL3D_ERR_CUDA;
+    cudaFree(c->mslab);
+    c->mslab = nullptr;
+    c->mslab_cap = 0;
+    const size_t cap = need + need / 8;
+    if (cudaMalloc((void**)&c->mslab, cap) != cudaSuccess) {
+        cudaGetLastError();
+        return PL3D_ERR_OUT_OF_MEMORY;
+    }
+    c->mslab_cap = cap;
+    return PL3D_OK;
+}
+
+}  // namespace
+
+extern "C" int pl3d_extract_mesh(pl3d_ctx* ctx, const float* points, const int32_t* labels, int H, int W,
+                                 int32_t* out_T, int32_t* out_Tmap, int32_t* out_HE, int64_t* out_counts,
+                                 int32_t* out_seg_labels, int32_t* out_seg_offsets, int32_t* out_seg_tris,
+                                 uint8_t* out_border, void* stream) {
+    if (!ctx || !points || !out_T || !out_Tmap || !out_HE || !out_counts) return PL3D_ERR_INVALID_ARG;
+    if (labels && (!out_seg_labels || !out_seg_offsets || !out_seg_tris)) return PL3D_ERR_INVALID_ARG;
+    // half-edge ids (3 |T| of them) must fit int32
+    if (H < 2 || W < 2 || 6LL * (H - 1) * (long long)(W - 1) >= (1LL << 31) || 3LL * H * W >= (1LL << 31))
+        return PL3D_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return PL3D_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t ntri = 2 * (size_t)(H - 1) * (W - 1);
+    const int C = (int)((ntri + mesh::kChunk - 1) / mesh::kChunk);
+    // scratch: chunk counts, root index, T labels, keys and values (double buffered), histograms
+    const size_t b_cnt = align_up(2 * (size_t)C * 4, 256), b_tri = align_up(ntri * 4, 256);
+    const size_t b_hist = align_up((size_t)mesh::kBins * C * 4, 256), b_bins = align_up(mesh::kBins * 4, 256);
+    int rc = grow_mesh(ctx, b_cnt + 6 * b_tri + b_hist + b_bins, s);
+    if (rc != PL3D_OK) return rc;
+    mesh::MeshArgs a;
+    memset(&a, 0, sizeof(a));
+    a.points = points;
+    a.labels = labels;
+    a.H = H;
+    a.W = W;
+    a.T = out_T;
+    a.Tmap = out_Tmap;
+    a.HE = out_HE;
+    a.counts = reinterpret_cast<long long*>(out_counts);
+    a.seg_labels = out_seg_labels;
+    a.seg_offsets = out_seg_offsets;
+    a.seg_tris = out_seg_tris;
+    a.border = out_border;
+    a.n_chunks = C;
+    unsigned char* p = ctx->mslab;
+    a.cnt = reinterpret_cast<int32_t*>(p);
+    p += b_cnt;
+    a.root_idx = reinterpret_cast<int32_t*>(p);
+    p += b_tri;
+    a.tlab = reinterpret_cast<int32_t*>(p);
+    p += b_tri;
+    for (int i = 0; i < 2; ++i) {
+        a.keys[i] = reinterpret_cast<int32_t*>(p);
+        p += b_tri;
+        a.vals[i] = reinterpret_cast<int32_t*>(p);
+        p += b_tri;
+    }
+    a.hist = reinterpret_cast<int32_t*>(p);
+    p += b_hist;
+    a.bin_tot = reinterpret_cast<int32_t*>(p);
+    a.barrier = ctx->barrier();
+    a.error = ctx->error();
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PL3D_ERR_CUDA;
+    const void* fn = reinterpret_cast<const void*>(&mesh::mesh_kernel);
+    const int want = C > mesh::kBins ? C : mesh::kBins;
+    const int grid = persistent_grid(fn, 0, dev, Tuning{0, 0, 0}, want);
+    if (grid <= 0) return PL3D_ERR_CUDA;
+    void* args[1] = {&a};
+    cudaEvent_t e0, e1;
+    record_start(ctx, s, &e0, &e1);
+    if (cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kThreads), args, 0, s) != cudaSuccess) {
+        cudaGetLastError();
+        return PL3D_ERR_CUDA;
+    }
+    record_stop(ctx, s, kSlotMesh, e0, e1);
+    ctx->launches += 1;
+    return PL3D_OK;
+}
