@@ -71,11 +71,13 @@ def _load():
     lib.orc_triangle_twins.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_int, _i64p]
     lib.orc_label.argtypes = [_u8p, ctypes.c_int, ctypes.c_int, _f64p, _f64p, ctypes.c_int, ctypes.c_double,
                               ctypes.c_int, _i32p]
+    lib.orc_label_seeded.argtypes = [_u8p, ctypes.c_int, ctypes.c_int, _f64p, _f64p, ctypes.c_int, ctypes.c_double,
+                                     ctypes.c_int, _i32p, _f64p]
     lib.orc_extract_triangles.argtypes = [_f64p, ctypes.c_int, ctypes.c_int, _i32p, _i32p]
     lib.orc_extract_triangles.restype = ctypes.c_int64
     lib.orc_extract_halfedges.argtypes = [_i32p, ctypes.c_int, ctypes.c_int, ctypes.c_int64, _i32p]
     for name in ("orc_laplacian", "orc_laplacian_jitter", "orc_bilateral_jitter", "orc_triangle_geometry", "orc_mask", "orc_bilateral", "orc_normalize_dominant",
-                 "orc_classify", "orc_label", "orc_extract_halfedges", "orc_triangle_twins"):
+                 "orc_classify", "orc_label", "orc_label_seeded", "orc_extract_halfedges", "orc_triangle_twins"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -192,6 +194,20 @@ def label(G: np.ndarray, H: int, W: int, C=None, nd_unit=None, max_offset: float
     return out
 
 
+def label_seeded(G: np.ndarray, H: int, W: int, C: np.ndarray, nd_unit: np.ndarray, ptp_max: float,
+                 tri_min: int = 0):
+    """Algorithm 5 with the seed-relative point-to-plane limit (seeds in GID order)
+    -> (int32 labels, smallest |offset - ptp_max| over the tests made)."""
+    G = np.ascontiguousarray(G, dtype=np.uint8)
+    out = np.empty(G.shape[0], np.int32)
+    C = np.ascontiguousarray(C, dtype=np.float64)
+    nd = np.ascontiguousarray(nd_unit, dtype=np.float64)
+    margin = np.zeros(1, np.float64)
+    _check(_load().orc_label_seeded(_p(G, _u8p), H, W, _p(C, _f64p), _p(nd, _f64p), nd.shape[0], float(ptp_max),
+                                    int(tri_min), _p(out, _i32p), _p(margin, _f64p)), "label_seeded")
+    return out, float(margin[0])
+
+
 def triangle_twins(gid: int, H: int, W: int):
     buf = np.empty(3, np.int64)
     n = _load().orc_triangle_twins(int(gid), H, W, _p(buf, _i64p))
@@ -276,8 +292,14 @@ class OracleParams:
     bil_kernel: int = 3
     max_edge: float = 0.1          # l_max, Algorithm 4 (<= 0 disables)
     min_dot: float = 0.95          # ang_min, Algorithm 4
-    max_offset: float = 0.0        # pairwise plane-offset join test (<= 0 disables)
+    max_offset: float = 0.0        # pairwise plane-offset join test (<= 0 disables), or ptp_max
     min_triangles: int = 0         # tri_min, Algorithm 5 (0 disables)
+    flags: int = 0                 # FLAG_SEED_PTP: max_offset is Algorithm 5's seed-relative ptp_max
+
+
+# flags bit: region growing with the seed-relative point-to-plane limit (Algorithm 5) instead of
+# the order-independent pairwise offset test
+FLAG_SEED_PTP = 1
 
 
 # Width of the band around a threshold inside which FP32 and FP64 may decide differently.
@@ -315,7 +337,11 @@ def extract_planes(points: np.ndarray, params, dominant_normals: np.ndarray, sen
     m, edge = mask(raw, smoothed, p.max_edge)
     nd_unit = normalize_dominant(dominant_normals)
     G, best, second = classify(N, m, nd_unit, p.min_dot)
-    labels = label(G, H, W, C, nd_unit, p.max_offset, p.min_triangles)
+    ptp_margin = None
+    if p.flags & FLAG_SEED_PTP:
+        labels, ptp_margin = label_seeded(G, H, W, C, nd_unit, p.max_offset, p.min_triangles)
+    else:
+        labels = label(G, H, W, C, nd_unit, p.max_offset, p.min_triangles)
     finite_edge = np.isfinite(edge)
     near_edge = finite_edge & (np.abs(np.where(finite_edge, edge, 0.0) - p.max_edge) < NEAR) & (p.max_edge > 0)
     has_best = np.isfinite(best)
@@ -335,4 +361,4 @@ def extract_planes(points: np.ndarray, params, dominant_normals: np.ndarray, sen
         ill = ang > ILL_CONDITIONED_RAD
     return dict(smoothed=smoothed, centroids=C, normals_raw=N0, normals=N, mask=m, edge=edge, groups=G,
                 best=best, second=second, labels=labels, nd_unit=nd_unit, near_edge=near_edge,
-                near_dot=near_dot, near_tie=near_tie, ill_conditioned=ill)
+                near_dot=near_dot, near_tie=near_tie, ill_conditioned=ill, ptp_margin=ptp_margin)

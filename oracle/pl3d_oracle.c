@@ -18,6 +18,7 @@
  *   orc_bilateral         bilateral normal filter, Jacobi iterations (Eq. 3-6, Section 5.2)
  *   orc_classify          group assignment                           (Algorithm 4)
  *   orc_label             edge-connected region growing per group    (Algorithm 5 over Algorithm 2 twins)
+ *   orc_label_seeded      region growing with the seed-relative point-to-plane limit (Algorithm 5)
  *   orc_extract_triangles explicit triangle set T and map T_map      (Algorithm 1)
  *   orc_extract_halfedges explicit twin array HE                     (Algorithm 2)
  *
@@ -529,6 +530,57 @@ int orc_label(const uint8_t* G, int H, int W, const double* C, const double* nd_
             for (int64_t a = 0; a < tail; ++a) labels[queue[a]] = -1;
         }
     }
+    free(queue);
+    return ORC_OK;
+}
+
+/* Algorithm 5 with its planarity constraint read as seed-relative: seeds in GID order (every
+ * group's task visits its triangles in order, and segments of different groups never meet, so
+ * one pass over all groups gives the same result); ExtractPlanarSegment takes the seed and every
+ * triangle reachable from it through twin half-edges over triangles of the seed's group that are
+ * in no segment yet and whose centroid lies within ptp_max of the plane through the seed's
+ * centroid with the group's dominant normal. The triangles of a segment of at most tri_min
+ * triangles are dropped (label -1) but stay consumed. Label = the seed's GID, the smallest GID of
+ * its segment (every smaller GID of the group was consumed before the seed was reached).
+ * margin_out (may be NULL) receives the smallest |offset - ptp_max| over every test made. */
+int orc_label_seeded(const uint8_t* G, int H, int W, const double* C, const double* nd_unit, int K, double ptp_max,
+                     int tri_min, int32_t* labels, double* margin_out) {
+    if (H < 2 || W < 2 || !C || !nd_unit) return ORC_EINVAL;
+    const int Hq = H - 1, Wq = W - 1;
+    const int64_t n = 2 * (int64_t)Hq * Wq;
+    if (n > INT32_MAX) return ORC_EINVAL;
+    int64_t* queue = (int64_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+    if (!queue) return ORC_ENOMEM;
+    const int32_t UNVISITED = -2;
+    double margin = INFINITY;
+    for (int64_t t = 0; t < n; ++t) labels[t] = (G[t] == 255) ? -1 : UNVISITED;
+    for (int64_t seed = 0; seed < n; ++seed) {
+        if (labels[seed] != UNVISITED) continue;
+        const uint8_t g = G[seed];
+        const double* d = nd_unit + 3 * (g < K ? g : 0);
+        const double* cs = C + 3 * seed;
+        int64_t head = 0, tail = 0;
+        queue[tail++] = seed;
+        labels[seed] = (int32_t)seed;
+        while (head < tail) {
+            const int64_t t = queue[head++];
+            int64_t nb[3];
+            const int m = tri_twins(t, Hq, Wq, nb);
+            for (int a = 0; a < m; ++a) {
+                const int64_t j = nb[a];
+                if (labels[j] != UNVISITED || G[j] != g) continue;
+                const double* cj = C + 3 * j;
+                const double off = fabs(d[0] * (cj[0] - cs[0]) + d[1] * (cj[1] - cs[1]) + d[2] * (cj[2] - cs[2]));
+                if (fabs(off - ptp_max) < margin) margin = fabs(off - ptp_max);
+                if (off > ptp_max) continue;
+                labels[j] = (int32_t)seed;
+                queue[tail++] = j;
+            }
+        }
+        if (tri_min > 0 && tail <= (int64_t)tri_min)
+            for (int64_t a = 0; a < tail; ++a) labels[queue[a]] = -1;
+    }
+    if (margin_out) *margin_out = margin;
     free(queue);
     return ORC_OK;
 }

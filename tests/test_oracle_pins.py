@@ -624,3 +624,51 @@ def test_segment_border_between_two_segments():
     # the labelled region's perimeter (its right side now faces the unlabelled column) plus the
     # dividing line counted on both sides
     assert bits.sum() == (2 * Hq + 2 * (Wq - 1)) + 2 * Hq
+
+
+# ----------------------------------------------------------------------------- Algorithm 5, seeded
+
+
+def _strip(nq):
+    """One quad row: chain position p of each GID (second(v) at 2v, first(v) at 2v+1, the order the
+    twins link them along the row) and centroids rising 0.1 m per chain position."""
+    gid = np.arange(2 * nq)
+    p = np.where(gid % 2 == 1, gid - 1, gid + 1)
+    C = np.zeros((2 * nq, 3))
+    C[:, 2] = 0.1 * p
+    return C
+
+
+def test_seeded_growing_hand_case():
+    """Seeds in GID order with ptp_max = 0.25 m. Seed 0 (z 0.1) takes GIDs 1 (z 0.0), 3 (0.2) and
+    2 (0.3) and stops at 5 (0.4); seed 4 (z 0.5) takes 5, 7, 6 and stops at 9; ... so the
+    segments are the GIDs 4s .. 4s+3, labelled 4s. The pairwise test with the same limit joins
+    every step of 0.1 m into one component instead: the seed-relative plane is what splits."""
+    nq = 10
+    H, W = 2, nq + 1
+    C = _strip(nq)
+    G = np.zeros(2 * nq, np.uint8)
+    nd = np.array([[0.0, 0.0, 1.0]])
+    labels, margin = oracle.label_seeded(G, H, W, C, nd, 0.25)
+    assert list(labels) == [4 * (g // 4) for g in range(2 * nq)]
+    assert abs(margin - 0.05) < 1e-12
+    pair = oracle.label(G, H, W, C, nd, max_offset=0.25)
+    assert np.all(pair == 0)
+    dropped, _ = oracle.label_seeded(G, H, W, C, nd, 0.25, tri_min=4)
+    assert np.all(dropped == -1)                          # |T^g_i| = 4 is not > 4
+    kept, _ = oracle.label_seeded(G, H, W, C, nd, 0.25, tri_min=3)
+    assert np.array_equal(kept, labels)
+
+
+def test_seeded_growing_without_limit_is_the_components():
+    f = synth.rgbd_120x160()
+    op = oracle.OracleParams(**f.params)
+    ref = oracle.extract_planes(f.points, op, f.dominant_normals, sensitivity=False)
+    seeded, _ = oracle.label_seeded(ref["groups"], f.H, f.W, ref["centroids"], ref["nd_unit"], 1e9)
+    assert np.array_equal(seeded, ref["labels"])
+    tight, _ = oracle.label_seeded(ref["groups"], f.H, f.W, ref["centroids"], ref["nd_unit"], 0.01)
+    # a tighter slab only splits segments: every seeded segment lies inside one component
+    lab = ref["labels"]
+    for s in np.unique(tight[tight >= 0]):
+        assert len(np.unique(lab[tight == s])) == 1
+    assert len(np.unique(tight[tight >= 0])) > len(np.unique(lab[lab >= 0]))
