@@ -561,6 +561,29 @@ def run_pl3d(args):
                 "frac": m_bytes / (m_us * 1e-6) / 1e9 / float(peaks_m["hbm_gbs"]),
                 "peak_source": f"{src_m} hbm_gbs", "l2": "flushed before every launch"}
 
+    # ---------------- Gaussian accumulator of the frame's filtered normals (pl3d_fastga, level 4)
+    fastga = None
+    if world == 1:
+        ga_counts = torch.empty(5120, dtype=torch.int32, device=dev)
+        step()
+        for _ in range(3):
+            pl3d.pl3d_fastga(ctx, normals, mask, ntri, 4, 1, ga_counts, None, stream)
+        g_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(50)]
+        for e_a, e_b in g_ev:
+            flush.fill_(0.75)
+            e_a.record(stream)
+            pl3d.pl3d_fastga(ctx, normals, mask, ntri, 4, 1, ga_counts, None, stream)
+            e_b.record(stream)
+        torch.cuda.synchronize()
+        g_us = statistics.median(a.elapsed_time(b) for a, b in g_ev) * 1e3
+        n_in = int(ga_counts.sum().item())
+        g_bytes = 13.0 * ntri                            # normal 12 B + mask 1 B per triangle
+        peaks_g, src_g = _peaks()
+        fastga = {"us": g_us, "level": 4, "cells": 5120, "triangles": ntri, "integrated": n_in,
+                  "mnormals_s": n_in / (g_us * 1e-6) / 1e6, "algorithmic_bytes": g_bytes,
+                  "achieved_gbs": g_bytes / (g_us * 1e-6) / 1e9, "hbm_frac": g_bytes / (g_us * 1e-6) / 1e9 /
+                  float(peaks_g["hbm_gbs"]), "peak_source": f"{src_g} hbm_gbs", "l2": "flushed before every launch"}
+
     # ---------------- batched (256 mixed frames, one launch) and served (Poisson trace) workloads
     batched = served = None
     if world == 1 and not args.no_batched:
@@ -630,6 +653,7 @@ def run_pl3d(args):
         "roofline": roofline,
         "cpu_baseline": cpu,
         "mesh": mesh,
+        "fastga": fastga,
         "batched": batched,
         "served": served,
         "step_ms_p50": statistics.median(step_ms),

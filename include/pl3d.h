@@ -76,8 +76,19 @@ typedef struct pl3d_ctx pl3d_ctx;
  *                  |n^d_g . (c_i - c_j)| <= max_offset (plane-offset test). <= 0 disables.
  *   min_triangles  [tri_min] if > 0, segments of at most min_triangles triangles are dropped
  *                  (Algorithm 5 keeps |T^g_i| > tri_min).
- *   flags          reserved, must be 0.
+ *   flags          0, or PL3D_FLAG_SEED_PTP: region growing as Algorithm 5 orders it, with
+ *                  max_offset (> 0 required) as ptp_max read seed-relative. Seeds are taken in
+ *                  GID order; a segment is its seed plus every triangle reachable through twin
+ *                  half-edges over triangles of the seed's group that are in no segment yet and
+ *                  whose centroid lies within ptp_max of the plane through the seed's centroid
+ *                  with the group's dominant normal; a dropped segment's triangles stay consumed;
+ *                  labels are still each segment's smallest GID (its seed). The GPU labels the
+ *                  order-independent components and flags those leaving their seed's slab; the
+ *                  host regrows only the flagged ones, so such calls synchronise the stream.
+ *                  Single-frame entry points only (batches, the server and the allocation-free
+ *                  entry return PL3D_ERR_UNSUPPORTED).
  */
+#define PL3D_FLAG_SEED_PTP 1u
 typedef struct pl3d_params {
     int32_t lap_iters;
     float lap_lambda;
@@ -159,7 +170,7 @@ const char* pl3d_status_string(int status);
  * writes per-phase total milliseconds and launch counts for up to n_slots phases
  * (ms_out, launches_out may be NULL) and returns the number of phases (PL3D_TIMING_SLOTS),
  * clearing the totals when reset != 0. Phase order: see pl3d_timing_slot_name. */
-#define PL3D_TIMING_SLOTS 7
+#define PL3D_TIMING_SLOTS 8
 int pl3d_set_timing(pl3d_ctx* ctx, int enable);
 int pl3d_read_timing(pl3d_ctx* ctx, double* ms_out, int64_t* launches_out, int n_slots, int reset);
 const char* pl3d_timing_slot_name(int slot);
@@ -363,6 +374,44 @@ void pl3d_server_destroy(pl3d_server* srv);
 int pl3d_extract_mesh(pl3d_ctx* ctx, const float* points, const int32_t* labels, int H, int W, int32_t* out_T,
                       int32_t* out_Tmap, int32_t* out_HE, int64_t* out_counts, int32_t* out_seg_labels,
                       int32_t* out_seg_offsets, int32_t* out_seg_tris, uint8_t* out_border, void* stream);
+
+/*
+ * Fast Gaussian Accumulator (Section 6): dominant plane normals from the triangle normals,
+ * replacing given dominant normals.
+ *
+ * Cells (Section 6.1.1): the faces of an icosahedron refined `level` times (0..5: 20 4^level
+ * cells). Level 0 has the 12 unit vertices (-1, phi, 0), (1, phi, 0), (-1, -phi, 0),
+ * (1, -phi, 0), (0, -1, phi), (0, 1, phi), (0, -1, -phi), (0, 1, -phi), (phi, 0, -1),
+ * (phi, 0, 1), (-phi, 0, -1), (-phi, 0, 1) (before scaling, in this order) and the 20 faces made
+ * by the triples of mutually adjacent vertices, in lexicographic order of the sorted triple,
+ * counter-clockwise from outside. Level l + 1 splits face p = (a, b, c) into faces 4p .. 4p + 3 =
+ * (a, ab, ca), (ab, b, bc), (ca, bc, c), (ab, bc, ca), midpoints projected onto the sphere. A
+ * cell's surface normal is its flat face's unit normal.
+ *
+ * pl3d_fastga_cells (host only) writes the level's surface normals (host, cells * 3 floats) and
+ * 1-ring neighbours (host, cells * 12 int32, ascending, -1 padded; either pointer may be NULL)
+ * and returns the number of cells.
+ *
+ * pl3d_fastga integrates every stride-th triangle of `normals` (device, n * 3 FP32, e.g. the
+ * out_normals of pl3d_extract_planes; Section 6.3's sampling) whose normal is finite and, when
+ * `mask` (device, n bytes) is given, whose mask byte is non-zero: each goes to the cell whose
+ * surface normal is closest (Section 6.1.3, Algorithm 3). out_counts (device, cells int32) receives
+ * the histogram; out_cells (device, n int32, or NULL) the cell of every triangle, -1 where not
+ * integrated. The first call for a level on a context uploads the level's tables (synchronously).
+ *
+ * pl3d_fastga_peaks (host only) detects peaks in a histogram (host, cells int32): a cell whose
+ * count is above v_min and not below any 1-ring neighbour's (a plateau keeps its lowest index),
+ * the cell graph standing in for the paper's unwrapped image and its 3 x 3 peak test
+ * (Section 6.2). Peaks whose surface normals are closer than d_peak are merged by single-linkage
+ * agglomerative clustering into their count-weighted mean normal. Up to max_peaks clusters are
+ * written by decreasing total count (out_normals host [max_peaks * 3], out_weights host or
+ * NULL); returns how many were written.
+ */
+int pl3d_fastga_cells(int level, float* out_normals, int32_t* out_neighbors);
+int pl3d_fastga(pl3d_ctx* ctx, const float* normals, const uint8_t* mask, int64_t n, int level, int stride,
+                int32_t* out_counts, int32_t* out_cells, void* stream);
+int pl3d_fastga_peaks(int level, const int32_t* counts, float v_min, float d_peak, int max_peaks, float* out_normals,
+                      int64_t* out_weights);
 
 /* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
 int pl3d_version(void);

@@ -21,7 +21,9 @@ from __future__ import annotations
 
 import numpy as np
 
+from . import FLAG_SEED_PTP as _FLAG_SEED_PTP
 from . import label as _label
+from . import label_seeded as _label_seeded
 
 POINT_TOL_M = 2e-5
 NORMAL_TOL_RAD = 1e-4
@@ -84,7 +86,11 @@ def compare(dev: dict, ref: dict, params, H: int, W: int, point_tol=POINT_TOL_M,
     else:
         G_sub = G_ref
     if rep["flagged"] and dev.get("groups") is not None:
-        want = _label(G_sub, H, W, ref["centroids"], ref["nd_unit"], params.max_offset, params.min_triangles)
+        if getattr(params, "flags", 0) & _FLAG_SEED_PTP:
+            want, _ = _label_seeded(G_sub, H, W, ref["centroids"], ref["nd_unit"], params.max_offset,
+                                    params.min_triangles)
+        else:
+            want = _label(G_sub, H, W, ref["centroids"], ref["nd_unit"], params.max_offset, params.min_triangles)
     else:
         want = ref["labels"]
     lm = lab != want

@@ -25,7 +25,8 @@ PL3D_ERR_TIMEOUT = -4
 PL3D_ERR_UNSUPPORTED = -5
 PL3D_MAX_GROUPS = 254
 PL3D_NO_GROUP = 255
-PL3D_TIMING_SLOTS = 7
+PL3D_TIMING_SLOTS = 8
+PL3D_FLAG_SEED_PTP = 1
 
 
 class pl3d_params(ctypes.Structure):
@@ -158,6 +159,9 @@ def lib():
                                    ctypes.POINTER(ctypes.c_int64)]
     L.pl3d_extract_mesh.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                     _vp]
+    L.pl3d_fastga_cells.argtypes = [ctypes.c_int, _vp, _vp]
+    L.pl3d_fastga.argtypes = [_vp, _vp, _vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]
+    L.pl3d_fastga_peaks.argtypes = [ctypes.c_int, _vp, ctypes.c_float, ctypes.c_float, ctypes.c_int, _vp, _vp]
     L.pl3d_server_create.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(pl3d_server_config)]
     L.pl3d_server_submit.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, P, _vp, ctypes.c_int, _vp, _vp, _vp,
                                      ctypes.POINTER(ctypes.c_uint64)]
@@ -442,6 +446,41 @@ def extract_mesh(ctx, points, labels, stream=None) -> dict:
         out.update(seg_labels=o["seg_labels"][:nS], seg_offsets=o["seg_offsets"][:nS + 1], seg_tris=o["seg_tris"][:nL],
                    border=o["border"][:nT])
     return out
+
+
+def pl3d_fastga_cells(level: int):
+    """(surface normals float32 [cells, 3], 1-ring neighbours int32 [cells, 12]) of a refinement level."""
+    import numpy as np
+    n = 20 * 4 ** int(level)
+    normals = np.empty((n, 3), np.float32)
+    nbrs = np.empty((n, 12), np.int32)
+    rc = lib().pl3d_fastga_cells(int(level), normals.ctypes.data, nbrs.ctypes.data)
+    if rc < 0:
+        raise PL3DError(rc, "pl3d_fastga_cells")
+    return normals, nbrs
+
+
+def pl3d_fastga(ctx, normals, mask, n, level, stride, out_counts, out_cells=None, stream=None) -> int:
+    """Histogram of device normals over the cells of `level` (see include/pl3d.h)."""
+    _check_tensor(normals, "normals", "torch.float32", 3 * n)
+    _check_tensor(mask, "mask", "torch.uint8", n)
+    _check_tensor(out_counts, "out_counts", "torch.int32", 20 * 4 ** int(level))
+    _check_tensor(out_cells, "out_cells", "torch.int32", n)
+    return _check(lib().pl3d_fastga(ctx, _ptr(normals), _ptr(mask), int(n), int(level), int(stride), _ptr(out_counts),
+                                    _ptr(out_cells), _stream(stream)), "pl3d_fastga")
+
+
+def pl3d_fastga_peaks(level, counts, v_min: float, d_peak: float, max_peaks: int = 16):
+    """-> (normals float32 [p, 3], weights int64 [p]) from a host histogram."""
+    import numpy as np
+    c = np.ascontiguousarray(counts.cpu().numpy() if hasattr(counts, "cpu") else counts, dtype=np.int32)
+    out = np.empty((max(1, max_peaks), 3), np.float32)
+    w = np.empty(max(1, max_peaks), np.int64)
+    k = lib().pl3d_fastga_peaks(int(level), c.ctypes.data, float(v_min), float(d_peak), int(max_peaks),
+                                out.ctypes.data, w.ctypes.data)
+    if k < 0:
+        raise PL3DError(k, "pl3d_fastga_peaks")
+    return out[:k].copy(), w[:k].copy()
 
 
 def pl3d_server_create(device: int = 0, max_inflight: int = 2, max_batch_frames: int = 64, hbm_bytes: int = 0) -> int:

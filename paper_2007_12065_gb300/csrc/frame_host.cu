@@ -151,6 +151,13 @@ static int fused_iters(int iters, int max_fuse, int requested) {
     return fuse < least ? least : fuse;
 }
 
+const float* final_disp(const FrameScratch& sc, const pl3d_params* p, const Tuning& t) {
+    const int rl = p->lap_iters > 0 ? p->lap_kernel / 2 : 1;
+    const int lf = fused_iters(p->lap_iters, kLapMaxHalo / rl, t.lap_fuse);
+    const int passes = p->lap_iters <= lf ? 1 : (p->lap_iters + lf - 1) / lf;   // as frame_build plans them
+    return sc.disp[(passes - 1) & 1];
+}
+
 size_t frame_smem_bytes(const pl3d_params* p, const Tuning& t) {
     const int rl = p->lap_iters > 0 ? p->lap_kernel / 2 : 1;
     const int rb = p->bil_iters > 0 ? p->bil_kernel / 2 : 1;

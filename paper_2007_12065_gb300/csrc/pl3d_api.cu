@@ -20,8 +20,9 @@ namespace {
 
 constexpr int kVersion = 2 * 10000 + 1 * 100 + 0;
 
-const char* const kSlotNames[PL3D_TIMING_SLOTS] = {"laplacian",    "bilateral",   "label_merge", "label_flatten",
-                                                    "frame_kernel", "host_copies", "mesh_kernel"};
+const char* const kSlotNames[PL3D_TIMING_SLOTS] = {"laplacian",   "bilateral",    "label_merge",
+                                                    "label_flatten", "frame_kernel", "host_copies",
+                                                    "mesh_kernel", "fastga_kernel"};
 
 bool finite_f(float x) { return isfinite(x) != 0; }
 
@@ -64,13 +65,34 @@ int run(pl3d_ctx* ctx, const float* points, int H, int W, const pl3d_params* p, 
     sc.barrier = ctx->barrier();
     sc.error = ctx->error();
     sc.phase_ns = ctx->timing ? ctx->phase_ns() : nullptr;
+    sc.seed_flags = nullptr;
+    sc.seed_centroids = nullptr;
 
+    const bool seeded = (p->flags & PL3D_FLAG_SEED_PTP) != 0;
+    pl3d_params q = *p;
+    if (seeded) {
+        // components first: no offset test, no tri_min (both belong to the seeded pass)
+        if ((rc = grow(&ctx->seed_flags, &ctx->cap_seed, ntri, 1, s)) != PL3D_OK ||
+            (rc = grow(&ctx->seed_centroids, &ctx->cap_seed_c, ntri, 3, s)) != PL3D_OK)
+            return rc;
+        sc.seed_flags = ctx->seed_flags;
+        sc.seed_centroids = ctx->seed_centroids;
+        q.max_offset = 0.f;
+        q.min_triangles = 0;
+        q.flags = 0;
+    }
     cudaEvent_t e0, e1;
     record_start(ctx, s, &e0, &e1);
-    rc = frame_launch(sc, points, H, W, p, nd_host, K, out_mask, out_normals, out_labels, out_points, out_groups,
+    rc = frame_launch(sc, points, H, W, &q, nd_host, K, out_mask, out_normals, out_labels, out_points, out_groups,
                       ctx->tuning, s);
     record_stop(ctx, s, kSlotKernel, e0, e1);
     if (rc != PL3D_OK) return rc;
+    if (seeded) {
+        rc = seeded_labels(sc, final_disp(sc, &q, ctx->tuning), points, H, W, p, nd_host, K,
+                           out_groups ? out_groups : ctx->groups, out_labels, s);
+        if (rc != PL3D_OK) return rc;
+        ctx->launches += 1;
+    }
     ctx->launches += 1;
     if (ctx->timing) ctx->timed_frames += 1;
     return PL3D_OK;
@@ -121,7 +143,8 @@ int pl3d_validate(const pl3d_params* p, int H, int W, const float* nd, int K) {
     if (H < 2 || W < 2) return PL3D_ERR_INVALID_ARG;
     if (2LL * (H - 1) * (long long)(W - 1) >= (1LL << 31) || 3LL * H * W >= (1LL << 31)) return PL3D_ERR_INVALID_ARG;
     if (K < 1 || K > PL3D_MAX_GROUPS) return PL3D_ERR_INVALID_ARG;
-    if (p->flags != 0) return PL3D_ERR_INVALID_ARG;
+    if ((p->flags & ~PL3D_FLAG_SEED_PTP) != 0) return PL3D_ERR_INVALID_ARG;
+    if ((p->flags & PL3D_FLAG_SEED_PTP) && !(p->max_offset > 0.f)) return PL3D_ERR_INVALID_ARG;
     if (p->lap_iters < 0 || p->bil_iters < 0 || p->min_triangles < 0) return PL3D_ERR_INVALID_ARG;
     if (p->lap_iters > 0) {
         if (p->lap_kernel != 3 && p->lap_kernel != 5 && p->lap_kernel != 7) return PL3D_ERR_UNSUPPORTED;
@@ -194,6 +217,9 @@ void pl3d_destroy(pl3d_ctx* c) {
         drop_graphs(c);
         cudaFree(c->bslab);
         cudaFree(c->mslab);
+        cudaFree(c->seed_flags);
+        cudaFree(c->seed_centroids);
+        cudaFree(c->ga_tables);
         cudaFree(c->bdesc);
         cudaFreeHost(c->bstage);
         if (c->bupload) cudaEventDestroy(c->bupload);

@@ -154,6 +154,7 @@ int check_frames(const pl3d_frame* frames, int n, int* rl_out, int* rb_out) {
             return PL3D_ERR_INVALID_ARG;
         const int rc = pl3d_validate(f.params, f.H, f.W, f.dominant_normals, f.K);
         if (rc != PL3D_OK) return rc;
+        if (f.params->flags & PL3D_FLAG_SEED_PTP) return PL3D_ERR_UNSUPPORTED;   // host-assisted: single frames
         if (f.params->lap_iters > 0) {
             const int r = f.params->lap_kernel / 2;
             if (rl && r != rl) return PL3D_ERR_UNSUPPORTED;

@@ -13,9 +13,9 @@ namespace pl3d {
 namespace ctxutil {
 
 // Timing slots: four phases of the persistent kernels (device %globaltimer, accumulated by the
-// kernel), the kernel as a whole, the host copies and the explicit-mesh launch (CUDA events on
-// the call's stream).
-enum Slot { kSlotLap = 0, kSlotBil, kSlotMerge, kSlotLabels, kSlotKernel, kSlotCopies, kSlotMesh };
+// kernel), the kernel as a whole, the host copies, the explicit-mesh launch and the Gaussian
+// accumulator (CUDA events on the call's stream).
+enum Slot { kSlotLap = 0, kSlotBil, kSlotMerge, kSlotLabels, kSlotKernel, kSlotCopies, kSlotMesh, kSlotFastga };
 
 struct TimedRange {
     int slot;
@@ -47,6 +47,10 @@ struct pl3d_ctx {
     int32_t* sizes = nullptr;       // cap_tri
     size_t cap_tri = 0;
     unsigned* ctl = nullptr;        // barrier [2], error word, pad, phase totals [4] (u64)
+    uint8_t* seed_flags = nullptr;  // PL3D_FLAG_SEED_PTP: per-root flags, cap_seed
+    size_t cap_seed = 0;
+    float* seed_centroids = nullptr;   // PL3D_FLAG_SEED_PTP: 3 cap_seed_c floats
+    size_t cap_seed_c = 0;
     // device staging for the host-buffer entry point
     float* st_points = nullptr;
     size_t st_cap_points = 0;
@@ -70,6 +74,10 @@ struct pl3d_ctx {
     // scratch of the explicit-mesh launch (pl3d_mesh.cu)
     unsigned char* mslab = nullptr;
     size_t mslab_cap = 0;
+    // Gaussian accumulator tables of one refinement level (pl3d_fastga.cu)
+    unsigned char* ga_tables = nullptr;
+    int ga_level = -1;
+    size_t ga_off[4] = {0, 0, 0, 0};
     // timing
     bool timing = false;
     int64_t timed_frames = 0;       // timed persistent launches

@@ -156,6 +156,8 @@ struct FrameScratch {
     unsigned* barrier;             // [2], zero before the first use
     int* error;                    // [1]
     unsigned long long* phase_ns;  // [4] or nullptr
+    uint8_t* seed_flags;           // >= 2 Q, PL3D_FLAG_SEED_PTP only
+    float* seed_centroids;         // >= 6 Q, PL3D_FLAG_SEED_PTP only
 };
 
 // Launch-shape choices that leave every result bit-identical (Jacobi iterations split over
@@ -168,6 +170,14 @@ struct Tuning {
 
 // Number of bilateral passes the parameters need (> 1 needs the carry buffers).
 int bilateral_passes(const pl3d_params* p, const Tuning& t);
+
+// The frame's final displacement buffer among sc.disp (smoothed point = input point + it).
+const float* final_disp(const FrameScratch& sc, const pl3d_params* p, const Tuning& t);
+
+// PL3D_FLAG_SEED_PTP: turns the component labels of a frame (computed without offset test and
+// tri_min) into Algorithm 5's seeded segments; synchronises the stream (pl3d_seeded.cu).
+int seeded_labels(const FrameScratch& sc, const float* disp, const float* points, int H, int W, const pl3d_params* p,
+                  const float* nd_host, int K, const uint8_t* groups, int32_t* labels, cudaStream_t s);
 
 // Dynamic shared memory the persistent kernels need for this frame under tuning t.
 size_t frame_smem_bytes(const pl3d_params* p, const Tuning& t);

@@ -336,6 +336,7 @@ int pl3d_server_submit(pl3d_server* S, const float* host_points, int H, int W, c
         return PL3D_ERR_INVALID_ARG;
     int rc = pl3d_validate(params, H, W, nd, K);
     if (rc != PL3D_OK) return rc;
+    if (params->flags & PL3D_FLAG_SEED_PTP) return PL3D_ERR_UNSUPPORTED;   // host-assisted: single frames
     Request r;
     r.h_points = host_points;
     r.H = H;

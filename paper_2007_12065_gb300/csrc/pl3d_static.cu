@@ -88,6 +88,7 @@ extern "C" int pl3d_extract_planes_static(const float* points, int H, int W, con
     if (!points || !nd_host || !out_mask || !out_normals || !out_labels) return PL3D_ERR_INVALID_ARG;
     int rc = pl3d_validate(p, H, W, nd_host, K);
     if (rc != PL3D_OK) return rc;
+    if (p->flags & PL3D_FLAG_SEED_PTP) return PL3D_ERR_UNSUPPORTED;   // host-assisted: needs a context
     if ((size_t)H * (size_t)W > kMaxPoints) return PL3D_ERR_INVALID_ARG;
     if (bilateral_passes(p, Tuning{0, 0, 0}) > 1) return PL3D_ERR_INVALID_ARG;   // would need the carry buffers
     int dev = -1;

@@ -51,7 +51,7 @@ def test_status_strings(pl3d):
     assert pl3d.pl3d_version() >= 10000
     names = [pl3d.pl3d_timing_slot_name(i) for i in range(pl3d.PL3D_TIMING_SLOTS)]
     assert names == ["laplacian", "bilateral", "label_merge", "label_flatten", "frame_kernel", "host_copies",
-                     "mesh_kernel"]
+                     "mesh_kernel", "fastga_kernel"]
 
 
 def test_default_params_are_paper_rgbd(pl3d):

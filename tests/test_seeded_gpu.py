@@ -1,0 +1,88 @@
+"""Algorithm 5 with the seed-relative point-to-plane limit (PL3D_FLAG_SEED_PTP) through the C ABI
+against the oracle's seeded region growing. ptp_max values are kept where the oracle made no
+test within 1e-5 of the limit (FP32 and FP64 centroids then decide alike)."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle.compare import compare
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    import paper_2007_12065_gb300 as pl3d
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    oracle.set_threads(os.cpu_count() or 1)
+    ex = pl3d.PlaneExtractor(0)
+    yield pl3d, ex, torch
+    ex.close()
+
+
+def _run(env, f, ptp, tri_min=0):
+    pl3d, ex, torch = env
+    params = dict(f.params, max_offset=ptp, min_triangles=tri_min, flags=1)
+    op = oracle.OracleParams(**params)
+    ref = oracle.extract_planes(f.points, op, f.dominant_normals)
+    if ref["ptp_margin"] < 1e-5:
+        return None, ref
+    out = ex(torch.from_numpy(f.points).cuda(), pl3d.make_params(**params), f.dominant_normals, want_points=True,
+             want_groups=True)
+    torch.cuda.synchronize()
+    dev = {k: v.cpu().numpy() for k, v in out.items()}
+    rep = compare(dev, ref, op, f.points.shape[0], f.points.shape[1])
+    return rep, ref
+
+
+@pytest.mark.parametrize("name", ["rgbd_120x160", "rgbd_480x640", "lidar_64x1024"])
+def test_seeded_segments_match_oracle(env, name):
+    f = synth.WORKLOADS[name]()
+    checked = 0
+    for ptp in (0.004, 0.007, 0.012, 0.02, 0.035, 0.06):
+        rep, ref = _run(env, f, ptp)
+        if rep is None:
+            continue
+        plain = oracle.extract_planes(f.points, oracle.OracleParams(**f.params), f.dominant_normals,
+                                      sensitivity=False)["labels"]
+        n_seeded = len(np.unique(ref["labels"][ref["labels"] >= 0]))
+        n_plain = len(np.unique(plain[plain >= 0]))
+        print(name, ptp, rep, "segments", n_seeded, "components", n_plain)
+        checked += 1
+    assert checked >= 2
+
+
+def test_seeded_with_tri_min(env):
+    f = synth.rgbd_120x160()
+    for ptp in (0.01, 0.03, 0.05):
+        rep, _ = _run(env, f, ptp, tri_min=25)
+        if rep is not None:
+            print(ptp, rep)
+            return
+    pytest.fail("no ptp_max with a clear margin")
+
+
+def test_seeded_flag_needs_a_limit_and_single_frames(env):
+    pl3d, ex, torch = env
+    f = synth.depth_camera_scene(16, 16, seed=1, n_boxes=1)
+    nd = f.dominant_normals
+    assert pl3d.pl3d_validate(pl3d.make_params(flags=1), 16, 16, nd) == pl3d.PL3D_ERR_INVALID_ARG
+    assert pl3d.pl3d_validate(pl3d.make_params(flags=1, max_offset=0.05), 16, 16, nd) == 0
+    assert pl3d.pl3d_validate(pl3d.make_params(flags=2, max_offset=0.05), 16, 16, nd) == pl3d.PL3D_ERR_INVALID_ARG
+    pts = torch.from_numpy(f.points).cuda()
+    n = 2 * 15 * 15
+    o = (torch.empty(n, dtype=torch.uint8, device="cuda"), torch.empty((n, 3), device="cuda"),
+         torch.empty(n, dtype=torch.int32, device="cuda"))
+    b = pl3d.Batch()
+    b.add(pts, 16, 16, pl3d.make_params(flags=1, max_offset=0.05), nd, *o)
+    with pytest.raises(pl3d.PL3DError) as e:
+        pl3d.pl3d_extract_planes_batched(ex.ctx, b)
+    assert e.value.status == pl3d.PL3D_ERR_UNSUPPORTED
+    with pytest.raises(pl3d.PL3DError) as e:
+        pl3d.pl3d_extract_planes_static(pts, 16, 16, pl3d.make_params(flags=1, max_offset=0.05), nd, nd.shape[0], *o)
+    assert e.value.status == pl3d.PL3D_ERR_UNSUPPORTED
