@@ -11,9 +11,9 @@
 //
 // Search (Section 6.1.3, Algorithm 3). The paper narrows the search with a space-filling-curve
 // id, an interpolated window and a binary search, then compares the cell found with its 12
-// neighbours. Here the first stage is a descent of the refinement: the children of a face tile
-// its spherical triangle exactly, so at each level the child whose three edge planes the normal
-// is most inside is the cell containing the normal. The nearest surface normal is then taken over
+// neighbours. Here the first stage is a descent of the refinement: the level-0 face with the
+// closest normal, then at each level the child containing the normal -- the children of a face
+// tile its spherical triangle exactly, and three inner edge planes tell them apart. The nearest surface normal is then taken over
 // that cell and its 1-ring neighbours (cells sharing a vertex), as in Algorithm 3; the nearest
 // cell always lies there (checked on dense random samples at levels 3 and 4).
 #include <math.h>
@@ -37,8 +37,9 @@ constexpr int kNbrs = 12;
 struct Tables {
     int level = -1;
     int cells = 0;
-    std::vector<float> edge_planes;   // per face of levels 0..level: 3 unit edge-plane normals (9 floats)
-    std::vector<int> level_offset;    // first face of each level in edge_planes
+    float face0[60];                  // unit normals of the 20 faces of level 0
+    std::vector<float> split_planes;  // per face of levels 0..level-1: its 3 inner edge planes (9 floats)
+    std::vector<int> level_offset;    // first face of each level in split_planes
     std::vector<float> normals;       // [cells][3] surface normals of the last level
     std::vector<int32_t> nbrs;        // [cells][12] 1-ring neighbours, ascending, -1 padded
 };
@@ -77,18 +78,14 @@ Tables build(int level) {
                 }
     Tables t;
     t.level = level;
-    auto push_planes = [&](const std::vector<std::array<int, 3>>& faces) {
-        t.level_offset.push_back((int)(t.edge_planes.size() / 9));
-        for (const auto& f : faces)
-            for (int e = 0; e < 3; ++e) {
-                const V3d p = unit(crs(V[f[e]], V[f[(e + 1) % 3]]));
-                t.edge_planes.push_back((float)p.x);
-                t.edge_planes.push_back((float)p.y);
-                t.edge_planes.push_back((float)p.z);
-            }
-    };
-    push_planes(F);
+    for (int i = 0; i < 20; ++i) {
+        const V3d n = unit(crs(sub(V[F[i][1]], V[F[i][0]]), sub(V[F[i][2]], V[F[i][0]])));
+        t.face0[3 * i] = (float)n.x;
+        t.face0[3 * i + 1] = (float)n.y;
+        t.face0[3 * i + 2] = (float)n.z;
+    }
     for (int l = 0; l < level; ++l) {
+        t.level_offset.push_back((int)(t.split_planes.size() / 9));
         std::map<std::pair<int, int>, int> mid;
         auto midpoint = [&](int a, int b) {
             const std::pair<int, int> key(std::min(a, b), std::max(a, b));
@@ -104,13 +101,21 @@ Tables build(int level) {
         for (const auto& f : F) {
             const int a = f[0], b = f[1], c = f[2];
             const int ab = midpoint(a, b), bc = midpoint(b, c), ca = midpoint(c, a);
+            // the inner edges cutting off the corner children 0 (at a), 1 (at b), 2 (at c): a normal
+            // of the face on the positive side of plane j lies in child j, on no positive side in
+            // the middle child 3
+            const V3d planes[3] = {unit(crs(V[ab], V[ca])), unit(crs(V[bc], V[ab])), unit(crs(V[ca], V[bc]))};
+            for (const V3d& p : planes) {
+                t.split_planes.push_back((float)p.x);
+                t.split_planes.push_back((float)p.y);
+                t.split_planes.push_back((float)p.z);
+            }
             nf.push_back({a, ab, ca});
             nf.push_back({ab, b, bc});
             nf.push_back({ca, bc, c});
             nf.push_back({ab, bc, ca});
         }
         F.swap(nf);
-        push_planes(F);
     }
     t.cells = (int)F.size();
     for (const auto& f : F) {
@@ -150,56 +155,59 @@ struct GaArgs {
     int stride;
     int level;
     int cells;
-    const float* planes;      // edge planes of all levels
-    const int* level_offset;  // [level + 1]
+    float face0[60];          // level-0 face normals (kernel parameter space: a broadcast read)
+    const float* planes;      // split planes of the faces of levels 0..level-1
+    const int* level_offset;  // [level]
     const float* cell_n;      // [cells][3]
     const int* nbrs;          // [cells][12]
     int* counts;              // [cells], zeroed before the launch
     int* out_cell;            // [n] or nullptr
 };
 
-// How far inside face f's three edge planes the normal lies (>= 0 inside).
-__device__ __forceinline__ float inside(const float* P, int f, float x, float y, float z) {
-    const float* p = P + 9 * f;
-    const float s0 = x * __ldg(p) + y * __ldg(p + 1) + z * __ldg(p + 2);
-    const float s1 = x * __ldg(p + 3) + y * __ldg(p + 4) + z * __ldg(p + 5);
-    const float s2 = x * __ldg(p + 6) + y * __ldg(p + 7) + z * __ldg(p + 8);
-    return fminf(s0, fminf(s1, s2));
-}
-
 __global__ void __launch_bounds__(kThreads) fastga_kernel(const __grid_constant__ GaArgs a) {
     extern __shared__ int hist[];   // [cells] private histogram of this CTA
     for (int i = threadIdx.x; i < a.cells; i += blockDim.x) hist[i] = 0;
     __syncthreads();
     const long long n_samples = (a.n + a.stride - 1) / a.stride;
-    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n_samples;
-         s += (long long)gridDim.x * blockDim.x) {
-        const long long i = s * a.stride;
+    const long long gstride = (long long)gridDim.x * blockDim.x;
+    const long long n_iter = (n_samples + gstride - 1) / gstride;   // uniform: whole warps stay together
+    for (long long it = 0; it < n_iter; ++it) {
+        const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x + it * gstride;
+        const bool in_range = s < n_samples;
+        const long long i = in_range ? s * a.stride : 0;
         int cell = -1;
-        const float x = __ldg(a.normals + 3 * i), y = __ldg(a.normals + 3 * i + 1), z = __ldg(a.normals + 3 * i + 2);
-        const bool use = (!a.mask || __ldg(a.mask + i) != 0) && isfinite(x) && isfinite(y) && isfinite(z);
+        float x = NAN, y = NAN, z = NAN;
+        if (in_range) {
+            x = __ldg(a.normals + 3 * i);
+            y = __ldg(a.normals + 3 * i + 1);
+            z = __ldg(a.normals + 3 * i + 2);
+        }
+        const bool use =
+            in_range && (!a.mask || __ldg(a.mask + i) != 0) && isfinite(x) && isfinite(y) && isfinite(z);
         if (use) {
-            // descent: the face of level 0, then at every level the child containing the normal
+            // descent. Level 0: the face whose normal is closest (for the regular icosahedron each
+            // face's spherical triangle is exactly the set of directions closest to its normal).
             int f = 0;
-            float best = inside(a.planes, 0, x, y, z);
+            float best = x * a.face0[0] + y * a.face0[1] + z * a.face0[2];
             for (int k = 1; k < 20; ++k) {
-                const float v = inside(a.planes, k, x, y, z);
+                const float v = x * a.face0[3 * k] + y * a.face0[3 * k + 1] + z * a.face0[3 * k + 2];
                 if (v > best) {
                     best = v;
                     f = k;
                 }
             }
-            for (int l = 1; l <= a.level; ++l) {
-                const int base = __ldg(a.level_offset + l) + 4 * f;
-                int c = 0;
-                best = inside(a.planes, base, x, y, z);
-                for (int k = 1; k < 4; ++k) {
-                    const float v = inside(a.planes, base + k, x, y, z);
-                    if (v > best) {
-                        best = v;
-                        c = k;
-                    }
-                }
+            // every further level: the corner child on whose side of its inner edge the normal
+            // lies, else the middle child (the four children tile the face exactly)
+            for (int l = 0; l < a.level; ++l) {
+                const float* p = a.planes + 9 * ((long long)__ldg(a.level_offset + l) + f);
+                const float s0 = x * __ldg(p) + y * __ldg(p + 1) + z * __ldg(p + 2);
+                const float s1 = x * __ldg(p + 3) + y * __ldg(p + 4) + z * __ldg(p + 5);
+                const float s2 = x * __ldg(p + 6) + y * __ldg(p + 7) + z * __ldg(p + 8);
+                int c = 3;
+                float m = 0.f;
+                if (s0 > m) m = s0, c = 0;
+                if (s1 > m) m = s1, c = 1;
+                if (s2 > m) m = s2, c = 2;
                 f = 4 * f + c;
             }
             // Algorithm 3's local search: the closest surface normal among f and its neighbours
@@ -215,9 +223,12 @@ __global__ void __launch_bounds__(kThreads) fastga_kernel(const __grid_constant_
                     cell = j;
                 }
             }
-            atomicAdd(hist + cell, 1);
         }
-        if (a.out_cell) a.out_cell[i] = cell;
+        // one shared-memory atomic per distinct cell in the warp: most normals of a scene fall in
+        // the few cells of its dominant planes
+        const unsigned peers = __match_any_sync(0xffffffffu, cell);
+        if (cell >= 0 && (int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(hist + cell, __popc(peers));
+        if (a.out_cell && in_range) a.out_cell[i] = cell;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < a.cells; i += blockDim.x)
@@ -254,14 +265,14 @@ int pl3d_fastga(pl3d_ctx* ctx, const float* normals, const uint8_t* mask, int64_
         cudaFree(ctx->ga_tables);
         ctx->ga_tables = nullptr;
         ctx->ga_level = -1;
-        const size_t b0 = t.edge_planes.size() * 4, b1 = t.level_offset.size() * 4, b2 = t.normals.size() * 4,
+        const size_t b0 = t.split_planes.size() * 4, b1 = t.level_offset.size() * 4, b2 = t.normals.size() * 4,
                      b3 = t.nbrs.size() * 4;
         const size_t o1 = (b0 + 255) / 256 * 256, o2 = o1 + (b1 + 255) / 256 * 256, o3 = o2 + (b2 + 255) / 256 * 256;
         if (cudaMalloc((void**)&ctx->ga_tables, o3 + b3) != cudaSuccess) {
             cudaGetLastError();
             return PL3D_ERR_OUT_OF_MEMORY;
         }
-        if (cudaMemcpy(ctx->ga_tables, t.edge_planes.data(), b0, cudaMemcpyHostToDevice) != cudaSuccess ||
+        if (cudaMemcpy(ctx->ga_tables, t.split_planes.data(), b0, cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemcpy(ctx->ga_tables + o1, t.level_offset.data(), b1, cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemcpy(ctx->ga_tables + o2, t.normals.data(), b2, cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemcpy(ctx->ga_tables + o3, t.nbrs.data(), b3, cudaMemcpyHostToDevice) != cudaSuccess)
@@ -284,6 +295,7 @@ int pl3d_fastga(pl3d_ctx* ctx, const float* normals, const uint8_t* mask, int64_
     a.stride = stride;
     a.level = level;
     a.cells = t.cells;
+    memcpy(a.face0, t.face0, sizeof(a.face0));
     a.planes = reinterpret_cast<const float*>(ctx->ga_tables + ctx->ga_off[0]);
     a.level_offset = reinterpret_cast<const int*>(ctx->ga_tables + ctx->ga_off[1]);
     a.cell_n = reinterpret_cast<const float*>(ctx->ga_tables + ctx->ga_off[2]);

@@ -5,7 +5,7 @@
 // Phases, one grid barrier apart, all over chunks of 2048 consecutive entries (8 per thread):
 //   A  per chunk of GIDs: valid triangles (all three points valid, Algorithm 1) and segment
 //      roots (a label is the smallest GID of its segment, so a root is labelled with itself)
-//   B  one CTA turns the chunk counts into exclusive offsets (and the totals)
+//      (no scan phase: each CTA sums the counts of the chunks before its own when it needs them)
 //   C  T, T_map, the label of each T entry, and the segment index of each root, in GID order
 //   D  HE from the neighbours' T_map (the twin rules of Algorithm 2); sort keys: the segment
 //      index of each T entry (the segment count for an unlabelled one, so it sorts last)
@@ -143,26 +143,27 @@ __global__ void __launch_bounds__(kThreads, 4) mesh_kernel(const __grid_constant
     }
     grid_barrier(a.barrier, a.error);
 
-    // B: exclusive offsets of the chunks, and the totals
-    if (blockIdx.x == 0) {
-        for (int arr = 0; arr < 2; ++arr) {
-            int32_t* x = a.cnt + arr * C;
-            long long carry = 0;
-            for (int base = 0; base < C; base += kThreads) {
-                const int i = base + threadIdx.x;
-                const int v = i < C ? __ldcg(x + i) : 0;
-                int tot;
-                const int e = block_exclusive(v, sh_scan, &tot);
-                if (i < C) x[i] = (int)(carry + e);
-                carry += tot;
-            }
-            if (threadIdx.x == 0) a.counts[arr] = carry;
+    // every CTA sums the chunk counts it needs itself (no separate scan phase): the totals, and
+    // below the counts of the chunks before each of its own
+    long long nT, nS_l;
+    {
+        long long st = 0, sr = 0;
+        for (int i = threadIdx.x; i < C; i += blockDim.x) {
+            st += __ldcg(cT + i);
+            sr += __ldcg(cR + i);
         }
-        if (threadIdx.x == 0) a.counts[2] = 0;
+        int tt, tr;
+        block_exclusive((int)st, sh_scan, &tt);
+        block_exclusive((int)sr, sh_scan, &tr);
+        nT = tt;
+        nS_l = tr;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            a.counts[0] = nT;
+            a.counts[1] = nS_l;
+            a.counts[2] = 0;
+        }
     }
-    grid_barrier(a.barrier, a.error);
-    const long long nT = __ldcg(a.counts);
-    const int nS = (int)__ldcg(a.counts + 1);
+    const int nS = (int)nS_l;
 
     // C: T, T_map, T labels, segment roots (GID order)
     for (int c = blockIdx.x; c < C; c += gridDim.x) {
@@ -175,9 +176,16 @@ __global__ void __launch_bounds__(kThreads, 4) mesh_kernel(const __grid_constant
             nt += f[j].valid;
             nr += f[j].root;
         }
-        int tt, tr;
-        int pt = __ldcg(cT + c) + block_exclusive(nt, sh_scan, &tt);
-        int pr = __ldcg(cR + c) + block_exclusive(nr, sh_scan, &tr);
+        long long bt = 0, br = 0;   // entries of the chunks before c
+        for (int i = threadIdx.x; i < c; i += blockDim.x) {
+            bt += __ldcg(cT + i);
+            br += __ldcg(cR + i);
+        }
+        int tt, tr, ct, cr;
+        block_exclusive((int)bt, sh_scan, &ct);
+        block_exclusive((int)br, sh_scan, &cr);
+        int pt = ct + block_exclusive(nt, sh_scan, &tt);
+        int pr = cr + block_exclusive(nr, sh_scan, &tr);
 #pragma unroll
         for (int j = 0; j < kPer; ++j) {
             const long long g = g0 + j;
@@ -450,6 +458,7 @@ extern "C" int pl3d_extract_mesh(pl3d_ctx* ctx, const float* points, const int32
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return PL3D_ERR_CUDA;
     const void* fn = reinterpret_cast<const void*>(&mesh::mesh_kernel);
+    // one CTA per chunk (at least one per digit of the radix scans), as many as are resident
     const int want = C > mesh::kBins ? C : mesh::kBins;
     const int grid = persistent_grid(fn, 0, dev, Tuning{0, 0, 0}, want);
     if (grid <= 0) return PL3D_ERR_CUDA;
