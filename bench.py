@@ -172,7 +172,19 @@ def fp32_peak_tflops(sm_count: int, mhz: float) -> float:
 # ----------------------------------------------------------------------------- oracle timing
 
 
-def time_oracle(frame, seconds_budget: float, threads: int) -> dict:
+def _cpu_name() -> str:
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part", "hardware")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def time_oracle(frame, seconds_budget: float, threads: int, max_frames: int = 50) -> dict:
+    """The oracle's method path on whole frames (its sensitivity reruns, test instrumentation, off)."""
     import oracle
     oracle.set_threads(threads)
     p = oracle.OracleParams(**frame.params)
@@ -180,9 +192,9 @@ def time_oracle(frame, seconds_budget: float, threads: int) -> dict:
     t_end = time.perf_counter() + seconds_budget
     while True:
         t0 = time.perf_counter()
-        oracle.extract_planes(frame.points, p, frame.dominant_normals)
+        oracle.extract_planes(frame.points, p, frame.dominant_normals, sensitivity=False)
         runs.append(time.perf_counter() - t0)
-        if time.perf_counter() >= t_end or len(runs) >= 50:
+        if time.perf_counter() >= t_end or len(runs) >= max_frames:
             break
     sec = statistics.median(runs)
     return {"seconds_per_frame": sec, "frames": len(runs), "threads": threads,
@@ -414,11 +426,11 @@ def run_reference(args):
     oracle.set_threads(cores)
     p = oracle.OracleParams(**frame.params)
     for _ in range(args.warmup):
-        oracle.extract_planes(frame.points, p, frame.dominant_normals)
+        oracle.extract_planes(frame.points, p, frame.dominant_normals, sensitivity=False)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle.extract_planes(frame.points, p, frame.dominant_normals)
+        oracle.extract_planes(frame.points, p, frame.dominant_normals, sensitivity=False)
         times.append(time.perf_counter() - t0)
     ms = 1e3 * sum(times) / len(times)
     value = frame.n_triangles / (ms / 1e3) / 1e6
@@ -428,7 +440,8 @@ def run_reference(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "H": frame.H, "W": frame.W, "triangles": frame.n_triangles},
         "cpu_baseline": {"value": value, "unit": "Mtri/s", "cores": cores, "kind": "oracle",
-                         "sample": f"whole {frame.H}x{frame.W} frame per step, FP64 C oracle, OpenMP {cores} threads"},
+                         "sample": f"whole {frame.H}x{frame.W} frame per step, FP64 C oracle, OpenMP {cores} threads "
+                                   "(sensitivity reruns off)"},
         "e2e": {"value": value, "unit": "Mtri/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -633,8 +646,14 @@ def run_pl3d(args):
     if world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
         r = time_oracle(frame, args.cpu_seconds, cores)
+        r1 = time_oracle(frame, 2.0, 1, max_frames=3)
+        r4 = time_oracle(frame, 2.0, 4, max_frames=5)
         cpu = {"value": r["mtri_s"], "unit": "Mtri/s", "cores": cores, "kind": "oracle",
-               "sample": f"{r['frames']} whole {H}x{W} frames, median wall time, FP64 C oracle with OpenMP"}
+               "sample": f"{r['frames']} whole {H}x{W} frames, median wall time, FP64 C oracle with OpenMP "
+                         f"on {cores} threads (its sensitivity reruns, test instrumentation, off)",
+               "single_thread": {"value": r1["mtri_s"], "frames": r1["frames"]},
+               "four_threads": {"value": r4["mtri_s"], "frames": r4["frames"]},
+               "cpu": _cpu_name()}
 
     line = {
         "metric": METRIC, "value": value, "unit": "Mtri/s", "n_gpus": world, "steps": args.steps,

@@ -43,9 +43,9 @@ int round4(int n) { return (n + 3) & ~3; }
 BoxGeom lap_box(int halo) { return {kTile + 2 * halo + 1, round4(3 * (kTile + 2 * halo) + 3)}; }
 BoxGeom bil_box(int halo) { return {kTile + 2 * halo + 1, round4(3 * (kTile + 2 * halo + 1) + 3)}; }
 
-size_t lap_smem(int halo) {
+size_t lap_smem(int halo, bool prefetch) {
     const BoxGeom b = lap_box(halo);
-    return 128 + 4 * (size_t)(3 * align_floats(b.rows * b.cols));
+    return 128 + 4 * (size_t)((prefetch ? 4 : 3) * align_floats(b.rows * b.cols));
 }
 
 size_t bil_smem(int halo) {
@@ -151,6 +151,15 @@ static int fused_iters(int iters, int max_fuse, int requested) {
     return fuse < least ? least : fuse;
 }
 
+size_t lap_smem_bytes(int halo, bool prefetch) { return lap_smem(halo, prefetch); }
+
+int lap_box_floats(int halo) {
+    const BoxGeom b = lap_box(halo);
+    return align_floats(b.rows * b.cols);
+}
+
+static bool lap_prefetch_fits(int halo) { return lap_smem(halo, true) <= (size_t)kTwoCtaSmem; }
+
 const float* final_disp(const FrameScratch& sc, const pl3d_params* p, const Tuning& t) {
     const int rl = p->lap_iters > 0 ? p->lap_kernel / 2 : 1;
     const int lf = fused_iters(p->lap_iters, kLapMaxHalo / rl, t.lap_fuse);
@@ -164,7 +173,8 @@ size_t frame_smem_bytes(const pl3d_params* p, const Tuning& t) {
     const int lf = fused_iters(p->lap_iters, kLapMaxHalo / rl, t.lap_fuse);
     const int bf = fused_iters(p->bil_iters, kBilMaxHalo / rb, t.bil_fuse);
     // the first pass of each filter fuses the most iterations, so it has the largest halo
-    const size_t l = lap_smem((p->lap_iters < lf ? p->lap_iters : lf) * rl);
+    const int lh = (p->lap_iters < lf ? p->lap_iters : lf) * rl;
+    const size_t l = lap_smem(lh, lap_prefetch_fits(lh));   // an upper bound: prefetch needs TMA too
     const size_t b = bil_smem((p->bil_iters < bf ? p->bil_iters : bf) * rb);
     return l > b ? l : b;
 }
@@ -176,7 +186,8 @@ int bilateral_passes(const pl3d_params* p, const Tuning& t) {
 }
 
 cudaError_t frame_configure() {
-    const size_t need = lap_smem(kLapMaxHalo) > bil_smem(kBilMaxHalo) ? lap_smem(kLapMaxHalo) : bil_smem(kBilMaxHalo);
+    const size_t need = lap_smem(kLapMaxHalo, true) > bil_smem(kBilMaxHalo) ? lap_smem(kLapMaxHalo, true)
+                                                                           : bil_smem(kBilMaxHalo);
     for (int rl = 1; rl <= 3; ++rl)
         for (int rb = 1; rb <= 3; ++rb)
             for (const void* fn : {kernel_for(rl, rb), batch_kernel_for(rl, rb)}) {
@@ -212,16 +223,20 @@ int frame_build(FrameArgs& a, FramePlan& plan, const FrameScratch& sc, const flo
         ph.halo = ph.iters * rl;
         ph.box = lap_box(ph.halo);
         ph.use_tma = a.n_lap == 0 && tma_ok;
+        ph.prefetch = ph.use_tma && lap_prefetch_fits(ph.halo);
         ph.d_in = a.n_lap == 0 ? nullptr : sc.disp[(a.n_lap - 1) & 1];
         ph.d_out = sc.disp[a.n_lap & 1];
         remaining -= ph.iters;
         ph.export_points = remaining == 0 ? out_points : nullptr;
-        const size_t m = lap_smem(ph.halo);
+        const size_t m = lap_smem(ph.halo, ph.prefetch);
         smem = m > smem ? m : smem;
         ++a.n_lap;
     } while (remaining > 0);
     a.disp = a.lap[a.n_lap - 1].d_out;
-    if (a.lap[0].use_tma && !encode_aos(&a.tm_pts_lap, points, H, W, a.lap[0].box, true)) a.lap[0].use_tma = 0;
+    if (a.lap[0].use_tma && !encode_aos(&a.tm_pts_lap, points, H, W, a.lap[0].box, true)) {
+        a.lap[0].use_tma = 0;
+        a.lap[0].prefetch = 0;
+    }
 
     // Bilateral passes (Eq. 3-6) and the quads' finish (Algorithms 1, 4, 5).
     const int rb = p->bil_iters > 0 ? p->bil_kernel / 2 : 1;

@@ -117,30 +117,49 @@ __device__ __forceinline__ void lap_add(LapAcc& A, const float* V0, const float*
 }
 
 // One Laplacian tile: T x T output points, `ph.iters` fused Jacobi iterations (Eq. 1-2).
+// Top-left element (x0, u0) of a Laplacian tile's box in the AoS array seen as H rows of 3W
+// floats, and the offset of the tile's first point inside its box row.
+struct LapOrigin {
+    int u0, c0, x0, dlt;
+};
+
+__device__ __forceinline__ LapOrigin lap_origin(const FrameArgs& a, const LapPhase& ph, int tile) {
+    const int tiles_x = div_up(a.W, T);
+    const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
+    LapOrigin o;
+    o.u0 = ty * T - ph.halo;
+    o.c0 = tx * T - ph.halo;
+    o.x0 = floor4(3 * o.c0);
+    o.dlt = 3 * o.c0 - o.x0;
+    return o;
+}
+
+// Issues the TMA load of a tile's box of input points into V0 (thread 0; completes on bar).
+__device__ __forceinline__ void lap_issue(const FrameArgs& a, const LapPhase& ph, const CUtensorMap* map, int tile,
+                                          float* V0, uint64_t* bar) {
+    if (threadIdx.x != 0) return;
+    const LapOrigin o = lap_origin(a, ph, tile);
+    fence_proxy_async_all();
+    mbar_arrive_expect_tx(bar, (unsigned)(ph.box.rows * ph.box.cols * 4));
+    tma_load_2d(V0, map, o.x0, o.u0, bar);
+}
+
+// One Laplacian tile: T x T output points, `ph.iters` fused Jacobi iterations (Eq. 1-2). The
+// input box is in V0, either already issued by TMA on `bar` (tma = true: wait for it) or to be
+// loaded here with plain loads. Da, Db: the displacement ping-pong.
 template <int R>
-__device__ void lap_tile(const FrameArgs& a, const LapPhase& ph, const CUtensorMap* map, int tile, float* smem,
-                         uint64_t* bar, unsigned& parity) {
+__device__ void lap_tile(const FrameArgs& a, const LapPhase& ph, int tile, float* V0, float* Da, float* Db, bool tma,
+                         uint64_t* bar, unsigned parity) {
     const int H = a.H, W = a.W;
     const int h = ph.halo;
     const int RH = T + 2 * h, RW = T + 2 * h;
     const BoxGeom& b = ph.box;                 // rows = RH + 1 (one spare row), cols >= 3 RW + delta
-    const int bsz = b.rows * b.cols;
-    float* V0 = smem;
-    float* Da = smem + align_floats(bsz);
-    float* Db = Da + align_floats(bsz);
-    const int tiles_x = div_up(W, T);
-    const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
-    const int u0 = ty * T - h, c0 = tx * T - h;
-    const int x0 = floor4(3 * c0);
-    const int dlt = 3 * c0 - x0;
+    const LapOrigin og = lap_origin(a, ph, tile);
+    const int u0 = og.u0, c0 = og.c0, x0 = og.x0, dlt = og.dlt;
 
-    if (map && threadIdx.x == 0) fence_proxy_async_all();
-    stage_box(V0, a.points, map, b, x0, u0, H, W, NAN, bar, 1, true);
+    if (!tma) stage_box(V0, a.points, nullptr, b, x0, u0, H, W, NAN, bar, 0, false);
     stage_box(Da, ph.d_in, nullptr, b, x0, u0, H, W, 0.f, bar, 0, false);
-    if (map) {
-        mbar_wait_bounded(bar, parity, a.error);
-        parity ^= 1u;
-    }
+    if (tma) mbar_wait_bounded(bar, parity, a.error);   // the caller flips its parity
     __syncthreads();
     // invalid points (non-finite or out of range, including outside the image) become the
     // finite sentinel with zero displacement
@@ -202,15 +221,28 @@ __device__ void lap_tile(const FrameArgs& a, const LapPhase& ph, const CUtensorM
         nxt = tmp;
     }
 
-    // The tile's own points: displacement out (AoS, row-contiguous), optional export.
+    // The tile's own points: displacement out (AoS, row-contiguous), optional export. With
+    // W % 4 == 0 a tile row (96 floats) starts 16-byte aligned both here (dlt + 3h = 0 mod 4, the
+    // box width a multiple of 4) and in the array (3W and 96 tx multiples of 4): float4 stores.
+    if ((W & 3) == 0) {
+        for (int e = threadIdx.x; e < T * (3 * T / 4); e += blockDim.x) {
+            const int r = e / (3 * T / 4), f = 4 * (e - r * (3 * T / 4));
+            const int gu = u0 + h + r, gv3 = 3 * (c0 + h) + f;
+            if (gu >= H || gv3 >= 3 * W) continue;   // then gv3 + 3 < 3W as well
+            const int o = (h + r) * b.cols + dlt + 3 * h + f;
+            *reinterpret_cast<float4*>(ph.d_out + (size_t)gu * 3 * W + gv3) =
+                *reinterpret_cast<const float4*>(cur + o);
+        }
+    }
     for (int e = threadIdx.x; e < T * 3 * T; e += blockDim.x) {
+        if ((W & 3) == 0 && !ph.export_points) break;
         const int r = e / (3 * T), f = e - r * (3 * T);
         const int gu = u0 + h + r, gv3 = 3 * (c0 + h) + f;
         if (gu >= H || gv3 >= 3 * W) continue;
         const int o = (h + r) * b.cols + dlt + 3 * h + f;
         const size_t g = (size_t)gu * 3 * W + gv3;
         const float d = cur[o];
-        ph.d_out[g] = d;
+        if ((W & 3) != 0) ph.d_out[g] = d;
         if (ph.export_points) {
             const int pt = o - (f % 3);
             ph.export_points[g] = V0[pt] != kInvalidCoord ? V0[o] + d : NAN;
@@ -925,25 +957,49 @@ __device__ __forceinline__ void phase_mark(const FrameArgs& a, int slot, uint64_
 template <int RL, int RB>
 __global__ void __launch_bounds__(kThreads, 2) frame_kernel(const __grid_constant__ FrameArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);   // [2]: staging of even and odd tiles
     float* smem = reinterpret_cast<float*>(smem_raw + 128);
-    if (threadIdx.x == 0) mbar_init(bar, 1);
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        mbar_init(bar + 1, 1);
+    }
     __syncthreads();
-    unsigned parity = 0;
+    unsigned par0 = 0, par1 = 0;   // mbarrier parities of the two staging slots
     uint64_t t_prev = 0;
     if (a.phase_ns && blockIdx.x == 0 && threadIdx.x == 0) t_prev = global_ns();
 
     const int tiles_lap = div_up(a.H, kTile) * div_up(a.W, kTile);
     for (int c = 0; c < a.n_lap; ++c) {
-        const CUtensorMap* map = a.lap[c].use_tma ? &a.tm_pts_lap : nullptr;
-        for (int t = blockIdx.x; t < tiles_lap; t += gridDim.x)
-            frame::lap_tile<RL>(a, a.lap[c], map, t, smem, bar, parity);
+        const LapPhase& ph = a.lap[c];
+        const CUtensorMap* map = ph.use_tma ? &a.tm_pts_lap : nullptr;
+        // buffers: [box 0][box 1][D a][D b]; with prefetch the next tile's box loads by TMA into
+        // the other box while this tile computes
+        const int P = align_floats(ph.box.rows * ph.box.cols);
+        const bool pf = ph.prefetch != 0;
+        float* box0 = smem;
+        float* box1 = smem + (pf ? P : 0);
+        float* Da = smem + (pf ? 2 : 1) * P;
+        float* Db = Da + P;
+        bool odd = false;   // this tile's slot
+        if (pf && (int)blockIdx.x < tiles_lap) frame::lap_issue(a, ph, map, blockIdx.x, box0, bar);
+        for (int t = blockIdx.x; t < tiles_lap; t += gridDim.x, odd = !odd) {
+            const int nxt = t + gridDim.x;
+            const bool slot1 = pf && odd;
+            if (pf && nxt < tiles_lap) frame::lap_issue(a, ph, map, nxt, slot1 ? box0 : box1, slot1 ? bar : bar + 1);
+            if (!pf && map) frame::lap_issue(a, ph, map, t, box0, bar);
+            frame::lap_tile<RL>(a, ph, t, slot1 ? box1 : box0, Da, Db, map != nullptr, slot1 ? bar + 1 : bar,
+                                slot1 ? par1 : par0);
+            if (map) {
+                if (slot1) par1 ^= 1u;
+                else par0 ^= 1u;
+            }
+        }
         grid_barrier(a.barrier, a.error);
     }
     frame::phase_mark(a, 0, t_prev);
     const int tiles_bil = div_up(a.H - 1, kTile) * div_up(a.W - 1, kTile);
     for (int c = 0; c < a.n_bil; ++c) {
-        for (int t = blockIdx.x; t < tiles_bil; t += gridDim.x) frame::bil_tile<RB>(a, a.bil[c], t, smem, bar, parity);
+        for (int t = blockIdx.x; t < tiles_bil; t += gridDim.x) frame::bil_tile<RB>(a, a.bil[c], t, smem, bar, par0);
         grid_barrier(a.barrier, a.error);
     }
     frame::phase_mark(a, 1, t_prev);
@@ -985,11 +1041,14 @@ __device__ __forceinline__ int advance_frame(const long long* pre, int f, long l
 template <int RL, int RB>
 __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const __grid_constant__ BatchArgs b) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);   // [2]: staging of even and odd tiles
     float* smem = reinterpret_cast<float*>(smem_raw + 128);
-    if (threadIdx.x == 0) mbar_init(bar, 1);
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        mbar_init(bar + 1, 1);
+    }
     __syncthreads();
-    unsigned parity = 0;
+    unsigned par0 = 0, par1 = 0;   // mbarrier parities of the two staging slots
     const int n = b.hdr->n, n_lap = b.hdr->n_lap, n_bil = b.hdr->n_bil;
     const bool any_filter = b.hdr->any_filter != 0;
     unsigned long long* pns = b.hdr->timing ? b.phase_ns : nullptr;
@@ -1007,12 +1066,44 @@ __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const __grid_constan
     for (int c = 0; c < n_lap; ++c) {
         const int* pre = b.lap_tiles + c * b.stride;
         const int total = __ldg(pre + n);
-        for (int t = blockIdx.x; t < total; t += gridDim.x) {
+        // buffers as in the frame kernel, sized for the largest box of this pass over the frames;
+        // a frame's tiles are prefetched when its pass stages by TMA and allows prefetch
+        const int P = b.hdr->lap_buf[c];
+        const bool pf = b.hdr->lap_prefetch[c] != 0;
+        float* box0 = smem;
+        float* box1 = smem + (pf ? P : 0);
+        float* Da = smem + (pf ? 2 : 1) * P;
+        float* Db = Da + P;
+        // TMA-issues tile t's box into the slot's buffer when its frame stages by TMA
+        auto issue = [&](int t, bool slot1) {
             const int f = frame::find_frame(pre, n, t);
             const FrameArgs& a = b.frames[f];
-            const CUtensorMap* map = a.lap[c].use_tma ? &a.tm_pts_lap : nullptr;
-            if (map && threadIdx.x == 0) tensormap_acquire(map);
-            frame::lap_tile<RL>(a, a.lap[c], map, t - __ldg(pre + f), smem, bar, parity);
+            if (!a.lap[c].use_tma) return false;
+            const CUtensorMap* map = &a.tm_pts_lap;
+            if (threadIdx.x == 0) tensormap_acquire(map);
+            frame::lap_issue(a, a.lap[c], map, t - __ldg(pre + f), slot1 ? box1 : box0, slot1 ? bar + 1 : bar);
+            return true;
+        };
+        bool issued0 = false, issued1 = false, odd = false;
+        if (pf && (int)blockIdx.x < total) issued0 = issue(blockIdx.x, false);
+        for (int t = blockIdx.x; t < total; t += gridDim.x, odd = !odd) {
+            const int nxt = t + gridDim.x;
+            const bool slot1 = pf && odd;
+            if (pf && nxt < total) {
+                const bool r = issue(nxt, !slot1);
+                if (slot1) issued0 = r;
+                else issued1 = r;
+            }
+            if (!pf) issued0 = issue(t, false);
+            const bool tma = slot1 ? issued1 : issued0;
+            const int f = frame::find_frame(pre, n, t);
+            const FrameArgs& a = b.frames[f];
+            frame::lap_tile<RL>(a, a.lap[c], t - __ldg(pre + f), slot1 ? box1 : box0, Da, Db, tma,
+                                slot1 ? bar + 1 : bar, slot1 ? par1 : par0);
+            if (tma) {
+                if (slot1) par1 ^= 1u;
+                else par0 ^= 1u;
+            }
         }
         grid_barrier(b.barrier, b.error);
     }
@@ -1027,7 +1118,7 @@ __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const __grid_constan
                 tensormap_acquire(&a.tm_pts_bil);
                 tensormap_acquire(&a.tm_disp_bil);
             }
-            frame::bil_tile<RB>(a, a.bil[c], t - __ldg(pre + f), smem, bar, parity);
+            frame::bil_tile<RB>(a, a.bil[c], t - __ldg(pre + f), smem, bar, par0);
         }
         grid_barrier(b.barrier, b.error);
     }

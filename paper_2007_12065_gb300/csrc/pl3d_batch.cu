@@ -241,6 +241,21 @@ int run_batch(pl3d_ctx* c, const pl3d_frame* frames, int n, cudaStream_t s) {
         }
         most_tiles = std::max(most_tiles, (long long)std::max(lp[n], bp[n]));
     }
+    // per Laplacian pass: buffers sized for the largest box; prefetch when some frame stages by
+    // TMA and the four buffers still fit two CTAs per SM
+    for (int c = 0; c < n_lap; ++c) {
+        int P = 0;
+        bool tma = false;
+        for (int i = 0; i < n; ++i) {
+            if (c >= fa[i].n_lap) continue;
+            P = std::max(P, lap_box_floats(fa[i].lap[c].halo));
+            tma |= fa[i].lap[c].use_tma != 0;
+        }
+        const bool pf = tma && 128 + 16 * (size_t)P <= (size_t)kTwoCtaSmem;
+        hdr->lap_buf[c] = P;
+        hdr->lap_prefetch[c] = pf ? 1 : 0;
+        smem = std::max(smem, 128 + 4 * (size_t)(pf ? 4 : 3) * P);
+    }
     hdr->n = n;
     hdr->n_lap = n_lap;
     hdr->n_bil = n_bil;

@@ -26,6 +26,9 @@ constexpr int kTile = 32;        // tile edge: 32 x 32 points (Laplacian) or qua
 constexpr int kLapMaxHalo = 8;   // largest halo (fused iterations x radius) of one Laplacian pass
 constexpr int kBilMaxHalo = 6;   // same for the bilateral
 constexpr int kExactCap = 256;   // deferred exact-normal quads a bilateral tile lists (then inline)
+// Shared memory per CTA that still lets two CTAs share an SM (the bilateral pass at halo 3 needs
+// this much); a Laplacian pass prefetches only when its fourth buffer fits within it.
+constexpr int kTwoCtaSmem = 114048;
 
 // Centroid given to a triangle without a normal: its bilateral weight underflows to
 // exactly 0 against any real triangle, so it drops out of every sum without a branch.
@@ -66,6 +69,7 @@ struct LapPhase {
     int iters;                     // Jacobi iterations fused in this pass
     int halo;                      // iters * radius
     int use_tma;                   // points staged by TMA (tm_pts_lap), else plain loads
+    int prefetch;                  // TMA of the next tile's box overlaps this tile (a second box buffer)
     BoxGeom box;                   // rows = 32 + 2 halo + 1 (a spare row), cols >= 3 (32 + 2 halo) + 3
     const float* d_in;             // displacement after the previous pass, or nullptr (zero)
     float* d_out;                  // displacement after this pass
@@ -126,6 +130,8 @@ struct BatchHeader {
     int n_lap, n_bil;              // most Laplacian / bilateral passes of any frame
     int any_filter;                // some frame has tri_min > 0
     int timing;                    // accumulate phase times into BatchArgs::phase_ns
+    int lap_buf[kMaxPasses];       // per Laplacian pass: floats of the largest box over the frames
+    int lap_prefetch[kMaxPasses];  // per Laplacian pass: double-buffered staging
     int pad[11];
 };
 
@@ -178,6 +184,11 @@ const float* final_disp(const FrameScratch& sc, const pl3d_params* p, const Tuni
 // tri_min) into Algorithm 5's seeded segments; synchronises the stream (pl3d_seeded.cu).
 int seeded_labels(const FrameScratch& sc, const float* disp, const float* points, int H, int W, const pl3d_params* p,
                   const float* nd_host, int K, const uint8_t* groups, int32_t* labels, cudaStream_t s);
+
+// Dynamic shared memory of a Laplacian pass with the given halo (prefetch: a second box buffer),
+// and floats of one of its (aligned) buffers.
+size_t lap_smem_bytes(int halo, bool prefetch);
+int lap_box_floats(int halo);
 
 // Dynamic shared memory the persistent kernels need for this frame under tuning t.
 size_t frame_smem_bytes(const pl3d_params* p, const Tuning& t);
