@@ -134,12 +134,14 @@ __device__ __forceinline__ LapOrigin lap_origin(const FrameArgs& a, const LapPha
     return o;
 }
 
-// Issues the TMA load of a tile's box of input points into V0 (thread 0; completes on bar).
+// Issues the TMA load of a tile's box of input points into V0 (thread 0; completes on bar). The
+// input points are never written inside the launch, so only the box's earlier shared-memory use
+// needs ordering -- a global proxy fence would also wait for this thread's own pending stores.
 __device__ __forceinline__ void lap_issue(const FrameArgs& a, const LapPhase& ph, const CUtensorMap* map, int tile,
                                           float* V0, uint64_t* bar) {
     if (threadIdx.x != 0) return;
     const LapOrigin o = lap_origin(a, ph, tile);
-    fence_proxy_async_all();
+    fence_proxy_async_shared();
     mbar_arrive_expect_tx(bar, (unsigned)(ph.box.rows * ph.box.cols * 4));
     tma_load_2d(V0, map, o.x0, o.u0, bar);
 }
@@ -158,18 +160,19 @@ __device__ void lap_tile(const FrameArgs& a, const LapPhase& ph, int tile, float
     const int u0 = og.u0, c0 = og.c0, x0 = og.x0, dlt = og.dlt;
 
     if (!tma) stage_box(V0, a.points, nullptr, b, x0, u0, H, W, NAN, bar, 0, false);
-    stage_box(Da, ph.d_in, nullptr, b, x0, u0, H, W, 0.f, bar, 0, false);
+    if (ph.d_in) stage_box(Da, ph.d_in, nullptr, b, x0, u0, H, W, 0.f, bar, 0, false);
     if (tma) mbar_wait_bounded(bar, parity, a.error);   // the caller flips its parity
     __syncthreads();
     // invalid points (non-finite or out of range, including outside the image) become the
-    // finite sentinel with zero displacement
+    // finite sentinel with zero displacement; the first pass starts from zero displacement
+    // everywhere (the spare row stays unwritten: only discarded strip halves read it)
+    const bool first = ph.d_in == nullptr;
     for (int i = threadIdx.x; i < RH * RW; i += blockDim.x) {
         const int r = i / RW, c = i - r * RW;
         const int o = r * b.cols + dlt + 3 * c;
-        if (!point_valid(V0[o], V0[o + 1], V0[o + 2])) {
-            V0[o] = V0[o + 1] = V0[o + 2] = kInvalidCoord;
-            Da[o] = Da[o + 1] = Da[o + 2] = 0.f;
-        }
+        const bool bad = !point_valid(V0[o], V0[o + 1], V0[o + 2]);
+        if (bad) V0[o] = V0[o + 1] = V0[o + 2] = kInvalidCoord;
+        if (bad || first) Da[o] = Da[o + 1] = Da[o + 2] = 0.f;
     }
     __syncthreads();
 

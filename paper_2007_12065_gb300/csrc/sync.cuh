@@ -30,6 +30,10 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
 
 // Orders earlier generic-proxy accesses (this CTA's shared memory; global memory written by
 // any CTA before a grid barrier) before later async-proxy (TMA) accesses.
+// Orders this CTA's earlier generic-proxy shared-memory accesses (made visible to the issuing
+// thread by a __syncthreads) before its later async-proxy (TMA) writes to shared memory.
+__device__ __forceinline__ void fence_proxy_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
 __device__ __forceinline__ void fence_proxy_async_all() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("fence.proxy.async.global;" ::: "memory");
