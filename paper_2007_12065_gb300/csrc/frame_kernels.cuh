@@ -1077,29 +1077,36 @@ __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const __grid_constan
         float* box1 = smem + (pf ? P : 0);
         float* Da = smem + (pf ? 2 : 1) * P;
         float* Db = Da + P;
-        // TMA-issues tile t's box into the slot's buffer when its frame stages by TMA
-        auto issue = [&](int t, bool slot1) {
-            const int f = frame::find_frame(pre, n, t);
+        // TMA-issues tile t (of frame f) into the slot's buffer when the frame stages by TMA. A
+        // CTA meets the frames in increasing order, so it acquires each frame's tensor map once.
+        int acquired = -1;
+        auto issue = [&](int t, int f, bool slot1) {
             const FrameArgs& a = b.frames[f];
             if (!a.lap[c].use_tma) return false;
             const CUtensorMap* map = &a.tm_pts_lap;
-            if (threadIdx.x == 0) tensormap_acquire(map);
+            if (f != acquired) {
+                if (threadIdx.x == 0) tensormap_acquire(map);
+                acquired = f;
+            }
             frame::lap_issue(a, a.lap[c], map, t - __ldg(pre + f), slot1 ? box1 : box0, slot1 ? bar + 1 : bar);
             return true;
         };
         bool issued0 = false, issued1 = false, odd = false;
-        if (pf && (int)blockIdx.x < total) issued0 = issue(blockIdx.x, false);
+        int f_cur = (int)blockIdx.x < total ? frame::find_frame(pre, n, blockIdx.x) : 0;
+        if (pf && (int)blockIdx.x < total) issued0 = issue(blockIdx.x, f_cur, false);
         for (int t = blockIdx.x; t < total; t += gridDim.x, odd = !odd) {
             const int nxt = t + gridDim.x;
             const bool slot1 = pf && odd;
+            const int f_nxt = nxt < total ? frame::find_frame(pre, n, nxt) : 0;
             if (pf && nxt < total) {
-                const bool r = issue(nxt, !slot1);
+                const bool r = issue(nxt, f_nxt, !slot1);
                 if (slot1) issued0 = r;
                 else issued1 = r;
             }
-            if (!pf) issued0 = issue(t, false);
+            if (!pf) issued0 = issue(t, f_cur, false);
             const bool tma = slot1 ? issued1 : issued0;
-            const int f = frame::find_frame(pre, n, t);
+            const int f = f_cur;
+            f_cur = f_nxt;
             const FrameArgs& a = b.frames[f];
             frame::lap_tile<RL>(a, a.lap[c], t - __ldg(pre + f), slot1 ? box1 : box0, Da, Db, tma,
                                 slot1 ? bar + 1 : bar, slot1 ? par1 : par0);
@@ -1114,12 +1121,16 @@ __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const __grid_constan
     for (int c = 0; c < n_bil; ++c) {
         const int* pre = b.bil_tiles + c * b.stride;
         const int total = __ldg(pre + n);
+        int acquired = -1;   // frames come in increasing order: each frame's maps acquired once
         for (int t = blockIdx.x; t < total; t += gridDim.x) {
             const int f = frame::find_frame(pre, n, t);
             const FrameArgs& a = b.frames[f];
-            if (a.bil[c].use_tma && threadIdx.x == 0) {
-                tensormap_acquire(&a.tm_pts_bil);
-                tensormap_acquire(&a.tm_disp_bil);
+            if (a.bil[c].use_tma && f != acquired) {
+                if (threadIdx.x == 0) {
+                    tensormap_acquire(&a.tm_pts_bil);
+                    tensormap_acquire(&a.tm_disp_bil);
+                }
+                acquired = f;
             }
             frame::bil_tile<RB>(a, a.bil[c], t - __ldg(pre + f), smem, bar, par0);
         }

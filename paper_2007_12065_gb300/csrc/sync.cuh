@@ -40,9 +40,10 @@ __device__ __forceinline__ void fence_proxy_async_all() {
 }
 
 // Makes a tensor map that the host copied into global memory before the launch visible to the
-// tensor-map proxy of this thread (issued before the thread's first TMA through that map).
+// tensor-map proxy of this thread (issued before the thread's first TMA through that map; the
+// map was written by a host-initiated copy, hence system scope).
 __device__ __forceinline__ void tensormap_acquire(const void* map) {
-    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(map) : "memory");
+    asm volatile("fence.proxy.tensormap::generic.acquire.sys [%0], 128;" ::"l"(map) : "memory");
 }
 
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
