@@ -167,9 +167,17 @@ __device__ void lap_tile(const FrameArgs& a, const LapPhase& ph, int tile, float
     // finite sentinel with zero displacement; the first pass starts from zero displacement
     // everywhere (the spare row stays unwritten: only discarded strip halves read it)
     const bool first = ph.d_in == nullptr;
+    // (row, column) of item i = threadIdx.x + k blockDim.x, stepped without a division per item
+    const int step_r = blockDim.x / RW, step_c = blockDim.x - step_r * RW;
+    int r = threadIdx.x / RW, c = threadIdx.x - r * RW;
     for (int i = threadIdx.x; i < RH * RW; i += blockDim.x) {
-        const int r = i / RW, c = i - r * RW;
         const int o = r * b.cols + dlt + 3 * c;
+        r += step_r;
+        c += step_c;
+        if (c >= RW) {
+            c -= RW;
+            ++r;
+        }
         const bool bad = !point_valid(V0[o], V0[o + 1], V0[o + 2]);
         if (bad) V0[o] = V0[o + 1] = V0[o + 2] = kInvalidCoord;
         if (bad || first) Da[o] = Da[o + 1] = Da[o + 2] = 0.f;
@@ -1030,6 +1038,12 @@ __device__ __forceinline__ int find_frame(const int* pre, int n, int t) {
     return lo;
 }
 
+// Tiles of a batch phase go to the CTAs in runs of kRun consecutive tiles, dealt round-robin.
+constexpr int kRun = 4;
+__device__ __forceinline__ int next_tile(int t) {
+    return (t + 1) % kRun != 0 ? t + 1 : (t / kRun + (int)gridDim.x) * kRun;
+}
+
 // Advances f (never backwards) to the frame whose range of pre holds item i.
 __device__ __forceinline__ int advance_frame(const long long* pre, int f, long long i) {
     while (__ldg(pre + f + 1) <= i) ++f;
@@ -1091,13 +1105,19 @@ __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const __grid_constan
             frame::lap_issue(a, a.lap[c], map, t - __ldg(pre + f), slot1 ? box1 : box0, slot1 ? bar + 1 : bar);
             return true;
         };
+        // runs of kRun consecutive tiles dealt round-robin: neighbouring tiles, whose halos
+        // overlap, close together in time, a map acquire per run, and the balance of a
+        // round-robin when frames differ in cost
+        const int t_begin = (int)blockIdx.x * frame::kRun;
         bool issued0 = false, issued1 = false, odd = false;
-        int f_cur = (int)blockIdx.x < total ? frame::find_frame(pre, n, blockIdx.x) : 0;
-        if (pf && (int)blockIdx.x < total) issued0 = issue(blockIdx.x, f_cur, false);
-        for (int t = blockIdx.x; t < total; t += gridDim.x, odd = !odd) {
-            const int nxt = t + gridDim.x;
+        int f_cur = t_begin < total ? frame::find_frame(pre, n, t_begin) : 0;
+        if (pf && t_begin < total) issued0 = issue(t_begin, f_cur, false);
+        for (int t = t_begin; t < total; t = frame::next_tile(t), odd = !odd) {
+            const int nxt = frame::next_tile(t);
             const bool slot1 = pf && odd;
-            const int f_nxt = nxt < total ? frame::find_frame(pre, n, nxt) : 0;
+            int f_nxt = f_cur;   // frames grow along the sequence
+            if (nxt < total)
+                while (__ldg(pre + f_nxt + 1) <= nxt) ++f_nxt;
             if (pf && nxt < total) {
                 const bool r = issue(nxt, f_nxt, !slot1);
                 if (slot1) issued0 = r;
@@ -1122,8 +1142,10 @@ __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const __grid_constan
         const int* pre = b.bil_tiles + c * b.stride;
         const int total = __ldg(pre + n);
         int acquired = -1;   // frames come in increasing order: each frame's maps acquired once
-        for (int t = blockIdx.x; t < total; t += gridDim.x) {
-            const int f = frame::find_frame(pre, n, t);
+        const int t_begin = (int)blockIdx.x * frame::kRun;
+        int f = t_begin < total ? frame::find_frame(pre, n, t_begin) : 0;
+        for (int t = t_begin; t < total; t = frame::next_tile(t)) {
+            while (__ldg(pre + f + 1) <= t) ++f;
             const FrameArgs& a = b.frames[f];
             if (a.bil[c].use_tma && f != acquired) {
                 if (threadIdx.x == 0) {
