@@ -280,6 +280,7 @@ def run_batched(pl3d, torch, dev, frames, reps: int) -> dict:
     pl3d.pl3d_set_tuning(ctx, None)
     ms_loop = timed(per_frame, reps)
     stats = pl3d.pl3d_batch_stats(ctx)
+    smoothing = one_iteration_smoothing(pl3d, torch, ctx, keep, frames, stream)
     pl3d.pl3d_destroy(ctx)
     sizes = {}
     for pts, _ in frames:
@@ -290,7 +291,44 @@ def run_batched(pl3d, torch, dev, frames, reps: int) -> dict:
             "ms_batched_default_tuning": ms_default, "tuning": tun.as_dict(),
             "ms_per_frame_launches": ms_loop, "mtri_s_per_frame_launches": tris / ms_loop / 1e3,
             "speedup_vs_per_frame": ms_loop / ms_batched, "graph_launches": stats["graph_launches"],
+            "one_iteration_smoothing": smoothing,
             "l2": "inputs (about 450 MB) larger than L2; no flush"}
+
+
+def one_iteration_smoothing(pl3d, torch, ctx, keep, frames, stream) -> dict:
+    """The smoothing filters at one iteration per pass over the whole batch (inputs far larger
+    than L2), as an HBM-roofline figure: the Laplacian phase reads the points (12 B/px) and writes
+    the displacement (12 B/px); the bilateral phase reads points and displacement (24 B/px) and
+    writes normals, mask, groups and labels (18 B/tri). Phase times come from the kernel's own
+    %globaltimer stamps; alu_floor_us is the arithmetic of the pass at full FP32 issue (16 FLOP
+    per Laplacian neighbour, 26 per bilateral window triangle, FMA = 2)."""
+    peaks, src = _peaks()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    fp32 = fp32_peak_tflops(sms, float(peaks.get("sm_max_mhz", 2070.0))) * 1e12
+    px = sum(p.shape[0] * p.shape[1] for p, _ in frames)
+    tri = sum(2 * (p.shape[0] - 1) * (p.shape[1] - 1) for p, _ in frames)
+    out = {}
+    for name, lap, bil in (("laplacian", 1, 0), ("bilateral", 0, 1)):
+        b = pl3d.Batch()
+        for (d, o, p, nd), (pts, base) in zip(keep, frames):
+            prm = dict(base.params, lap_iters=lap, bil_iters=bil, min_dot=1.5)
+            b.add(d, pts.shape[0], pts.shape[1], pl3d.make_params(**prm), nd, *o)
+        pl3d.pl3d_extract_planes_batched(ctx, b, stream)
+        torch.cuda.synchronize()
+        pl3d.pl3d_set_timing(ctx, True)
+        pl3d.pl3d_read_timing(ctx, reset=True)
+        for _ in range(3):
+            pl3d.pl3d_extract_planes_batched(ctx, b, stream)
+        t = pl3d.pl3d_read_timing(ctx, reset=True)
+        pl3d.pl3d_set_timing(ctx, False)
+        us = t[name][0] / t[name][1] * 1e3
+        nbytes = 24.0 * px if name == "laplacian" else 24.0 * px + 18.0 * tri
+        flop = 16.0 * 8 * px if name == "laplacian" else 26.0 * 18 * tri
+        gbs = nbytes / (us * 1e-6) / 1e9
+        out[name] = {"us": us, "algorithmic_bytes": nbytes, "achieved_gbs": gbs,
+                     "hbm_frac": gbs / float(peaks["hbm_gbs"]), "hbm_floor_us": nbytes / float(peaks["hbm_gbs"]) / 1e3,
+                     "alu_floor_us": flop / fp32 * 1e6, "peak_source": f"{src} hbm_gbs"}
+    return out
 
 
 def run_served(pl3d, torch, sensor_frames, rate: float, seconds: float, max_inflight: int, max_batch: int,
