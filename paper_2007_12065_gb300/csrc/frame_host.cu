@@ -5,6 +5,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "pl3d_internal.cuh"
@@ -40,13 +41,10 @@ const void* batch_kernel_for(int rl, int rb) {
 
 int round4(int n) { return (n + 3) & ~3; }
 
-BoxGeom lap_box(int halo) { return {kTile + 2 * halo + 1, round4(3 * (kTile + 2 * halo) + 3)}; }
+// Laplacian box: the tile, its halo and 3 spare rows for the 4-point strips that run past it.
+BoxGeom lap_box(int halo, int tile_h) { return {tile_h + 2 * halo + 3, round4(3 * (kTile + 2 * halo) + 3)}; }
 BoxGeom bil_box(int halo) { return {kTile + 2 * halo + 1, round4(3 * (kTile + 2 * halo + 1) + 3)}; }
 
-size_t lap_smem(int halo, bool prefetch) {
-    const BoxGeom b = lap_box(halo);
-    return 128 + 4 * (size_t)((prefetch ? 4 : 3) * align_floats(b.rows * b.cols));
-}
 
 size_t bil_smem(int halo) {
     const BoxGeom b = bil_box(halo);
@@ -151,14 +149,23 @@ static int fused_iters(int iters, int max_fuse, int requested) {
     return fuse < least ? least : fuse;
 }
 
-size_t lap_smem_bytes(int halo, bool prefetch) { return lap_smem(halo, prefetch); }
-
-int lap_box_floats(int halo) {
-    const BoxGeom b = lap_box(halo);
+int lap_box_floats(int halo, int tile_h) {
+    const BoxGeom b = lap_box(halo, tile_h);
     return align_floats(b.rows * b.cols);
 }
 
-static bool lap_prefetch_fits(int halo) { return lap_smem(halo, true) <= (size_t)kTwoCtaSmem; }
+size_t lap_smem_for(int box_floats, int stages, int dbufs) {
+    return 128 + 4 * (size_t)(stages + dbufs) * box_floats;
+}
+
+int lap_stages_for(int box_floats, int dbufs) {
+    int ns = kLapMaxStages;
+    while (ns > 1 && lap_smem_for(box_floats, ns, dbufs) > (size_t)kTwoCtaSmem) --ns;
+    return ns;
+}
+
+// A single-iteration first pass reads no displacement: taller tiles, one displacement buffer.
+static bool lap_thin(int iters, bool first) { return first && iters == 1; }
 
 const float* final_disp(const FrameScratch& sc, const pl3d_params* p, const Tuning& t) {
     const int rl = p->lap_iters > 0 ? p->lap_kernel / 2 : 1;
@@ -173,8 +180,12 @@ size_t frame_smem_bytes(const pl3d_params* p, const Tuning& t) {
     const int lf = fused_iters(p->lap_iters, kLapMaxHalo / rl, t.lap_fuse);
     const int bf = fused_iters(p->bil_iters, kBilMaxHalo / rb, t.bil_fuse);
     // the first pass of each filter fuses the most iterations, so it has the largest halo
-    const int lh = (p->lap_iters < lf ? p->lap_iters : lf) * rl;
-    const size_t l = lap_smem(lh, lap_prefetch_fits(lh));   // an upper bound: prefetch needs TMA too
+    const int li = p->lap_iters < lf ? p->lap_iters : lf;
+    const int lh = li * rl;
+    const bool thin = lap_thin(li, true);
+    const int ld = thin ? 1 : 2;
+    const int lb = lap_box_floats(lh, thin ? kLapThinTileH : kTile);
+    const size_t l = lap_smem_for(lb, lap_stages_for(lb, ld), ld);   // an upper bound: several stages need TMA
     const size_t b = bil_smem((p->bil_iters < bf ? p->bil_iters : bf) * rb);
     return l > b ? l : b;
 }
@@ -186,8 +197,9 @@ int bilateral_passes(const pl3d_params* p, const Tuning& t) {
 }
 
 cudaError_t frame_configure() {
-    const size_t need = lap_smem(kLapMaxHalo, true) > bil_smem(kBilMaxHalo) ? lap_smem(kLapMaxHalo, true)
-                                                                           : bil_smem(kBilMaxHalo);
+    const int lb = lap_box_floats(kLapMaxHalo, kTile), lt = lap_box_floats(1 * 3, kLapThinTileH);
+    const size_t lap_need = std::max(lap_smem_for(lb, lap_stages_for(lb, 2), 2), lap_smem_for(lt, lap_stages_for(lt, 1), 1));
+    const size_t need = lap_need > bil_smem(kBilMaxHalo) ? lap_need : bil_smem(kBilMaxHalo);
     for (int rl = 1; rl <= 3; ++rl)
         for (int rb = 1; rb <= 3; ++rb)
             for (const void* fn : {kernel_for(rl, rb), batch_kernel_for(rl, rb)}) {
@@ -221,21 +233,25 @@ int frame_build(FrameArgs& a, FramePlan& plan, const FrameScratch& sc, const flo
         LapPhase& ph = a.lap[a.n_lap];
         ph.iters = remaining < lfuse ? remaining : lfuse;
         ph.halo = ph.iters * rl;
-        ph.box = lap_box(ph.halo);
+        const bool thin = lap_thin(ph.iters, a.n_lap == 0);
+        ph.tile_h = thin ? kLapThinTileH : kTile;
+        ph.tiles = div_up(H, ph.tile_h) * div_up(W, kTile);
+        ph.dbufs = thin ? 1 : 2;
+        ph.box = lap_box(ph.halo, ph.tile_h);
         ph.use_tma = a.n_lap == 0 && tma_ok;
-        ph.prefetch = ph.use_tma && lap_prefetch_fits(ph.halo);
+        ph.stages = ph.use_tma ? lap_stages_for(lap_box_floats(ph.halo, ph.tile_h), ph.dbufs) : 1;
         ph.d_in = a.n_lap == 0 ? nullptr : sc.disp[(a.n_lap - 1) & 1];
         ph.d_out = sc.disp[a.n_lap & 1];
         remaining -= ph.iters;
         ph.export_points = remaining == 0 ? out_points : nullptr;
-        const size_t m = lap_smem(ph.halo, ph.prefetch);
+        const size_t m = lap_smem_for(lap_box_floats(ph.halo, ph.tile_h), ph.stages, ph.dbufs);
         smem = m > smem ? m : smem;
         ++a.n_lap;
     } while (remaining > 0);
     a.disp = a.lap[a.n_lap - 1].d_out;
     if (a.lap[0].use_tma && !encode_aos(&a.tm_pts_lap, points, H, W, a.lap[0].box, true)) {
         a.lap[0].use_tma = 0;
-        a.lap[0].prefetch = 0;
+        a.lap[0].stages = 1;
     }
 
     // Bilateral passes (Eq. 3-6) and the quads' finish (Algorithms 1, 4, 5).
@@ -296,7 +312,8 @@ int frame_build(FrameArgs& a, FramePlan& plan, const FrameScratch& sc, const flo
     plan.rl = rl;
     plan.rb = rb;
     plan.smem = smem;
-    plan.tiles_lap = div_up(H, kTile) * div_up(W, kTile);
+    plan.tiles_lap = 0;   // the most tiles of any Laplacian pass
+    for (int c = 0; c < a.n_lap; ++c) plan.tiles_lap = std::max(plan.tiles_lap, a.lap[c].tiles);
     plan.tiles_bil = div_up(H - 1, kTile) * div_up(W - 1, kTile);
     const int Hq = H - 1, Wq = W - 1;
     plan.merge_items = (long long)(div_up(Hq, kTile) - 1) * Wq + (long long)(div_up(Wq, kTile) - 1) * Hq;

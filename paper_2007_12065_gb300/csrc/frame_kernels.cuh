@@ -87,51 +87,119 @@ __device__ __forceinline__ void stage_box(float* dst, const float* src, const CU
 
 // ------------------------------------------------------------------------------ Laplacian
 
+// A Jacobi iteration updates strips of kLapStrip vertically adjacent points per thread: the
+// strip shares the loads of its (kLapStrip + 2R) x (2R + 1) window, and two strip points closer
+// than the radius share one weight (w_ij = w_ji, opposite differences).
+constexpr int kLapStrip = 4;
+
+// A point as an iteration sees it: input position (invalid -> kInvalidCoord) and displacement.
+struct LapPt {
+    float x, y, z, dx, dy, dz;
+};
+
+// WITH_D = false: the displacement is zero everywhere (the first iteration of the first pass),
+// so it is neither loaded nor summed -- the same values as adding zeros.
+template <bool WITH_D>
+__device__ __forceinline__ LapPt lap_load(const float* V0, const float* D, int o) {
+    LapPt p;
+    p.x = V0[o];
+    p.y = V0[o + 1];
+    p.z = V0[o + 2];
+    if (WITH_D) {
+        p.dx = D[o];
+        p.dy = D[o + 1];
+        p.dz = D[o + 2];
+    } else {
+        p.dx = p.dy = p.dz = 0.f;
+    }
+    return p;
+}
+
 struct LapAcc {
-    float x, y, z, dx, dy, dz;   // centre: v0 and displacement
+    LapPt c;                     // centre
     float sx, sy, sz, ws;        // weighted sums
 };
 
-__device__ __forceinline__ void lap_begin(LapAcc& A, const float* V0, const float* D, int o) {
-    A.x = V0[o];
-    A.y = V0[o + 1];
-    A.z = V0[o + 2];
-    A.dx = D[o];
-    A.dy = D[o + 1];
-    A.dz = D[o + 2];
-    A.sx = A.sy = A.sz = A.ws = 0.f;
+// Difference q - p of two smoothed points, input and displacement parts subtracted separately.
+template <bool WITH_D>
+__device__ __forceinline__ void lap_diff(const LapPt& p, const LapPt& q, float& ex, float& ey, float& ez) {
+    if (WITH_D) {
+        ex = (q.x - p.x) + (q.dx - p.dx);
+        ey = (q.y - p.y) + (q.dy - p.dy);
+        ez = (q.z - p.z) + (q.dz - p.dz);
+    } else {
+        ex = q.x - p.x;
+        ey = q.y - p.y;
+        ez = q.z - p.z;
+    }
 }
 
-// One neighbour (Eq. 2): w = 1 / |v_j - v|; a neighbour at distance 0 is skipped. An invalid
-// neighbour holds kInvalidCoord: the squared distance overflows to +inf, rsqrt(+inf) = 0.
-__device__ __forceinline__ void lap_add(LapAcc& A, const float* V0, const float* D, int o) {
-    const float ex = (V0[o] - A.x) + (D[o] - A.dx);
-    const float ey = (V0[o + 1] - A.y) + (D[o + 1] - A.dy);
-    const float ez = (V0[o + 2] - A.z) + (D[o + 2] - A.dz);
+// Eq. 2: w = 1 / |v_j - v|; a neighbour at distance 0 is skipped. An invalid point holds
+// kInvalidCoord: the squared distance overflows to +inf and rsqrt(+inf) = 0.
+__device__ __forceinline__ float lap_weight(float ex, float ey, float ez) {
     const float d2 = ex * ex + ey * ey + ez * ez;
-    const float w = d2 > 0.f ? rsqrt_approx(d2) : 0.f;
+    return d2 > 0.f ? rsqrt_approx(d2) : 0.f;
+}
+
+template <bool WITH_D>
+__device__ __forceinline__ void lap_add(LapAcc& A, const LapPt& q) {
+    float ex, ey, ez;
+    lap_diff<WITH_D>(A.c, q, ex, ey, ez);
+    const float w = lap_weight(ex, ey, ez);
     A.sx = fmaf(w, ex, A.sx);
     A.sy = fmaf(w, ey, A.sy);
     A.sz = fmaf(w, ez, A.sz);
     A.ws += w;
 }
 
-// One Laplacian tile: T x T output points, `ph.iters` fused Jacobi iterations (Eq. 1-2).
 // Top-left element (x0, u0) of a Laplacian tile's box in the AoS array seen as H rows of 3W
-// floats, and the offset of the tile's first point inside its box row.
+// floats, and the offset of the tile's first point inside its box row. Tiles are th points high
+// (th = 32, or 64 for a single-iteration first pass) and T = 32 points wide.
 struct LapOrigin {
     int u0, c0, x0, dlt;
 };
 
-__device__ __forceinline__ LapOrigin lap_origin(const FrameArgs& a, const LapPhase& ph, int tile) {
-    const int tiles_x = div_up(a.W, T);
+__device__ __forceinline__ LapOrigin lap_origin(int W, int halo, int th, int tile) {
+    const int tiles_x = div_up(W, T);
     const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
     LapOrigin o;
-    o.u0 = ty * T - ph.halo;
-    o.c0 = tx * T - ph.halo;
+    o.u0 = ty * th - halo;
+    o.c0 = tx * T - halo;
     o.x0 = floor4(3 * o.c0);
     o.dlt = 3 * o.c0 - o.x0;
     return o;
+}
+
+// What a Laplacian tile needs, read from the frame's arguments once per tile: the batch kernel
+// keeps them in global memory, where every barrier would make the compiler load them again.
+struct LapJob {
+    const float* points;
+    const float* d_in;             // previous pass's displacement, or nullptr (first pass)
+    float* d_out;
+    float* export_points;
+    int* error;
+    int H, W, iters, halo, th;
+    BoxGeom box;
+    float lambda;
+    LapOrigin og;
+};
+
+__device__ __forceinline__ LapJob lap_job(const FrameArgs& a, const LapPhase& ph, int tile) {
+    LapJob j;
+    j.points = a.points;
+    j.d_in = ph.d_in;
+    j.d_out = ph.d_out;
+    j.export_points = ph.export_points;
+    j.error = a.error;
+    j.H = a.H;
+    j.W = a.W;
+    j.iters = ph.iters;
+    j.halo = ph.halo;
+    j.th = ph.tile_h;
+    j.box = ph.box;
+    j.lambda = a.lambda;
+    j.og = lap_origin(j.W, j.halo, j.th, tile);
+    return j;
 }
 
 // Issues the TMA load of a tile's box of input points into V0 (thread 0; completes on bar). The
@@ -140,33 +208,116 @@ __device__ __forceinline__ LapOrigin lap_origin(const FrameArgs& a, const LapPha
 __device__ __forceinline__ void lap_issue(const FrameArgs& a, const LapPhase& ph, const CUtensorMap* map, int tile,
                                           float* V0, uint64_t* bar) {
     if (threadIdx.x != 0) return;
-    const LapOrigin o = lap_origin(a, ph, tile);
+    const LapOrigin o = lap_origin(a.W, ph.halo, ph.tile_h, tile);
     fence_proxy_async_shared();
     mbar_arrive_expect_tx(bar, (unsigned)(ph.box.rows * ph.box.cols * 4));
     tma_load_2d(V0, map, o.x0, o.u0, bar);
 }
+// One Jacobi iteration (Eq. 1-2) over the region [lo, RH - lo) x [lo, RW - lo) of the staged
+// tile: from `cur` (displacements; unused when WITH_D = false) into `nxt`. A strip that runs
+// past the region's last row computes its extra points from the box's spare rows and discards
+// them; each kept point's window lies inside the region the previous iteration wrote.
+template <int R, bool WITH_D>
+__device__ __forceinline__ void lap_iteration(int H, int W, float lambda, int cols, const LapOrigin& og, int RH, int RW,
+                                              int lo, const float* V0, const float* cur, float* nxt) {
+    constexpr int S = kLapStrip;
+    const int cw = RW - 2 * lo;
+    const int strips = (RH - 2 * lo + S - 1) / S;
+    // (strip, column) of item i = threadIdx.x + k blockDim.x, stepped without a division per item
+    const int step_s = (int)blockDim.x / cw, step_c = (int)blockDim.x - step_s * cw;
+    int sr = (int)threadIdx.x / cw, cc = (int)threadIdx.x - sr * cw;
+    for (; sr < strips; sr += step_s, cc += step_c) {
+        if (cc >= cw) {
+            cc -= cw;
+            ++sr;
+            if (sr >= strips) break;
+        }
+        const int r = lo + S * sr, c = lo + cc;
+        const int rows = min(S, RH - lo - r);
+        const int o0 = r * cols + og.dlt + 3 * c;
+        LapAcc A[S];
+#pragma unroll
+        for (int k = 0; k < S; ++k) {
+            A[k].c = lap_load<WITH_D>(V0, cur, o0 + k * cols);
+            A[k].sx = A[k].sy = A[k].sz = A[k].ws = 0.f;
+        }
+        // Each point takes its window in row-major order whatever its place in the strip, so a
+        // point's sum does not depend on how the strips fall (fused or split passes give the
+        // same bits). Strip points m < k within the radius share one weight: computed when the
+        // traversal reaches row m (where k needs it), kept for row k (where m needs it).
+        float pex[S][S], pey[S][S], pez[S][S], pw[S][S];
+#pragma unroll
+        for (int dr = -R; dr < S + R; ++dr) {
+#pragma unroll
+            for (int dc = -R; dc <= R; ++dc) {
+                if (dc == 0 && dr >= 0 && dr < S) {
+                    const int m = dr;   // a strip point
+#pragma unroll
+                    for (int k = 0; k < S; ++k) {
+                        if (k > m && k <= m + R) {
+                            lap_diff<WITH_D>(A[m].c, A[k].c, pex[m][k], pey[m][k], pez[m][k]);
+                            const float w = lap_weight(pex[m][k], pey[m][k], pez[m][k]);
+                            pw[m][k] = w;
+                            A[k].sx = fmaf(-w, pex[m][k], A[k].sx);
+                            A[k].sy = fmaf(-w, pey[m][k], A[k].sy);
+                            A[k].sz = fmaf(-w, pez[m][k], A[k].sz);
+                            A[k].ws += w;
+                        }
+                        if (k < m && k >= m - R) {
+                            const float w = pw[k][m];
+                            A[k].sx = fmaf(w, pex[k][m], A[k].sx);
+                            A[k].sy = fmaf(w, pey[k][m], A[k].sy);
+                            A[k].sz = fmaf(w, pez[k][m], A[k].sz);
+                            A[k].ws += w;
+                        }
+                    }
+                    continue;
+                }
+                const LapPt q = lap_load<WITH_D>(V0, cur, o0 + dr * cols + 3 * dc);
+#pragma unroll
+                for (int k = 0; k < S; ++k)
+                    if (dr - k >= -R && dr - k <= R) lap_add<WITH_D>(A[k], q);
+            }
+        }
+        // Eq. 1 on the displacement; the pinned border ring, invalid points and points without
+        // a usable neighbour keep their displacement
+        const int gu = og.u0 + r, gv = og.c0 + c;
+        const bool colpin = gv < R || gv >= W - R;
+#pragma unroll
+        for (int k = 0; k < S; ++k) {
+            if (k >= rows) break;
+            const bool keep = colpin || gu + k < R || gu + k >= H - R || A[k].c.x == kInvalidCoord || !(A[k].ws > 0.f);
+            const float s = keep ? 0.f : __fdividef(lambda, A[k].ws);
+            const int o = o0 + k * cols;
+            nxt[o] = fmaf(s, A[k].sx, A[k].c.dx);
+            nxt[o + 1] = fmaf(s, A[k].sy, A[k].c.dy);
+            nxt[o + 2] = fmaf(s, A[k].sz, A[k].c.dz);
+        }
+    }
+}
 
-// One Laplacian tile: T x T output points, `ph.iters` fused Jacobi iterations (Eq. 1-2). The
-// input box is in V0, either already issued by TMA on `bar` (tma = true: wait for it) or to be
-// loaded here with plain loads. Da, Db: the displacement ping-pong.
+// One Laplacian tile: th x T output points, `iters` fused Jacobi iterations (Eq. 1-2). The input
+// box is in V0, either already issued by TMA on `bar` (tma = true: wait for it) or to be loaded
+// here with plain loads. Da, Db: the displacement ping-pong (a single-iteration first pass reads
+// no displacement and writes only Db; then Da may alias Db). The box has kLapStrip - 1 spare rows
+// below the tile's halo for the strips that run past the region.
 template <int R>
-__device__ void lap_tile(const FrameArgs& a, const LapPhase& ph, int tile, float* V0, float* Da, float* Db, bool tma,
-                         uint64_t* bar, unsigned parity) {
-    const int H = a.H, W = a.W;
-    const int h = ph.halo;
-    const int RH = T + 2 * h, RW = T + 2 * h;
-    const BoxGeom& b = ph.box;                 // rows = RH + 1 (one spare row), cols >= 3 RW + delta
-    const LapOrigin og = lap_origin(a, ph, tile);
-    const int u0 = og.u0, c0 = og.c0, x0 = og.x0, dlt = og.dlt;
+__device__ void lap_tile(const LapJob& j, float* V0, float* Da, float* Db, bool tma, uint64_t* bar, unsigned parity) {
+    const int H = j.H, W = j.W, h = j.halo, th = j.th;
+    const int RH = th + 2 * h, RW = T + 2 * h;
+    const BoxGeom b = j.box;                   // rows = RH + kLapStrip - 1, cols >= 3 RW + delta
+    const LapOrigin og = j.og;
+    const int u0 = og.u0, c0 = og.c0, dlt = og.dlt;
+    const bool first = j.d_in == nullptr;
 
-    if (!tma) stage_box(V0, a.points, nullptr, b, x0, u0, H, W, NAN, bar, 0, false);
-    if (ph.d_in) stage_box(Da, ph.d_in, nullptr, b, x0, u0, H, W, 0.f, bar, 0, false);
-    if (tma) mbar_wait_bounded(bar, parity, a.error);   // the caller flips its parity
+    if (!tma) stage_box(V0, j.points, nullptr, b, og.x0, u0, H, W, NAN, bar, 0, false);
+    if (!first) stage_box(Da, j.d_in, nullptr, b, og.x0, u0, H, W, 0.f, bar, 0, false);
+    if (tma) mbar_wait_bounded(bar, parity, j.error);   // the caller flips its parity
     __syncthreads();
     // invalid points (non-finite or out of range, including outside the image) become the
-    // finite sentinel with zero displacement; the first pass starts from zero displacement
-    // everywhere (the spare row stays unwritten: only discarded strip halves read it)
-    const bool first = ph.d_in == nullptr;
+    // finite sentinel with zero displacement; the first pass reads no displacement, and without
+    // iterations (lap_iters = 0) its output is the zero displacement itself
+    const bool zero_all = first && j.iters == 0;
     // (row, column) of item i = threadIdx.x + k blockDim.x, stepped without a division per item
     const int step_r = blockDim.x / RW, step_c = blockDim.x - step_r * RW;
     int r = threadIdx.x / RW, c = threadIdx.x - r * RW;
@@ -180,52 +331,15 @@ __device__ void lap_tile(const FrameArgs& a, const LapPhase& ph, int tile, float
         }
         const bool bad = !point_valid(V0[o], V0[o + 1], V0[o + 2]);
         if (bad) V0[o] = V0[o + 1] = V0[o + 2] = kInvalidCoord;
-        if (bad || first) Da[o] = Da[o + 1] = Da[o + 2] = 0.f;
+        if ((bad && !first) || zero_all) Da[o] = Da[o + 1] = Da[o + 2] = 0.f;
     }
     __syncthreads();
 
     float* cur = Da;
     float* nxt = Db;
-    for (int t = 1; t <= ph.iters; ++t) {
-        const int lo = t * R;
-        const int ch = RH - 2 * lo, cw = RW - 2 * lo;
-        const int strips = (ch + 1) >> 1;
-        for (int i = threadIdx.x; i < strips * cw; i += blockDim.x) {
-            const int sr = i / cw;
-            const int r = lo + 2 * sr, c = lo + (i - sr * cw);
-            const bool two = r + 1 < RH - lo;
-            const int oA = r * b.cols + dlt + 3 * c, oB = oA + b.cols;
-            const int gu = u0 + r, gv = c0 + c;
-            const bool colpin = gv < R || gv >= W - R;
-            // both points are always computed; a missing second point reads the spare row and
-            // is not stored, so the unrolled window has no data-dependent branch
-            LapAcc A, B;
-            lap_begin(A, V0, cur, oA);
-            lap_begin(B, V0, cur, oB);
-#pragma unroll
-            for (int dr = -R; dr <= R + 1; ++dr) {
-#pragma unroll
-                for (int dc = -R; dc <= R; ++dc) {
-                    const int o = oA + dr * b.cols + 3 * dc;
-                    if (dr <= R && !(dr == 0 && dc == 0)) lap_add(A, V0, cur, o);
-                    if (dr >= 1 - R && !(dr == 1 && dc == 0)) lap_add(B, V0, cur, o);
-                }
-            }
-            // Eq. 1 on the displacement; the pinned border ring, invalid points and points
-            // without a usable neighbour keep their displacement
-            const bool keepA = colpin || gu < R || gu >= H - R || A.x == kInvalidCoord || !(A.ws > 0.f);
-            const float sA = keepA ? 0.f : __fdividef(a.lambda, A.ws);
-            nxt[oA] = fmaf(sA, A.sx, A.dx);
-            nxt[oA + 1] = fmaf(sA, A.sy, A.dy);
-            nxt[oA + 2] = fmaf(sA, A.sz, A.dz);
-            if (two) {
-                const bool keepB = colpin || gu + 1 < R || gu + 1 >= H - R || B.x == kInvalidCoord || !(B.ws > 0.f);
-                const float sB = keepB ? 0.f : __fdividef(a.lambda, B.ws);
-                nxt[oB] = fmaf(sB, B.sx, B.dx);
-                nxt[oB + 1] = fmaf(sB, B.sy, B.dy);
-                nxt[oB + 2] = fmaf(sB, B.sz, B.dz);
-            }
-        }
+    for (int t = 1; t <= j.iters; ++t) {
+        if (first && t == 1) lap_iteration<R, false>(H, W, j.lambda, b.cols, og, RH, RW, R, V0, cur, nxt);
+        else lap_iteration<R, true>(H, W, j.lambda, b.cols, og, RH, RW, t * R, V0, cur, nxt);
         __syncthreads();
         float* tmp = cur;
         cur = nxt;
@@ -236,32 +350,38 @@ __device__ void lap_tile(const FrameArgs& a, const LapPhase& ph, int tile, float
     // W % 4 == 0 a tile row (96 floats) starts 16-byte aligned both here (dlt + 3h = 0 mod 4, the
     // box width a multiple of 4) and in the array (3W and 96 tx multiples of 4): float4 stores.
     if ((W & 3) == 0) {
-        for (int e = threadIdx.x; e < T * (3 * T / 4); e += blockDim.x) {
-            const int r = e / (3 * T / 4), f = 4 * (e - r * (3 * T / 4));
-            const int gu = u0 + h + r, gv3 = 3 * (c0 + h) + f;
-            if (gu >= H || gv3 >= 3 * W) continue;   // then gv3 + 3 < 3W as well
-            const int o = (h + r) * b.cols + dlt + 3 * h + f;
-            *reinterpret_cast<float4*>(ph.d_out + (size_t)gu * 3 * W + gv3) =
-                *reinterpret_cast<const float4*>(cur + o);
+        // thread -> tile rows threadIdx.x / 8 + 32 k and float4 columns (threadIdx.x % 8) + 8 m
+        static_assert(kThreads == 8 * T && (3 * T / 4) % 8 == 0, "one tile row per 8 threads");
+        const int q = threadIdx.x & 7;
+        const int gv3 = 3 * (c0 + h) + 4 * q;
+        for (int rr = threadIdx.x >> 3; rr < th; rr += kThreads / 8) {
+            const int gu = u0 + h + rr;
+            if (gu >= H) break;
+            const float* src = cur + (h + rr) * b.cols + dlt + 3 * h + 4 * q;
+            float* dst = j.d_out + (size_t)gu * 3 * W + gv3;
+#pragma unroll
+            for (int m = 0; m < 3 * T / 32; ++m)
+                if (gv3 + 32 * m < 3 * W)   // then gv3 + 32 m + 3 < 3W as well
+                    *reinterpret_cast<float4*>(dst + 32 * m) = *reinterpret_cast<const float4*>(src + 32 * m);
         }
     }
-    for (int e = threadIdx.x; e < T * 3 * T; e += blockDim.x) {
-        if ((W & 3) == 0 && !ph.export_points) break;
-        const int r = e / (3 * T), f = e - r * (3 * T);
-        const int gu = u0 + h + r, gv3 = 3 * (c0 + h) + f;
-        if (gu >= H || gv3 >= 3 * W) continue;
-        const int o = (h + r) * b.cols + dlt + 3 * h + f;
-        const size_t g = (size_t)gu * 3 * W + gv3;
-        const float d = cur[o];
-        if ((W & 3) != 0) ph.d_out[g] = d;
-        if (ph.export_points) {
-            const int pt = o - (f % 3);
-            ph.export_points[g] = V0[pt] != kInvalidCoord ? V0[o] + d : NAN;
+    if ((W & 3) != 0 || j.export_points) {
+        for (int e = threadIdx.x; e < th * 3 * T; e += blockDim.x) {
+            const int r = e / (3 * T), f = e - r * (3 * T);
+            const int gu = u0 + h + r, gv3 = 3 * (c0 + h) + f;
+            if (gu >= H || gv3 >= 3 * W) continue;
+            const int o = (h + r) * b.cols + dlt + 3 * h + f;
+            const size_t g = (size_t)gu * 3 * W + gv3;
+            const float d = cur[o];
+            if ((W & 3) != 0) j.d_out[g] = d;
+            if (j.export_points) {
+                const int pt = o - (f % 3);
+                j.export_points[g] = V0[pt] != kInvalidCoord ? V0[o] + d : NAN;
+            }
         }
     }
     __syncthreads();
 }
-
 // ------------------------------------------------------------------------------ bilateral
 
 // A staged point: input position and displacement.
@@ -968,47 +1088,47 @@ __device__ __forceinline__ void phase_mark(const FrameArgs& a, int slot, uint64_
 template <int RL, int RB>
 __global__ void __launch_bounds__(kThreads, 2) frame_kernel(const __grid_constant__ FrameArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);   // [2]: staging of even and odd tiles
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);   // [kLapMaxStages]: one per staging slot
     float* smem = reinterpret_cast<float*>(smem_raw + 128);
-    if (threadIdx.x == 0) {
-        mbar_init(bar, 1);
-        mbar_init(bar + 1, 1);
-    }
+    if (threadIdx.x == 0)
+        for (int i = 0; i < kLapMaxStages; ++i) mbar_init(bar + i, 1);
     __syncthreads();
-    unsigned par0 = 0, par1 = 0;   // mbarrier parities of the two staging slots
+    unsigned par = 0;   // mbarrier parities of the staging slots, one bit each
     uint64_t t_prev = 0;
     if (a.phase_ns && blockIdx.x == 0 && threadIdx.x == 0) t_prev = global_ns();
 
-    const int tiles_lap = div_up(a.H, kTile) * div_up(a.W, kTile);
     for (int c = 0; c < a.n_lap; ++c) {
         const LapPhase& ph = a.lap[c];
+        const int tiles_lap = ph.tiles;
         const CUtensorMap* map = ph.use_tma ? &a.tm_pts_lap : nullptr;
-        // buffers: [box 0][box 1][D a][D b]; with prefetch the next tile's box loads by TMA into
-        // the other box while this tile computes
+        // buffers: [box 0 .. box ns-1][D a][D b] (one D buffer for a single-iteration first
+        // pass); the box of this CTA's tile k is slot k mod ns, and the TMA loads of its next
+        // ns - 1 tiles are in flight while tile k computes
         const int P = align_floats(ph.box.rows * ph.box.cols);
-        const bool pf = ph.prefetch != 0;
-        float* box0 = smem;
-        float* box1 = smem + (pf ? P : 0);
-        float* Da = smem + (pf ? 2 : 1) * P;
-        float* Db = Da + P;
-        bool odd = false;   // this tile's slot
-        if (pf && (int)blockIdx.x < tiles_lap) frame::lap_issue(a, ph, map, blockIdx.x, box0, bar);
-        for (int t = blockIdx.x; t < tiles_lap; t += gridDim.x, odd = !odd) {
-            const int nxt = t + gridDim.x;
-            const bool slot1 = pf && odd;
-            if (pf && nxt < tiles_lap) frame::lap_issue(a, ph, map, nxt, slot1 ? box0 : box1, slot1 ? bar : bar + 1);
-            if (!pf && map) frame::lap_issue(a, ph, map, t, box0, bar);
-            frame::lap_tile<RL>(a, ph, t, slot1 ? box1 : box0, Da, Db, map != nullptr, slot1 ? bar + 1 : bar,
-                                slot1 ? par1 : par0);
+        const int ns = map ? ph.stages : 1;
+        float* Da = smem + ns * P;
+        float* Db = Da + (ph.dbufs - 1) * P;
+        for (int k = 0; k + 1 < ns; ++k) {
+            const int t = (int)blockIdx.x + k * (int)gridDim.x;
+            if (t < tiles_lap) frame::lap_issue(a, ph, map, t, smem + k * P, bar + k);
+        }
+        int s = 0;
+        for (int t = blockIdx.x; t < tiles_lap; t += gridDim.x) {
             if (map) {
-                if (slot1) par1 ^= 1u;
-                else par0 ^= 1u;
+                const int ahead = t + (ns - 1) * (int)gridDim.x;
+                const int sa = s == 0 ? ns - 1 : s - 1;   // the slot of the previous tile, now free
+                if (ahead < tiles_lap) frame::lap_issue(a, ph, map, ahead, smem + sa * P, bar + sa);
             }
+            const frame::LapJob j = frame::lap_job(a, ph, t);
+            frame::lap_tile<RL>(j, smem + s * P, Da, Db, map != nullptr, bar + s, (par >> s) & 1u);
+            if (map) par ^= 1u << s;
+            s = s + 1 == ns ? 0 : s + 1;
         }
         grid_barrier(a.barrier, a.error);
     }
     frame::phase_mark(a, 0, t_prev);
     const int tiles_bil = div_up(a.H - 1, kTile) * div_up(a.W - 1, kTile);
+    unsigned par0 = par & 1u;   // the bilateral stages through slot 0
     for (int c = 0; c < a.n_bil; ++c) {
         for (int t = blockIdx.x; t < tiles_bil; t += gridDim.x) frame::bil_tile<RB>(a, a.bil[c], t, smem, bar, par0);
         grid_barrier(a.barrier, a.error);
@@ -1058,14 +1178,12 @@ __device__ __forceinline__ int advance_frame(const long long* pre, int f, long l
 template <int RL, int RB>
 __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const __grid_constant__ BatchArgs b) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);   // [2]: staging of even and odd tiles
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);   // [kLapMaxStages]: one per staging slot
     float* smem = reinterpret_cast<float*>(smem_raw + 128);
-    if (threadIdx.x == 0) {
-        mbar_init(bar, 1);
-        mbar_init(bar + 1, 1);
-    }
+    if (threadIdx.x == 0)
+        for (int i = 0; i < kLapMaxStages; ++i) mbar_init(bar + i, 1);
     __syncthreads();
-    unsigned par0 = 0, par1 = 0;   // mbarrier parities of the two staging slots
+    unsigned par = 0;   // mbarrier parities of the staging slots, one bit each
     const int n = b.hdr->n, n_lap = b.hdr->n_lap, n_bil = b.hdr->n_bil;
     const bool any_filter = b.hdr->any_filter != 0;
     unsigned long long* pns = b.hdr->timing ? b.phase_ns : nullptr;
@@ -1083,61 +1201,64 @@ __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const __grid_constan
     for (int c = 0; c < n_lap; ++c) {
         const int* pre = b.lap_tiles + c * b.stride;
         const int total = __ldg(pre + n);
-        // buffers as in the frame kernel, sized for the largest box of this pass over the frames;
-        // a frame's tiles are prefetched when its pass stages by TMA and allows prefetch
+        // buffers as in the frame kernel, sized for the largest box of this pass over the frames:
+        // [box 0 .. box ns-1][D a][D b]; the box of this CTA's k-th tile is slot k mod ns
         const int P = b.hdr->lap_buf[c];
-        const bool pf = b.hdr->lap_prefetch[c] != 0;
-        float* box0 = smem;
-        float* box1 = smem + (pf ? P : 0);
-        float* Da = smem + (pf ? 2 : 1) * P;
-        float* Db = Da + P;
-        // TMA-issues tile t (of frame f) into the slot's buffer when the frame stages by TMA. A
-        // CTA meets the frames in increasing order, so it acquires each frame's tensor map once.
+        const int ns = b.hdr->lap_stages[c];
+        float* Da = smem + ns * P;
+        float* Db = Da + (b.hdr->lap_dbufs[c] - 1) * P;
+        // TMA-issues tile t (of frame f) into a slot when the frame stages by TMA. A CTA meets the
+        // frames in increasing order, so it acquires each frame's tensor map once.
         int acquired = -1;
-        auto issue = [&](int t, int f, bool slot1) {
+        auto issue = [&](int t, int f, int slot) {
             const FrameArgs& a = b.frames[f];
-            if (!a.lap[c].use_tma) return false;
+            if (!a.lap[c].use_tma) return;
             const CUtensorMap* map = &a.tm_pts_lap;
             if (f != acquired) {
                 if (threadIdx.x == 0) tensormap_acquire(map);
                 acquired = f;
             }
-            frame::lap_issue(a, a.lap[c], map, t - __ldg(pre + f), slot1 ? box1 : box0, slot1 ? bar + 1 : bar);
-            return true;
+            frame::lap_issue(a, a.lap[c], map, t - __ldg(pre + f), smem + slot * P, bar + slot);
         };
         // runs of kRun consecutive tiles dealt round-robin: neighbouring tiles, whose halos
         // overlap, close together in time, a map acquire per run, and the balance of a
         // round-robin when frames differ in cost
         const int t_begin = (int)blockIdx.x * frame::kRun;
-        bool issued0 = false, issued1 = false, odd = false;
         int f_cur = t_begin < total ? frame::find_frame(pre, n, t_begin) : 0;
-        if (pf && t_begin < total) issued0 = issue(t_begin, f_cur, false);
-        for (int t = t_begin; t < total; t = frame::next_tile(t), odd = !odd) {
-            const int nxt = frame::next_tile(t);
-            const bool slot1 = pf && odd;
-            int f_nxt = f_cur;   // frames grow along the sequence
-            if (nxt < total)
-                while (__ldg(pre + f_nxt + 1) <= nxt) ++f_nxt;
-            if (pf && nxt < total) {
-                const bool r = issue(nxt, f_nxt, !slot1);
-                if (slot1) issued0 = r;
-                else issued1 = r;
+        // the furthest tile of the sequence issued so far, and its frame (frames grow along it)
+        int t_ahd = t_begin, f_ahd = f_cur;
+        if (ns > 1 && t_begin < total) {
+            issue(t_begin, f_cur, 0);
+            for (int k = 1; k + 1 < ns; ++k) {
+                t_ahd = frame::next_tile(t_ahd);
+                if (t_ahd >= total) break;
+                while (__ldg(pre + f_ahd + 1) <= t_ahd) ++f_ahd;
+                issue(t_ahd, f_ahd, k);
             }
-            if (!pf) issued0 = issue(t, f_cur, false);
-            const bool tma = slot1 ? issued1 : issued0;
-            const int f = f_cur;
-            f_cur = f_nxt;
-            const FrameArgs& a = b.frames[f];
-            frame::lap_tile<RL>(a, a.lap[c], t - __ldg(pre + f), slot1 ? box1 : box0, Da, Db, tma,
-                                slot1 ? bar + 1 : bar, slot1 ? par1 : par0);
-            if (tma) {
-                if (slot1) par1 ^= 1u;
-                else par0 ^= 1u;
+        }
+        int s = 0;
+        for (int t = t_begin; t < total; t = frame::next_tile(t)) {
+            while (__ldg(pre + f_cur + 1) <= t) ++f_cur;
+            if (ns > 1) {
+                t_ahd = frame::next_tile(t_ahd);
+                if (t_ahd < total) {
+                    while (__ldg(pre + f_ahd + 1) <= t_ahd) ++f_ahd;
+                    issue(t_ahd, f_ahd, s == 0 ? ns - 1 : s - 1);   // the previous tile's slot, now free
+                }
+            } else {
+                issue(t, f_cur, 0);
             }
+            const FrameArgs& a = b.frames[f_cur];
+            const bool tma = a.lap[c].use_tma != 0;
+            const frame::LapJob j = frame::lap_job(a, a.lap[c], t - __ldg(pre + f_cur));
+            frame::lap_tile<RL>(j, smem + s * P, Da, Db, tma, bar + s, (par >> s) & 1u);
+            if (tma) par ^= 1u << s;
+            s = s + 1 == ns ? 0 : s + 1;
         }
         grid_barrier(b.barrier, b.error);
     }
     mark(0);
+    unsigned par0 = par & 1u;   // the bilateral stages through slot 0
     for (int c = 0; c < n_bil; ++c) {
         const int* pre = b.bil_tiles + c * b.stride;
         const int total = __ldg(pre + n);

@@ -198,7 +198,7 @@ int run_batch(pl3d_ctx* c, const pl3d_frame* frames, int n, cudaStream_t s) {
     unsigned char* cursor = c->bslab;
     size_t smem = 0;
     int n_lap = 0, n_bil = 0, any_filter = 0;
-    std::vector<int> lap_tiles(n), bil_tiles(n), lap_passes(n), bil_passes(n);
+    std::vector<int> bil_tiles(n), lap_passes(n), bil_passes(n);
     for (int i = 0; i < n; ++i) {
         const pl3d_frame& f = frames[i];
         const FrameNeeds need = frame_needs(f, t);
@@ -221,7 +221,6 @@ int run_batch(pl3d_ctx* c, const pl3d_frame* frames, int n, cudaStream_t s) {
                          f.out_normals, f.out_labels, f.out_points, f.out_groups, t);
         if (rc != PL3D_OK) return rc;
         smem = std::max(smem, plan.smem);
-        lap_tiles[i] = plan.tiles_lap;
         bil_tiles[i] = plan.tiles_bil;
         lap_passes[i] = fa[i].n_lap;
         bil_passes[i] = fa[i].n_bil;
@@ -236,25 +235,27 @@ int run_batch(pl3d_ctx* c, const pl3d_frame* frames, int n, cudaStream_t s) {
         int* lp = lap_pre + pass * stride;
         int* bp = bil_pre + pass * stride;
         for (int i = 0; i < n; ++i) {
-            lp[i + 1] = lp[i] + (pass < lap_passes[i] ? lap_tiles[i] : 0);
+            lp[i + 1] = lp[i] + (pass < lap_passes[i] ? fa[i].lap[pass].tiles : 0);
             bp[i + 1] = bp[i] + (pass < bil_passes[i] ? bil_tiles[i] : 0);
         }
         most_tiles = std::max(most_tiles, (long long)std::max(lp[n], bp[n]));
     }
-    // per Laplacian pass: buffers sized for the largest box; prefetch when some frame stages by
-    // TMA and the four buffers still fit two CTAs per SM
+    // per Laplacian pass: buffers sized for the largest box; staged ahead when some frame stages
+    // by TMA, as many boxes as still fit two CTAs per SM
     for (int c = 0; c < n_lap; ++c) {
-        int P = 0;
+        int P = 0, dbufs = 1;
         bool tma = false;
         for (int i = 0; i < n; ++i) {
             if (c >= fa[i].n_lap) continue;
-            P = std::max(P, lap_box_floats(fa[i].lap[c].halo));
+            P = std::max(P, lap_box_floats(fa[i].lap[c].halo, fa[i].lap[c].tile_h));
+            dbufs = std::max(dbufs, fa[i].lap[c].dbufs);
             tma |= fa[i].lap[c].use_tma != 0;
         }
-        const bool pf = tma && 128 + 16 * (size_t)P <= (size_t)kTwoCtaSmem;
+        const int ns = tma ? lap_stages_for(P, dbufs) : 1;
         hdr->lap_buf[c] = P;
-        hdr->lap_prefetch[c] = pf ? 1 : 0;
-        smem = std::max(smem, 128 + 4 * (size_t)(pf ? 4 : 3) * P);
+        hdr->lap_stages[c] = ns;
+        hdr->lap_dbufs[c] = dbufs;
+        smem = std::max(smem, lap_smem_for(P, ns, dbufs));
     }
     hdr->n = n;
     hdr->n_lap = n_lap;

@@ -27,8 +27,10 @@ constexpr int kLapMaxHalo = 8;   // largest halo (fused iterations x radius) of 
 constexpr int kBilMaxHalo = 6;   // same for the bilateral
 constexpr int kExactCap = 256;   // deferred exact-normal quads a bilateral tile lists (then inline)
 // Shared memory per CTA that still lets two CTAs share an SM (the bilateral pass at halo 3 needs
-// this much); a Laplacian pass prefetches only when its fourth buffer fits within it.
+// this much); a Laplacian pass stages as many boxes ahead as fit within it.
 constexpr int kTwoCtaSmem = 114048;
+constexpr int kLapMaxStages = 3;   // box buffers of a Laplacian pass: this tile's and up to 2 ahead
+constexpr int kLapThinTileH = 64;  // tile height of a single-iteration first Laplacian pass
 
 // Centroid given to a triangle without a normal: its bilateral weight underflows to
 // exactly 0 against any real triangle, so it drops out of every sum without a branch.
@@ -69,8 +71,13 @@ struct LapPhase {
     int iters;                     // Jacobi iterations fused in this pass
     int halo;                      // iters * radius
     int use_tma;                   // points staged by TMA (tm_pts_lap), else plain loads
-    int prefetch;                  // TMA of the next tile's box overlaps this tile (a second box buffer)
-    BoxGeom box;                   // rows = 32 + 2 halo + 1 (a spare row), cols >= 3 (32 + 2 halo) + 3
+    int stages;                    // box buffers (1..kLapMaxStages): TMA loads of the next stages - 1
+                                   // tiles overlap this tile
+    int tile_h;                    // tile height in points: 32, or kLapThinTileH for a single-iteration
+                                   // first pass (tiles are 32 points wide)
+    int tiles;                     // tiles of this pass
+    int dbufs;                     // displacement buffers: 1 for a single-iteration first pass, else 2
+    BoxGeom box;                   // rows = tile_h + 2 halo + 3 (spare rows), cols >= 3 (32 + 2 halo) + 3
     const float* d_in;             // displacement after the previous pass, or nullptr (zero)
     float* d_out;                  // displacement after this pass
     float* export_points;          // optional AoS export of v0 + d (last pass only)
@@ -131,8 +138,9 @@ struct BatchHeader {
     int any_filter;                // some frame has tri_min > 0
     int timing;                    // accumulate phase times into BatchArgs::phase_ns
     int lap_buf[kMaxPasses];       // per Laplacian pass: floats of the largest box over the frames
-    int lap_prefetch[kMaxPasses];  // per Laplacian pass: double-buffered staging
-    int pad[11];
+    int lap_stages[kMaxPasses];    // per Laplacian pass: box buffers (1..kLapMaxStages)
+    int lap_dbufs[kMaxPasses];     // per Laplacian pass: displacement buffers (1 or 2)
+    int pad[3];
 };
 
 struct BatchArgs {
@@ -185,10 +193,12 @@ const float* final_disp(const FrameScratch& sc, const pl3d_params* p, const Tuni
 int seeded_labels(const FrameScratch& sc, const float* disp, const float* points, int H, int W, const pl3d_params* p,
                   const float* nd_host, int K, const uint8_t* groups, int32_t* labels, cudaStream_t s);
 
-// Dynamic shared memory of a Laplacian pass with the given halo (prefetch: a second box buffer),
-// and floats of one of its (aligned) buffers.
-size_t lap_smem_bytes(int halo, bool prefetch);
-int lap_box_floats(int halo);
+// Floats of one (aligned) buffer of a Laplacian pass with the given halo and tile height, the
+// shared memory of such a pass with `stages` box buffers and `dbufs` displacement buffers, and the
+// most stages (1..kLapMaxStages) that keep two CTAs per SM for buffers of `box_floats`.
+int lap_box_floats(int halo, int tile_h);
+size_t lap_smem_for(int box_floats, int stages, int dbufs);
+int lap_stages_for(int box_floats, int dbufs);
 
 // Dynamic shared memory the persistent kernels need for this frame under tuning t.
 size_t frame_smem_bytes(const pl3d_params* p, const Tuning& t);

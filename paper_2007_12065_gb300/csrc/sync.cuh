@@ -50,12 +50,15 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned by
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
 
+// Tests for the completion of phase `parity`; a thread whose phase is still pending is suspended
+// in hardware for up to kSuspendNs (or until the phase completes) instead of spinning.
+constexpr uint32_t kSuspendNs = 100000;
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
     uint32_t ok;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendNs)
         : "memory");
     return ok != 0;
 }
@@ -73,11 +76,12 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
 // Waits for the phase `parity` of `bar` to complete. On timeout it records the error, waits
 // once more (bounded) for the copies still in flight, and returns false.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, int* err) {
+    if (mbar_try_wait(bar, parity)) return true;
     for (int attempt = 0; attempt < 2; ++attempt) {
         const uint64_t t0 = global_ns();
-        for (uint32_t i = 0; i < (1u << 28); ++i) {
+        for (uint32_t i = 0; i < (1u << 24); ++i) {
             if (mbar_try_wait(bar, parity)) return attempt == 0;
-            if ((i & 63u) == 63u && global_ns() - t0 > kWaitLimitNs) break;
+            if (global_ns() - t0 > kWaitLimitNs) break;
         }
         if (attempt == 0) atomicOr(err, kErrTmaTimeout);
     }
