@@ -422,6 +422,14 @@ __device__ __forceinline__ float rounded_part(float diff, float p, float q) {
     return ad < fminf(fabsf(p), fabsf(q)) ? 0.f : ad;
 }
 
+// Edge b - a in FP32 (the same value as fast_edge(a, b).e).
+__device__ __forceinline__ V3 edge_of(const SP& a, const SP& b) {
+    return {(b.x - a.x) + (b.dx - a.dx), (b.y - a.y) + (b.dy - a.dy), (b.z - a.z) + (b.dz - a.dz)};
+}
+
+// Dominant normals up to this count are held in registers by the group assignment.
+constexpr int kRegGroups = 4;
+
 __device__ __forceinline__ FastEdge fast_edge(const SP& a, const SP& b) {
     const float ax = b.x - a.x, ay = b.y - a.y, az = b.z - a.z;
     const float dx = b.dx - a.dx, dy = b.dy - a.dy, dz = b.dz - a.dz;
@@ -569,12 +577,19 @@ __device__ __forceinline__ void quad_neighbour(QuadAcc& A, f2 a2, f2 cx, f2 cy, 
 template <int R>
 __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float* smem, uint64_t* bar,
                          unsigned& parity) {
+    // the frame's arguments, read once (the batch kernel keeps them in global memory, where every
+    // barrier and every global store would make the compiler load them again)
     const int H = a.H, W = a.W, Hq = H - 1, Wq = W - 1;
-    const int h = ph.halo;
+    const int h = ph.halo, iters = ph.iters;
+    const bool first = ph.first != 0, last = ph.last != 0;
+    const float* const carry_in = ph.carry_in;
+    float* const carry_out = ph.carry_out;
+    int* const error = a.error;
+    const float max_edge2 = a.max_edge2;
     const int RQH = T + 2 * h, RQW = T + 2 * h;          // staged quads
     const int nq = RQH * RQW;
     const int nqs = nq + RQW;                            // one spare row of quads
-    const BoxGeom& b = ph.box;                           // rows = RQH + 1 points, cols >= 3 (RQW + 1) + delta
+    const BoxGeom b = ph.box;                            // rows = RQH + 1 points, cols >= 3 (RQW + 1) + delta
     const int bsz = align_floats(b.rows * b.cols);
     float* Cq = smem;                                    // [nqs][6] scaled centroids
     float* Na = Cq + align_floats(6 * nqs);              // [nqs][6] normals
@@ -599,18 +614,29 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
     stage_box(V0, a.points, mp, b, x0, qu0, H, W, NAN, bar, 2, true);
     stage_box(Dp, a.disp, md, b, x0, qu0, H, W, 0.f, bar, 0, true);
     if (mp) {
-        mbar_wait_bounded(bar, parity, a.error);
+        mbar_wait_bounded(bar, parity, error);
         parity ^= 1u;
     }
     __syncthreads();
     int* n_exact = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(bar) + 64);   // in the smem header
     if (threadIdx.x == 0) *n_exact = 0;
-    for (int i = threadIdx.x; i < (RQH + 1) * (RQW + 1); i += blockDim.x) {
-        const int r = i / (RQW + 1), c = i - r * (RQW + 1);
-        const int o = r * b.cols + dlt + 3 * c;
-        if (!point_valid(V0[o], V0[o + 1], V0[o + 2])) {
-            V0[o] = V0[o + 1] = V0[o + 2] = NAN;
-            Dp[o] = Dp[o + 1] = Dp[o + 2] = 0.f;
+    {
+        // (row, column) of point i = threadIdx.x + k blockDim.x, stepped without a division
+        const int PW = RQW + 1;
+        const int step_r = blockDim.x / PW, step_c = blockDim.x - step_r * PW;
+        int r = threadIdx.x / PW, c = threadIdx.x - r * PW;
+        for (int i = threadIdx.x; i < (RQH + 1) * PW; i += blockDim.x) {
+            const int o = r * b.cols + dlt + 3 * c;
+            r += step_r;
+            c += step_c;
+            if (c >= PW) {
+                c -= PW;
+                ++r;
+            }
+            if (!point_valid(V0[o], V0[o + 1], V0[o + 2])) {
+                V0[o] = V0[o + 1] = V0[o + 2] = NAN;
+                Dp[o] = Dp[o + 1] = Dp[o + 2] = 0.f;
+            }
         }
     }
     __syncthreads();
@@ -652,14 +678,14 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
         const int o1 = qr * b.cols + dlt + 3 * qc;
         const SP p1 = load_sp(V0, Dp, o1), p2 = load_sp(V0, Dp, o1 + 3);
         const SP p3 = load_sp(V0, Dp, o1 + b.cols + 3), p4 = load_sp(V0, Dp, o1 + b.cols);
-        const bool own = ph.last && qr >= h && qr < h + T && qc >= h && qc < h + T;
+        const bool own = last && qr >= h && qr < h + T && qc >= h && qc < h + T;
         const bool v1 = p1.x == p1.x, v2 = p2.x == p2.x, v3 = p3.x == p3.x, v4 = p4.x == p4.x;
         const bool valid0 = exists && v1 && v2 && v3;                            // Algorithm 1
         const bool valid1 = exists && v1 && v3 && v4;
         V3 nn[2] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-        if (ph.first) {
-            // first = {p3, p2, p1}: (p2 - p3) x (p1 - p3);  second = {p1, p4, p3}: (p4 - p1) x (p3 - p1)
-            const FastEdge er = fast_edge(p3, p2), ed = fast_edge(p3, p1), el = fast_edge(p1, p4);
+        // first = {p3, p2, p1}: (p2 - p3) x (p1 - p3);  second = {p1, p4, p3}: (p4 - p1) x (p3 - p1)
+        const FastEdge er = fast_edge(p3, p2), ed = fast_edge(p3, p1), el = fast_edge(p1, p4);
+        if (first) {
             const FastEdge edn = {{-ed.e.x, -ed.e.y, -ed.e.z}, ed.m, ed.l1};
             V3 cr0 = cross(er.e, ed.e), cr1 = cross(el.e, edn.e);
             const bool exact0 = valid0 && !fast_cross_ok(er, ed, cr0);
@@ -683,22 +709,21 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
             for (int k = 0; k < 2; ++k) {
                 if (!vk[k]) continue;
                 const size_t gid = 2 * ((size_t)gu * Wq + gv) + k;
-                const float nx = __ldcg(ph.carry_in + 3 * gid);   // written by the previous pass
-                if (nx == nx) nn[k] = {nx, __ldcg(ph.carry_in + 3 * gid + 1), __ldcg(ph.carry_in + 3 * gid + 2)};
+                const float nx = __ldcg(carry_in + 3 * gid);   // written by the previous pass
+                if (nx == nx) nn[k] = {nx, __ldcg(carry_in + 3 * gid + 1), __ldcg(carry_in + 3 * gid + 2)};
             }
         }
         const V3 cc0 = scaled_centroid(p3, p2, p1, nn[0]), cc1 = scaled_centroid(p1, p4, p3, nn[1]);
         if (own) {                                                               // Algorithm 4, l_max
             // FP32 edges: ~1e-7 relative error, far inside the 1e-5 m band where FP32 and FP64
             // may disagree
-            const V3 er = fast_edge(p3, p2).e, et = fast_edge(p2, p1).e, ed = fast_edge(p3, p1).e;
-            const V3 el = fast_edge(p1, p4).e, eb = fast_edge(p4, p3).e;
-            const float d2 = dot(ed, ed);
-            const float l0 = fmaxf(d2, fmaxf(dot(er, er), dot(et, et)));
-            const float l1 = fmaxf(d2, fmaxf(dot(el, el), dot(eb, eb)));
+            const V3 et = edge_of(p2, p1), eb = edge_of(p4, p3);
+            const float d2 = dot(ed.e, ed.e);
+            const float l0 = fmaxf(d2, fmaxf(dot(er.e, er.e), dot(et, et)));
+            const float l1 = fmaxf(d2, fmaxf(dot(el.e, el.e), dot(eb, eb)));
             const int t = 2 * ((qr - h) * T + (qc - h));
-            Mk[t] = (valid0 && l0 <= a.max_edge2) ? 1 : 0;
-            Mk[t + 1] = (valid1 && l1 <= a.max_edge2) ? 1 : 0;
+            Mk[t] = (valid0 && l0 <= max_edge2) ? 1 : 0;
+            Mk[t + 1] = (valid1 && l1 <= max_edge2) ? 1 : 0;
         }
         store_quad(Cq, q, cc0, cc1);
         store_quad(Na, q, nn[0], nn[1]);
@@ -737,7 +762,7 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
     float* nxt = Nb;
     const float an = a.a_norm;
     const f2 a2 = bc(an);
-    for (int it = 1; it <= ph.iters; ++it) {
+    for (int it = 1; it <= iters; ++it) {
         const int lo = it * R;
         const int ch = RQH - 2 * lo, cw = RQW - 2 * lo;
         const int strips = (ch + 1) >> 1;
@@ -772,7 +797,7 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
         nxt = tmp;
     }
 
-    if (!ph.last) {
+    if (!last) {
         for (int i = threadIdx.x; i < T * T; i += blockDim.x) {
             const int r = i / T, c = i - r * T;
             const int gu = ty * T + r, gv = tx * T + c;
@@ -783,7 +808,7 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
                 const bool has = has_normal(n[k]);
-                float* o = ph.carry_out + 3 * (gid0 + k);
+                float* o = carry_out + 3 * (gid0 + k);
                 o[0] = has ? n[k].x : NAN;
                 o[1] = has ? n[k].y : NAN;
                 o[2] = has ? n[k].z : NAN;
@@ -798,6 +823,17 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
     int32_t* Lp = reinterpret_cast<int32_t*>(nxt);
     int32_t* RunOf = Lp + 2 * T * T;
     int32_t* RootOf = RunOf + 2 * T * T;
+    uint8_t* const out_mask = a.out_mask;
+    float* const out_normals = a.out_normals;
+    uint8_t* const out_groups = a.groups;
+    int32_t* const sizes = a.sizes;
+    const float min_dot = a.min_dot;
+    // up to kRegGroups dominant normals held in registers; more are read from the arguments
+    const int K = a.nd.K;
+    const float* const ndv = a.nd.v;
+    float nd[3 * kRegGroups];
+#pragma unroll
+    for (int j = 0; j < 3 * kRegGroups; ++j) nd[j] = j < 3 * K ? ndv[j] : 0.f;
     for (int i = threadIdx.x; i < T * T; i += blockDim.x) {
         const int r = i / T, c = i - r * T;
         const int gu = ty * T + r, gv = tx * T + c;
@@ -813,24 +849,36 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
             int g = PL3D_NO_GROUP;
             if (exists && kept && has) {                                         // Algorithm 4, ang_min
                 float best = -1.0f;
-                for (int j = 0; j < a.nd.K; ++j) {
-                    const float s = n[k].x * a.nd.v[3 * j] + n[k].y * a.nd.v[3 * j + 1] + n[k].z * a.nd.v[3 * j + 2];
-                    if (s > best) {
-                        best = s;
-                        g = j;
+                if (K <= kRegGroups) {
+#pragma unroll
+                    for (int j = 0; j < kRegGroups; ++j) {
+                        if (j >= K) break;
+                        const float s = n[k].x * nd[3 * j] + n[k].y * nd[3 * j + 1] + n[k].z * nd[3 * j + 2];
+                        if (s > best) {
+                            best = s;
+                            g = j;
+                        }
+                    }
+                } else {
+                    for (int j = 0; j < K; ++j) {
+                        const float s = n[k].x * ndv[3 * j] + n[k].y * ndv[3 * j + 1] + n[k].z * ndv[3 * j + 2];
+                        if (s > best) {
+                            best = s;
+                            g = j;
+                        }
                     }
                 }
-                if (best < a.min_dot) g = PL3D_NO_GROUP;
+                if (best < min_dot) g = PL3D_NO_GROUP;
             }
             if (exists) {
                 const size_t gid = gid0 + k;
-                a.out_mask[gid] = kept ? 1 : 0;
-                float* o = a.out_normals + 3 * gid;
+                out_mask[gid] = kept ? 1 : 0;
+                float* o = out_normals + 3 * gid;
                 o[0] = has ? n[k].x : NAN;
                 o[1] = has ? n[k].y : NAN;
                 o[2] = has ? n[k].z : NAN;
-                a.groups[gid] = (uint8_t)g;
-                if (a.sizes) a.sizes[gid] = 0;
+                out_groups[gid] = (uint8_t)g;
+                if (sizes) sizes[gid] = 0;
             }
             Gs[t] = exists ? (uint8_t)g : (uint8_t)PL3D_NO_GROUP;
         }
@@ -841,8 +889,8 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
     const bool offs = a.max_offset_scaled > 0.f;
     const float lim = a.max_offset_scaled;
     auto offset_ok = [&](int g, V3 ci, V3 cj) {
-        const float* nd = a.nd.v + 3 * g;
-        return !offs || fabsf(nd[0] * (ci.x - cj.x) + nd[1] * (ci.y - cj.y) + nd[2] * (ci.z - cj.z)) <= lim;
+        const float* n = ndv + 3 * g;
+        return !offs || fabsf(n[0] * (ci.x - cj.x) + n[1] * (ci.y - cj.y) + n[2] * (ci.z - cj.z)) <= lim;
     };
     constexpr unsigned kFull = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -903,28 +951,13 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
         if (link && !dup) uf_unite(Lp, ra, rb);
     }
     __syncthreads();
-    // (3) Only the run representatives were linked by the unions. Synchronous pointer jumping
-    // over them: every round points each representative at its grandparent (an ancestor), so the
-    // depth halves per round, however deep the concurrent unions left the forest.
-    {
-        bool changed = true;
-        while (__syncthreads_or(changed)) {
-            changed = false;
-            for (int t = threadIdx.x; t < 2 * T * T; t += blockDim.x) {
-                if (RunOf[t] != t) continue;
-                volatile int32_t* vl = Lp;
-                const int p = vl[t], gp = vl[p];
-                if (gp != p) {
-                    vl[t] = gp;
-                    changed = true;
-                }
-            }
-        }
-        for (int t = threadIdx.x; t < 2 * T * T; t += blockDim.x)
-            if (RunOf[t] == t) RootOf[t] = Lp[t];
-    }
+    // (3) Only the run representatives were linked by the unions: each finds its root, halving
+    // the path as it walks (concurrent walks only shorten paths, so they stay valid).
+    for (int t = threadIdx.x; t < 2 * T * T; t += blockDim.x)
+        if (RunOf[t] == t) RootOf[t] = uf_find(Lp, t);
     __syncthreads();
     // (4) Each triangle leaves with the GID of its tile-local root (-1 without a group).
+    int32_t* const labels = a.labels;
     for (int i = threadIdx.x; i < T * T; i += blockDim.x) {
         const int r = i / T, c = i - r * T;
         const int gu = ty * T + r, gv = tx * T + c;
@@ -939,7 +972,7 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
                 const int rq = root >> 1, rr = rq / T, rc = rq - rr * T;
                 lab = (int)(2 * ((size_t)(ty * T + rr) * Wq + (tx * T + rc)) + (root & 1));
             }
-            a.labels[gid0 + k] = lab;
+            labels[gid0 + k] = lab;
         }
     }
     __syncthreads();
