@@ -671,8 +671,17 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
         }
         return c;
     };
+    // (row, column) of quad q = threadIdx.x + k blockDim.x, stepped without a division per quad
+    const int gstep_r = blockDim.x / RQW, gstep_c = blockDim.x - gstep_r * RQW;
+    int g_qr = threadIdx.x / RQW, g_qc = threadIdx.x - g_qr * RQW;
     for (int q = threadIdx.x; q < nq; q += blockDim.x) {
-        const int qr = q / RQW, qc = q - qr * RQW;
+        const int qr = g_qr, qc = g_qc;
+        g_qr += gstep_r;
+        g_qc += gstep_c;
+        if (g_qc >= RQW) {
+            g_qc -= RQW;
+            ++g_qr;
+        }
         const int gu = qu0 + qr, gv = qv0 + qc;
         const bool exists = gu >= 0 && gu < Hq && gv >= 0 && gv < Wq;
         const int o1 = qr * b.cols + dlt + 3 * qc;
