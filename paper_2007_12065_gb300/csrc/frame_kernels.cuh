@@ -318,20 +318,40 @@ __device__ void lap_tile(const LapJob& j, float* V0, float* Da, float* Db, bool 
     // finite sentinel with zero displacement; the first pass reads no displacement, and without
     // iterations (lap_iters = 0) its output is the zero displacement itself
     const bool zero_all = first && j.iters == 0;
-    // (row, column) of item i = threadIdx.x + k blockDim.x, stepped without a division per item
-    const int step_r = blockDim.x / RW, step_c = blockDim.x - step_r * RW;
-    int r = threadIdx.x / RW, c = threadIdx.x - r * RW;
-    for (int i = threadIdx.x; i < RH * RW; i += blockDim.x) {
-        const int o = r * b.cols + dlt + 3 * c;
-        r += step_r;
-        c += step_c;
-        if (c >= RW) {
-            c -= RW;
-            ++r;
+    // (row, column) of item i = threadIdx.x + k blockDim.x, stepped without a division per item;
+    // four items per round, their loads issued together
+    {
+        constexpr int U = 4;
+        const int step_r = blockDim.x / RW, step_c = blockDim.x - step_r * RW;
+        int r = threadIdx.x / RW, c = threadIdx.x - r * RW;
+        for (int i0 = threadIdx.x; i0 < RH * RW; i0 += U * blockDim.x) {
+            int o[U];
+            float x[U], y[U], z[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                o[u] = r * b.cols + dlt + 3 * c;
+                r += step_r;
+                c += step_c;
+                if (c >= RW) {
+                    c -= RW;
+                    ++r;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const bool in = i0 + u * (int)blockDim.x < RH * RW;
+                x[u] = in ? V0[o[u]] : 0.f;
+                y[u] = in ? V0[o[u] + 1] : 0.f;
+                z[u] = in ? V0[o[u] + 2] : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (i0 + u * (int)blockDim.x >= RH * RW) break;
+                const bool bad = !point_valid(x[u], y[u], z[u]);
+                if (bad) V0[o[u]] = V0[o[u] + 1] = V0[o[u] + 2] = kInvalidCoord;
+                if ((bad && !first) || zero_all) Da[o[u]] = Da[o[u] + 1] = Da[o[u] + 2] = 0.f;
+            }
         }
-        const bool bad = !point_valid(V0[o], V0[o + 1], V0[o + 2]);
-        if (bad) V0[o] = V0[o + 1] = V0[o + 2] = kInvalidCoord;
-        if ((bad && !first) || zero_all) Da[o] = Da[o + 1] = Da[o + 2] = 0.f;
     }
     __syncthreads();
 
@@ -621,21 +641,39 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
     int* n_exact = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(bar) + 64);   // in the smem header
     if (threadIdx.x == 0) *n_exact = 0;
     {
-        // (row, column) of point i = threadIdx.x + k blockDim.x, stepped without a division
-        const int PW = RQW + 1;
+        // (row, column) of point i = threadIdx.x + k blockDim.x, stepped without a division; four
+        // points per round, their loads issued together
+        constexpr int U = 4;
+        const int PW = RQW + 1, NP = (RQH + 1) * PW;
         const int step_r = blockDim.x / PW, step_c = blockDim.x - step_r * PW;
         int r = threadIdx.x / PW, c = threadIdx.x - r * PW;
-        for (int i = threadIdx.x; i < (RQH + 1) * PW; i += blockDim.x) {
-            const int o = r * b.cols + dlt + 3 * c;
-            r += step_r;
-            c += step_c;
-            if (c >= PW) {
-                c -= PW;
-                ++r;
+        for (int i0 = threadIdx.x; i0 < NP; i0 += U * blockDim.x) {
+            int o[U];
+            float x[U], y[U], z[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                o[u] = r * b.cols + dlt + 3 * c;
+                r += step_r;
+                c += step_c;
+                if (c >= PW) {
+                    c -= PW;
+                    ++r;
+                }
             }
-            if (!point_valid(V0[o], V0[o + 1], V0[o + 2])) {
-                V0[o] = V0[o + 1] = V0[o + 2] = NAN;
-                Dp[o] = Dp[o + 1] = Dp[o + 2] = 0.f;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const bool in = i0 + u * (int)blockDim.x < NP;
+                x[u] = in ? V0[o[u]] : 0.f;
+                y[u] = in ? V0[o[u] + 1] : 0.f;
+                z[u] = in ? V0[o[u] + 2] : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (i0 + u * (int)blockDim.x >= NP) break;
+                if (!point_valid(x[u], y[u], z[u])) {
+                    V0[o[u]] = V0[o[u] + 1] = V0[o[u] + 2] = NAN;
+                    Dp[o[u]] = Dp[o[u] + 1] = Dp[o[u] + 2] = 0.f;
+                }
             }
         }
     }

@@ -28,7 +28,8 @@ def env():
 
 def _frames():
     """Uneven sizes (ragged tails, single tiles, W % 4 != 0 without TMA), both parameter sets,
-    and per-frame variations of iterations, thresholds, offsets and tri_min."""
+    and per-frame variations of iterations (single-iteration Laplacian passes beside fused ones
+    in the same pass), thresholds, offsets and tri_min."""
     out = []
     shapes = [(120, 160), (64, 1024), (2, 2), (33, 65), (97, 131), (240, 320), (5, 7), (128, 250), (48, 64),
               (31, 31), (61, 1021)]
@@ -49,6 +50,8 @@ def _frames():
             params.update(bil_iters=9, lap_iters=10)      # several passes of each filter
         if i == 8:
             params.update(bil_iters=0, max_edge=0.0)
+        if i in (3, 10):
+            params.update(lap_iters=1)                    # 64-row tiles, one displacement buffer
         out.append((f, params))
     return out
 

@@ -115,6 +115,15 @@ def test_kernel_sizes(env, lk, bk):
     run_pair(env, f.points, prm, f.dominant_normals)
 
 
+@pytest.mark.parametrize("H,W,lk", [(200, 96, 3), (150, 130, 3), (131, 68, 5), (70, 45, 7)])
+def test_single_iteration_laplacian_tiles(env, H, W, lk):
+    """A single-iteration first Laplacian pass runs 64-row tiles with one displacement buffer:
+    several tile rows with a ragged last one, rows staged without TMA (W % 4 != 0), and the
+    larger kernels' halos."""
+    f = synth.depth_camera_scene(H, W, seed=H + W + lk, n_boxes=2, noise_sigma=0.004, nan_frac=0.03)
+    run_pair(env, f.points, dict(f.params, lap_iters=1, lap_kernel=lk), f.dominant_normals)
+
+
 @pytest.mark.parametrize("li,bi", [(0, 0), (0, 3), (4, 0), (1, 1), (8, 6), (9, 7), (20, 13)])
 def test_iteration_counts_including_multi_launch(env, li, bi):
     """Iteration counts above one launch's halo are split into several launches."""
