@@ -88,31 +88,47 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
     return false;
 }
 
+// Acquire load, acquire-release add and release add at GPU scope (PTX memory consistency model).
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned atom_add_acq_rel_gpu(unsigned* p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+__device__ __forceinline__ void red_release_gpu_add(unsigned* p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 // Grid-wide barrier for a co-resident (cooperatively launched) grid. bar[0] counts arrivals,
-// bar[1] is the generation; the last CTA to arrive resets the count and advances the
-// generation. Global writes made before the barrier are visible to every CTA after it.
+// bar[1] is the generation. Thread 0 of each CTA arrives with an acquire-release add, which
+// publishes the writes its CTA made before the __syncthreads (cumulativity) and, for the last
+// arriver, acquires everyone else's; the last arriver resets the count and opens the barrier
+// with a release add on the generation, which the others wait for with acquire loads. Global
+// writes made before the barrier are visible to every thread of the grid after it.
 __device__ __forceinline__ void grid_barrier(unsigned* bar, int* err) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned* vgen = bar + 1;
         const unsigned nblocks = gridDim.x * gridDim.y * gridDim.z;
-        const unsigned g = *vgen;
-        __threadfence();
-        if (atomicAdd(bar, 1u) + 1u == nblocks) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
+        const unsigned g = ld_acquire_gpu(bar + 1);   // cannot advance before this CTA arrives
+        if (atom_add_acq_rel_gpu(bar, 1u) + 1u == nblocks) {
+            *reinterpret_cast<volatile unsigned*>(bar) = 0u;   // ordered before the release below
+            red_release_gpu_add(bar + 1, 1u);
         } else {
             const uint64_t t0 = global_ns();
-            for (uint32_t i = 1; *vgen == g; ++i) {
+            for (uint32_t i = 1; ld_acquire_gpu(bar + 1) == g; ++i) {
                 if ((i & 63u) == 0u && global_ns() - t0 > kWaitLimitNs) {
                     atomicOr(err, kErrBarrierTimeout);
                     break;
                 }
-                __nanosleep(32);
+                __nanosleep(16);
             }
         }
-        __threadfence();
     }
     __syncthreads();
 }
