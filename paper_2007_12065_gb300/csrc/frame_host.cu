@@ -215,7 +215,8 @@ cudaError_t frame_configure() {
 
 int frame_build(FrameArgs& a, FramePlan& plan, const FrameScratch& sc, const float* points, int H, int W,
                 const pl3d_params* p, const float* nd_host, int K, uint8_t* out_mask, float* out_normals,
-                int32_t* out_labels, float* out_points, uint8_t* out_groups, const Tuning& t) {
+                int32_t* out_labels, float* out_points, uint8_t* out_groups, const Tuning& t,
+                int32_t* out_labels_copy) {
     memset(&a, 0, sizeof(a));
     a.points = points;
     a.H = H;
@@ -286,6 +287,7 @@ int frame_build(FrameArgs& a, FramePlan& plan, const FrameScratch& sc, const flo
     a.out_normals = out_normals;
     a.groups = out_groups ? out_groups : sc.groups;
     a.labels = out_labels;
+    a.labels_copy = out_labels_copy;
     a.sizes = p->min_triangles > 0 ? sc.sizes : nullptr;
     a.c_scale = c_scale;
     a.a_norm = a_norm;
@@ -335,14 +337,14 @@ int persistent_grid(const void* fn, size_t smem, int dev, const Tuning& t, long 
 
 int frame_launch(const FrameScratch& sc, const float* points, int H, int W, const pl3d_params* p, const float* nd_host,
                  int K, uint8_t* out_mask, float* out_normals, int32_t* out_labels, float* out_points,
-                 uint8_t* out_groups, const Tuning& t, cudaStream_t s) {
+                 uint8_t* out_groups, const Tuning& t, cudaStream_t s, int32_t* out_labels_copy) {
     static_assert(sizeof(FrameArgs) < 32000, "kernel parameters must fit the 32 KB parameter space");
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return PL3D_ERR_CUDA;
     FrameArgs a;
     FramePlan plan;
     int rc = frame_build(a, plan, sc, points, H, W, p, nd_host, K, out_mask, out_normals, out_labels, out_points,
-                         out_groups, t);
+                         out_groups, t, out_labels_copy);
     if (rc != PL3D_OK) return rc;
     const int work = plan.tiles_lap > plan.tiles_bil ? plan.tiles_lap : plan.tiles_bil;
     const int grid = persistent_grid(plan.frame_fn, plan.smem, dev, t, work);

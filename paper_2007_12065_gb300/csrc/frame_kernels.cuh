@@ -1119,6 +1119,8 @@ __device__ __forceinline__ void flatten_phase(const FrameArgs& a) {
     const long long n_iter = (n + stride - 1) / stride;   // uniform: whole warps stay together
     const long long base = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     int32_t* L = a.labels;
+    int32_t* const sizes = a.sizes;
+    int32_t* const copy = sizes ? nullptr : a.labels_copy;   // with tri_min the filter writes it
     for (long long it0 = 0; it0 < n_iter; it0 += U) {
         int lab[U], par[U];
 #pragma unroll
@@ -1136,10 +1138,11 @@ __device__ __forceinline__ void flatten_phase(const FrameArgs& a) {
                 root = root_from(L, lab[u], par[u]);
                 L[i] = root;
             }
-            if (a.sizes) {
+            if (copy && it0 + u < n_iter && i < n) copy[i] = root;
+            if (sizes) {
                 const unsigned peers = __match_any_sync(0xffffffffu, root);
                 const int leader = __ffs(peers) - 1;
-                if (root >= 0 && (int)(threadIdx.x & 31) == leader) atomicAdd(a.sizes + root, __popc(peers));
+                if (root >= 0 && (int)(threadIdx.x & 31) == leader) atomicAdd(sizes + root, __popc(peers));
             }
         }
     }
@@ -1148,10 +1151,16 @@ __device__ __forceinline__ void flatten_phase(const FrameArgs& a) {
 // Algorithm 5 keeps a segment only when it has more than tri_min triangles.
 __device__ __forceinline__ void filter_phase(const FrameArgs& a) {
     const long long n = 2LL * (a.H - 1) * (a.W - 1);
+    int32_t* const labels = a.labels;
+    int32_t* const copy = a.labels_copy;
+    const int32_t* const sizes = a.sizes;
+    const int min_triangles = a.min_triangles;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-        const int l = __ldcg(a.labels + i);
-        if (l >= 0 && __ldcg(a.sizes + l) <= a.min_triangles) a.labels[i] = -1;   // sizes: other CTAs' atomics
+        const int l = __ldcg(labels + i);
+        const bool drop = l >= 0 && __ldcg(sizes + l) <= min_triangles;   // sizes: other CTAs' atomics
+        if (drop) labels[i] = -1;
+        if (copy) copy[i] = drop ? -1 : l;
     }
 }
 

@@ -45,9 +45,20 @@ int grow_tri(pl3d_ctx* ctx, size_t need, cudaStream_t s) {
     return PL3D_OK;
 }
 
+// The device address of a page-locked (cudaHostAlloc'd or registered) host buffer, or nullptr
+// for memory the device cannot address directly (pageable memory, device memory).
+void* device_view(void* host) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, host) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 int run(pl3d_ctx* ctx, const float* points, int H, int W, const pl3d_params* p, const float* nd_host, int K,
         uint8_t* out_mask, float* out_normals, int32_t* out_labels, float* out_points, uint8_t* out_groups,
-        cudaStream_t s) {
+        cudaStream_t s, int32_t* out_labels_copy = nullptr) {
     const size_t npts = (size_t)H * W;
     const size_t ntri = 2 * (size_t)(H - 1) * (W - 1);
     int rc;
@@ -84,7 +95,7 @@ int run(pl3d_ctx* ctx, const float* points, int H, int W, const pl3d_params* p, 
     cudaEvent_t e0, e1;
     record_start(ctx, s, &e0, &e1);
     rc = frame_launch(sc, points, H, W, &q, nd_host, K, out_mask, out_normals, out_labels, out_points, out_groups,
-                      ctx->tuning, s);
+                      ctx->tuning, s, seeded ? nullptr : out_labels_copy);
     record_stop(ctx, s, kSlotKernel, e0, e1);
     if (rc != PL3D_OK) return rc;
     if (seeded) {
@@ -284,21 +295,30 @@ int pl3d_extract_planes_host(pl3d_ctx* ctx, const float* host_points, int H, int
         }
         ctx->st_cap_tri = n;
     }
+    // A page-locked mask and labels buffer that the device can address is written by the kernel
+    // itself: the mask as the tiles finish, the final labels by the last label phase (the labels
+    // also serve as the union-find parents and stay in device memory). That spares two copies
+    // after the kernel. The normals are copied: written from the tiles into host memory, their
+    // 12-byte records would slow the kernel more than the copy costs.
+    uint8_t* d_mask = static_cast<uint8_t*>(device_view(host_tri_mask));
+    int32_t* d_labels = static_cast<int32_t*>(device_view(host_labels));
+    const bool seeded = (params->flags & PL3D_FLAG_SEED_PTP) != 0;   // labels finished on the host
+    if (seeded) d_labels = nullptr;
     cudaEvent_t e0, e1;
     record_start(ctx, s, &e0, &e1);
     if (cudaMemcpyAsync(ctx->st_points, host_points, npts * 3 * sizeof(float), cudaMemcpyHostToDevice, s) !=
         cudaSuccess)
         return PL3D_ERR_CUDA;
     record_stop(ctx, s, kSlotCopies, e0, e1);
-    rc = run(ctx, ctx->st_points, H, W, params, dominant_normals, K, ctx->st_mask, ctx->st_normals, ctx->st_labels,
-             nullptr, nullptr, s);
+    rc = run(ctx, ctx->st_points, H, W, params, dominant_normals, K, d_mask ? d_mask : ctx->st_mask, ctx->st_normals,
+             ctx->st_labels, nullptr, nullptr, s, d_labels);
     if (rc != PL3D_OK) return rc;
     record_start(ctx, s, &e0, &e1);
-    if (cudaMemcpyAsync(host_tri_mask, ctx->st_mask, ntri, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+    if ((!d_mask && cudaMemcpyAsync(host_tri_mask, ctx->st_mask, ntri, cudaMemcpyDeviceToHost, s) != cudaSuccess) ||
         cudaMemcpyAsync(host_normals, ctx->st_normals, ntri * 3 * sizeof(float), cudaMemcpyDeviceToHost, s) !=
             cudaSuccess ||
-        cudaMemcpyAsync(host_labels, ctx->st_labels, ntri * sizeof(int32_t), cudaMemcpyDeviceToHost, s) !=
-            cudaSuccess)
+        (!d_labels &&
+         cudaMemcpyAsync(host_labels, ctx->st_labels, ntri * sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess))
         return PL3D_ERR_CUDA;
     record_stop(ctx, s, kSlotCopies, e0, e1);
     if (cudaStreamSynchronize(s) != cudaSuccess) return PL3D_ERR_CUDA;

@@ -111,6 +111,8 @@ struct FrameArgs {
     float* out_normals;
     uint8_t* groups;
     int32_t* labels;
+    int32_t* labels_copy;          // optional second destination of the final labels (for example
+                                   // page-locked host memory), written by the last label phase
     int32_t* sizes;                // zeroed in the bilateral pass when tri_min > 0, else nullptr
     float c_scale;                 // sqrt(log2(e) / (2 sigma_c^2)): centroid pre-scale
     float a_norm;                  // log2(e) / sigma_s^2
@@ -217,7 +219,8 @@ struct FramePlan {
 // Fills the arguments of one frame (no CUDA call besides tensor-map encoding).
 int frame_build(FrameArgs& a, FramePlan& plan, const FrameScratch& sc, const float* points, int H, int W,
                 const pl3d_params* p, const float* nd_host, int K, uint8_t* out_mask, float* out_normals,
-                int32_t* out_labels, float* out_points, uint8_t* out_groups, const Tuning& t);
+                int32_t* out_labels, float* out_points, uint8_t* out_groups, const Tuning& t,
+                int32_t* out_labels_copy = nullptr);
 
 // batch_kernel<rl, rb>, or nullptr outside radii 1..3.
 const void* batch_kernel_for_radii(int rl, int rb);
@@ -231,7 +234,7 @@ cudaError_t frame_configure();
 // Enqueues the whole path for one frame on `s` (one cooperative launch). Returns a PL3D status.
 int frame_launch(const FrameScratch& sc, const float* points, int H, int W, const pl3d_params* p, const float* nd_host,
                  int K, uint8_t* out_mask, float* out_normals, int32_t* out_labels, float* out_points,
-                 uint8_t* out_groups, const Tuning& t, cudaStream_t s);
+                 uint8_t* out_groups, const Tuning& t, cudaStream_t s, int32_t* out_labels_copy = nullptr);
 
 // Grid size of a persistent launch: all resident CTAs (or ctas_per_sm per SM), at most `work`.
 int persistent_grid(const void* fn, size_t smem, int dev, const Tuning& t, long long work);

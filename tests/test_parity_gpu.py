@@ -211,6 +211,38 @@ def test_deterministic_and_host_entry_matches(env):
     assert torch.equal(hl, a["labels"].cpu())
 
 
+@pytest.mark.parametrize("pinned,extra", [((True, True, True), {}), ((True, True, True), dict(min_triangles=25)),
+                                          ((False, False, False), {}), ((True, False, True), {}),
+                                          ((False, True, False), dict(min_triangles=25)),
+                                          ((True, True, True), dict(flags=1, max_offset=0.02, min_triangles=5))])
+def test_host_entry_point_outputs(env, pinned, extra):
+    """Host buffers: page-locked ones are written by the kernel itself (labels by the last label
+    phase, also when tri_min filters), pageable ones get copies; the seeded flag finishes the
+    labels on the host. Every mix gives the device entry point's bits."""
+    pl3d, ex, torch = env
+    f = synth.depth_camera_scene(90, 120, seed=31, n_boxes=3, ramp=True)
+    p = pl3d.make_params(**dict(f.params, **extra))
+    a = ex(torch.from_numpy(f.points).cuda(), p, f.dominant_normals)
+    torch.cuda.synchronize()
+    n = 2 * (f.H - 1) * (f.W - 1)
+
+    def buf(shape, dtype, pin):
+        t = torch.full(shape, 7, dtype=dtype)
+        return t.pin_memory() if pin else t
+
+    hm = buf((n,), torch.uint8, pinned[0])
+    hn = buf((n, 3), torch.float32, pinned[1])
+    hl = buf((n,), torch.int32, pinned[2])
+    hp = torch.from_numpy(f.points)
+    for _ in range(2):   # a second call must not see the first one's results
+        hl.fill_(-7)
+        pl3d.pl3d_extract_planes_host(ex.ctx, hp, f.H, f.W, p, f.dominant_normals, f.dominant_normals.shape[0],
+                                      hm, hn, hl)
+        assert torch.equal(hm, a["mask"].cpu())
+        assert torch.equal(hn.nan_to_num(7.0), a["normals"].cpu().nan_to_num(7.0))
+        assert torch.equal(hl, a["labels"].cpu())
+
+
 def test_side_stream_and_timing(env):
     pl3d, ex, torch = env
     f = synth.rgbd_120x160()
