@@ -8,8 +8,9 @@ writing a 256 MB buffer before every timed step, outside the step's CUDA events.
 
 Prints one JSON line. `value` is Mtri/s over all ranks (triangles = 2(H-1)(W-1) per frame),
 `e2e` repeats the measurement through pl3d_extract_planes_host with pinned host buffers (the
-points copied in, the normals copied out, the mask and labels written by the kernel into the
-pinned buffers; all of it inside the timed region), `roofline` describes the kernel with the largest share of
+points copied in, the normals copied out beside the segment launch, the mask and labels written
+by the kernel into the pinned buffers; all of it inside the timed region), `roofline` describes
+the kernel with the largest share of
 device time, `cpu_baseline` times the FP64 oracle on the host cores on a bounded sample.
 
 --impl reference times the FP64 oracle itself (the paper has no code to run) on the same
@@ -715,8 +716,8 @@ def run_pl3d(args):
         "e2e": {"value": aggregate_mtri_s(ntri, world, e2e_ms), "unit": "Mtri/s", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": int(h_pts.numel() * 4),
                 "d2h_bytes_per_step": int(h_mask.numel() + h_normals.numel() * 4 + h_labels.numel() * 4),
-                "d2h": "normals by copy after the kernel; mask and labels written by the kernel into the pinned "
-                       "host buffers"},
+                "d2h": "normals by copy once they are final (beside the second launch, which joins the segments "
+                       "across tiles); mask and labels written by the kernel into the pinned host buffers"},
         "gpu_launches": int(launches),
         "roofline": roofline,
         "cpu_baseline": cpu,

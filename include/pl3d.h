@@ -156,8 +156,10 @@ int pl3d_extract_planes_ex(pl3d_ctx* ctx, const float* points, int H, int W, con
  * returning. Page-locked host buffers make the copies asynchronous DMA; pageable ones work
  * but are slower. A page-locked mask or labels buffer that the device can address is written
  * by the kernel itself (the mask as each tile finishes, the final labels by the last label
- * phase), so only the normals are copied after the kernel; the results are the same either
- * way. Device staging buffers are owned by the context. */
+ * phase). The path runs as two launches here: once mask, normals and groups are final, the
+ * normals are copied out on a stream of the context while the second launch joins the
+ * segments across tiles. The results are the same either way. Device staging buffers and the
+ * copy stream are owned by the context. */
 int pl3d_extract_planes_host(pl3d_ctx* ctx, const float* host_points, int H, int W, const pl3d_params* params,
                              const float* dominant_normals, int K, uint8_t* host_tri_mask, float* host_normals,
                              int32_t* host_labels, void* stream);

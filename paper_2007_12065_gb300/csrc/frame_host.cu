@@ -337,7 +337,8 @@ int persistent_grid(const void* fn, size_t smem, int dev, const Tuning& t, long 
 
 int frame_launch(const FrameScratch& sc, const float* points, int H, int W, const pl3d_params* p, const float* nd_host,
                  int K, uint8_t* out_mask, float* out_normals, int32_t* out_labels, float* out_points,
-                 uint8_t* out_groups, const Tuning& t, cudaStream_t s, int32_t* out_labels_copy) {
+                 uint8_t* out_groups, const Tuning& t, cudaStream_t s, int32_t* out_labels_copy,
+                 cudaEvent_t normals_ready) {
     static_assert(sizeof(FrameArgs) < 32000, "kernel parameters must fit the 32 KB parameter space");
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return PL3D_ERR_CUDA;
@@ -350,9 +351,15 @@ int frame_launch(const FrameScratch& sc, const float* points, int H, int W, cons
     const int grid = persistent_grid(plan.frame_fn, plan.smem, dev, t, work);
     if (grid <= 0) return PL3D_ERR_CUDA;
     void* args[1] = {&a};
-    if (cudaLaunchCooperativeKernel(plan.frame_fn, dim3(grid), dim3(kThreads), args, plan.smem, s) != cudaSuccess) {
-        cudaGetLastError();
-        return PL3D_ERR_CUDA;
+    // one launch, or two with the event between them: the first ends once mask, normals and
+    // groups are final, the second joins the segments across tiles (the same arguments)
+    for (int part = normals_ready ? 1 : 0; part <= (normals_ready ? 2 : 0); ++part) {
+        a.part = part;
+        if (cudaLaunchCooperativeKernel(plan.frame_fn, dim3(grid), dim3(kThreads), args, plan.smem, s) != cudaSuccess) {
+            cudaGetLastError();
+            return PL3D_ERR_CUDA;
+        }
+        if (part == 1 && cudaEventRecord(normals_ready, s) != cudaSuccess) return PL3D_ERR_CUDA;
     }
     return PL3D_OK;
 }

@@ -1186,43 +1186,48 @@ __global__ void __launch_bounds__(kThreads, 2) frame_kernel(const __grid_constan
     uint64_t t_prev = 0;
     if (a.phase_ns && blockIdx.x == 0 && threadIdx.x == 0) t_prev = global_ns();
 
-    for (int c = 0; c < a.n_lap; ++c) {
-        const LapPhase& ph = a.lap[c];
-        const int tiles_lap = ph.tiles;
-        const CUtensorMap* map = ph.use_tma ? &a.tm_pts_lap : nullptr;
-        // buffers: [box 0 .. box ns-1][D a][D b] (one D buffer for a single-iteration first
-        // pass); the box of this CTA's tile k is slot k mod ns, and the TMA loads of its next
-        // ns - 1 tiles are in flight while tile k computes
-        const int P = align_floats(ph.box.rows * ph.box.cols);
-        const int ns = map ? ph.stages : 1;
-        float* Da = smem + ns * P;
-        float* Db = Da + (ph.dbufs - 1) * P;
-        for (int k = 0; k + 1 < ns; ++k) {
-            const int t = (int)blockIdx.x + k * (int)gridDim.x;
-            if (t < tiles_lap) frame::lap_issue(a, ph, map, t, smem + k * P, bar + k);
-        }
-        int s = 0;
-        for (int t = blockIdx.x; t < tiles_lap; t += gridDim.x) {
-            if (map) {
-                const int ahead = t + (ns - 1) * (int)gridDim.x;
-                const int sa = s == 0 ? ns - 1 : s - 1;   // the slot of the previous tile, now free
-                if (ahead < tiles_lap) frame::lap_issue(a, ph, map, ahead, smem + sa * P, bar + sa);
+    // a launch may run part of the path (a.part): the smoothing and tile-local segments, or the
+    // segments across tiles; the launch boundary then orders the two
+    if (a.part != 2) {
+        for (int c = 0; c < a.n_lap; ++c) {
+            const LapPhase& ph = a.lap[c];
+            const int tiles_lap = ph.tiles;
+            const CUtensorMap* map = ph.use_tma ? &a.tm_pts_lap : nullptr;
+            // buffers: [box 0 .. box ns-1][D a][D b] (one D buffer for a single-iteration first
+            // pass); the box of this CTA's tile k is slot k mod ns, and the TMA loads of its next
+            // ns - 1 tiles are in flight while tile k computes
+            const int P = align_floats(ph.box.rows * ph.box.cols);
+            const int ns = map ? ph.stages : 1;
+            float* Da = smem + ns * P;
+            float* Db = Da + (ph.dbufs - 1) * P;
+            for (int k = 0; k + 1 < ns; ++k) {
+                const int t = (int)blockIdx.x + k * (int)gridDim.x;
+                if (t < tiles_lap) frame::lap_issue(a, ph, map, t, smem + k * P, bar + k);
             }
-            const frame::LapJob j = frame::lap_job(a, ph, t);
-            frame::lap_tile<RL>(j, smem + s * P, Da, Db, map != nullptr, bar + s, (par >> s) & 1u);
-            if (map) par ^= 1u << s;
-            s = s + 1 == ns ? 0 : s + 1;
+            int s = 0;
+            for (int t = blockIdx.x; t < tiles_lap; t += gridDim.x) {
+                if (map) {
+                    const int ahead = t + (ns - 1) * (int)gridDim.x;
+                    const int sa = s == 0 ? ns - 1 : s - 1;   // the slot of the previous tile, now free
+                    if (ahead < tiles_lap) frame::lap_issue(a, ph, map, ahead, smem + sa * P, bar + sa);
+                }
+                const frame::LapJob j = frame::lap_job(a, ph, t);
+                frame::lap_tile<RL>(j, smem + s * P, Da, Db, map != nullptr, bar + s, (par >> s) & 1u);
+                if (map) par ^= 1u << s;
+                s = s + 1 == ns ? 0 : s + 1;
+            }
+            grid_barrier(a.barrier, a.error);
         }
-        grid_barrier(a.barrier, a.error);
+        frame::phase_mark(a, 0, t_prev);
+        const int tiles_bil = div_up(a.H - 1, kTile) * div_up(a.W - 1, kTile);
+        unsigned par0 = par & 1u;   // the bilateral stages through slot 0
+        for (int c = 0; c < a.n_bil; ++c) {
+            for (int t = blockIdx.x; t < tiles_bil; t += gridDim.x) frame::bil_tile<RB>(a, a.bil[c], t, smem, bar, par0);
+            if (a.part == 0 || c + 1 < a.n_bil) grid_barrier(a.barrier, a.error);
+        }
+        frame::phase_mark(a, 1, t_prev);
     }
-    frame::phase_mark(a, 0, t_prev);
-    const int tiles_bil = div_up(a.H - 1, kTile) * div_up(a.W - 1, kTile);
-    unsigned par0 = par & 1u;   // the bilateral stages through slot 0
-    for (int c = 0; c < a.n_bil; ++c) {
-        for (int t = blockIdx.x; t < tiles_bil; t += gridDim.x) frame::bil_tile<RB>(a, a.bil[c], t, smem, bar, par0);
-        grid_barrier(a.barrier, a.error);
-    }
-    frame::phase_mark(a, 1, t_prev);
+    if (a.part == 1) return;
     frame::merge_phase(a);
     grid_barrier(a.barrier, a.error);
     frame::phase_mark(a, 2, t_prev);

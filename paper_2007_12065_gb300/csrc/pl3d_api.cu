@@ -58,7 +58,7 @@ void* device_view(void* host) {
 
 int run(pl3d_ctx* ctx, const float* points, int H, int W, const pl3d_params* p, const float* nd_host, int K,
         uint8_t* out_mask, float* out_normals, int32_t* out_labels, float* out_points, uint8_t* out_groups,
-        cudaStream_t s, int32_t* out_labels_copy = nullptr) {
+        cudaStream_t s, int32_t* out_labels_copy = nullptr, cudaEvent_t normals_ready = nullptr) {
     const size_t npts = (size_t)H * W;
     const size_t ntri = 2 * (size_t)(H - 1) * (W - 1);
     int rc;
@@ -95,7 +95,7 @@ int run(pl3d_ctx* ctx, const float* points, int H, int W, const pl3d_params* p, 
     cudaEvent_t e0, e1;
     record_start(ctx, s, &e0, &e1);
     rc = frame_launch(sc, points, H, W, &q, nd_host, K, out_mask, out_normals, out_labels, out_points, out_groups,
-                      ctx->tuning, s, seeded ? nullptr : out_labels_copy);
+                      ctx->tuning, s, seeded ? nullptr : out_labels_copy, normals_ready);
     record_stop(ctx, s, kSlotKernel, e0, e1);
     if (rc != PL3D_OK) return rc;
     if (seeded) {
@@ -104,7 +104,7 @@ int run(pl3d_ctx* ctx, const float* points, int H, int W, const pl3d_params* p, 
         if (rc != PL3D_OK) return rc;
         ctx->launches += 1;
     }
-    ctx->launches += 1;
+    ctx->launches += normals_ready ? 2 : 1;
     if (ctx->timing) ctx->timed_frames += 1;
     return PL3D_OK;
 }
@@ -225,6 +225,9 @@ void pl3d_destroy(pl3d_ctx* c) {
         cudaFree(c->st_mask);
         cudaFree(c->st_normals);
         cudaFree(c->st_labels);
+        if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+        if (c->normals_ready) cudaEventDestroy(c->normals_ready);
+        if (c->normals_copied) cudaEventDestroy(c->normals_copied);
         drop_graphs(c);
         cudaFree(c->bslab);
         cudaFree(c->mslab);
@@ -304,6 +307,13 @@ int pl3d_extract_planes_host(pl3d_ctx* ctx, const float* host_points, int H, int
     int32_t* d_labels = static_cast<int32_t*>(device_view(host_labels));
     const bool seeded = (params->flags & PL3D_FLAG_SEED_PTP) != 0;   // labels finished on the host
     if (seeded) d_labels = nullptr;
+    // The normals are final before the segments across tiles: the path runs as two launches,
+    // and the normals' copy runs on a second stream beside the second launch.
+    if (!ctx->copy_stream &&
+        (cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
+         cudaEventCreateWithFlags(&ctx->normals_ready, cudaEventDisableTiming) != cudaSuccess ||
+         cudaEventCreateWithFlags(&ctx->normals_copied, cudaEventDisableTiming) != cudaSuccess))
+        return PL3D_ERR_CUDA;
     cudaEvent_t e0, e1;
     record_start(ctx, s, &e0, &e1);
     if (cudaMemcpyAsync(ctx->st_points, host_points, npts * 3 * sizeof(float), cudaMemcpyHostToDevice, s) !=
@@ -311,14 +321,18 @@ int pl3d_extract_planes_host(pl3d_ctx* ctx, const float* host_points, int H, int
         return PL3D_ERR_CUDA;
     record_stop(ctx, s, kSlotCopies, e0, e1);
     rc = run(ctx, ctx->st_points, H, W, params, dominant_normals, K, d_mask ? d_mask : ctx->st_mask, ctx->st_normals,
-             ctx->st_labels, nullptr, nullptr, s, d_labels);
+             ctx->st_labels, nullptr, nullptr, s, d_labels, ctx->normals_ready);
     if (rc != PL3D_OK) return rc;
+    if (cudaStreamWaitEvent(ctx->copy_stream, ctx->normals_ready, 0) != cudaSuccess ||
+        cudaMemcpyAsync(host_normals, ctx->st_normals, ntri * 3 * sizeof(float), cudaMemcpyDeviceToHost,
+                        ctx->copy_stream) != cudaSuccess ||
+        cudaEventRecord(ctx->normals_copied, ctx->copy_stream) != cudaSuccess)
+        return PL3D_ERR_CUDA;
     record_start(ctx, s, &e0, &e1);
     if ((!d_mask && cudaMemcpyAsync(host_tri_mask, ctx->st_mask, ntri, cudaMemcpyDeviceToHost, s) != cudaSuccess) ||
-        cudaMemcpyAsync(host_normals, ctx->st_normals, ntri * 3 * sizeof(float), cudaMemcpyDeviceToHost, s) !=
-            cudaSuccess ||
         (!d_labels &&
-         cudaMemcpyAsync(host_labels, ctx->st_labels, ntri * sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess))
+         cudaMemcpyAsync(host_labels, ctx->st_labels, ntri * sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess) ||
+        cudaStreamWaitEvent(s, ctx->normals_copied, 0) != cudaSuccess)
         return PL3D_ERR_CUDA;
     record_stop(ctx, s, kSlotCopies, e0, e1);
     if (cudaStreamSynchronize(s) != cudaSuccess) return PL3D_ERR_CUDA;

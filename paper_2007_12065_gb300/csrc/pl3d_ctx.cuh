@@ -58,6 +58,11 @@ struct pl3d_ctx {
     float* st_normals = nullptr;
     int32_t* st_labels = nullptr;
     size_t st_cap_tri = 0;
+    // the host-buffer entry point copies the normals out on this stream while the second half
+    // of the path (the segments across tiles) still runs on the caller's
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t normals_ready = nullptr;
+    cudaEvent_t normals_copied = nullptr;
     // launch shape
     pl3d::Tuning tuning = {0, 0, 0};
     // batches: per-frame scratch slab, descriptor block (device + pinned staging), graphs

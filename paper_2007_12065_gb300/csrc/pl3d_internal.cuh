@@ -124,6 +124,8 @@ struct FrameArgs {
     unsigned* barrier;             // [2] grid barrier state
     int* error;                    // device error word (sync.cuh bits)
     unsigned long long* phase_ns;  // [4] accumulated phase times, or nullptr
+    int part;                      // 0: the whole path; 1: smoothing and tile-local segments only
+                                   // (mask, normals, groups final); 2: the segments across tiles only
     Dominant nd;
 };
 
@@ -232,9 +234,12 @@ int resident_ctas(const void* fn, size_t smem, int dev);
 cudaError_t frame_configure();
 
 // Enqueues the whole path for one frame on `s` (one cooperative launch). Returns a PL3D status.
+// With `normals_ready`, the path runs as two launches and the event is recorded between them,
+// once mask, normals and groups are final (the segments across tiles come after it).
 int frame_launch(const FrameScratch& sc, const float* points, int H, int W, const pl3d_params* p, const float* nd_host,
                  int K, uint8_t* out_mask, float* out_normals, int32_t* out_labels, float* out_points,
-                 uint8_t* out_groups, const Tuning& t, cudaStream_t s, int32_t* out_labels_copy = nullptr);
+                 uint8_t* out_groups, const Tuning& t, cudaStream_t s, int32_t* out_labels_copy = nullptr,
+                 cudaEvent_t normals_ready = nullptr);
 
 // Grid size of a persistent launch: all resident CTAs (or ctas_per_sm per SM), at most `work`.
 int persistent_grid(const void* fn, size_t smem, int dev, const Tuning& t, long long work);
