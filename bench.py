@@ -694,8 +694,8 @@ def run_pl3d(args):
     if world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
         r = time_oracle(frame, args.cpu_seconds, cores)
-        r1 = time_oracle(frame, 2.0, 1, max_frames=3)
-        r4 = time_oracle(frame, 2.0, 4, max_frames=5)
+        r1 = time_oracle(frame, 6.0, 1, max_frames=10)   # medians of 10 frames (fewer past the budget)
+        r4 = time_oracle(frame, 3.0, 4, max_frames=10)
         cpu = {"value": r["mtri_s"], "unit": "Mtri/s", "cores": cores, "kind": "oracle",
                "sample": f"{r['frames']} whole {H}x{W} frames, median wall time, FP64 C oracle with OpenMP "
                          f"on {cores} threads (its sensitivity reruns, test instrumentation, off)",
