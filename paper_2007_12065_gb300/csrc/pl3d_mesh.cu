@@ -2,7 +2,8 @@
 // HE) and the triangle lists and boundary half-edges of its planar segments (the inputs of the
 // polygon extraction of Section 7.2), in one cooperative launch (pl3d_extract_mesh).
 //
-// Phases, one grid barrier apart, all over chunks of 2048 consecutive entries (8 per thread):
+// Phases, one grid barrier apart, all over chunks of 2048 consecutive entries (8 per thread:
+// consecutive ones in the sort, one per round of 256 consecutive GIDs in A and C):
 //   A  per chunk of GIDs: valid triangles (all three points valid, Algorithm 1) and segment
 //      roots (a label is the smallest GID of its segment, so a root is labelled with itself)
 //      (no scan phase: each CTA sums the counts of the chunks before its own when it needs them)
@@ -122,16 +123,19 @@ __global__ void __launch_bounds__(kThreads, 4) mesh_kernel(const __grid_constant
     int32_t* cT = a.cnt;
     int32_t* cR = a.cnt + C;
 
-    // A: counts per chunk; every GID's root index starts undefined
+    // A: counts per chunk; every GID's root index starts undefined. A chunk is kPer rounds of
+    // kThreads consecutive GIDs (thread t takes GID t of each round), so a warp's loads and
+    // stores cover consecutive triangles.
     for (int c = blockIdx.x; c < C; c += gridDim.x) {
-        const long long g0 = (long long)c * kChunk + threadIdx.x * kPer;
+        const long long c0 = (long long)c * kChunk;
         int nt = 0, nr = 0;
 #pragma unroll
         for (int j = 0; j < kPer; ++j) {
-            const Flags f = gid_flags(a, g0 + j, n);
+            const long long g = c0 + j * kThreads + threadIdx.x;
+            const Flags f = gid_flags(a, g, n);
             nt += f.valid;
             nr += f.root;
-            if (a.labels && g0 + j < n) a.root_idx[g0 + j] = -1;
+            if (a.labels && g < n) a.root_idx[g] = -1;
         }
         int tt, tr;
         block_exclusive(nt, sh_scan, &tt);
@@ -165,47 +169,83 @@ __global__ void __launch_bounds__(kThreads, 4) mesh_kernel(const __grid_constant
     }
     const int nS = (int)nS_l;
 
-    // C: T, T_map, T labels, segment roots (GID order)
+    // C: T, T_map, T labels, segment roots (GID order). A GID's place among the chunk's entries
+    // is the count of (round, warp) blocks before its own plus its lane's rank in its warp's
+    // ballot; the per-block counts live in sh_wc (free until the sort).
+    static_assert(kPer * kWarps == 64, "one (round, warp) count per lane pair of warp 0");
+    int* const cntT = &sh_wc[0][0];
+    int* const cntR = cntT + 64;
+    int* const preT = cntT + 128;
+    int* const preR = cntT + 192;
     for (int c = blockIdx.x; c < C; c += gridDim.x) {
-        const long long g0 = (long long)c * kChunk + threadIdx.x * kPer;
+        const long long c0 = (long long)c * kChunk;
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
         Flags f[kPer];
-        int nt = 0, nr = 0;
+        unsigned bv[kPer], brt[kPer];
 #pragma unroll
         for (int j = 0; j < kPer; ++j) {
-            f[j] = gid_flags(a, g0 + j, n);
-            nt += f[j].valid;
-            nr += f[j].root;
+            f[j] = gid_flags(a, c0 + j * kThreads + threadIdx.x, n);
+            bv[j] = __ballot_sync(0xffffffffu, f[j].valid);
+            brt[j] = __ballot_sync(0xffffffffu, f[j].root);
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int j = 0; j < kPer; ++j) {
+                cntT[j * kWarps + warp] = __popc(bv[j]);
+                cntR[j * kWarps + warp] = __popc(brt[j]);
+            }
         }
         long long bt = 0, br = 0;   // entries of the chunks before c
         for (int i = threadIdx.x; i < c; i += blockDim.x) {
             bt += __ldcg(cT + i);
             br += __ldcg(cR + i);
         }
-        int tt, tr, ct, cr;
-        block_exclusive((int)bt, sh_scan, &ct);
+        int ct, cr;
+        block_exclusive((int)bt, sh_scan, &ct);   // (its barriers also publish the counts above)
         block_exclusive((int)br, sh_scan, &cr);
-        int pt = ct + block_exclusive(nt, sh_scan, &tt);
-        int pr = cr + block_exclusive(nr, sh_scan, &tr);
+        if (warp == 0) {   // exclusive prefix over the 64 (round, warp) blocks, two per lane
+            const int k0 = 2 * lane;
+            const int t0 = cntT[k0], t1 = cntT[k0 + 1], r0 = cntR[k0], r1 = cntR[k0 + 1];
+            int st = t0 + t1, sr = r0 + r1;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int yt = __shfl_up_sync(0xffffffffu, st, o), yr = __shfl_up_sync(0xffffffffu, sr, o);
+                if (lane >= o) {
+                    st += yt;
+                    sr += yr;
+                }
+            }
+            preT[k0] = st - (t0 + t1);
+            preT[k0 + 1] = st - t1;
+            preR[k0] = sr - (r0 + r1);
+            preR[k0 + 1] = sr - r1;
+        }
+        __syncthreads();
+        const unsigned below = (1u << lane) - 1u;
 #pragma unroll
         for (int j = 0; j < kPer; ++j) {
-            const long long g = g0 + j;
-            if (g >= n) break;
+            const long long g = c0 + j * kThreads + threadIdx.x;
+            if (g >= n) continue;
+            const int k = j * kWarps + warp;
             if (f[j].valid) {
+                const int pt = ct + preT[k] + __popc(bv[j] & below);
                 long long v[3];
                 tri_vertices(g, a.W, Wq, v);
                 a.T[3LL * pt] = (int32_t)v[0];
                 a.T[3LL * pt + 1] = (int32_t)v[1];
                 a.T[3LL * pt + 2] = (int32_t)v[2];
                 a.tlab[pt] = a.labels ? __ldg(a.labels + g) : -1;
-                a.Tmap[g] = pt++;
+                a.Tmap[g] = pt;
             } else {
                 a.Tmap[g] = -1;
             }
             if (f[j].root) {
+                const int pr = cr + preR[k] + __popc(brt[j] & below);
                 a.seg_labels[pr] = (int32_t)g;
-                a.root_idx[g] = pr++;
+                a.root_idx[g] = pr;
             }
         }
+        __syncthreads();   // the next chunk rewrites the block counts
     }
     grid_barrier(a.barrier, a.error);
 
