@@ -309,11 +309,21 @@ int pl3d_extract_planes_host(pl3d_ctx* ctx, const float* host_points, int H, int
     if (seeded) d_labels = nullptr;
     // The normals are final before the segments across tiles: the path runs as two launches,
     // and the normals' copy runs on a second stream beside the second launch.
-    if (!ctx->copy_stream &&
-        (cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
-         cudaEventCreateWithFlags(&ctx->normals_ready, cudaEventDisableTiming) != cudaSuccess ||
-         cudaEventCreateWithFlags(&ctx->normals_copied, cudaEventDisableTiming) != cudaSuccess))
+    // each created on first use and kept only once created; one that failed is tried again by
+    // the next call
+    auto make_event = [](cudaEvent_t* e) {
+        cudaEvent_t t = nullptr;
+        if (!*e && cudaEventCreateWithFlags(&t, cudaEventDisableTiming) == cudaSuccess) *e = t;
+        return *e != nullptr;
+    };
+    if (!ctx->copy_stream) {
+        cudaStream_t t = nullptr;
+        if (cudaStreamCreateWithFlags(&t, cudaStreamNonBlocking) == cudaSuccess) ctx->copy_stream = t;
+    }
+    if (!ctx->copy_stream || !make_event(&ctx->normals_ready) || !make_event(&ctx->normals_copied)) {
+        cudaGetLastError();
         return PL3D_ERR_CUDA;
+    }
     cudaEvent_t e0, e1;
     record_start(ctx, s, &e0, &e1);
     if (cudaMemcpyAsync(ctx->st_points, host_points, npts * 3 * sizeof(float), cudaMemcpyHostToDevice, s) !=

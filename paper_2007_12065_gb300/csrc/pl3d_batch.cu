@@ -267,8 +267,14 @@ int run_batch(pl3d_ctx* c, const pl3d_frame* frames, int n, cudaStream_t s) {
     const size_t used = L.frames + (size_t)n * sizeof(FrameArgs);
     if (c->blast.size() != used || memcmp(c->blast.data(), st, used) != 0) {
         if (cudaMemcpyAsync(c->bdesc, st, used, cudaMemcpyHostToDevice, s) != cudaSuccess) return PL3D_ERR_CUDA;
-        if (!c->bupload && cudaEventCreateWithFlags(&c->bupload, cudaEventDisableTiming) != cudaSuccess)
-            return PL3D_ERR_CUDA;
+        if (!c->bupload) {
+            cudaEvent_t e = nullptr;
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+                cudaGetLastError();
+                return PL3D_ERR_CUDA;
+            }
+            c->bupload = e;
+        }
         if (cudaEventRecord(c->bupload, s) != cudaSuccess) return PL3D_ERR_CUDA;
         c->blast.assign(st, st + used);
         c->desc_uploads += 1;

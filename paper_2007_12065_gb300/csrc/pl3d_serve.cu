@@ -308,8 +308,9 @@ int pl3d_server_create(pl3d_server** out, const pl3d_server_config* cfg) {
         sl->srv = S;
         S->slots.push_back(sl);
         if ((rc = pl3d_create(&sl->ctx, cfg->device)) != PL3D_OK) break;
-        if (cudaStreamCreateWithFlags(&sl->stream, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaMalloc((void**)&sl->arena, S->arena_cap) != cudaSuccess) {
+        cudaStream_t st = nullptr;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess) sl->stream = st;
+        if (!sl->stream || cudaMalloc((void**)&sl->arena, S->arena_cap) != cudaSuccess) {
             cudaGetLastError();
             rc = PL3D_ERR_OUT_OF_MEMORY;
             break;
