@@ -199,12 +199,16 @@ def _stream(stream) -> Optional[int]:
     return stream.cuda_stream
 
 
-def _nd_host(dominant_normals):
-    """Dominant normals as a contiguous host float32 buffer (kept alive by the caller)."""
+def _nd_host(dominant_normals, K: Optional[int] = None):
+    """Dominant normals as a contiguous host float32 buffer (kept alive by the caller); with K,
+    the buffer must hold at least K rows, since the library reads K * 3 floats from it."""
     import numpy as np
     if hasattr(dominant_normals, "detach"):
         dominant_normals = dominant_normals.detach().cpu().numpy()
-    return np.ascontiguousarray(dominant_normals, dtype=np.float32).reshape(-1, 3)
+    nd = np.ascontiguousarray(dominant_normals, dtype=np.float32).reshape(-1, 3)
+    if K is not None and int(K) > nd.shape[0]:
+        raise ValueError(f"K = {int(K)} but dominant_normals holds {nd.shape[0]} normals")
+    return nd
 
 
 def _check(status: int, what: str) -> int:
@@ -214,6 +218,8 @@ def _check(status: int, what: str) -> int:
 
 
 def _check_tensor(t, name, dtype, numel, device_kind="cuda"):
+    """A torch tensor on the right device, or (host buffers only) a numpy array, contiguous, of
+    the right dtype and element count. Raw int addresses are passed through unchecked."""
     if t is None:
         return
     if hasattr(t, "is_cuda"):
@@ -225,6 +231,15 @@ def _check_tensor(t, name, dtype, numel, device_kind="cuda"):
             raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
         if t.numel() != numel:
             raise ValueError(f"{name} must have {numel} elements, got {t.numel()}")
+    elif hasattr(t, "__array_interface__"):
+        if device_kind == "cuda":
+            raise ValueError(f"{name} must be a cuda tensor, got a host array")
+        if not t.flags["C_CONTIGUOUS"]:
+            raise ValueError(f"{name} must be contiguous")
+        if str(t.dtype) != dtype.split(".")[-1]:
+            raise ValueError(f"{name} must be {dtype.split('.')[-1]}, got {t.dtype}")
+        if t.size != numel:
+            raise ValueError(f"{name} must have {numel} elements, got {t.size}")
 
 
 # ----------------------------------------------------------------------------- the C ABI, by name
@@ -263,6 +278,8 @@ def pl3d_validate(params: pl3d_params, H: int, W: int, dominant_normals=None, K:
     nd = _nd_host(dominant_normals) if dominant_normals is not None else None
     if K is None:
         K = nd.shape[0] if nd is not None else 1
+    if nd is not None and int(K) > nd.shape[0]:
+        return PL3D_ERR_INVALID_ARG   # the library would read K normals from a shorter buffer
     return int(lib().pl3d_validate(ctypes.byref(params), int(H), int(W), _ptr(nd), int(K)))
 
 
@@ -293,7 +310,7 @@ def pl3d_extract_planes_ex(ctx, points, H, W, params, dominant_normals, K, out_t
     _check_tensor(out_labels, "out_labels", "torch.int32", n_tri)
     _check_tensor(out_points, "out_points", "torch.float32", H * W * 3)
     _check_tensor(out_groups, "out_groups", "torch.uint8", n_tri)
-    nd = _nd_host(dominant_normals)
+    nd = _nd_host(dominant_normals, K)
     return _check(lib().pl3d_extract_planes_ex(ctx, _ptr(points), int(H), int(W), ctypes.byref(params), _ptr(nd),
                                                int(K), _ptr(out_tri_mask), _ptr(out_normals), _ptr(out_labels),
                                                _ptr(out_points), _ptr(out_groups), _stream(stream)),
@@ -308,7 +325,7 @@ def pl3d_extract_planes_host(ctx, points, H, W, params, dominant_normals, K, out
     _check_tensor(out_tri_mask, "out_tri_mask", "torch.uint8", n_tri, "cpu")
     _check_tensor(out_normals, "out_normals", "torch.float32", n_tri * 3, "cpu")
     _check_tensor(out_labels, "out_labels", "torch.int32", n_tri, "cpu")
-    nd = _nd_host(dominant_normals)
+    nd = _nd_host(dominant_normals, K)
     return _check(lib().pl3d_extract_planes_host(ctx, _ptr(points), int(H), int(W), ctypes.byref(params), _ptr(nd),
                                                  int(K), _ptr(out_tri_mask), _ptr(out_normals), _ptr(out_labels),
                                                  _stream(stream)), "pl3d_extract_planes_host")
@@ -323,7 +340,7 @@ def pl3d_extract_planes_static(points, H, W, params, dominant_normals, K, out_tr
     _check_tensor(out_tri_mask, "out_tri_mask", "torch.uint8", n_tri)
     _check_tensor(out_normals, "out_normals", "torch.float32", n_tri * 3)
     _check_tensor(out_labels, "out_labels", "torch.int32", n_tri)
-    nd = _nd_host(dominant_normals)
+    nd = _nd_host(dominant_normals, K)
     return _check(lib().pl3d_extract_planes_static(_ptr(points), int(H), int(W), ctypes.byref(params), _ptr(nd),
                                                    int(K), _ptr(out_tri_mask), _ptr(out_normals), _ptr(out_labels),
                                                    _stream(stream)), "pl3d_extract_planes_static")
@@ -498,7 +515,7 @@ def pl3d_server_submit(srv, points, H, W, params, dominant_normals, K, out_tri_m
     _check_tensor(out_tri_mask, "out_tri_mask", "torch.uint8", n_tri, "cpu")
     _check_tensor(out_normals, "out_normals", "torch.float32", n_tri * 3, "cpu")
     _check_tensor(out_labels, "out_labels", "torch.int32", n_tri, "cpu")
-    nd = _nd_host(dominant_normals)
+    nd = _nd_host(dominant_normals, K)
     t = ctypes.c_uint64()
     _check(lib().pl3d_server_submit(srv, _ptr(points), int(H), int(W), ctypes.byref(params), _ptr(nd), int(K),
                                     _ptr(out_tri_mask), _ptr(out_normals), _ptr(out_labels), ctypes.byref(t)),

@@ -86,6 +86,32 @@ def test_validate(pl3d):
     assert pl3d.pl3d_validate(pl3d.make_params(lap_iters=0, lap_kernel=4, bil_iters=0, bil_kernel=2), 10, 10, nd) == 0
 
 
+def test_binding_checks_buffers_before_the_library(pl3d):
+    """The binding rejects host arrays of the wrong dtype, size or layout, host arrays handed to a
+    device entry point, and K beyond the dominant normals it holds -- before any library call."""
+    H, W = 4, 5
+    n = 2 * (H - 1) * (W - 1)
+    p = pl3d.make_params()
+    nd = np.array([[0, 0, 1]], np.float32)
+    pts = np.zeros((H, W, 3), np.float32)
+    mask, nrm, lab = np.zeros(n, np.uint8), np.zeros((n, 3), np.float32), np.zeros(n, np.int32)
+    host = pl3d.pl3d_extract_planes_host
+    with pytest.raises(ValueError, match="out_labels must be int32"):
+        host(0, pts, H, W, p, nd, 1, mask, nrm, lab.astype(np.int64))
+    with pytest.raises(ValueError, match="out_normals must have"):
+        host(0, pts, H, W, p, nd, 1, mask, nrm[:-1], lab)
+    with pytest.raises(ValueError, match="points must be contiguous"):
+        host(0, np.zeros((H, W, 6), np.float32)[:, :, ::2], H, W, p, nd, 1, mask, nrm, lab)
+    with pytest.raises(ValueError, match="K = 2"):
+        host(0, pts, H, W, p, nd, 2, mask, nrm, lab)
+    with pytest.raises(ValueError, match="must be a cuda tensor"):
+        pl3d.pl3d_extract_planes(0, pts, H, W, p, nd, 1, mask, nrm, lab)
+    with pytest.raises(ValueError, match="K = 3"):
+        pl3d.pl3d_server_submit(0, pts, H, W, p, nd, 3, mask, nrm, lab)
+    assert pl3d.pl3d_validate(p, H, W, nd, K=2) == pl3d.PL3D_ERR_INVALID_ARG
+    assert pl3d.pl3d_validate(p, H, W, np.tile(nd, (2, 1)), K=2) == 0
+
+
 def test_null_arguments_rejected_before_any_cuda_call(pl3d):
     L = pl3d.lib()
     p = pl3d.make_params()
