@@ -35,6 +35,33 @@ MUTATIONS = {
                            "if (tri_min > 0 && tail < (int64_t)tri_min) {"),
     "halfedge_top_wrong_edge": ("if (top != -1) HE[3 * (int64_t)first + 1] = 3 * top + 1;",
                                 "if (top != -1) HE[3 * (int64_t)first + 1] = 3 * top;"),
+    "laplacian_nan_neighbour_used": ("                        if (isnan(vj[0])) continue;\n", ""),
+    "laplacian_zero_distance_used": ("                        if (d == 0.0) continue;\n", ""),
+    "laplacian_border_width_one": ("int border = (u < r) || (u >= H - r) || (v < r) || (v >= W - r);",
+                                   "int border = (u < 1) || (u >= H - 1) || (v < 1) || (v >= W - 1);"),
+    "laplacian_lambda_dropped": ("vo[1] = vi[1] + j1 * (lambda * sy / wsum);", "vo[1] = vi[1] + j1 * (sy / wsum);"),
+    "laplacian_in_place_sweep": ("const double* vj = cur + 3 * ((size_t)(u + du) * W + (v + dv));",
+                                 "const double* vj = (du < 0 || (du == 0 && dv < 0) ? nxt : cur) + "
+                                 "3 * ((size_t)(u + du) * W + (v + dv));"),
+    "bilateral_centroid_term_uses_sigma_s": ("exp(-(dcx * dcx + dcy * dcy + dcz * dcz) / two_sc2)",
+                                             "exp(-(dcx * dcx + dcy * dcy + dcz * dcz) / two_ss2)"),
+    "bilateral_in_place_sweep": ("const double* nj = cur + 3 * j;", "const double* nj = (j < i ? nxt : cur) + 3 * j;"),
+    "normal_not_unit": ("                nn[0] = nx / len;\n", "                nn[0] = nx;\n"),
+    "classify_unsigned_dot": ("double s = n[0] * d[0] + n[1] * d[1] + n[2] * d[2];\n                if (s > max_similarity) {",
+                              "double s = fabs(n[0] * d[0] + n[1] * d[1] + n[2] * d[2]);\n"
+                              "                if (s > max_similarity) {"),
+    "offset_test_signed": ("if (fabs(off) > max_offset) continue;", "if (off > max_offset) continue;"),
+    "offset_drops_y_term": ("double off = d[0] * (ct[0] - cj[0]) + d[1] * (ct[1] - cj[1]) +",
+                            "double off = d[0] * (ct[0] - cj[0]) + d[1] * (ct[1] - ct[1]) +"),
+    "label_ignores_group": ("if (labels[j] != UNVISITED || G[j] != g) continue;\n                if (max_offset > 0.0 && g < K) {",
+                            "if (labels[j] != UNVISITED) continue;\n                if (max_offset > 0.0 && g < K) {"),
+    "label_seeds_reversed": ("const int32_t UNVISITED = -2;\n    for (int64_t t = 0; t < n; ++t) labels[t] = (G[t] == 255) ? -1 : "
+                             "UNVISITED;\n    for (int64_t seed = 0; seed < n; ++seed) {",
+                             "const int32_t UNVISITED = -2;\n    for (int64_t t = 0; t < n; ++t) labels[t] = (G[t] == 255) ? -1 : "
+                             "UNVISITED;\n    for (int64_t seed = n - 1; seed >= 0; --seed) {"),
+    "seeded_offset_from_previous_triangle": (
+        "fabs(d[0] * (cj[0] - cs[0]) + d[1] * (cj[1] - cs[1]) + d[2] * (cj[2] - cs[2]))",
+        "fabs(d[0] * (cj[0] - C[3 * t]) + d[1] * (cj[1] - C[3 * t + 1]) + d[2] * (cj[2] - C[3 * t + 2]))"),
 }
 
 

@@ -208,6 +208,28 @@ def test_labels_with_offset_test_match_union_find():
     np.testing.assert_array_equal(got, want)
 
 
+def test_labels_with_offset_test_on_a_tilted_plane():
+    """The offset test along a dominant normal with three non-zero components, on a plane
+    perpendicular to it with range noise along it: every component of the centroid difference
+    counts."""
+    rng = np.random.default_rng(11)
+    H, W = 8, 9
+    nrm = np.array([0.36, 0.48, 0.8])
+    A = np.array([0.8, 0.0, -0.36])
+    B = np.cross(nrm, A)
+    u, v = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+    P = (0.05 * u[..., None] * A + 0.05 * v[..., None] * B
+         + rng.normal(0, 0.01, (H, W))[..., None] * nrm).astype(np.float32)
+    C, _ = oracle.triangle_geometry(oracle.widen(P))
+    nd = oracle.normalize_dominant(np.array([nrm, [1, 0, 0]], np.float32))
+    n = C.shape[0]
+    G = np.zeros(n, np.uint8)
+    got = oracle.label(G, H, W, C, nd, max_offset=0.003)
+    want = brute_labels(P, G, 0, C, nd, 0.003)
+    np.testing.assert_array_equal(got, want)
+    assert 1 < len(np.unique(got)) < n      # the threshold splits the plane, not every triangle
+
+
 def test_uniform_plane_is_one_component():
     H, W = 9, 11
     n = 2 * (H - 1) * (W - 1)
@@ -309,6 +331,25 @@ def test_laplacian_jacobi_two_iterations_by_hand():
     r1 = step(xs)
     np.testing.assert_allclose(oracle.laplacian(P, 3, lam, 1)[1, 1:6, 0], r1, atol=1e-14)
     np.testing.assert_allclose(oracle.laplacian(P, 3, lam, 2)[1, 1:6, 0], step(r1), atol=1e-14)
+
+
+def test_laplacian_two_interior_points_read_the_previous_iterate():
+    """3x4 grid, kernel 3: the interior points A (1,1) and B (1,2) see each other; the border
+    points C (1,0) and D (1,3) each sit in one window only. By hand, with lambda = 1:
+    |B - A| = 5 (w = 1/5), |C - A| = 2 (w = 1/2), |D - B| = 12 (w = 1/12);
+    A' = [(3,4,0)/5 + (0,-2,0)/2] / (7/10) = (6/7, -2/7, 0);
+    B' = (3,4,0) + [(-3,-4,0)/5 + (0,0,12)/12] / (17/60) = (15/17, 20/17, 60/17).
+    In 1-D the weighted differences are only signs, so this 2-D case is what separates Jacobi
+    from an in-place (Gauss-Seidel) sweep, which would move B with A' instead of A."""
+    P = np.full((3, 4, 3), np.nan)
+    P[1, 1] = (0, 0, 0)
+    P[1, 2] = (3, 4, 0)
+    P[1, 0] = (0, -2, 0)
+    P[1, 3] = (3, 4, 12)
+    S = oracle.laplacian(P, 3, 1.0, 1)
+    np.testing.assert_allclose(S[1, 1], (6 / 7, -2 / 7, 0), atol=1e-15)
+    np.testing.assert_allclose(S[1, 2], (15 / 17, 20 / 17, 60 / 17), atol=1e-14)
+    assert np.array_equal(S[1, 0], P[1, 0]) and np.array_equal(S[1, 3], P[1, 3])
 
 
 def test_laplacian_equivariance():
