@@ -59,6 +59,16 @@ MUTATIONS = {
                              "UNVISITED;\n    for (int64_t seed = 0; seed < n; ++seed) {",
                              "const int32_t UNVISITED = -2;\n    for (int64_t t = 0; t < n; ++t) labels[t] = (G[t] == 255) ? -1 : "
                              "UNVISITED;\n    for (int64_t seed = n - 1; seed >= 0; --seed) {"),
+    "mask_edges_on_raw_points": ("const double* a = P_smooth + 3 * idx[m];\n                    const double* b = P_smooth + 3 * idx[(m + 1) % 3];",
+                                 "const double* a = P_raw + 3 * idx[m];\n                    const double* b = P_raw + 3 * idx[(m + 1) % 3];"),
+    "mask_two_edges_only": ("                for (int m = 0; m < 3; ++m) {\n                    const double* a = P_smooth",
+                            "                for (int m = 0; m < 2; ++m) {\n                    const double* a = P_smooth"),
+    "extract_misses_third_vertex": ("if (isnan(P_raw[3 * idx[0]]) || isnan(P_raw[3 * idx[1]]) ||\n                    isnan(P_raw[3 * idx[2]])) {",
+                                    "if (isnan(P_raw[3 * idx[0]]) || isnan(P_raw[3 * idx[1]])) {"),
+    "halfedge_bottom_wrong_edge": ("if (bottom != -1) HE[3 * (int64_t)second + 1] = 3 * bottom + 1;",
+                                   "if (bottom != -1) HE[3 * (int64_t)second + 1] = 3 * bottom;"),
+    "halfedge_left_wrong_triangle": ("int32_t left = (v - 1 >= 0) ? Tmap[2 * ((int64_t)u * Wq + v - 1)] : -1;",
+                                     "int32_t left = (v - 1 >= 0) ? Tmap[2 * ((int64_t)u * Wq + v - 1) + 1] : -1;"),
     "seeded_offset_from_previous_triangle": (
         "fabs(d[0] * (cj[0] - cs[0]) + d[1] * (cj[1] - cs[1]) + d[2] * (cj[2] - cs[2]))",
         "fabs(d[0] * (cj[0] - C[3 * t]) + d[1] * (cj[1] - C[3 * t + 1]) + d[2] * (cj[2] - C[3 * t + 2]))"),

@@ -120,6 +120,46 @@ def test_halfedges_are_reversed_shared_edges(seed):
         assert g2 in oracle.triangle_twins(g1, H, W)
 
 
+@pytest.mark.parametrize("seed", range(4))
+def test_extracted_triangles_are_exactly_the_valid_ones(seed):
+    """Algorithm 1 keeps a triangle iff its three vertices are valid: |T| is 2 (H-1)(W-1) minus
+    the triangles with a NaN corner, counted here over the quads' corners (first takes p1, p2,
+    p3 and second p1, p3, p4); every T entry has three finite vertices; T_map inverts T."""
+    rng = np.random.default_rng(40 + seed)
+    H, W = int(rng.integers(2, 10)), int(rng.integers(2, 10))
+    P = affine_grid(H, W)
+    P[rng.random((H, W)) < 0.25] = np.nan
+    bad = np.isnan(P[..., 0])
+    want = 0
+    for u in range(H - 1):
+        for v in range(W - 1):
+            p1, p2, p3, p4 = bad[u, v], bad[u, v + 1], bad[u + 1, v + 1], bad[u + 1, v]
+            want += int(not (p1 or p2 or p3)) + int(not (p1 or p3 or p4))
+    T, Tmap = oracle.extract_triangles(oracle.widen(P))
+    assert T.shape[0] == want
+    flat = P.reshape(-1, 3)
+    assert np.isfinite(flat[T.reshape(-1), 0]).all()
+    kept = np.nonzero(Tmap >= 0)[0]
+    assert kept.size == want and np.array_equal(Tmap[kept], np.arange(want))
+
+
+def test_edge_test_reads_smoothed_vertices_validity_reads_raw():
+    """Algorithm 4 measures edges on the points after smoothing; Algorithm 1 takes validity from
+    the raw cloud. A spike in one copy only moves the decision of the copy that is measured."""
+    P = oracle.widen(affine_grid(4, 5, A=(0.0, 0.0625, 0.0), B=(0.0625, 0.0, 0.0)))
+    spiked = P.copy()
+    spiked[1, 2, 2] += 1.0
+    m, _ = oracle.mask(spiked, P, 0.1)            # raw spike, smooth surface: all kept
+    assert m.all()
+    m, e = oracle.mask(P, spiked, 0.1)            # the smoothed copy carries the spike
+    touching = ~(e <= 0.1)
+    assert 0 < touching.sum() < m.size and not m[touching].any() and m[~touching].all()
+    holed = P.copy()
+    holed[1, 2] = np.nan
+    m, _ = oracle.mask(holed, P, 0.1)             # validity from the raw copy
+    assert (m == 0).sum() == 6                    # the six triangles around an interior vertex
+
+
 def test_first_triangle_vertex_order_and_gid():
     """Algorithm 1: first = {p3, p2, p1}, second = {p1, p4, p3}; GID = 2 (u (N-1) + v) + k."""
     H, W = 3, 4
