@@ -51,3 +51,24 @@ def test_peaks_match_oracle(pl3d, seed):
         got_n, got_w = pl3d.pl3d_fastga_peaks(level, counts.astype(np.int32), 20.0, d_peak, max_peaks=64)
         assert np.array_equal(got_w, ref_w)
         assert np.abs(got_n - ref_n).max() < 1e-6
+
+
+def test_peaks_plateau_and_threshold_match_oracle(pl3d):
+    """The conventions the random histograms rarely meet: a two-cell plateau (one peak, the lower
+    index) and a count equal to v_min (no peak)."""
+    level = 2
+    V, F = fastga.icosahedron(level)
+    nb = fastga.neighbours(F)
+    a = 37
+    cases = []
+    c = np.zeros(len(F), np.int64)
+    c[a] = c[max(nb[a])] = 50
+    cases.append((c, 10.0))
+    c = np.zeros(len(F), np.int64)
+    c[a] = 20
+    cases += [(c, 20.0), (c, 19.0)]
+    for counts, v_min in cases:
+        ref_n, ref_w = fastga.peaks(counts, level, v_min=v_min, d_peak=0.01)
+        got_n, got_w = pl3d.pl3d_fastga_peaks(level, counts.astype(np.int32), v_min, 0.01, max_peaks=8)
+        assert np.array_equal(got_w, ref_w)
+        assert got_n.shape == ref_n.shape and (got_n.size == 0 or np.abs(got_n - ref_n).max() < 1e-6)

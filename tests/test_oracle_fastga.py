@@ -120,3 +120,23 @@ def test_peaks_find_planted_directions_and_merge_close_ones():
     assert np.allclose(pk2[0], mean / np.linalg.norm(mean))
     pk3, wt3 = fastga.peaks(c2, level, v_min=10, d_peak=0.3)
     assert len(pk3) == 2 and list(wt3) == [300, 100]
+
+
+def test_peak_plateau_and_threshold_by_hand():
+    """The peak rule as defined: a plateau of two neighbouring cells gives one peak, at its lower
+    index; a count equal to v_min is not above it."""
+    level = 2
+    V, F = fastga.icosahedron(level)
+    N = fastga.cell_normals(V, F)
+    nb = fastga.neighbours(F)
+    a = 37
+    b = max(nb[a])                      # a 1-ring neighbour with a higher index
+    counts = np.zeros(len(F), np.int64)
+    counts[a] = counts[b] = 50
+    pk, wt = fastga.peaks(counts, level, v_min=10, d_peak=0.01)
+    assert len(pk) == 1 and list(wt) == [50] and np.allclose(pk[0], N[a])
+    lone = np.zeros(len(F), np.int64)
+    lone[a] = 20
+    assert len(fastga.peaks(lone, level, v_min=20, d_peak=0.01)[0]) == 0
+    pk, wt = fastga.peaks(lone, level, v_min=19, d_peak=0.01)
+    assert len(pk) == 1 and list(wt) == [20] and np.allclose(pk[0], N[a])

@@ -1,5 +1,6 @@
 """The pins catch plausible mistakes: each case plants one slip in a temporary copy of the oracle's C
-source (on the CPU) and requires the pin suite to fail against it."""
+source, or of its Gaussian-accumulator module (on the CPU), and requires the pin suite to fail
+against it."""
 import os
 import shutil
 import subprocess
@@ -85,5 +86,38 @@ def test_planted_mistake_fails_a_pin(name, tmp_path):
     shutil.copy(os.path.join(ROOT, "pytest.ini"), tmp_path / "pytest.ini")
     (tmp_path / "oracle" / "pl3d_oracle.c").write_text(src.replace(old, new))
     r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_pins.py", "-q", "-x", "-p", "no:cacheprovider"],
+                       cwd=tmp_path, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 1 and "failed" in r.stdout, r.stdout[-2000:]
+
+
+FASTGA_MUTATIONS = {
+    "child_order_swapped": ("nxt += [(a, ab, ca), (ab, b, bc), (ca, bc, c), (ab, bc, ca)]",
+                            "nxt += [(ab, b, bc), (a, ab, ca), (ca, bc, c), (ab, bc, ca)]"),
+    "centre_child_reversed": ("nxt += [(a, ab, ca), (ab, b, bc), (ca, bc, c), (ab, bc, ca)]",
+                              "nxt += [(a, ab, ca), (ab, b, bc), (ca, bc, c), (ab, ca, bc)]"),
+    "midpoint_not_projected": ("V.append(p / np.linalg.norm(p))", "V.append(p / 2.0)"),
+    "cell_normals_not_unit": ("return n / np.linalg.norm(n, axis=1)[:, None]", "return n"),
+    "nearest_smallest_dot": ("out[s:s + chunk] = (normals[s:s + chunk] @ N.T).argmax(1)",
+                             "out[s:s + chunk] = (normals[s:s + chunk] @ N.T).argmin(1)"),
+    "sampling_offset": ("idx = np.arange(0, len(normals), stride)", "idx = np.arange(stride - 1, len(normals), stride)"),
+    "mask_ignored": ("ok &= np.asarray(mask).reshape(-1)[idx] != 0", "ok &= np.asarray(mask).reshape(-1)[idx] >= 0"),
+    "plateau_keeps_highest_index": ("(counts[i] == counts[j] and i < j)", "(counts[i] == counts[j] and i > j)"),
+    "plateau_drops_all": ("counts[i] > counts[j] or (counts[i] == counts[j] and i < j) for j in nb[i])",
+                          "counts[i] > counts[j] for j in nb[i])"),
+    "v_min_not_strict": ("counts[i] > v_min and all(", "counts[i] >= v_min and all("),
+    "merge_unweighted": ("w = counts[members].astype(np.float64)", "w = np.ones(len(members))"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(FASTGA_MUTATIONS))
+def test_planted_fastga_mistake_fails_a_pin(name, tmp_path):
+    old, new = FASTGA_MUTATIONS[name]
+    src = open(os.path.join(ROOT, "oracle", "fastga.py")).read()
+    assert src.count(old) == 1, f"mutation anchor for {name} not found exactly once"
+    for d in ("oracle", "tests"):
+        shutil.copytree(os.path.join(ROOT, d), tmp_path / d, ignore=shutil.ignore_patterns("*.so", "__pycache__"))
+    shutil.copy(os.path.join(ROOT, "pytest.ini"), tmp_path / "pytest.ini")
+    (tmp_path / "oracle" / "fastga.py").write_text(src.replace(old, new))
+    r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_fastga.py", "-q", "-x", "-p", "no:cacheprovider"],
                        cwd=tmp_path, capture_output=True, text=True, timeout=600)
     assert r.returncode == 1 and "failed" in r.stdout, r.stdout[-2000:]
