@@ -1,0 +1,143 @@
+"""The acceptance check itself (`oracle/compare.py`), on the CPU: the oracle's own result, cast to
+the device's FP32 types, passes with zero errors, and each planted deviation fails on the side of
+its bound the parity bar puts it -- so a GPU parity test cannot pass by a lax checker."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import compare
+import synth
+
+
+@pytest.fixture(scope="module")
+def case():
+    f = synth.depth_camera_scene(24, 32, seed=9, n_boxes=2)
+    p = oracle.OracleParams(**f.params)
+    ref = oracle.extract_planes(f.points, p, f.dominant_normals)
+    dev = dict(mask=ref["mask"].copy(), normals=ref["normals"].astype(np.float32), labels=ref["labels"].copy(),
+               groups=ref["groups"].copy(), points=ref["smoothed"].astype(np.float32))
+    return f, p, ref, dev
+
+
+def _copy(dev):
+    return {k: v.copy() for k, v in dev.items()}
+
+
+def _run(case, dev, ref=None):
+    f, p, r, _ = case
+    H, W = f.points.shape[:2]
+    return compare.compare(dev, r if ref is None else ref, p, H, W)
+
+
+def _largest_segment(ref):
+    seg, cnt = np.unique(ref["labels"][ref["labels"] >= 0], return_counts=True)
+    return seg[cnt.argmax()]
+
+
+def _rotate(n, t):
+    """n turned by t radians about an axis perpendicular to it."""
+    a = np.cross(n, [1.0, 0.0, 0.0])
+    if np.linalg.norm(a) < 0.5:
+        a = np.cross(n, [0.0, 1.0, 0.0])
+    a /= np.linalg.norm(a)
+    return n * np.cos(t) + np.cross(a, n) * np.sin(t)
+
+
+def test_angle_by_hand():
+    t = np.array([1e-7, 1e-4, 0.5, np.pi / 2, 3.0])
+    a = np.tile([1.0, 0.0, 0.0], (len(t), 1))
+    b = np.stack([np.cos(t), np.sin(t), np.zeros_like(t)], 1)
+    np.testing.assert_allclose(compare.angle_rad(a, b), t, rtol=1e-12)   # exact at small angles too
+    assert compare.angle_rad(a[:1], -a[:1])[0] == pytest.approx(np.pi)
+
+
+def test_the_oracle_itself_passes(case):
+    rep = _run(case, _copy(case[3]))
+    assert rep["mask_mismatch"] == 0 and rep["label_mismatch"] == 0 and rep["group_mismatch"] == 0
+    assert rep["normals_max_err_rad"] < 1e-6 and rep["points_max_err_m"] < 1e-6
+    assert rep["segments"] > 1
+
+
+def test_normal_bound(case):
+    ref = case[2]
+    well = ~np.isnan(ref["normals"][:, 0]) & ~ref["ill_conditioned"]
+    i = int(np.nonzero(well)[0][len(np.nonzero(well)[0]) // 2])
+    for t, ok in ((5e-5, True), (2e-4, False)):
+        dev = _copy(case[3])
+        dev["normals"][i] = _rotate(ref["normals"][i], t).astype(np.float32)
+        if ok:
+            assert _run(case, dev)["normals_max_err_rad"] == pytest.approx(t, rel=1e-2)
+        else:
+            with pytest.raises(AssertionError, match="normals off"):
+                _run(case, dev)
+    dev = _copy(case[3])
+    dev["normals"][i] = np.nan
+    with pytest.raises(AssertionError, match="NaN pattern"):
+        _run(case, dev)
+
+
+def test_point_bound(case):
+    ref = case[2]
+    ok = np.argwhere(~np.isnan(ref["smoothed"][..., 0]))
+    u, v = ok[len(ok) // 2]
+    for d, good in ((1e-5, True), (3e-5, False)):
+        dev = _copy(case[3])
+        dev["points"] = ref["smoothed"].copy()
+        dev["points"][u, v, 1] += d
+        if good:
+            assert _run(case, dev)["points_max_err_m"] == pytest.approx(d, rel=1e-6)
+        else:
+            with pytest.raises(AssertionError, match="smoothed points"):
+                _run(case, dev)
+
+
+def test_mask_is_bit_exact_except_near_the_edge_threshold(case):
+    ref = case[2]
+    i = int(np.nonzero(ref["mask"] == 1)[0][5])
+    dev = _copy(case[3])
+    dev["mask"][i] = 0
+    with pytest.raises(AssertionError, match="mask differs"):
+        _run(case, dev)
+    # the same flip on a triangle the oracle flags as near l_max is accepted
+    r2 = dict(ref)
+    r2["near_edge"] = ref["near_edge"].copy()
+    r2["near_edge"][i] = True
+    assert _run(case, dev, r2)["mask_mismatch"] == 1
+
+
+def test_labels_are_bit_exact(case):
+    ref = case[2]
+    members = np.nonzero(ref["labels"] == _largest_segment(ref))[0]
+    assert members.size > 1
+    dev = _copy(case[3])
+    dev["labels"][members[-1]] = -1                     # one triangle dropped from its segment
+    with pytest.raises(AssertionError, match="labels differ"):
+        _run(case, dev)
+    dev = _copy(case[3])
+    dev["labels"][members] = members[-1]                # same partition, not named by its smallest GID
+    with pytest.raises(AssertionError, match="labels differ"):
+        _run(case, dev)
+
+
+def test_group_change_needs_a_flag_and_then_the_labels_follow_it(case):
+    ref = case[2]
+    i = int(np.nonzero(ref["labels"] == _largest_segment(ref))[0][0])
+    dev = _copy(case[3])
+    dev["groups"][i] = 255
+    with pytest.raises(AssertionError, match="groups differ"):
+        _run(case, dev)
+    # flagged as a near tie: accepted, and the labels must be those of the substituted groups
+    r2 = dict(ref)
+    r2["near_tie"] = ref["near_tie"].copy()
+    r2["near_tie"][i] = True
+    G = ref["groups"].copy()
+    G[i] = 255
+    f = case[0]
+    p = case[1]
+    H, W = f.points.shape[:2]
+    dev["labels"] = oracle.label(G, H, W, ref["centroids"], ref["nd_unit"], p.max_offset, p.min_triangles)
+    rep = _run(case, dev, r2)
+    assert rep["group_mismatch"] == 1 and rep["label_mismatch"] == 0
+    dev["labels"] = ref["labels"].copy()                # the unsubstituted labels no longer match
+    with pytest.raises(AssertionError, match="labels differ"):
+        _run(case, dev, r2)
