@@ -141,3 +141,32 @@ def test_group_change_needs_a_flag_and_then_the_labels_follow_it(case):
     dev["labels"] = ref["labels"].copy()                # the unsubstituted labels no longer match
     with pytest.raises(AssertionError, match="labels differ"):
         _run(case, dev, r2)
+
+
+def test_near_threshold_flags_by_construction():
+    """The flags that let a decision differ are set exactly where the quantity lies within NEAR of
+    its threshold, never more widely. A noise-free affine plane does not move under the filters;
+    every triangle's normal is (0, 0, -1) and its longest edge the quad diagonal."""
+    H, W, h = 6, 7, 0.0625
+    u, v = np.meshgrid(np.arange(H, dtype=np.float64), np.arange(W, dtype=np.float64), indexing="ij")
+    P = np.stack([0.25 + v * h, -0.5 + u * h, np.full_like(u, 2.0)], -1).astype(np.float32)
+    diag = np.hypot(h, h)
+    n_tri = 2 * (H - 1) * (W - 1)
+    assert oracle.NEAR == 1e-5
+
+    def flags(max_edge, dots):
+        nd = np.array([[np.sqrt(1 - c * c), 0.0, -c] if k == 0 else [-np.sqrt(1 - c * c), 0.0, -c]
+                       for k, c in enumerate(dots)])
+        r = oracle.extract_planes(P, oracle.OracleParams(max_edge=max_edge, min_dot=0.95), nd, sensitivity=False)
+        np.testing.assert_allclose(r["edge"], diag, rtol=0, atol=1e-15)
+        np.testing.assert_allclose(r["normals"], np.tile([0.0, 0.0, -1.0], (n_tri, 1)), atol=1e-15)
+        return r["near_edge"], r["near_dot"], r["near_tie"]
+
+    e, d, t = flags(diag + 5e-6, [0.95 + 5e-6])
+    assert e.all() and d.all() and not t.any()          # one dominant normal: no runner-up
+    e, d, t = flags(diag + 5e-5, [0.95 + 5e-5])
+    assert not e.any() and not d.any() and not t.any()
+    e, d, t = flags(diag + 5e-5, [0.97, 0.97])          # two dominant normals at equal angles
+    assert not e.any() and not d.any() and t.all()
+    e, d, t = flags(diag + 5e-5, [0.97, 0.97 - 5e-5])
+    assert not t.any()
