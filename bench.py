@@ -336,8 +336,8 @@ def one_iteration_smoothing(pl3d, torch, ctx, keep, frames, stream) -> dict:
 def run_served(pl3d, torch, sensor_frames, rate: float, seconds: float, max_inflight: int, max_batch: int,
                seed: int) -> dict:
     """Replays a Poisson trace (total `rate` frames/s over the sensors, sensor of each arrival
-    uniform) against a server; latency = completion - scheduled arrival (the driver's own lag
-    included)."""
+    uniform) against a server; latency = completion - scheduled arrival (the replay's own lag,
+    submission - scheduled arrival, included)."""
     ring = 8
     srv = pl3d.pl3d_server_create(0, max_inflight=max_inflight, max_batch_frames=max_batch, hbm_bytes=24 << 30)
     host_pts = [[torch.from_numpy(f.points).pin_memory() for f in fs] for fs in sensor_frames]
@@ -413,7 +413,7 @@ def run_served(pl3d, torch, sensor_frames, rate: float, seconds: float, max_infl
             "mtri_s": tris / (t_end - t0) / 1e6, "achieved_fps": n / (t_end - t0),
             "mean_batch_frames": float(bf.mean()), "max_batch_frames": int(bf.max()),
             "batches": stats["batches"] - base_stats["batches"], "max_inflight": stats["max_inflight"],
-            "driver_lag_p99_ms": float(np.percentile(lags, 99)),
+            "replay_lag_p99_ms": float(np.percentile(lags, 99)),
             "all_ok": all(done[t]["status"] == 0 for t in lag)}
 
 
