@@ -242,19 +242,20 @@ int run_batch(pl3d_ctx* c, const pl3d_frame* frames, int n, cudaStream_t s) {
     }
     // per Laplacian pass: buffers sized for the largest box; staged ahead when some frame stages
     // by TMA, as many boxes as still fit two CTAs per SM
-    for (int c = 0; c < n_lap; ++c) {
+    for (int lp_pass = 0; lp_pass < n_lap; ++lp_pass) {
         int P = 0, dbufs = 1;
         bool tma = false;
         for (int i = 0; i < n; ++i) {
-            if (c >= fa[i].n_lap) continue;
-            P = std::max(P, lap_box_floats(fa[i].lap[c].halo, fa[i].lap[c].tile_h));
-            dbufs = std::max(dbufs, fa[i].lap[c].dbufs);
-            tma |= fa[i].lap[c].use_tma != 0;
+            if (lp_pass >= fa[i].n_lap) continue;
+            const LapPhase& ph = fa[i].lap[lp_pass];
+            P = std::max(P, lap_box_floats(ph.halo, ph.tile_h));
+            dbufs = std::max(dbufs, ph.dbufs);
+            tma |= ph.use_tma != 0;
         }
         const int ns = tma ? lap_stages_for(P, dbufs) : 1;
-        hdr->lap_buf[c] = P;
-        hdr->lap_stages[c] = ns;
-        hdr->lap_dbufs[c] = dbufs;
+        hdr->lap_buf[lp_pass] = P;
+        hdr->lap_stages[lp_pass] = ns;
+        hdr->lap_dbufs[lp_pass] = dbufs;
         smem = std::max(smem, lap_smem_for(P, ns, dbufs));
     }
     hdr->n = n;
