@@ -49,6 +49,7 @@ MUTATIONS = {
     "bilateral_border_replicated": ("                        int uu = u + du;\n                        if (uu < 0 || uu >= Hq) continue;",
                                     "                        int uu = u + du;\n                        uu = uu < 0 ? 0 : (uu >= Hq ? Hq - 1 : uu);"),
     "bilateral_in_place_sweep": ("const double* nj = cur + 3 * j;", "const double* nj = (j < i ? nxt : cur) + 3 * j;"),
+    "degenerate_threshold_zero": ("if (!(len > 1e-20)) {", "if (!(len > 0.0)) {"),
     "normal_not_unit": ("                nn[0] = nx / len;\n", "                nn[0] = nx;\n"),
     "classify_unsigned_dot": ("double s = n[0] * d[0] + n[1] * d[1] + n[2] * d[2];\n                if (s > max_similarity) {",
                               "double s = fabs(n[0] * d[0] + n[1] * d[1] + n[2] * d[2]);\n"

@@ -442,6 +442,17 @@ def test_tilted_plane_normals_face_sensor():
         np.testing.assert_allclose(np.abs(N @ nu), 1.0, atol=1e-5)
 
 
+def test_degenerate_triangle_has_no_normal_but_keeps_its_centroid():
+    """A triangle whose cross product is at most 1e-20 long has no normal (NaN), while its centroid
+    stays. Grids scaled to 1e-11 (cross ~ 2e-24 ... 1e-22) and to 1e-9 (cross ~ 1e-18) sit on
+    either side of the threshold."""
+    for scale, none in ((1e-11, True), (1e-9, False)):
+        P = oracle.widen(affine_grid(4, 5, o=(0.0, 0.0, 0.0), A=(0.0, 1.0, 0.0), B=(1.0, 0.0, 0.0))) * scale
+        C, N = oracle.triangle_geometry(P)
+        assert np.isfinite(C).all()
+        assert np.isnan(N).all() if none else np.isfinite(N).all()
+
+
 def test_nan_vertex_gives_nan_triangle():
     P = affine_grid(4, 4)
     P[1, 1, 2] = np.inf       # any non-finite coordinate invalidates the point
