@@ -1,6 +1,6 @@
 """The pins catch plausible mistakes: each case plants one slip in a temporary copy of the oracle's C
-source, or of its Gaussian-accumulator module (on the CPU), and requires the pin suite to fail
-against it."""
+source, of its Python layer (pipeline, near-threshold flags, segment lists and borders) or of its
+Gaussian-accumulator module (on the CPU), and requires the pin suite to fail against it."""
 import os
 import shutil
 import subprocess
@@ -123,4 +123,37 @@ def test_planted_fastga_mistake_fails_a_pin(name, tmp_path):
     (tmp_path / "oracle" / "fastga.py").write_text(src.replace(old, new))
     r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_fastga.py", "-q", "-x", "-p", "no:cacheprovider"],
                        cwd=tmp_path, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 1 and "failed" in r.stdout, r.stdout[-2000:]
+
+
+PY_MUTATIONS = {
+    "pipeline_mask_on_raw": ("m, edge = mask(raw, smoothed, p.max_edge)", "m, edge = mask(raw, raw, p.max_edge)"),
+    "pipeline_smoothing_skipped": ("smoothed = laplacian(raw, p.lap_kernel, p.lap_lambda, p.lap_iters)\n",
+                                   "smoothed = raw\n"),
+    "border_labels_by_t_index": ("T_labels = np.asarray(labels)[gid_of]", "T_labels = np.asarray(labels)[:len(T)]"),
+    "border_ignores_other_label": ("border = (T_labels >= 0) & ((tw < 0) | (other != T_labels))",
+                                   "border = (T_labels >= 0) & (tw < 0)"),
+    "border_on_unlabelled": ("border = (T_labels >= 0) & ((tw < 0) | (other != T_labels))",
+                             "border = (tw < 0) | (other != T_labels)"),
+    "segment_lists_gids_not_t": ("Tmap[gids[order]].astype(np.int32)", "gids[order].astype(np.int32)"),
+    "segment_lists_not_by_label": ('order = np.argsort(lab, kind="stable")', "order = np.arange(len(lab))"),
+    "near_edge_wider": ("< NEAR) & (p.max_edge > 0)", "< 10 * NEAR) & (p.max_edge > 0)"),
+    "near_tie_reversed": ("((np.where(has_second, best - second, 1.0)) < NEAR)",
+                          "((np.where(has_second, second - best, 1.0)) < NEAR)"),
+    "near_dot_wider": ("near_dot = has_best & (np.abs(np.where(has_best, best, 0.0) - p.min_dot) < NEAR)",
+                       "near_dot = has_best & (np.abs(np.where(has_best, best, 0.0) - p.min_dot) < 1e-3)"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(PY_MUTATIONS))
+def test_planted_pipeline_mistake_fails_a_pin(name, tmp_path):
+    old, new = PY_MUTATIONS[name]
+    src = open(os.path.join(ROOT, "oracle", "__init__.py")).read()
+    assert src.count(old) == 1, f"mutation anchor for {name} not found exactly once"
+    for d in ("oracle", "synth", "tests"):
+        shutil.copytree(os.path.join(ROOT, d), tmp_path / d, ignore=shutil.ignore_patterns("*.so", "__pycache__"))
+    shutil.copy(os.path.join(ROOT, "pytest.ini"), tmp_path / "pytest.ini")
+    (tmp_path / "oracle" / "__init__.py").write_text(src.replace(old, new))
+    r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_pins.py", "tests/test_compare_host.py", "-q",
+                        "-x", "-p", "no:cacheprovider"], cwd=tmp_path, capture_output=True, text=True, timeout=600)
     assert r.returncode == 1 and "failed" in r.stdout, r.stdout[-2000:]

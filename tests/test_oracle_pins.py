@@ -718,6 +718,47 @@ def test_segment_border_between_two_segments():
     assert bits.sum() == (2 * Hq + 2 * (Wq - 1)) + 2 * Hq
 
 
+@pytest.mark.parametrize("seed", range(3))
+def test_segment_border_with_holes_matches_the_implicit_twins(seed):
+    """With NaN holes T indices and GIDs part ways. A triangle's half-edge is a boundary one iff the
+    triangle is labelled and the quad-grid neighbour across that edge (found from the vertex lists,
+    not from HE) is missing, unlabelled or labelled otherwise."""
+    rng = np.random.default_rng(70 + seed)
+    H, W = 7, 9
+    pts = affine_grid(H, W)
+    pts[rng.random((H, W)) < 0.15] = np.nan
+    n = 2 * (H - 1) * (W - 1)
+    labels = rng.choice(np.array([-1, 0, 5, 9], np.int32), size=n)
+    out = oracle.mesh_outputs(pts, labels)
+    T = out["T"]
+    gid_of = np.nonzero(out["Tmap"] >= 0)[0]
+    owner = {}                                            # directed edge -> GID of its triangle
+    for t, g in enumerate(gid_of):
+        for e in range(3):
+            owner[(int(T[t, e]), int(T[t, (e + 1) % 3]))] = int(g)
+    bits = np.unpackbits(out["border"][:, None], axis=1, bitorder="little")[:, :3]
+    for t, g in enumerate(gid_of):
+        for e in range(3):
+            a, b = int(T[t, e]), int(T[t, (e + 1) % 3])
+            other = owner.get((b, a))
+            want = labels[g] >= 0 and (other is None or labels[other] != labels[g])
+            assert bits[t, e] == want, (t, e)
+
+
+def test_pipeline_measures_edges_after_smoothing():
+    """The whole path applies the l_max test to the smoothed points (Algorithm 4 after the
+    Laplacian): a spike that smoothing pulls back keeps triangles the raw spike would reject."""
+    P = affine_grid(6, 7)
+    P[3, 3, 2] += 0.2
+    p = oracle.OracleParams(lap_iters=5, max_edge=0.15, min_dot=0.5)
+    r = oracle.extract_planes(P, p, np.array([[0.0, 0.0, -1.0]], np.float32), sensitivity=False)
+    raw = oracle.widen(P)
+    m_raw, _ = oracle.mask(raw, raw, 0.15)
+    m_smooth, _ = oracle.mask(raw, r["smoothed"], 0.15)
+    assert (m_raw == 0).sum() == 6 and m_smooth.all()   # the six triangles around the spike
+    assert np.array_equal(r["mask"], m_smooth)
+
+
 # ----------------------------------------------------------------------------- Algorithm 5, seeded
 
 
