@@ -73,6 +73,12 @@ MUTATIONS = {
                                    "if (bottom != -1) HE[3 * (int64_t)second + 1] = 3 * bottom;"),
     "halfedge_left_wrong_triangle": ("int32_t left = (v - 1 >= 0) ? Tmap[2 * ((int64_t)u * Wq + v - 1)] : -1;",
                                      "int32_t left = (v - 1 >= 0) ? Tmap[2 * ((int64_t)u * Wq + v - 1) + 1] : -1;"),
+    "seeded_dropped_triangles_released": (
+        "if (tri_min > 0 && tail <= (int64_t)tri_min)\n            for (int64_t a = 0; a < tail; ++a) labels[queue[a]] = -1;",
+        "if (tri_min > 0 && tail <= (int64_t)tri_min)\n            for (int64_t a = 0; a < tail; ++a) "
+        "labels[queue[a]] = a == 0 ? -1 : UNVISITED;"),
+    "seeded_tri_min_not_strict": ("if (tri_min > 0 && tail <= (int64_t)tri_min)\n            for",
+                                  "if (tri_min > 0 && tail < (int64_t)tri_min)\n            for"),
     "seeded_offset_from_previous_triangle": (
         "fabs(d[0] * (cj[0] - cs[0]) + d[1] * (cj[1] - cs[1]) + d[2] * (cj[2] - cs[2]))",
         "fabs(d[0] * (cj[0] - C[3 * t]) + d[1] * (cj[1] - C[3 * t + 1]) + d[2] * (cj[2] - C[3 * t + 2]))"),

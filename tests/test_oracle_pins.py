@@ -793,6 +793,27 @@ def test_seeded_growing_hand_case():
     assert np.array_equal(kept, labels)
 
 
+def test_seeded_growing_dropped_segment_stays_consumed():
+    """A segment dropped by tri_min keeps its triangles: a later seed does not take them. One quad
+    row, chain positions 0..7 at heights 0, 0, 0.25, 0.45, ... with ptp_max 0.3: seed 0 (position
+    1) takes positions 0 and 2 (GIDs 1 and 3) and stops at 0.45; with tri_min 3 that segment of 3
+    is dropped. Seed 2 (position 3, 0.45) then takes positions 3..7 but not GID 3 (0.25, within
+    0.3 of it), which stays consumed. With tri_min 2 the first segment is kept."""
+    nq = 4
+    H, W = 2, nq + 1
+    gid = np.arange(2 * nq)
+    pos = np.where(gid % 2 == 1, gid - 1, gid + 1)
+    z = np.array([0.0, 0.0, 0.25, 0.45, 0.45, 0.45, 0.45, 0.45])
+    C = np.zeros((2 * nq, 3))
+    C[:, 2] = z[pos]
+    G = np.zeros(2 * nq, np.uint8)
+    nd = np.array([[0.0, 0.0, 1.0]])
+    dropped, _ = oracle.label_seeded(G, H, W, C, nd, 0.3, tri_min=3)
+    assert list(dropped) == [-1, -1, 2, -1, 2, 2, 2, 2]
+    kept, _ = oracle.label_seeded(G, H, W, C, nd, 0.3, tri_min=2)
+    assert list(kept) == [0, 0, 2, 0, 2, 2, 2, 2]
+
+
 def test_seeded_growing_without_limit_is_the_components():
     f = synth.rgbd_120x160()
     op = oracle.OracleParams(**f.params)
