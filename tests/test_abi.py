@@ -178,3 +178,23 @@ def test_server_structs_and_config_checks(pl3d):
     assert L.pl3d_server_drain(None) == pl3d.PL3D_ERR_INVALID_ARG
     assert L.pl3d_server_get_stats(None, None) == pl3d.PL3D_ERR_INVALID_ARG
     L.pl3d_server_destroy(None)
+
+
+def test_static_entry_point_limits_before_any_cuda_call(pl3d):
+    """The allocation-free call refuses what its fixed scratch cannot hold -- frames above
+    640 x 480 points, more than one bilateral pass, the host-assisted seeded mode -- on the host,
+    before it touches the device (the device pointers here are placeholders never dereferenced)."""
+    L = pl3d.lib()
+    nd = np.array([[0, 0, 1]], np.float32)
+    dummy = 256
+
+    def call(H, W, **kw):
+        p = pl3d.make_params(**kw)
+        return L.pl3d_extract_planes_static(dummy, H, W, ctypes.byref(p), nd.ctypes.data, 1, dummy, dummy, dummy,
+                                            None)
+    assert call(481, 640) == pl3d.PL3D_ERR_INVALID_ARG          # 307,840 points > 307,200
+    assert call(640, 481) == pl3d.PL3D_ERR_INVALID_ARG
+    assert call(120, 160, bil_iters=12) == pl3d.PL3D_ERR_INVALID_ARG   # halo 12 > 6 quads: two passes
+    assert call(120, 160, flags=pl3d.PL3D_FLAG_SEED_PTP, max_offset=0.1) == pl3d.PL3D_ERR_UNSUPPORTED
+    assert call(1, 160) == pl3d.PL3D_ERR_INVALID_ARG
+    assert pl3d.pl3d_static_scratch_bytes() >= 307200 * 24
