@@ -34,6 +34,11 @@ def test_every_declared_symbol_is_exported(pl3d):
     assert not missing, missing
 
 
+def test_every_declared_function_has_a_same_named_wrapper(pl3d):
+    missing = [n for n in declared_functions() if not callable(getattr(pl3d, n, None))]
+    assert not missing, missing
+
+
 def test_library_is_sm103a_only(pl3d):
     from paper_2007_12065_gb300 import build
     assert "arch=compute_103a,code=sm_103a" in build.ARCH
