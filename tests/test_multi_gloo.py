@@ -55,3 +55,28 @@ def test_single_rank_needs_no_process_group():
     import bench
     assert bench.max_over_ranks(3.5, 1) == 3.5
     assert bench.aggregate_mtri_s(1_000_000, 1, 1.0) == 1000.0
+
+
+def test_reference_arm_prints_on_rank_zero_only():
+    """Under torchrun the oracle arm runs on rank 0 alone; every other rank exits 0 without work.
+    The line carries the fields of the contract (impl, cpu_baseline, e2e with no copies)."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cmd = [sys.executable, "bench.py", "--impl", "reference", "--workload", "rgbd_120x160", "--gpus", "2",
+           "--steps", "1", "--warmup", "3"]
+    out = {}
+    for rank in (0, 1):
+        env = dict(os.environ, RANK=str(rank), WORLD_SIZE="2", LOCAL_RANK=str(rank))
+        r = subprocess.run(cmd, cwd=root, env=env, capture_output=True, text=True, timeout=300)
+        assert r.returncode == 0, r.stderr[-2000:]
+        out[rank] = [l for l in r.stdout.splitlines() if l.strip()]
+    assert out[1] == []
+    assert len(out[0]) == 1
+    line = json.loads(out[0][0])
+    assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["unit"] == "Mtri/s"
+    assert line["value"] > 0 and line["cpu_baseline"]["value"] == line["value"]
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"] == {"value": line["value"], "unit": "Mtri/s", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
