@@ -297,6 +297,19 @@ def run_batched(pl3d, torch, dev, frames, reps: int) -> dict:
             "l2": "inputs (about 450 MB) larger than L2; no flush"}
 
 
+def one_iteration_work(name: str, px: int, tri: int) -> tuple[float, float]:
+    """(algorithmic bytes, FLOP) of one filter iteration over px points and tri triangles with
+    3 x 3 windows. Laplacian: read the points, write the displacement (12 + 12 B per point);
+    16 FLOP per window neighbour, 8 neighbours. Bilateral pass: read points and displacement
+    (24 B per point), write normal, mask, group and label (12 + 1 + 1 + 4 B per triangle); 26 FLOP
+    per window triangle, 18 of them."""
+    if name == "laplacian":
+        return 24.0 * px, 16.0 * 8 * px
+    if name == "bilateral":
+        return 24.0 * px + 18.0 * tri, 26.0 * 18 * tri
+    raise ValueError(name)
+
+
 def one_iteration_smoothing(pl3d, torch, ctx, keep, frames, stream) -> dict:
     """The smoothing filters at one iteration per pass over the whole batch (inputs far larger
     than L2), as an HBM-roofline figure: the Laplacian phase reads the points (12 B/px) and writes
@@ -324,8 +337,7 @@ def one_iteration_smoothing(pl3d, torch, ctx, keep, frames, stream) -> dict:
         t = pl3d.pl3d_read_timing(ctx, reset=True)
         pl3d.pl3d_set_timing(ctx, False)
         us = t[name][0] / t[name][1] * 1e3
-        nbytes = 24.0 * px if name == "laplacian" else 24.0 * px + 18.0 * tri
-        flop = 16.0 * 8 * px if name == "laplacian" else 26.0 * 18 * tri
+        nbytes, flop = one_iteration_work(name, px, tri)
         gbs = nbytes / (us * 1e-6) / 1e9
         out[name] = {"us": us, "algorithmic_bytes": nbytes, "achieved_gbs": gbs,
                      "hbm_frac": gbs / float(peaks["hbm_gbs"]), "hbm_floor_us": nbytes / float(peaks["hbm_gbs"]) / 1e3,

@@ -72,3 +72,14 @@ def test_committed_profile_carries_a_traffic_figure():
     text = open(os.path.join(bench.ROOT, "profiles", "frame_kernel_rgbd_480x640.md")).read()
     keys = [line.split(":")[0].strip() for line in text.splitlines() if ":" in line]
     assert "traffic_bytes_per_launch" in keys and "kernel_sources_sha256" in keys
+
+
+def test_one_iteration_work_by_hand():
+    # a 480 x 640 frame: 307,200 points, 612,162 triangles
+    px, tri = 480 * 640, 612162
+    b, f = bench.one_iteration_work("laplacian", px, tri)
+    assert b == 24 * 307200 == 7372800 and f == 128 * 307200
+    b, f = bench.one_iteration_work("bilateral", px, tri)
+    assert b == 24 * 307200 + 18 * 612162 and f == 468 * 612162
+    with pytest.raises(ValueError):
+        bench.one_iteration_work("merge", px, tri)
