@@ -324,9 +324,10 @@ def extract_planes(points: np.ndarray, params, dominant_normals: np.ndarray, sen
     Keys: smoothed [H,W,3], centroids [T,3], normals_raw [T,3], normals [T,3], mask [T] u8,
     edge [T], groups [T] u8, best [T], second [T], labels [T] i32, nd_unit [K,3],
     near_edge / near_dot / near_tie [T] bool (decisions within NEAR of a threshold),
-    ill_conditioned [T] bool (sensitivity=True: the normal moves by more than ILL_CONDITIONED_RAD
-    when the Laplacian updates and bilateral sums are perturbed by JITTER relative -- FP32
-    arithmetic cannot be expected to reproduce it to the 1e-4 rad bound).
+    sensitivity [T] FP64 (sensitivity=True: the largest angle by which the normal moves when the
+    Laplacian updates and bilateral sums are perturbed by JITTER relative, over the JITTER_SEEDS
+    runs; 0 without a normal), ill_conditioned [T] bool (sensitivity > ILL_CONDITIONED_RAD: FP32
+    arithmetic cannot be expected to reproduce that normal to the 1e-4 rad bound).
     """
     p = params
     H, W = points.shape[:2]
@@ -349,8 +350,8 @@ def extract_planes(points: np.ndarray, params, dominant_normals: np.ndarray, sen
     has_second = has_best & np.isfinite(second)
     near_tie = has_second & ((np.where(has_second, best - second, 1.0)) < NEAR)
     ill = np.zeros(m.shape[0], bool)
+    ang = np.zeros(m.shape[0])
     if sensitivity:
-        ang = np.zeros(m.shape[0])
         for seed in JITTER_SEEDS:
             Sj = laplacian(raw, p.lap_kernel, p.lap_lambda, p.lap_iters, JITTER, seed)
             Cj, Nj0 = triangle_geometry(Sj)
@@ -361,4 +362,4 @@ def extract_planes(points: np.ndarray, params, dominant_normals: np.ndarray, sen
         ill = ang > ILL_CONDITIONED_RAD
     return dict(smoothed=smoothed, centroids=C, normals_raw=N0, normals=N, mask=m, edge=edge, groups=G,
                 best=best, second=second, labels=labels, nd_unit=nd_unit, near_edge=near_edge,
-                near_dot=near_dot, near_tie=near_tie, ill_conditioned=ill, ptp_margin=ptp_margin)
+                near_dot=near_dot, near_tie=near_tie, ill_conditioned=ill, sensitivity=ang, ptp_margin=ptp_margin)

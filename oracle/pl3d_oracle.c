@@ -22,8 +22,8 @@
  *   orc_extract_triangles explicit triangle set T and map T_map      (Algorithm 1)
  *   orc_extract_halfedges explicit twin array HE                     (Algorithm 2)
  *
- * Readings taken where the paper is silent or garbled (each one is listed with
- * its reason in the design notes of the repository):
+ * Readings taken where the paper is silent or garbled, each with the reason
+ * it is taken:
  *   - Eq. 1 prints a product and an outward sign; the standard umbrella form
  *     v' = v + (lambda / W) * sum_j w_j (v_j - v) is used (Taubin, cited there).
  *   - Laplacian neighbours: the k x k image window minus the vertex itself,

@@ -170,3 +170,76 @@ def test_near_threshold_flags_by_construction():
     assert not e.any() and not d.any() and t.all()
     e, d, t = flags(diag + 5e-5, [0.97, 0.97 - 5e-5])
     assert not t.any()
+
+
+def _ill_ref(ref, i, sens):
+    r2 = dict(ref)
+    r2["ill_conditioned"] = ref["ill_conditioned"].copy()
+    r2["sensitivity"] = ref["sensitivity"].copy()
+    r2["ill_conditioned"][i] = True
+    r2["sensitivity"][i] = sens
+    return r2
+
+
+def _clear_triangle(case):
+    """A grouped triangle of the largest segment whose decisions are far from every threshold."""
+    f, p, ref, _ = case
+    members = np.nonzero(ref["labels"] == _largest_segment(ref))[0]
+    second = np.where(np.isfinite(ref["second"]), ref["second"], -2.0)
+    far = (ref["best"][members] - p.min_dot > 1e-2) & (ref["best"][members] - second[members] > 2e-2)
+    return int(members[far][0])
+
+
+def test_ill_conditioned_normals_are_held_to_their_own_bound(case):
+    """An ill-conditioned normal (sensitivity s > 2.5e-5 rad) may be off by ILL_FACTOR s, never
+    less than 1e-4 and never more than ILL_CAP_RAD: an error beyond that fails."""
+    ref = case[2]
+    i = _clear_triangle(case)
+    assert compare.ILL_FACTOR == 8.0 and compare.ILL_CAP_RAD == 1e-3
+    r2 = _ill_ref(ref, i, 5e-5)                          # bound 4e-4 rad
+    dev = _copy(case[3])
+    dev["normals"][i] = _rotate(ref["normals"][i], 3e-4).astype(np.float32)
+    rep = _run(case, dev, r2)
+    assert rep["ill_conditioned"] >= 1 and rep["ill_conditioned_max_err_rad"] == pytest.approx(3e-4, rel=1e-2)
+    assert rep["ill_conditioned_max_ratio"] == pytest.approx(6.0, rel=1e-2)
+    dev["normals"][i] = _rotate(ref["normals"][i], 5e-4).astype(np.float32)
+    with pytest.raises(AssertionError, match="ill-conditioned normals off"):
+        _run(case, dev, r2)
+    # however large the sensitivity, the bound stops at ILL_CAP_RAD
+    r3 = _ill_ref(ref, i, 1e-2)
+    dev["normals"][i] = _rotate(ref["normals"][i], 1e-2).astype(np.float32)
+    with pytest.raises(AssertionError, match="ill-conditioned normals off"):
+        _run(case, dev, r3)
+    # and never below the ordinary 1e-4 rad
+    r4 = _ill_ref(ref, i, 3e-6)
+    dev["normals"][i] = _rotate(ref["normals"][i], 9e-5).astype(np.float32)
+    _run(case, dev, r4)
+
+
+def test_ill_conditioned_group_changes_only_near_a_threshold(case):
+    """An ill-conditioned triangle's group may differ only where its bound reaches ang_min or the
+    runner-up's dot; elsewhere a group flip fails, and an accepted flip needs the rerun labels."""
+    f, p, ref, _ = case
+    i = _clear_triangle(case)
+    H, W = f.points.shape[:2]
+    r2 = _ill_ref(ref, i, 5e-5)                          # bound 4e-4: best is 1e-2 from ang_min
+    dev = _copy(case[3])
+    dev["groups"][i] = 255
+    with pytest.raises(AssertionError, match="groups differ"):
+        _run(case, dev, r2)
+    r3 = dict(r2)
+    r3["best"] = ref["best"].copy()
+    r3["best"][i] = p.min_dot + 3e-4                     # within the bound of ang_min
+    G = ref["groups"].copy()
+    G[i] = 255
+    dev["labels"] = oracle.label(G, H, W, ref["centroids"], ref["nd_unit"], p.max_offset, p.min_triangles)
+    rep = _run(case, dev, r3)
+    assert rep["ill_conditioned_group_flagged"] == 1 and rep["group_mismatch"] == 1
+    dev["labels"] = ref["labels"].copy()
+    with pytest.raises(AssertionError, match="labels differ"):
+        _run(case, dev, r3)
+    r4 = dict(r2)
+    r4["second"] = ref["second"].copy()
+    r4["second"][i] = ref["best"][i] - 7e-4              # within twice the bound of the best dot
+    dev["labels"] = oracle.label(G, H, W, ref["centroids"], ref["nd_unit"], p.max_offset, p.min_triangles)
+    assert _run(case, dev, r4)["ill_conditioned_group_flagged"] == 1

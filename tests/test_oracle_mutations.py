@@ -11,6 +11,9 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 MUTATIONS = {
+    "widen_nan_in_x_only": ("if (isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2])) {", "if (!isnan(p[0])) {"),
+    "widen_keeps_inf": ("if (isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2])) {",
+                        "if (!isnan(p[0]) && !isnan(p[1]) && !isnan(p[2])) {"),
     "laplacian_sign": ("vo[0] = vi[0] + j0 * (lambda * sx / wsum);", "vo[0] = vi[0] - j0 * (lambda * sx / wsum);"),
     "laplacian_weight": ("double w = 1.0 / d; /* Eq. 2 */", "double w = 1.0 / (d * d);"),
     "laplacian_border": ("int border = (u < r) || (u >= H - r) || (v < r) || (v >= W - r);",

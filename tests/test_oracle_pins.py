@@ -143,6 +143,42 @@ def test_extracted_triangles_are_exactly_the_valid_ones(seed):
     assert kept.size == want and np.array_equal(Tmap[kept], np.arange(want))
 
 
+def test_any_non_finite_coordinate_makes_the_point_invalid():
+    """Sections 3 and 4.2: a missing return leaves a non-finite point in the organized cloud, and
+    such a point is invalid whichever coordinate is non-finite -- inf in x, -inf in z, NaN in y
+    only or in z only. It widens to NaN in all three coordinates; Algorithm 1 keeps only the
+    triangles whose three corners have all coordinates finite (counted over the quads' corners);
+    the whole path gives the same outputs, bit for bit, as the frame with those points written
+    all-NaN (so no filter reads a finite coordinate of an invalid point)."""
+    f = synth.depth_camera_scene(12, 14, seed=77, n_boxes=1, nan_frac=0.0)
+    pts = f.points.copy()
+    hits = [((3, 4), 0, np.inf), ((5, 6), 1, np.nan), ((7, 8), 2, np.nan), ((8, 3), 2, -np.inf),
+            ((0, 5), 0, -np.inf), ((6, 11), 1, np.inf)]
+    for (u, v), c, val in hits:
+        pts[u, v, c] = val
+    ok = np.isfinite(pts).all(-1)
+    assert (~ok).sum() == len(hits)
+    wid = oracle.widen(pts)
+    assert np.isnan(wid[~ok]).all()
+    assert np.array_equal(wid[ok], pts[ok].astype(np.float64))
+    bad = ~ok
+    H, W = bad.shape
+    want = sum(int(not (bad[u, v] or bad[u, v + 1] or bad[u + 1, v + 1])) +
+               int(not (bad[u, v] or bad[u + 1, v + 1] or bad[u + 1, v]))
+               for u in range(H - 1) for v in range(W - 1))
+    T, _ = oracle.extract_triangles(wid)
+    assert T.shape[0] == want
+    all_nan = pts.copy()
+    all_nan[bad] = np.nan
+    p = oracle.OracleParams(**f.params)
+    a = oracle.extract_planes(pts, p, f.dominant_normals, sensitivity=False)
+    b = oracle.extract_planes(all_nan, p, f.dominant_normals, sensitivity=False)
+    for k in ("smoothed", "normals", "mask", "groups", "labels"):
+        assert np.array_equal(a[k], b[k], equal_nan=a[k].dtype.kind == "f"), k
+    assert np.isnan(a["smoothed"][bad]).all()
+    assert (a["mask"] == 1).sum() <= want
+
+
 def test_edge_test_reads_smoothed_vertices_validity_reads_raw():
     """Algorithm 4 measures edges on the points after smoothing; Algorithm 1 takes validity from
     the raw cloud. A spike in one copy only moves the decision of the copy that is measured."""

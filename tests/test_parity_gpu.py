@@ -28,6 +28,16 @@ def env():
     ex.close()
 
 
+# Ill-conditioned normals (held to their own measured bound, not 1e-4 rad) may be at most this
+# fraction of a frame's triangles (plus a few): slivers at depth discontinuities are rare.
+ILL_CONDITIONED_CAP = 5e-5
+
+
+def assert_ill_conditioned_rare(rep, H, W):
+    n_tri = 2 * (H - 1) * (W - 1)
+    assert rep["ill_conditioned"] <= ILL_CONDITIONED_CAP * n_tri + 5, rep
+
+
 def run_pair(env, points, params: dict, nd, check=True):
     pl3d, ex, torch = env
     p = pl3d.make_params(**params)
@@ -49,6 +59,7 @@ def test_workload_parity(env, name):
     dev, ref, rep = run_pair(env, f.points, f.params, f.dominant_normals)
     print(name, rep)
     assert rep["segments"] > 10
+    assert_ill_conditioned_rare(rep, f.H, f.W)
 
 
 @pytest.mark.parametrize("H,W", [(720, 1280), (128, 2048), (240, 320)])
@@ -56,6 +67,7 @@ def test_large_and_mixed_sizes(env, H, W):
     f = synth.mixed_frame(H, W, seed=H * 7 + W)
     dev, ref, rep = run_pair(env, f.points, f.params, f.dominant_normals)
     print(H, W, rep)
+    assert_ill_conditioned_rare(rep, H, W)
 
 
 # ----------------------------------------------------------------------------- shapes and edge cases
