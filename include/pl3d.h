@@ -164,8 +164,25 @@ int pl3d_extract_planes_host(pl3d_ctx* ctx, const float* host_points, int H, int
                              const float* dominant_normals, int K, uint8_t* host_tri_mask, float* host_normals,
                              int32_t* host_labels, void* stream);
 
-/* Waits for `stream` and reports any pending CUDA error as PL3D_ERR_CUDA. */
+/* Waits for `stream` and reports any pending CUDA error as PL3D_ERR_CUDA. Then reads the
+ * context's device error word: when a bounded device wait of an earlier call gave up (a grid
+ * barrier or a TMA copy not completing within 1 s), the results of the calls since the last
+ * pl3d_sync are void; the word and the grid-barrier state are cleared and PL3D_ERR_TIMEOUT is
+ * returned, after which the context runs new calls normally. */
 int pl3d_sync(pl3d_ctx* ctx, void* stream);
+
+/* Self-test of the device-side timeout path (no counterpart in the paper). Enqueues on `stream`
+ * one small cooperative kernel that makes one of the library's bounded waits run out, with the
+ * limit limit_ns (1e5 .. 1e10 nanoseconds) instead of 1 s:
+ *   kind 1  the grid barrier of the path's kernels, in a grid of two CTAs one of which returns
+ *           without arriving;
+ *   kind 2  an mbarrier of the kind TMA copies complete on, which nothing arms (no copy issued).
+ * The waiting thread records the timeout in the device error word of `ctx` -- or, with ctx NULL,
+ * in that of the allocation-free entry point on the current device -- and returns; nothing
+ * faults, traps or waits without bound. The next pl3d_sync(ctx, stream) (pl3d_static_sync(stream)
+ * for NULL) then returns PL3D_ERR_TIMEOUT and clears the words. Returns PL3D_ERR_INVALID_ARG for
+ * another kind or limit, else the launch status. */
+int pl3d_selftest_wait_timeout(pl3d_ctx* ctx, int kind, int64_t limit_ns, void* stream);
 
 /* Static, human-readable text for a status code. Never NULL. */
 const char* pl3d_status_string(int status);
@@ -199,7 +216,9 @@ int64_t pl3d_launch_count(const pl3d_ctx* ctx);
  *   - The first call on a device (the current device) looks up the array's device address
  *     and configures the kernels; make that first call before any stream capture.
  *   - Every call uses the same array: calls whose work overlaps on the GPU race and must be
- *     serialised by the caller. Nothing needs clearing between calls.
+ *     serialised by the caller. Nothing needs clearing between calls that succeed.
+ *   - Device-side errors (a bounded wait that gave up) are recorded in the array's error word;
+ *     pl3d_static_sync reports them. Call it after the calls whose results you use.
  */
 #define PL3D_STATIC_MAX_POINTS 307200
 int pl3d_extract_planes_static(const float* points, int H, int W, const pl3d_params* params,
@@ -207,6 +226,13 @@ int pl3d_extract_planes_static(const float* points, int H, int W, const pl3d_par
                                int32_t* out_labels, void* stream);
 /* Bytes of device memory the allocation-free entry point reserves on every GPU. */
 size_t pl3d_static_scratch_bytes(void);
+/* pl3d_sync for the allocation-free entry point on the current device: waits for `stream`,
+ * reports a pending CUDA error as PL3D_ERR_CUDA, then reads the array's device error word. When
+ * a bounded wait of a call since the last check gave up, those calls' results are void: the
+ * error word and the grid-barrier words are cleared (a memset into the same array, enqueued on
+ * `stream` and waited for) and PL3D_ERR_TIMEOUT is returned; later calls run normally. Allocates
+ * nothing. */
+int pl3d_static_sync(void* stream);
 
 /*
  * Batches. The paper runs its pipeline one frame at a time; a batch runs the whole path of

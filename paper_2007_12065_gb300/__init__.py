@@ -149,6 +149,8 @@ def lib():
     L.pl3d_launch_count.restype = ctypes.c_int64
     L.pl3d_extract_planes_static.argtypes = [_vp, ctypes.c_int, ctypes.c_int, P, _vp, ctypes.c_int, _vp, _vp, _vp, _vp]
     L.pl3d_static_scratch_bytes.restype = ctypes.c_size_t
+    L.pl3d_static_sync.argtypes = [_vp]
+    L.pl3d_selftest_wait_timeout.argtypes = [_vp, ctypes.c_int, ctypes.c_int64, _vp]
     F = ctypes.POINTER(pl3d_frame)
     T = ctypes.POINTER(pl3d_tuning)
     L.pl3d_extract_planes_batched.argtypes = [_vp, F, ctypes.c_int, _vp]
@@ -351,6 +353,18 @@ def pl3d_static_scratch_bytes() -> int:
 
 
 PL3D_STATIC_MAX_POINTS = 307200
+
+
+def pl3d_static_sync(stream=None) -> int:
+    """Waits for the stream and reports a device-side timeout of the allocation-free calls."""
+    return _check(lib().pl3d_static_sync(_stream(stream)), "pl3d_static_sync")
+
+
+def pl3d_selftest_wait_timeout(ctx, kind: int, limit_ns: int, stream=None) -> int:
+    """Makes a bounded device wait run out (kind 1: grid barrier, 2: mbarrier); ctx None targets
+    the allocation-free entry point's error word. See include/pl3d.h."""
+    return _check(lib().pl3d_selftest_wait_timeout(ctx or None, int(kind), int(limit_ns), _stream(stream)),
+                  "pl3d_selftest_wait_timeout")
 
 
 class Batch:

@@ -241,6 +241,10 @@ int frame_launch(const FrameScratch& sc, const float* points, int H, int W, cons
                  uint8_t* out_groups, const Tuning& t, cudaStream_t s, int32_t* out_labels_copy = nullptr,
                  cudaEvent_t normals_ready = nullptr);
 
+// Device address of the allocation-free entry point's control words (barrier [2], error word,
+// pad) on the current device (pl3d_static.cu).
+int static_control_words(unsigned** ctl);
+
 // Grid size of a persistent launch: all resident CTAs (or ctas_per_sm per SM), at most `work`.
 int persistent_grid(const void* fn, size_t smem, int dev, const Tuning& t, long long work);
 

@@ -107,6 +107,8 @@ struct ServeSlot {
     bool busy = false;
     std::atomic<int64_t> t_done{0};       // set by the stream's host function
     int status = PL3D_OK;
+    int* h_err = nullptr;                 // page-locked copy of the context's device error word,
+                                          // taken after each batch (before the host function)
 };
 
 namespace {
@@ -167,6 +169,10 @@ int launch_slot(pl3d_server* S, ServeSlot* sl) {
             cudaMemcpyAsync(r.h_labels, f.out_labels, ntri * 4, cudaMemcpyDeviceToHost, sl->stream) != cudaSuccess)
             rc = PL3D_ERR_CUDA;
     }
+    // the batch's device error word (a bounded wait that gave up) travels with the results
+    if (rc == PL3D_OK && cudaMemcpyAsync(sl->h_err, sl->ctx->error(), sizeof(int), cudaMemcpyDeviceToHost,
+                                         sl->stream) != cudaSuccess)
+        rc = PL3D_ERR_CUDA;
     if (rc == PL3D_OK && cudaLaunchHostFunc(sl->stream, on_batch_done, sl) != cudaSuccess) rc = PL3D_ERR_CUDA;
     if (rc != PL3D_OK) {
         cudaGetLastError();
@@ -176,9 +182,16 @@ int launch_slot(pl3d_server* S, ServeSlot* sl) {
     return rc;
 }
 
-// Moves a finished slot's requests to the completion list (mu held).
+// Moves a finished slot's requests to the completion list (mu held). A batch whose device error
+// word was set (a grid-barrier or TMA wait gave up) completes with PL3D_ERR_TIMEOUT, and the
+// slot's control words start over before its next batch (ordered on the slot's stream).
 void retire_slot(pl3d_server* S, ServeSlot* sl) {
     const int64_t t = sl->t_done.load(std::memory_order_acquire);
+    if (sl->status == PL3D_OK && *sl->h_err != 0) {
+        sl->status = PL3D_ERR_TIMEOUT;
+        *sl->h_err = 0;
+        if (cudaMemsetAsync(sl->ctx->ctl, 0, 4 * sizeof(unsigned), sl->stream) != cudaSuccess) cudaGetLastError();
+    }
     for (const Request& r : sl->reqs) {
         pl3d_completion c;
         c.ticket = r.ticket;
@@ -252,6 +265,7 @@ void free_server(pl3d_server* S) {
     for (ServeSlot* sl : S->slots) {
         if (sl->stream) cudaStreamSynchronize(sl->stream);
         cudaFree(sl->arena);
+        if (sl->h_err) cudaFreeHost(sl->h_err);
         if (sl->ctx) pl3d_destroy(sl->ctx);
         if (sl->stream) cudaStreamDestroy(sl->stream);
         delete sl;
@@ -310,11 +324,13 @@ int pl3d_server_create(pl3d_server** out, const pl3d_server_config* cfg) {
         if ((rc = pl3d_create(&sl->ctx, cfg->device)) != PL3D_OK) break;
         cudaStream_t st = nullptr;
         if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess) sl->stream = st;
-        if (!sl->stream || cudaMalloc((void**)&sl->arena, S->arena_cap) != cudaSuccess) {
+        if (!sl->stream || cudaMalloc((void**)&sl->arena, S->arena_cap) != cudaSuccess ||
+            cudaHostAlloc((void**)&sl->h_err, sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
             cudaGetLastError();
             rc = PL3D_ERR_OUT_OF_MEMORY;
             break;
         }
+        *sl->h_err = 0;
         if (cfg->max_batch_frames > 1)
             rc = batch_reserve(sl->ctx, S->scratch_cap, cfg->max_batch_frames, sl->stream);
     }

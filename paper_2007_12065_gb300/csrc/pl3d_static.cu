@@ -17,9 +17,13 @@
 //
 // All calls share the one array: calls whose work overlaps on the GPU (different streams,
 // or host threads that do not order their streams) race on it and must be serialised by
-// the caller. Nothing in it needs clearing between calls: every scratch value is written before
-// it is read within a call, and the barrier words return to their starting state at the end of
-// each call (the array starts zeroed when the library's device code loads).
+// the caller. Nothing in it needs clearing between calls that succeed: every scratch value is
+// written before it is read within a call, and the barrier words return to their starting state
+// at the end of each call (the array starts zeroed when the library's device code loads). A
+// bounded device wait that gives up (grid barrier or TMA, 1 s) leaves the error word set and the
+// barrier's arrival count off; pl3d_static_sync reads the error word after the stream's work,
+// and when it is set clears it and the barrier words (plain copies and a memset into the same
+// array: still no allocation) and reports PL3D_ERR_TIMEOUT.
 #include <float.h>
 #include <math.h>
 
@@ -78,9 +82,46 @@ int setup_device(int dev, unsigned char** scratch) {
     return s.status;
 }
 
+constexpr size_t kCtlOffset = kDispBytes + kGroupBytes + kSizeBytes;
+
 }  // namespace
 
+namespace pl3d {
+
+// Device address of the allocation-free path's control words (barrier [2], error word, pad) on
+// the current device, after the same once-per-device set-up as the entry point.
+int static_control_words(unsigned** ctl) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return PL3D_ERR_CUDA;
+    }
+    unsigned char* scratch = nullptr;
+    const int rc = setup_device(dev, &scratch);
+    if (rc != PL3D_OK) return rc;
+    *ctl = reinterpret_cast<unsigned*>(scratch + kCtlOffset);
+    return PL3D_OK;
+}
+
+}  // namespace pl3d
+
 extern "C" size_t pl3d_static_scratch_bytes(void) { return kScratchBytes; }
+
+extern "C" int pl3d_static_sync(void* stream) {
+    unsigned* ctl = nullptr;
+    int rc = static_control_words(&ctl);
+    if (rc != PL3D_OK) return rc;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return PL3D_ERR_CUDA;
+    if (cudaGetLastError() != cudaSuccess) return PL3D_ERR_CUDA;
+    int err = 0;
+    if (cudaMemcpy(&err, ctl + 2, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return PL3D_ERR_CUDA;
+    if (err == 0) return PL3D_OK;
+    // a wait gave up: the affected calls' results are void; the control words start over
+    if (cudaMemsetAsync(ctl, 0, 4 * sizeof(unsigned), (cudaStream_t)stream) != cudaSuccess ||
+        cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess)
+        return PL3D_ERR_CUDA;
+    return PL3D_ERR_TIMEOUT;
+}
 
 extern "C" int pl3d_extract_planes_static(const float* points, int H, int W, const pl3d_params* p,
                                           const float* nd_host, int K, uint8_t* out_mask, float* out_normals,
@@ -105,7 +146,7 @@ extern "C" int pl3d_extract_planes_static(const float* points, int H, int W, con
     sc.carry[0] = sc.carry[1] = nullptr;
     sc.groups = scratch + kDispBytes;
     sc.sizes = reinterpret_cast<int32_t*>(scratch + kDispBytes + kGroupBytes);
-    unsigned* ctl = reinterpret_cast<unsigned*>(scratch + kDispBytes + kGroupBytes + kSizeBytes);
+    unsigned* ctl = reinterpret_cast<unsigned*>(scratch + kCtlOffset);
     sc.barrier = ctl;
     sc.error = reinterpret_cast<int*>(ctl + 2);
     sc.phase_ns = nullptr;

@@ -1,8 +1,9 @@
 // sync.cuh -- TMA tile loads, mbarriers and a grid-wide barrier, all with bounded waits.
 //
-// Every wait here gives up after kWaitLimitNs of %globaltimer time (and an iteration cap),
-// records the reason in the frame's device error word and returns, so a fault elsewhere
-// surfaces as PL3D_ERR_TIMEOUT on the host instead of a hung GPU.
+// Every wait here gives up after limit_ns of %globaltimer time (kWaitLimitNs unless the caller
+// passes a shorter limit, as the wait self-test kernel does) and an iteration cap, records the
+// reason in the frame's device error word and returns, so a fault elsewhere surfaces as
+// PL3D_ERR_TIMEOUT on the host instead of a hung GPU.
 #pragma once
 
 #include <cuda.h>
@@ -75,13 +76,14 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
 
 // Waits for the phase `parity` of `bar` to complete. On timeout it records the error, waits
 // once more (bounded) for the copies still in flight, and returns false.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, int* err) {
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, int* err,
+                                                  uint64_t limit_ns = kWaitLimitNs) {
     if (mbar_try_wait(bar, parity)) return true;
     for (int attempt = 0; attempt < 2; ++attempt) {
         const uint64_t t0 = global_ns();
         for (uint32_t i = 0; i < (1u << 24); ++i) {
             if (mbar_try_wait(bar, parity)) return attempt == 0;
-            if (global_ns() - t0 > kWaitLimitNs) break;
+            if (global_ns() - t0 > limit_ns) break;
         }
         if (attempt == 0) atomicOr(err, kErrTmaTimeout);
     }
@@ -111,7 +113,7 @@ __device__ __forceinline__ void red_release_gpu_add(unsigned* p, unsigned v) {
 // arriver, acquires everyone else's; the last arriver resets the count and opens the barrier
 // with a release add on the generation, which the others wait for with acquire loads. Global
 // writes made before the barrier are visible to every thread of the grid after it.
-__device__ __forceinline__ void grid_barrier(unsigned* bar, int* err) {
+__device__ __forceinline__ void grid_barrier(unsigned* bar, int* err, uint64_t limit_ns = kWaitLimitNs) {
     __syncthreads();
     if (threadIdx.x == 0) {
         const unsigned nblocks = gridDim.x * gridDim.y * gridDim.z;
@@ -122,7 +124,7 @@ __device__ __forceinline__ void grid_barrier(unsigned* bar, int* err) {
         } else {
             const uint64_t t0 = global_ns();
             for (uint32_t i = 1; ld_acquire_gpu(bar + 1) == g; ++i) {
-                if ((i & 63u) == 0u && global_ns() - t0 > kWaitLimitNs) {
+                if ((i & 63u) == 0u && global_ns() - t0 > limit_ns) {
                     atomicOr(err, kErrBarrierTimeout);
                     break;
                 }

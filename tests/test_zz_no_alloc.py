@@ -71,5 +71,41 @@ def test_static_entry_matches_context_entry_on_two_calls_in_a_row():
                                             torch.empty((n, 3), device="cuda"),
                                             torch.empty(n, dtype=torch.int32, device="cuda"))
         assert e.value.status == pl3d.PL3D_ERR_INVALID_ARG
+        pl3d.pl3d_static_sync()                          # no device-side error was recorded
     finally:
         pl3d.pl3d_destroy(ctx)
+
+
+def test_static_entry_allocates_nothing_and_keeps_its_bilateral_limit():
+    """Once the first call has loaded the library's device code (and with it the fixed array),
+    later calls leave the device's free memory unchanged. The fixed scratch has no carry buffers,
+    so a kernel-3 bilateral runs at most 6 iterations (one tile pass): 6 is accepted and matches
+    the context entry point, 7 is refused before anything is enqueued."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2007_12065_gb300 as pl3d
+    f = synth.depth_camera_scene(120, 160, seed=33, n_boxes=3, ramp=True)
+    H, W, n = f.H, f.W, f.n_triangles
+    nd = f.dominant_normals
+    pts = torch.from_numpy(f.points).cuda()
+    outs = [(torch.empty(n, dtype=torch.uint8, device="cuda"), torch.empty((n, 3), device="cuda"),
+             torch.empty(n, dtype=torch.int32, device="cuda")) for _ in range(2)]
+    p6 = pl3d.make_params(**dict(f.params, bil_iters=6))
+    pl3d.pl3d_extract_planes_static(pts, H, W, p6, nd, nd.shape[0], *outs[0])
+    pl3d.pl3d_static_sync()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        pl3d.pl3d_extract_planes_static(pts, H, W, p6, nd, nd.shape[0], *outs[1])
+        pl3d.pl3d_static_sync()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert all(torch.equal(a.nan_to_num(7.0), b.nan_to_num(7.0)) for a, b in zip(*outs))
+    ctx = pl3d.pl3d_create(0)
+    try:
+        _both(pl3d, torch, ctx, f, p6)
+    finally:
+        pl3d.pl3d_destroy(ctx)
+    with pytest.raises(pl3d.PL3DError) as e:
+        pl3d.pl3d_extract_planes_static(pts, H, W, pl3d.make_params(**dict(f.params, bil_iters=7)), nd,
+                                        nd.shape[0], *outs[1])
+    assert e.value.status == pl3d.PL3D_ERR_INVALID_ARG
