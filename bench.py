@@ -109,21 +109,40 @@ class ClockSampler:
 # ----------------------------------------------------------------------------- algorithmic work per launch
 
 
-def algorithmic_flop(H: int, W: int, prm: dict, K: int) -> dict:
-    """FP32 operations per frame the method defines (an FMA counts 2, an exp or rsqrt 1), phase by phase.
+# FLOP per unit of work, from the operation lists of the method's arithmetic (Eq. 1-6, Algorithm 4)
+# counted the way the FP32 peak counts them: an add, sub or mul is 1 FLOP, an FMA 2, an exp or
+# rsqrt 1 (the survey's per-unit lists write "3 FMA" for a squared norm and count each listed
+# operation once; the table below spells every one out at FMA = 2, the unit of the peak).
+FLOP_PER_UNIT = {
+    # per point, iteration and window neighbour: difference 3 sub (3), squared norm 1 mul + 2 FMA
+    # (5), 1/sqrt (1), weighted sum 3 FMA (6), weight sum 1 add (1)
+    "laplacian_neighbour": 16.0,
+    # per triangle, iteration and window triangle: centroid difference 3 sub + squared norm 5, normal
+    # difference 3 sub + squared norm 5, exponent 2 adds + 1 mul (3), exp (1), weighted sum 3 FMA (6)
+    "bilateral_window_triangle": 26.0,
+    # per triangle: 2 edges (6 sub), cross product 3 mul + 3 FMA (9), unit length 1 mul + 2 FMA +
+    # rsqrt + 3 mul (9), centroid 6 add + 3 mul (9) = 33, rounded down to 30 (edges shared in a quad)
+    "geometry_triangle": 30.0,
+    # per triangle and dominant normal: dot 1 mul + 2 FMA (5)
+    "group_dot": 5.0,
+}
 
-    Laplacian (Eq. 1-2), per point, iteration and window neighbour: difference 3, squared norm 5,
-    1/sqrt 1, weighted sum 6, weight sum 1 = 16. Bilateral (Eq. 3-6), per triangle, iteration and
-    window triangle: centroid difference 3 + squared 5, normal difference 3 + squared 5, exponent
-    3, exp 1, weighted sum 6 = 26. Geometry 30 per triangle; group assignment 5 per triangle and
-    dominant normal."""
+
+def algorithmic_flop(H: int, W: int, prm: dict, K: int) -> dict:
+    """FP32 FLOP per frame the method defines, phase by phase, from FLOP_PER_UNIT: Laplacian (Eq. 1-2)
+    per point, iteration and window neighbour (k^2 - 1 of them); bilateral (Eq. 3-6) per triangle,
+    iteration and window triangle (2 k^2 of them); geometry per triangle; group assignment per
+    triangle and dominant normal. The unit counts are returned with them (`units`)."""
     npx = H * W
     ntri = 2 * (H - 1) * (W - 1)
     kl, kb = prm["lap_kernel"], prm["bil_kernel"]
-    lap = 16.0 * (kl * kl - 1) * npx * prm["lap_iters"]
-    bil = 26.0 * 2 * kb * kb * ntri * prm["bil_iters"] + 30.0 * ntri
-    cls = 5.0 * K * ntri
-    return {"laplacian": lap, "bilateral": bil + cls, "total": lap + bil + cls}
+    units = {"laplacian_neighbour": (kl * kl - 1) * npx * prm["lap_iters"],
+             "bilateral_window_triangle": 2 * kb * kb * ntri * prm["bil_iters"],
+             "geometry_triangle": ntri, "group_dot": K * ntri}
+    f = {k: FLOP_PER_UNIT[k] * float(u) for k, u in units.items()}
+    lap = f["laplacian_neighbour"]
+    bil = f["bilateral_window_triangle"] + f["geometry_triangle"] + f["group_dot"]
+    return {"laplacian": lap, "bilateral": bil, "total": lap + bil, "units": units, "flop_per_unit": FLOP_PER_UNIT}
 
 
 def algorithmic_bytes(H: int, W: int) -> float:
@@ -300,13 +319,17 @@ def run_batched(pl3d, torch, dev, frames, reps: int) -> dict:
 def one_iteration_work(name: str, px: int, tri: int) -> tuple[float, float]:
     """(algorithmic bytes, FLOP) of one filter iteration over px points and tri triangles with
     3 x 3 windows. Laplacian: read the points, write the displacement (12 + 12 B per point);
-    16 FLOP per window neighbour, 8 neighbours. Bilateral pass: read points and displacement
-    (24 B per point), write normal, mask, group and label (12 + 1 + 1 + 4 B per triangle); 26 FLOP
-    per window triangle, 18 of them."""
+    8 window neighbours at FLOP_PER_UNIT. Bilateral pass: read points and displacement (24 B per
+    point), write normal, mask, group and label (12 + 1 + 1 + 4 B per triangle); 18 window
+    triangles at FLOP_PER_UNIT. Bilateral iteration alone (the filter step of Eq. 3-6 without
+    geometry, groups, outputs and labels): read normal and centroid, write normal (36 B per
+    triangle), the same 18 window triangles."""
     if name == "laplacian":
-        return 24.0 * px, 16.0 * 8 * px
+        return 24.0 * px, FLOP_PER_UNIT["laplacian_neighbour"] * 8 * px
     if name == "bilateral":
-        return 24.0 * px + 18.0 * tri, 26.0 * 18 * tri
+        return 24.0 * px + 18.0 * tri, FLOP_PER_UNIT["bilateral_window_triangle"] * 18 * tri
+    if name == "bilateral_iteration":
+        return 36.0 * tri, FLOP_PER_UNIT["bilateral_window_triangle"] * 18 * tri
     raise ValueError(name)
 
 
@@ -342,91 +365,52 @@ def one_iteration_smoothing(pl3d, torch, ctx, keep, frames, stream) -> dict:
         out[name] = {"us": us, "algorithmic_bytes": nbytes, "achieved_gbs": gbs,
                      "hbm_frac": gbs / float(peaks["hbm_gbs"]), "hbm_floor_us": nbytes / float(peaks["hbm_gbs"]) / 1e3,
                      "alu_floor_us": flop / fp32 * 1e6, "peak_source": f"{src} hbm_gbs"}
+        if name == "bilateral":
+            # the phase split by the tiles' stage totals (CTA time): its shares apply to the phase
+            stages = {k: t[f"bil_{k}_cta"][0] for k in ("staging", "geometry", "iterations", "finish", "labels")}
+            total = sum(stages.values()) or 1.0
+            out[name]["stages_us"] = {k: us * v / total for k, v in stages.items()}
+            it_us = us * stages["iterations"] / total
+            ib, iflop = one_iteration_work("bilateral_iteration", px, tri)
+            floor_us = max(ib / float(peaks["hbm_gbs"]) / 1e3, iflop / fp32 * 1e6)
+            out["bilateral_iteration"] = {"us": it_us, "algorithmic_bytes": ib, "flop": iflop,
+                                          "hbm_floor_us": ib / float(peaks["hbm_gbs"]) / 1e3,
+                                          "alu_floor_us": iflop / fp32 * 1e6, "floor_us": floor_us,
+                                          "frac_of_floor": floor_us / it_us,
+                                          "tflops": iflop / (it_us * 1e-6) / 1e12}
     return out
 
 
 def run_served(pl3d, torch, sensor_frames, rate: float, seconds: float, max_inflight: int, max_batch: int,
                seed: int) -> dict:
-    """Replays a Poisson trace (total `rate` frames/s over the sensors, sensor of each arrival
-    uniform) against a server; latency = completion - scheduled arrival (the replay's own lag,
-    submission - scheduled arrival, included)."""
+    """Replays a Poisson trace (total `rate` frames/s over the sensors, the sensor of each arrival
+    uniform) against a server through the library's own trace driver (pl3d_server_replay: the
+    submissions at their scheduled times and the collection of results run in native code);
+    latency = end of the result's copy-out - scheduled arrival (the driver's submit lag included)."""
     ring = 8
     srv = pl3d.pl3d_server_create(0, max_inflight=max_inflight, max_batch_frames=max_batch, hbm_bytes=24 << 30)
-    host_pts = [[torch.from_numpy(f.points).pin_memory() for f in fs] for fs in sensor_frames]
-    params = [pl3d.make_params(**fs[0].params) for fs in sensor_frames]
-    outs = []
+    sources = []
     for fs in sensor_frames:
         H, W = fs[0].points.shape[:2]
         n = 2 * (H - 1) * (W - 1)
-        outs.append([(torch.empty(n, dtype=torch.uint8).pin_memory(), torch.empty((n, 3)).pin_memory(),
-                      torch.empty(n, dtype=torch.int32).pin_memory()) for _ in range(ring)])
-    tri = [2 * (fs[0].points.shape[0] - 1) * (fs[0].points.shape[1] - 1) for fs in sensor_frames]
-
-    def submit(s, k):
-        f = sensor_frames[s][k % len(sensor_frames[s])]
-        H, W = f.points.shape[:2]
-        return pl3d.pl3d_server_submit(srv, host_pts[s][k % len(host_pts[s])], H, W, params[s], f.dominant_normals,
-                                       f.dominant_normals.shape[0], *outs[s][k % ring])
-
-    done = {}
-
-    def collect(wait_ms=0):
-        for c in pl3d.pl3d_server_poll(srv, max_n=4096, wait_ms=wait_ms):
-            done[c["ticket"]] = c
-
+        sources.append(dict(points=[torch.from_numpy(f.points).pin_memory() for f in fs],
+                            params=pl3d.make_params(**fs[0].params), dominant_normals=fs[0].dominant_normals,
+                            outputs=[(torch.empty(n, dtype=torch.uint8).pin_memory(), torch.empty((n, 3)).pin_memory(),
+                                      torch.empty(n, dtype=torch.int32).pin_memory()) for _ in range(ring)]))
+    rng = np.random.default_rng(seed)
+    n = max(1, int(rate * seconds))
+    t_arr = np.cumsum(rng.exponential(1.0 / rate, n))
+    which = rng.integers(0, len(sensor_frames), n)
     try:
-        for s in range(len(sensor_frames)):              # warm-up: every sensor once
-            submit(s, 0)
-        pl3d.pl3d_server_drain(srv)
-        collect()
-        done.clear()
-        base_stats = pl3d.pl3d_server_get_stats(srv)
-        rng = np.random.default_rng(seed)
-        n = max(1, int(rate * seconds))
-        t_arr = np.cumsum(rng.exponential(1.0 / rate, n))
-        which = rng.integers(0, len(sensor_frames), n)
-        count = [0] * len(sensor_frames)
-        ring_ticket = [[0] * ring for _ in sensor_frames]
-        lag, sensor_of = {}, {}
-        t0 = time.perf_counter()
-        for i in range(n):
-            target = t0 + t_arr[i]
-            while True:
-                now = time.perf_counter()
-                if now >= target:
-                    break
-                if target - now > 0.0015:
-                    time.sleep(0.0005)
-            s = int(which[i])
-            k = count[s]
-            count[s] += 1
-            prev = ring_ticket[s][k % ring]
-            while prev and prev not in done:            # the output buffers are still in use
-                collect(wait_ms=1)
-            t_sub = time.perf_counter()
-            tk = submit(s, k)
-            lag[tk] = t_sub - target
-            sensor_of[tk] = s
-            ring_ticket[s][k % ring] = tk
-            if i % 16 == 0:
-                collect()
-        pl3d.pl3d_server_drain(srv)
-        t_end = time.perf_counter()
-        collect()
-        stats = pl3d.pl3d_server_get_stats(srv)
+        rep = pl3d.pl3d_server_replay(srv, sources, t_arr, which)
     finally:
         pl3d.pl3d_server_destroy(srv)
-    lat = np.array([done[t]["latency_ms"] + 1e3 * lag[t] for t in lag])
-    lags = np.array(list(lag.values())) * 1e3
-    tris = sum(tri[sensor_of[t]] for t in lag)
-    bf = np.array([done[t]["batch_frames"] for t in lag])
-    return {"rate_fps": rate, "seconds": seconds, "requests": n, "p50_ms": float(np.percentile(lat, 50)),
-            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
-            "mtri_s": tris / (t_end - t0) / 1e6, "achieved_fps": n / (t_end - t0),
-            "mean_batch_frames": float(bf.mean()), "max_batch_frames": int(bf.max()),
-            "batches": stats["batches"] - base_stats["batches"], "max_inflight": stats["max_inflight"],
-            "replay_lag_p99_ms": float(np.percentile(lags, 99)),
-            "all_ok": all(done[t]["status"] == 0 for t in lag)}
+    return {"rate_fps": rate, "seconds": seconds, "requests": n, "p50_ms": rep["p50_ms"], "p90_ms": rep["p90_ms"],
+            "p99_ms": rep["p99_ms"], "max_ms": rep["max_ms"], "mean_ms": rep["mean_ms"], "mtri_s": rep["mtri_s"],
+            "achieved_fps": rep["achieved_fps"], "mean_batch_frames": rep["mean_batch_frames"],
+            "max_batch_frames": rep["max_batch_frames"], "batches": rep["batches"],
+            "max_inflight": rep["max_inflight"], "submit_lag_p99_ms": rep["submit_lag_p99_ms"],
+            "all_ok": rep["failed"] == 0 and rep["completed"] == n, "driver": "pl3d_server_replay (native)"}
 
 
 def served_sensor_frames(procs: int, seed: int = 105):
@@ -671,6 +655,10 @@ def run_pl3d(args):
                   "continuous_batching": run_served(pl3d, torch, sf, args.served_rate, args.served_seconds, 2, 64,
                                                     105),
                   "sequential_fifo": run_served(pl3d, torch, sf, args.served_rate, args.served_seconds, 1, 1, 105)}
+        # the low and the saturating end of the swept range, both modes on the same traces
+        served["rates"] = [{"mode": mode, **run_served(pl3d, torch, sf, r, args.served_seconds, mi, mb, 105)}
+                           for r in args.served_rates if r != args.served_rate
+                           for mode, mi, mb in (("continuous_batching", 2, 64), ("sequential_fifo", 1, 1))]
         if args.served_sweep:
             served["sweep"] = [{"mode": mode, **run_served(pl3d, torch, sf, r, 10.0, mi, mb, 105)}
                                for r in (200, 500, 1000, 2000, 5000)
@@ -697,6 +685,7 @@ def run_pl3d(args):
                 "traffic": recorded_traffic("frame_kernel", args.workload),
                 "peak_source": f"FP32 CUDA-core peak: {sm_count} SMs x 128 lanes x 2 FLOP x {mhz} MHz",
                 "avg_launch_us": avg_launch_s * 1e6, "work_per_launch": flop["total"], "work_unit": "FLOP",
+                "work_units": flop["units"], "flop_per_unit": flop["flop_per_unit"],
                 "hbm": {"algorithmic_bytes": nbytes, "achieved_gbs": nbytes / avg_launch_s / 1e9,
                         "peak_gbs": float(peaks["hbm_gbs"]), "peak_source": f"{peak_src} hbm_gbs"},
                 "phases_us": phases}
@@ -761,7 +750,9 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-frame batched workload")
     ap.add_argument("--no-served", action="store_true", help="skip the served (Poisson trace) workload")
     ap.add_argument("--served-rate", type=float, default=2000.0, help="frames/s of the served trace")
-    ap.add_argument("--served-seconds", type=float, default=2.0)
+    ap.add_argument("--served-seconds", type=float, default=5.0, help="seconds of every served trace")
+    ap.add_argument("--served-rates", type=float, nargs="*", default=[500.0, 5000.0],
+                    help="further served rates (frames/s), each run in both modes")
     ap.add_argument("--served-sweep", action="store_true", help="also sweep 200..5000 frames/s, 10 s each")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -191,8 +191,13 @@ const char* pl3d_status_string(int status);
  * pl3d_set_timing(ctx, 1) starts recording; pl3d_read_timing waits for the recorded events,
  * writes per-phase total milliseconds and launch counts for up to n_slots phases
  * (ms_out, launches_out may be NULL) and returns the number of phases (PL3D_TIMING_SLOTS),
- * clearing the totals when reset != 0. Phase order: see pl3d_timing_slot_name. */
-#define PL3D_TIMING_SLOTS 8
+ * clearing the totals when reset != 0. Phase order: see pl3d_timing_slot_name. Slots 0-3 are
+ * wall times of the phases (the device clock read by one CTA at each phase boundary; the
+ * single-iteration Laplacian kernel's own span counts as the Laplacian phase); slots 4-7 are CUDA
+ * event times of whole launches and copies; slots 8-12 ("..._cta") are the bilateral tiles' time
+ * in each stage -- staging, geometry, iterations, finish, tile labels -- summed over tiles (CTA
+ * time, not wall time: their shares split the bilateral phase). */
+#define PL3D_TIMING_SLOTS 13
 int pl3d_set_timing(pl3d_ctx* ctx, int enable);
 int pl3d_read_timing(pl3d_ctx* ctx, double* ms_out, int64_t* launches_out, int n_slots, int reset);
 const char* pl3d_timing_slot_name(int slot);
@@ -280,22 +285,33 @@ int pl3d_extract_planes_batched(pl3d_ctx* ctx, const pl3d_frame* frames, int n, 
  *   bil_fuse     the same for the bilateral (halo of 6 quads).
  *                Either depth is raised where needed so that a filter takes at most 8 passes.
  *   ctas_per_sm  resident CTAs per SM of the persistent launch (0 = as many as fit, at most 2).
- * pl3d_set_tuning(ctx, NULL) restores the defaults {0, 0, 0}. Negative fields are rejected.
+ *   lap_tile_h   Laplacian tile height in points, a multiple of 8 in [16, 64] (0 = 32, or 64 for a
+ *                single-iteration first pass); tiles are 32 points wide. A height whose buffers
+ *                would not fit two CTAs per SM for a pass falls back to 32 for that pass.
+ *   bil_tile_h   bilateral tile height in quads, a multiple of 8 in [8, 32] (0 = 32); tiles are
+ *                32 quads wide (a warp labels one tile row).
+ * Smaller tiles spread a frame over more CTAs (more tiles per CTA to balance their costs) at the
+ * price of more halo per output. pl3d_set_tuning(ctx, NULL) restores the defaults (all 0).
+ * Negative fields and other tile heights are rejected with PL3D_ERR_INVALID_ARG.
  */
 typedef struct pl3d_tuning {
     int32_t lap_fuse;
     int32_t bil_fuse;
     int32_t ctas_per_sm;
+    int32_t lap_tile_h;
+    int32_t bil_tile_h;
 } pl3d_tuning;
 
 int pl3d_set_tuning(pl3d_ctx* ctx, const pl3d_tuning* tuning);
 int pl3d_get_tuning(const pl3d_ctx* ctx, pl3d_tuning* tuning);
 
 /*
- * Autotuner: times the batch under every launch shape of a small candidate set (fused depths
- * of 1, 2 or 3 passes per filter, 1 or 2 CTAs per SM), `reps` timed runs each after one
- * untimed run, on `stream` with CUDA events, and keeps the fastest median as the context's
- * tuning. Writes the choice to *best and its median milliseconds to *best_ms (either may be
+ * Autotuner: times the batch under launch shapes, `reps` timed runs each after one untimed run,
+ * on `stream` with CUDA events, and keeps the fastest median as the context's tuning. It searches
+ * in two rounds: first the fused depths (1, 2 or 3 passes per filter, and one iteration per
+ * Laplacian pass when its window is 3 x 3) x 1 or 2 CTAs per SM at the default tile shapes, then,
+ * at the best of those, the tile heights (Laplacian 16, 32, 48, 64 points; bilateral 16, 24, 32
+ * quads; 32 wide). Writes the choice to *best and its median milliseconds to *best_ms (either may be
  * NULL). Runs the batch (1 + reps) times per candidate and once more under the choice, so the
  * outputs hold that run's (identical) results. Synchronises the stream. reps in [1, 50].
  */
@@ -375,6 +391,58 @@ int pl3d_server_poll(pl3d_server* srv, pl3d_completion* out, int max, int wait_m
 int pl3d_server_drain(pl3d_server* srv);
 int pl3d_server_get_stats(const pl3d_server* srv, pl3d_server_stats* out);
 void pl3d_server_destroy(pl3d_server* srv);
+
+/*
+ * Trace replay on a server (no counterpart in the paper): submits requests at scheduled arrival
+ * times from the calling thread, the way sensors would, collects their completions and reports
+ * latency from each scheduled arrival to the end of its result's copy-out, so that a host-side
+ * replay loop in another language does not add its own lag to the measured tail.
+ *
+ * A source is one sensor: n_variants page-locked host frames of H x W points (submitted in turn),
+ * its parameters and dominant normals, and `ring` sets of host output buffers (page-locked), used
+ * in turn; a request that would reuse a set still in flight waits for it first (counted as
+ * submit lag). Request i arrives arrival_s[i] seconds after the replay starts (non-decreasing)
+ * from source source_of[i]. Every source frame is submitted once and drained before the clock
+ * starts (warm-up). The call returns after the last completion.
+ *
+ * The report: requests, completed, failed (completions with an error status), batches launched
+ * and the largest batch and number of batches in flight during the replay; wall seconds from the
+ * first scheduled arrival to the last completion; latency percentiles p50 / p90 / p99 / max and
+ * the mean in milliseconds; Mtri/s over the wall time; achieved frames/s; mean frames per batch
+ * over the requests; and the p99 of the submit lag (submission time minus scheduled arrival).
+ * Returns PL3D_ERR_INVALID_ARG for bad arguments, else the first submit error, else PL3D_OK.
+ */
+typedef struct pl3d_replay_source {
+    const float* const* host_points;   /* [n_variants] frames, H * W * 3 floats each */
+    int32_t n_variants;
+    int32_t H, W;
+    int32_t K;
+    const pl3d_params* params;
+    const float* dominant_normals;      /* K * 3 */
+    int32_t ring;                       /* output buffer sets */
+    int32_t reserved;                   /* must be 0 */
+    uint8_t* const* host_mask;          /* [ring] */
+    float* const* host_normals;         /* [ring] */
+    int32_t* const* host_labels;        /* [ring] */
+} pl3d_replay_source;
+
+typedef struct pl3d_replay_report {
+    int64_t requests;
+    int64_t completed;
+    int64_t failed;
+    int64_t batches;
+    int64_t max_batch_frames;
+    int64_t max_inflight;
+    double seconds;
+    double p50_ms, p90_ms, p99_ms, max_ms, mean_ms;
+    double mtri_s;
+    double achieved_fps;
+    double mean_batch_frames;
+    double submit_lag_p99_ms;
+} pl3d_replay_report;
+
+int pl3d_server_replay(pl3d_server* srv, const pl3d_replay_source* sources, int n_sources, const double* arrival_s,
+                       const int32_t* source_of, int64_t n, pl3d_replay_report* report);
 
 /*
  * Explicit half-edge mesh and segment lists of one frame, the inputs of polygon extraction

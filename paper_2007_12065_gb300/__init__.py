@@ -25,7 +25,7 @@ PL3D_ERR_TIMEOUT = -4
 PL3D_ERR_UNSUPPORTED = -5
 PL3D_MAX_GROUPS = 254
 PL3D_NO_GROUP = 255
-PL3D_TIMING_SLOTS = 8
+PL3D_TIMING_SLOTS = 13
 PL3D_FLAG_SEED_PTP = 1
 
 
@@ -73,6 +73,8 @@ class pl3d_tuning(ctypes.Structure):
         ("lap_fuse", ctypes.c_int32),
         ("bil_fuse", ctypes.c_int32),
         ("ctas_per_sm", ctypes.c_int32),
+        ("lap_tile_h", ctypes.c_int32),
+        ("bil_tile_h", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:
@@ -102,6 +104,35 @@ class pl3d_completion(ctypes.Structure):
 class pl3d_server_stats(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int64) for name in ("submitted", "completed", "rejected", "batches", "triangles",
                                                    "max_batch_frames", "max_inflight", "slot_bytes")]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class pl3d_replay_source(ctypes.Structure):
+    """Mirror of the C struct pl3d_replay_source (one sensor of a trace replay)."""
+    _fields_ = [
+        ("host_points", ctypes.POINTER(ctypes.c_void_p)),
+        ("n_variants", ctypes.c_int32),
+        ("H", ctypes.c_int32),
+        ("W", ctypes.c_int32),
+        ("K", ctypes.c_int32),
+        ("params", ctypes.POINTER(pl3d_params)),
+        ("dominant_normals", ctypes.c_void_p),
+        ("ring", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("host_mask", ctypes.POINTER(ctypes.c_void_p)),
+        ("host_normals", ctypes.POINTER(ctypes.c_void_p)),
+        ("host_labels", ctypes.POINTER(ctypes.c_void_p)),
+    ]
+
+
+class pl3d_replay_report(ctypes.Structure):
+    _fields_ = ([(name, ctypes.c_int64) for name in ("requests", "completed", "failed", "batches", "max_batch_frames",
+                                                     "max_inflight")] +
+                [(name, ctypes.c_double) for name in ("seconds", "p50_ms", "p90_ms", "p99_ms", "max_ms", "mean_ms",
+                                                      "mtri_s", "achieved_fps", "mean_batch_frames",
+                                                      "submit_lag_p99_ms")])
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -172,6 +203,8 @@ def lib():
     L.pl3d_server_get_stats.argtypes = [_vp, ctypes.POINTER(pl3d_server_stats)]
     L.pl3d_server_destroy.argtypes = [_vp]
     L.pl3d_server_destroy.restype = None
+    L.pl3d_server_replay.argtypes = [_vp, ctypes.POINTER(pl3d_replay_source), ctypes.c_int, _vp, _vp, ctypes.c_int64,
+                                     ctypes.POINTER(pl3d_replay_report)]
     _lib = L
     return L
 
@@ -558,6 +591,51 @@ def pl3d_server_get_stats(srv) -> dict:
 
 def pl3d_server_destroy(srv) -> None:
     lib().pl3d_server_destroy(srv)
+
+
+def pl3d_server_replay(srv, sources: list, arrival_s, source_of) -> dict:
+    """Native trace replay (see include/pl3d.h). sources: dicts with keys points (list of pinned CPU
+    tensors, one per variant), params, dominant_normals, outputs (list of (mask, normals, labels)
+    pinned CPU tensors, the ring). arrival_s: non-decreasing seconds; source_of: source of each
+    arrival. Returns the report as a dict."""
+    import numpy as np
+    keep = []
+    arr_src = (pl3d_replay_source * len(sources))()
+    for i, sd in enumerate(sources):
+        pts = sd["points"]
+        H, W = int(pts[0].shape[0]), int(pts[0].shape[1])
+        for t in pts:
+            _check_tensor(t, "points", "torch.float32", H * W * 3, "cpu")
+        n_tri = 2 * (H - 1) * (W - 1)
+        for m, nrm, lab in sd["outputs"]:
+            _check_tensor(m, "out_tri_mask", "torch.uint8", n_tri, "cpu")
+            _check_tensor(nrm, "out_normals", "torch.float32", n_tri * 3, "cpu")
+            _check_tensor(lab, "out_labels", "torch.int32", n_tri, "cpu")
+        nd = _nd_host(sd["dominant_normals"])
+        P = (ctypes.c_void_p * len(pts))(*[_ptr(t) for t in pts])
+        M = (ctypes.c_void_p * len(sd["outputs"]))(*[_ptr(o[0]) for o in sd["outputs"]])
+        N = (ctypes.c_void_p * len(sd["outputs"]))(*[_ptr(o[1]) for o in sd["outputs"]])
+        L = (ctypes.c_void_p * len(sd["outputs"]))(*[_ptr(o[2]) for o in sd["outputs"]])
+        prm = sd["params"]
+        keep += [P, M, N, L, nd, prm]
+        a = arr_src[i]
+        a.host_points = ctypes.cast(P, ctypes.POINTER(ctypes.c_void_p))
+        a.n_variants = len(pts)
+        a.H, a.W, a.K = H, W, int(nd.shape[0])
+        a.params = ctypes.pointer(prm)
+        a.dominant_normals = _ptr(nd)
+        a.ring = len(sd["outputs"])
+        a.reserved = 0
+        a.host_mask = ctypes.cast(M, ctypes.POINTER(ctypes.c_void_p))
+        a.host_normals = ctypes.cast(N, ctypes.POINTER(ctypes.c_void_p))
+        a.host_labels = ctypes.cast(L, ctypes.POINTER(ctypes.c_void_p))
+    arr = np.ascontiguousarray(arrival_s, dtype=np.float64)
+    which = np.ascontiguousarray(source_of, dtype=np.int32)
+    rep = pl3d_replay_report()
+    _check(lib().pl3d_server_replay(srv, arr_src, len(sources), _ptr(arr), _ptr(which), int(arr.shape[0]),
+                                    ctypes.byref(rep)), "pl3d_server_replay")
+    del keep
+    return rep.as_dict()
 
 
 def pl3d_sync(ctx, stream=None) -> int:

@@ -43,13 +43,13 @@ int round4(int n) { return (n + 3) & ~3; }
 
 // Laplacian box: the tile, its halo and 3 spare rows for the 4-point strips that run past it.
 BoxGeom lap_box(int halo, int tile_h) { return {tile_h + 2 * halo + 3, round4(3 * (kTile + 2 * halo) + 3)}; }
-BoxGeom bil_box(int halo) { return {kTile + 2 * halo + 1, round4(3 * (kTile + 2 * halo + 1) + 3)}; }
+// Bilateral box: th x kTile quads, their halo, and one more row and column of points.
+BoxGeom bil_box(int halo, int th) { return {th + 2 * halo + 1, round4(3 * (kTile + 2 * halo + 1) + 3)}; }
 
-
-size_t bil_smem(int halo) {
-    const BoxGeom b = bil_box(halo);
-    const int rq = kTile + 2 * halo;
-    const int quads = align_floats(6 * (rq * rq + rq));
+size_t bil_smem(int halo, int th) {
+    const BoxGeom b = bil_box(halo, th);
+    const int rq = kTile + 2 * halo, rh = th + 2 * halo;
+    const int quads = align_floats(6 * (rh * rq + rq));
     const int boxes = 2 * align_floats(b.rows * b.cols);
     return 128 + 4 * (size_t)(2 * quads + (quads > boxes ? quads : boxes)) + 4 * (size_t)kTile * kTile +
            4 * (size_t)kExactCap;
@@ -167,6 +167,18 @@ int lap_stages_for(int box_floats, int dbufs) {
 // A single-iteration first pass reads no displacement: taller tiles, one displacement buffer.
 static bool lap_thin(int iters, bool first) { return first && iters == 1; }
 
+// Tile height of a Laplacian pass: the tuning's, else 64 for a single-iteration first pass and 32
+// otherwise; a height whose box and displacement buffers would not fit two CTAs per SM even
+// without staging ahead falls back to 32.
+static int lap_tile_h(int iters, bool first, int halo, int requested) {
+    const bool thin = lap_thin(iters, first);
+    const int dbufs = thin ? 1 : 2;
+    const int th = requested > 0 ? requested : (thin ? kLapThinTileH : kTile);
+    return lap_smem_for(lap_box_floats(halo, th), 1, dbufs) <= (size_t)kTwoCtaSmem ? th : kTile;
+}
+
+static int bil_tile_h(const Tuning& t) { return t.bil_tile_h > 0 ? t.bil_tile_h : kTile; }
+
 const float* final_disp(const FrameScratch& sc, const pl3d_params* p, const Tuning& t) {
     const int rl = p->lap_iters > 0 ? p->lap_kernel / 2 : 1;
     const int lf = fused_iters(p->lap_iters, kLapMaxHalo / rl, t.lap_fuse);
@@ -184,9 +196,9 @@ size_t frame_smem_bytes(const pl3d_params* p, const Tuning& t) {
     const int lh = li * rl;
     const bool thin = lap_thin(li, true);
     const int ld = thin ? 1 : 2;
-    const int lb = lap_box_floats(lh, thin ? kLapThinTileH : kTile);
+    const int lb = lap_box_floats(lh, lap_tile_h(li, true, lh, t.lap_tile_h));
     const size_t l = lap_smem_for(lb, lap_stages_for(lb, ld), ld);   // an upper bound: several stages need TMA
-    const size_t b = bil_smem((p->bil_iters < bf ? p->bil_iters : bf) * rb);
+    const size_t b = bil_smem((p->bil_iters < bf ? p->bil_iters : bf) * rb, bil_tile_h(t));
     return l > b ? l : b;
 }
 
@@ -199,7 +211,7 @@ int bilateral_passes(const pl3d_params* p, const Tuning& t) {
 cudaError_t frame_configure() {
     const int lb = lap_box_floats(kLapMaxHalo, kTile), lt = lap_box_floats(1 * 3, kLapThinTileH);
     const size_t lap_need = std::max(lap_smem_for(lb, lap_stages_for(lb, 2), 2), lap_smem_for(lt, lap_stages_for(lt, 1), 1));
-    const size_t need = lap_need > bil_smem(kBilMaxHalo) ? lap_need : bil_smem(kBilMaxHalo);
+    const size_t need = std::max({lap_need, (size_t)kTwoCtaSmem, bil_smem(kBilMaxHalo, kTile)});
     for (int rl = 1; rl <= 3; ++rl)
         for (int rb = 1; rb <= 3; ++rb)
             for (const void* fn : {kernel_for(rl, rb), batch_kernel_for(rl, rb)}) {
@@ -210,6 +222,13 @@ cudaError_t frame_configure() {
                                              cudaSharedmemCarveoutMaxShared);
                 if (e != cudaSuccess) return e;
             }
+    // the single-iteration Laplacian keeps its rings in static shared memory: all of it as shared
+    // memory, so that its CTAs fit as many per SM as their registers allow
+    for (bool with_d : {false, true}) {
+        const cudaError_t e = cudaFuncSetAttribute(lap1_kernel_for(with_d), cudaFuncAttributePreferredSharedMemoryCarveout,
+                                                   cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
+    }
     return cudaSuccess;
 }
 
@@ -235,7 +254,7 @@ int frame_build(FrameArgs& a, FramePlan& plan, const FrameScratch& sc, const flo
         ph.iters = remaining < lfuse ? remaining : lfuse;
         ph.halo = ph.iters * rl;
         const bool thin = lap_thin(ph.iters, a.n_lap == 0);
-        ph.tile_h = thin ? kLapThinTileH : kTile;
+        ph.tile_h = lap_tile_h(ph.iters, a.n_lap == 0, ph.halo, t.lap_tile_h);
         ph.tiles = div_up(H, ph.tile_h) * div_up(W, kTile);
         ph.dbufs = thin ? 1 : 2;
         ph.box = lap_box(ph.halo, ph.tile_h);
@@ -260,6 +279,8 @@ int frame_build(FrameArgs& a, FramePlan& plan, const FrameScratch& sc, const flo
     const int bfuse = fused_iters(p->bil_iters, kBilMaxHalo / rb, t.bil_fuse);
     const int nb = bilateral_passes(p, t);
     if (nb > kMaxPasses) return PL3D_ERR_UNSUPPORTED;
+    const int bth = bil_tile_h(t);
+    a.bil_th = bth;
     if (nb > 1 && (!sc.carry[0] || !sc.carry[1])) return PL3D_ERR_INVALID_ARG;
     int bremaining = p->bil_iters;
     for (int c = 0; c < nb; ++c) {
@@ -267,13 +288,13 @@ int frame_build(FrameArgs& a, FramePlan& plan, const FrameScratch& sc, const flo
         ph.iters = bremaining < bfuse ? bremaining : bfuse;
         bremaining -= ph.iters;
         ph.halo = ph.iters * rb;
-        ph.box = bil_box(ph.halo);
+        ph.box = bil_box(ph.halo, bth);
         ph.first = c == 0;
         ph.last = c + 1 == nb;
         ph.carry_in = c > 0 ? sc.carry[(c - 1) & 1] : nullptr;
         ph.carry_out = c + 1 < nb ? sc.carry[c & 1] : nullptr;
         ph.use_tma = c == 0 && tma_ok && aligned16(a.disp);
-        const size_t m = bil_smem(ph.halo);
+        const size_t m = bil_smem(ph.halo, bth);
         smem = m > smem ? m : smem;
     }
     a.n_bil = nb;
@@ -316,9 +337,9 @@ int frame_build(FrameArgs& a, FramePlan& plan, const FrameScratch& sc, const flo
     plan.smem = smem;
     plan.tiles_lap = 0;   // the most tiles of any Laplacian pass
     for (int c = 0; c < a.n_lap; ++c) plan.tiles_lap = std::max(plan.tiles_lap, a.lap[c].tiles);
-    plan.tiles_bil = div_up(H - 1, kTile) * div_up(W - 1, kTile);
+    plan.tiles_bil = div_up(H - 1, bth) * div_up(W - 1, kTile);
     const int Hq = H - 1, Wq = W - 1;
-    plan.merge_items = (long long)(div_up(Hq, kTile) - 1) * Wq + (long long)(div_up(Wq, kTile) - 1) * Hq;
+    plan.merge_items = (long long)(div_up(Hq, bth) - 1) * Wq + (long long)(div_up(Wq, kTile) - 1) * Hq;
     plan.tris = 2LL * Hq * Wq;
     return PL3D_OK;
 }
@@ -335,10 +356,24 @@ int persistent_grid(const void* fn, size_t smem, int dev, const Tuning& t, long 
     return work < resident ? (int)(work > 0 ? work : 1) : resident;
 }
 
+bool lap1_eligible(const FrameArgs& a, int rl) {
+    if (rl != 1) return false;
+    for (int c = 0; c < a.n_lap; ++c)
+        if (a.lap[c].iters > 1) return false;
+    return true;
+}
+
+int lap1_grid(int dev, bool with_d, long long tasks) {
+    const int resident = resident_ctas(lap1_kernel_for(with_d), 0, dev);
+    if (resident <= 0 || tasks < 0) return resident;
+    const long long need = (tasks + kThreads / 32 - 1) / (kThreads / 32);
+    return need < resident ? (int)(need > 0 ? need : 1) : resident;
+}
+
 int frame_launch(const FrameScratch& sc, const float* points, int H, int W, const pl3d_params* p, const float* nd_host,
                  int K, uint8_t* out_mask, float* out_normals, int32_t* out_labels, float* out_points,
                  uint8_t* out_groups, const Tuning& t, cudaStream_t s, int32_t* out_labels_copy,
-                 cudaEvent_t normals_ready) {
+                 cudaEvent_t normals_ready, int* launches) {
     static_assert(sizeof(FrameArgs) < 32000, "kernel parameters must fit the 32 KB parameter space");
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return PL3D_ERR_CUDA;
@@ -350,6 +385,29 @@ int frame_launch(const FrameScratch& sc, const float* points, int H, int W, cons
     const int work = plan.tiles_lap > plan.tiles_bil ? plan.tiles_lap : plan.tiles_bil;
     const int grid = persistent_grid(plan.frame_fn, plan.smem, dev, t, work);
     if (grid <= 0) return PL3D_ERR_CUDA;
+    int n_launched = 0;
+    if (lap1_eligible(a, plan.rl)) {
+        // the Laplacian passes as kernels of their own; the persistent kernel starts at the bilateral
+        for (int c = 0; c < a.n_lap; ++c) {
+            const LapPhase& ph = a.lap[c];
+            Lap1Args la;
+            memset(&la, 0, sizeof(la));
+            la.one = Lap1Frame{points, ph.d_in, ph.d_out, ph.export_points, H, W, ph.iters, a.lambda};
+            la.pass = c;
+            la.stamp = sc.phase_ns ? sc.phase_ns + 4 : nullptr;
+            la.phase_ns = sc.phase_ns;
+            const bool with_d = ph.d_in != nullptr;
+            const int g = lap1_grid(dev, with_d, lap1_tasks(H, W));
+            if (g <= 0) return PL3D_ERR_CUDA;
+            void* largs[1] = {&la};
+            if (cudaLaunchKernel(lap1_kernel_for(with_d), dim3(g), dim3(kThreads), largs, 0, s) != cudaSuccess) {
+                cudaGetLastError();
+                return PL3D_ERR_CUDA;
+            }
+            ++n_launched;
+        }
+        a.n_lap = 0;
+    }
     void* args[1] = {&a};
     // one launch, or two with the event between them: the first ends once mask, normals and
     // groups are final, the second joins the segments across tiles (the same arguments)
@@ -359,8 +417,10 @@ int frame_launch(const FrameScratch& sc, const float* points, int H, int W, cons
             cudaGetLastError();
             return PL3D_ERR_CUDA;
         }
+        ++n_launched;
         if (part == 1 && cudaEventRecord(normals_ready, s) != cudaSuccess) return PL3D_ERR_CUDA;
     }
+    if (launches) *launches = n_launched;
     return PL3D_OK;
 }
 

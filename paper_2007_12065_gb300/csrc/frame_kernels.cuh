@@ -120,36 +120,51 @@ struct LapAcc {
     float sx, sy, sz, ws;        // weighted sums
 };
 
+// The Laplacian arithmetic below is written with explicit rounding intrinsics (no contraction
+// left to the compiler), so that every kernel that evaluates Eq. 1-2 -- the fused tile passes and
+// the single-iteration pass (lap1.cu) -- gives the same bits for the same point.
+
 // Difference q - p of two smoothed points, input and displacement parts subtracted separately.
 template <bool WITH_D>
 __device__ __forceinline__ void lap_diff(const LapPt& p, const LapPt& q, float& ex, float& ey, float& ez) {
     if (WITH_D) {
-        ex = (q.x - p.x) + (q.dx - p.dx);
-        ey = (q.y - p.y) + (q.dy - p.dy);
-        ez = (q.z - p.z) + (q.dz - p.dz);
+        ex = __fadd_rn(__fsub_rn(q.x, p.x), __fsub_rn(q.dx, p.dx));
+        ey = __fadd_rn(__fsub_rn(q.y, p.y), __fsub_rn(q.dy, p.dy));
+        ez = __fadd_rn(__fsub_rn(q.z, p.z), __fsub_rn(q.dz, p.dz));
     } else {
-        ex = q.x - p.x;
-        ey = q.y - p.y;
-        ez = q.z - p.z;
+        ex = __fsub_rn(q.x, p.x);
+        ey = __fsub_rn(q.y, p.y);
+        ez = __fsub_rn(q.z, p.z);
     }
 }
 
 // Eq. 2: w = 1 / |v_j - v|; a neighbour at distance 0 is skipped. An invalid point holds
-// kInvalidCoord: the squared distance overflows to +inf and rsqrt(+inf) = 0.
+// kInvalidCoord: the squared distance overflows to +inf and rsqrt(+inf) = 0. A difference and its
+// negation give the same weight (w_ij = w_ji).
 __device__ __forceinline__ float lap_weight(float ex, float ey, float ez) {
-    const float d2 = ex * ex + ey * ey + ez * ez;
+    const float d2 = fmaf(ez, ez, fmaf(ey, ey, __fmul_rn(ex, ex)));
     return d2 > 0.f ? rsqrt_approx(d2) : 0.f;
+}
+
+// s += w e for a neighbour difference e and its weight w (the centre's sums of Eq. 1).
+__device__ __forceinline__ void lap_accumulate(float& sx, float& sy, float& sz, float& ws, float w, float ex, float ey,
+                                               float ez) {
+    sx = fmaf(w, ex, sx);
+    sy = fmaf(w, ey, sy);
+    sz = fmaf(w, ez, sz);
+    ws = __fadd_rn(ws, w);
 }
 
 template <bool WITH_D>
 __device__ __forceinline__ void lap_add(LapAcc& A, const LapPt& q) {
     float ex, ey, ez;
     lap_diff<WITH_D>(A.c, q, ex, ey, ez);
-    const float w = lap_weight(ex, ey, ez);
-    A.sx = fmaf(w, ex, A.sx);
-    A.sy = fmaf(w, ey, A.sy);
-    A.sz = fmaf(w, ez, A.sz);
-    A.ws += w;
+    lap_accumulate(A.sx, A.sy, A.sz, A.ws, lap_weight(ex, ey, ez), ex, ey, ez);
+}
+
+// Eq. 1 on the displacement of a centre point: d' = d + (lambda / W) s, or d unchanged (keep).
+__device__ __forceinline__ float lap_scale(bool keep, float lambda, float ws) {
+    return keep ? 0.f : __fdividef(lambda, ws);
 }
 
 // Top-left element (x0, u0) of a Laplacian tile's box in the AoS array seen as H rows of 3W
@@ -258,18 +273,15 @@ __device__ __forceinline__ void lap_iteration(int H, int W, float lambda, int co
                             lap_diff<WITH_D>(A[m].c, A[k].c, pex[m][k], pey[m][k], pez[m][k]);
                             const float w = lap_weight(pex[m][k], pey[m][k], pez[m][k]);
                             pw[m][k] = w;
+                            // fma(-w, e) = fma(w, -e): the same bits as k's own term for m
                             A[k].sx = fmaf(-w, pex[m][k], A[k].sx);
                             A[k].sy = fmaf(-w, pey[m][k], A[k].sy);
                             A[k].sz = fmaf(-w, pez[m][k], A[k].sz);
-                            A[k].ws += w;
+                            A[k].ws = __fadd_rn(A[k].ws, w);
                         }
-                        if (k < m && k >= m - R) {
-                            const float w = pw[k][m];
-                            A[k].sx = fmaf(w, pex[k][m], A[k].sx);
-                            A[k].sy = fmaf(w, pey[k][m], A[k].sy);
-                            A[k].sz = fmaf(w, pez[k][m], A[k].sz);
-                            A[k].ws += w;
-                        }
+                        if (k < m && k >= m - R)
+                            lap_accumulate(A[k].sx, A[k].sy, A[k].sz, A[k].ws, pw[k][m], pex[k][m], pey[k][m],
+                                           pez[k][m]);
                     }
                     continue;
                 }
@@ -287,7 +299,7 @@ __device__ __forceinline__ void lap_iteration(int H, int W, float lambda, int co
         for (int k = 0; k < S; ++k) {
             if (k >= rows) break;
             const bool keep = colpin || gu + k < R || gu + k >= H - R || A[k].c.x == kInvalidCoord || !(A[k].ws > 0.f);
-            const float s = keep ? 0.f : __fdividef(lambda, A[k].ws);
+            const float s = lap_scale(keep, lambda, A[k].ws);
             const int o = o0 + k * cols;
             nxt[o] = fmaf(s, A[k].sx, A[k].c.dx);
             nxt[o + 1] = fmaf(s, A[k].sy, A[k].c.dy);
@@ -396,7 +408,7 @@ __device__ void lap_tile(const LapJob& j, float* V0, float* Da, float* Db, bool 
             if ((W & 3) != 0) j.d_out[g] = d;
             if (j.export_points) {
                 const int pt = o - (f % 3);
-                j.export_points[g] = V0[pt] != kInvalidCoord ? V0[o] + d : NAN;
+                j.export_points[g] = V0[pt] != kInvalidCoord ? __fadd_rn(V0[o], d) : NAN;
             }
         }
     }
@@ -591,12 +603,25 @@ __device__ __forceinline__ void quad_neighbour(QuadAcc& A, f2 a2, f2 cx, f2 cy, 
     own_add(A.t1, own_weights(A.t1, a2, cx, cy, cz, nx, ny, nz), nx, ny, nz);
 }
 
-// One bilateral tile: T x T quads; geometry, `ph.iters` fused iterations (Eq. 3-6), then either
+// One bilateral tile: TH x T quads (TH = a.bil_th rows of T = 32, so that a warp spans a tile row);
+// geometry, `ph.iters` fused iterations (Eq. 3-6), then either
 // the carry for the next chunk or mask, normals, groups (Algorithm 4) and the tile-local
 // segments (Algorithm 5).
+// With timing on (sns != nullptr), thread 0 adds the tile's time in each stage -- staging,
+// geometry, iterations, finish (groups and outputs, or the carry), tile labels -- to sns[0..4]
+// (%globaltimer nanoseconds summed over tiles: CTA time, not wall time).
 template <int R>
 __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float* smem, uint64_t* bar,
-                         unsigned& parity) {
+                         unsigned& parity, unsigned long long* sns = nullptr) {
+    uint64_t t_stage = 0;
+    auto stage_mark = [&](int k) {
+        if (sns && threadIdx.x == 0) {
+            const uint64_t t = global_ns();
+            if (k >= 0) atomicAdd(sns + k, (unsigned long long)(t - t_stage));
+            t_stage = t;
+        }
+    };
+    stage_mark(-1);
     // the frame's arguments, read once (the batch kernel keeps them in global memory, where every
     // barrier and every global store would make the compiler load them again)
     const int H = a.H, W = a.W, Hq = H - 1, Wq = W - 1;
@@ -606,7 +631,8 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
     float* const carry_out = ph.carry_out;
     int* const error = a.error;
     const float max_edge2 = a.max_edge2;
-    const int RQH = T + 2 * h, RQW = T + 2 * h;          // staged quads
+    const int TH = a.bil_th;
+    const int RQH = TH + 2 * h, RQW = T + 2 * h;         // staged quads
     const int nq = RQH * RQW;
     const int nqs = nq + RQW;                            // one spare row of quads
     const BoxGeom b = ph.box;                            // rows = RQH + 1 points, cols >= 3 (RQW + 1) + delta
@@ -618,12 +644,12 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
     float* V0 = X;
     float* Dp = X + bsz;
     const int xw = max(align_floats(6 * nqs), 2 * bsz);
-    uint8_t* Mk = reinterpret_cast<uint8_t*>(X + xw);    // [T*T*2] own masks
-    uint8_t* Gs = Mk + 2 * T * T;                        // [T*T*2] own groups
+    uint8_t* Mk = reinterpret_cast<uint8_t*>(X + xw);    // [TH*T*2] own masks (room for T*T*2)
+    uint8_t* Gs = Mk + 2 * T * T;                        // [TH*T*2] own groups
     int* ex_list = reinterpret_cast<int*>(Gs + 2 * T * T);   // [kExactCap] deferred exact normals
     const int tiles_x = div_up(Wq, T);
     const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
-    const int qu0 = ty * T - h, qv0 = tx * T - h;
+    const int qu0 = ty * TH - h, qv0 = tx * T - h;
     const int x0 = floor4(3 * qv0);
     const int dlt = 3 * qv0 - x0;
     const float cs = a.c_scale;
@@ -678,6 +704,7 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
         }
     }
     __syncthreads();
+    stage_mark(0);
 
     // Centroids and normals of every staged triangle; masks of the tile's own quads. A normal
     // whose FP32 error bound fails is deferred: its quad goes on a short list that a second
@@ -725,7 +752,7 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
         const int o1 = qr * b.cols + dlt + 3 * qc;
         const SP p1 = load_sp(V0, Dp, o1), p2 = load_sp(V0, Dp, o1 + 3);
         const SP p3 = load_sp(V0, Dp, o1 + b.cols + 3), p4 = load_sp(V0, Dp, o1 + b.cols);
-        const bool own = last && qr >= h && qr < h + T && qc >= h && qc < h + T;
+        const bool own = last && qr >= h && qr < h + TH && qc >= h && qc < h + T;
         const bool v1 = p1.x == p1.x, v2 = p2.x == p2.x, v3 = p3.x == p3.x, v4 = p4.x == p4.x;
         const bool valid0 = exists && v1 && v2 && v3;                            // Algorithm 1
         const bool valid1 = exists && v1 && v3 && v4;
@@ -803,6 +830,7 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
         }
     }
     __syncthreads();   // the staged boxes are dead from here on; Nb reuses their space
+    stage_mark(1);
 
     // Fused bilateral iterations: each work item is a vertical pair of quads.
     float* cur = Na;
@@ -843,11 +871,12 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
         cur = nxt;
         nxt = tmp;
     }
+    stage_mark(2);
 
     if (!last) {
-        for (int i = threadIdx.x; i < T * T; i += blockDim.x) {
+        for (int i = threadIdx.x; i < TH * T; i += blockDim.x) {
             const int r = i / T, c = i - r * T;
-            const int gu = ty * T + r, gv = tx * T + c;
+            const int gu = ty * TH + r, gv = tx * T + c;
             if (gu >= Hq || gv >= Wq) continue;
             V3 n[2];
             load_quad(cur, (r + h) * RQW + (c + h), n[0], n[1]);
@@ -862,14 +891,15 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
             }
         }
         __syncthreads();
+        stage_mark(3);
         return;
     }
 
-    // free after the last iteration (>= 6 * 1056 floats): union-find parents, the run
-    // representative of each triangle, and the tile root of each representative [T*T*2] each
+    // free after the last iteration (>= 6 * nqs floats, nqs >= (TH + 1) T): union-find parents, the
+    // run representative of each triangle, and the tile root of each representative [TH*T*2] each
     int32_t* Lp = reinterpret_cast<int32_t*>(nxt);
-    int32_t* RunOf = Lp + 2 * T * T;
-    int32_t* RootOf = RunOf + 2 * T * T;
+    int32_t* RunOf = Lp + 2 * TH * T;
+    int32_t* RootOf = RunOf + 2 * TH * T;
     uint8_t* const out_mask = a.out_mask;
     float* const out_normals = a.out_normals;
     uint8_t* const out_groups = a.groups;
@@ -881,9 +911,9 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
     float nd[3 * kRegGroups];
 #pragma unroll
     for (int j = 0; j < 3 * kRegGroups; ++j) nd[j] = j < 3 * K ? ndv[j] : 0.f;
-    for (int i = threadIdx.x; i < T * T; i += blockDim.x) {
+    for (int i = threadIdx.x; i < TH * T; i += blockDim.x) {
         const int r = i / T, c = i - r * T;
-        const int gu = ty * T + r, gv = tx * T + c;
+        const int gu = ty * TH + r, gv = tx * T + c;
         const bool exists = gu < Hq && gv < Wq;
         V3 n[2];
         load_quad(cur, (r + h) * RQW + (c + h), n[0], n[1]);
@@ -931,6 +961,7 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
         }
     }
     __syncthreads();
+    stage_mark(3);
 
     // Connected components inside the tile (twins of Algorithm 2 that stay in the tile).
     const bool offs = a.max_offset_scaled > 0.f;
@@ -942,7 +973,7 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
     constexpr unsigned kFull = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // (1) Runs along each quad row. Chain position 2v is second(v), 2v+1 is first(v).
-    for (int r = warp; r < T; r += kThreads / 32) {
+    for (int r = warp; r < TH; r += kThreads / 32) {
         const int tf = 2 * (r * T + lane), ts = tf + 1;
         const int gf = Gs[tf], gs = Gs[ts];
         V3 cf = {0.f, 0.f, 0.f}, cs2 = cf;
@@ -982,7 +1013,7 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
     __syncthreads();
     // (2) Rows joined across horizontal edges: first(r, v) with second(r-1, v); one union per
     // run pair (a lane skips the pair its left neighbour already joined).
-    for (int r = 1 + warp; r < T; r += kThreads / 32) {
+    for (int r = 1 + warp; r < TH; r += kThreads / 32) {
         const int tf = 2 * (r * T + lane), tu = 2 * ((r - 1) * T + lane) + 1;
         const int gf = Gs[tf];
         bool link = gf != PL3D_NO_GROUP && Gs[tu] == gf;
@@ -1000,14 +1031,14 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
     __syncthreads();
     // (3) Only the run representatives were linked by the unions: each finds its root, halving
     // the path as it walks (concurrent walks only shorten paths, so they stay valid).
-    for (int t = threadIdx.x; t < 2 * T * T; t += blockDim.x)
+    for (int t = threadIdx.x; t < 2 * TH * T; t += blockDim.x)
         if (RunOf[t] == t) RootOf[t] = uf_find(Lp, t);
     __syncthreads();
     // (4) Each triangle leaves with the GID of its tile-local root (-1 without a group).
     int32_t* const labels = a.labels;
-    for (int i = threadIdx.x; i < T * T; i += blockDim.x) {
+    for (int i = threadIdx.x; i < TH * T; i += blockDim.x) {
         const int r = i / T, c = i - r * T;
-        const int gu = ty * T + r, gv = tx * T + c;
+        const int gu = ty * TH + r, gv = tx * T + c;
         if (gu >= Hq || gv >= Wq) continue;
         const size_t gid0 = 2 * ((size_t)gu * Wq + gv);
 #pragma unroll
@@ -1017,12 +1048,13 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
             if (rep >= 0) {
                 const int root = RootOf[rep];
                 const int rq = root >> 1, rr = rq / T, rc = rq - rr * T;
-                lab = (int)(2 * ((size_t)(ty * T + rr) * Wq + (tx * T + rc)) + (root & 1));
+                lab = (int)(2 * ((size_t)(ty * TH + rr) * Wq + (tx * T + rc)) + (root & 1));
             }
             labels[gid0 + k] = lab;
         }
     }
     __syncthreads();
+    stage_mark(4);
 }
 
 // ------------------------------------------------------------------------- segments (Alg. 5)
@@ -1041,15 +1073,16 @@ __device__ __forceinline__ V3 centroid_global(const FrameArgs& a, int u, int v, 
 }
 
 // Twins that cross a tile border: the top edge of a tile's first quad row and the right edge of
-// its last quad column. Work items: (row borders) x Wq, then (column borders) x Hq. Returns
+// its last quad column (tiles of a.bil_th x T quads). Work items: (row borders) x Wq, then
+// (column borders) x Hq. Returns
 // whether item w joins two triangles, and then their current labels (each in its triangle's
 // set: the tile root, or an ancestor of it once a union has linked that root).
 __device__ __forceinline__ bool merge_pair(const FrameArgs& a, long long w, int& ra, int& rb) {
-    const int Wq = a.W - 1, Hq = a.H - 1;
-    const long long n_row_items = (long long)(div_up(Hq, T) - 1) * Wq;
+    const int Wq = a.W - 1, Hq = a.H - 1, TH = a.bil_th;
+    const long long n_row_items = (long long)(div_up(Hq, TH) - 1) * Wq;
     int u, v, uj, vj;
     if (w < n_row_items) {
-        u = (int)(w / Wq + 1) * T;
+        u = (int)(w / Wq + 1) * TH;
         v = (int)(w % Wq);
         uj = u - 1;
         vj = v;
@@ -1087,7 +1120,7 @@ __device__ __forceinline__ void merge_unite(int32_t* labels, bool link, int ra, 
 
 __device__ __forceinline__ void merge_phase(const FrameArgs& a) {
     const int Wq = a.W - 1, Hq = a.H - 1;
-    const long long n = (long long)(div_up(Hq, T) - 1) * Wq + (long long)(div_up(Wq, T) - 1) * Hq;
+    const long long n = (long long)(div_up(Hq, a.bil_th) - 1) * Wq + (long long)(div_up(Wq, T) - 1) * Hq;
     const long long stride = (long long)gridDim.x * blockDim.x;
     const long long n_iter = (n + stride - 1) / stride;   // uniform: whole warps stay together
     const long long base = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -1219,10 +1252,11 @@ __global__ void __launch_bounds__(kThreads, 2) frame_kernel(const __grid_constan
             grid_barrier(a.barrier, a.error);
         }
         frame::phase_mark(a, 0, t_prev);
-        const int tiles_bil = div_up(a.H - 1, kTile) * div_up(a.W - 1, kTile);
+        const int tiles_bil = div_up(a.H - 1, a.bil_th) * div_up(a.W - 1, kTile);
         unsigned par0 = par & 1u;   // the bilateral stages through slot 0
         for (int c = 0; c < a.n_bil; ++c) {
-            for (int t = blockIdx.x; t < tiles_bil; t += gridDim.x) frame::bil_tile<RB>(a, a.bil[c], t, smem, bar, par0);
+            for (int t = blockIdx.x; t < tiles_bil; t += gridDim.x)
+                frame::bil_tile<RB>(a, a.bil[c], t, smem, bar, par0, a.phase_ns ? a.phase_ns + kStageSlot : nullptr);
             if (a.part == 0 || c + 1 < a.n_bil) grid_barrier(a.barrier, a.error);
         }
         frame::phase_mark(a, 1, t_prev);
@@ -1369,7 +1403,7 @@ __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const __grid_constan
                 }
                 acquired = f;
             }
-            frame::bil_tile<RB>(a, a.bil[c], t - __ldg(pre + f), smem, bar, par0);
+            frame::bil_tile<RB>(a, a.bil[c], t - __ldg(pre + f), smem, bar, par0, pns ? pns + kStageSlot : nullptr);
         }
         grid_barrier(b.barrier, b.error);
     }

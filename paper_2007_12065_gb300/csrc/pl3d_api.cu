@@ -20,9 +20,11 @@ namespace {
 
 constexpr int kVersion = 2 * 10000 + 1 * 100 + 0;
 
-const char* const kSlotNames[PL3D_TIMING_SLOTS] = {"laplacian",   "bilateral",    "label_merge",
-                                                    "label_flatten", "frame_kernel", "host_copies",
-                                                    "mesh_kernel", "fastga_kernel"};
+const char* const kSlotNames[PL3D_TIMING_SLOTS] = {
+    "laplacian",      "bilateral",     "label_merge",        "label_flatten",  "frame_kernel",
+    "host_copies",    "mesh_kernel",   "fastga_kernel",      "bil_staging_cta", "bil_geometry_cta",
+    "bil_iterations_cta", "bil_finish_cta", "bil_labels_cta"};
+static_assert(kSlotBilStage0 + kBilStages == PL3D_TIMING_SLOTS, "timing slots");
 
 bool finite_f(float x) { return isfinite(x) != 0; }
 
@@ -94,8 +96,9 @@ int run(pl3d_ctx* ctx, const float* points, int H, int W, const pl3d_params* p, 
     }
     cudaEvent_t e0, e1;
     record_start(ctx, s, &e0, &e1);
+    int n_launched = 0;
     rc = frame_launch(sc, points, H, W, &q, nd_host, K, out_mask, out_normals, out_labels, out_points, out_groups,
-                      ctx->tuning, s, seeded ? nullptr : out_labels_copy, normals_ready);
+                      ctx->tuning, s, seeded ? nullptr : out_labels_copy, normals_ready, &n_launched);
     record_stop(ctx, s, kSlotKernel, e0, e1);
     if (rc != PL3D_OK) return rc;
     if (seeded) {
@@ -104,7 +107,7 @@ int run(pl3d_ctx* ctx, const float* points, int H, int W, const pl3d_params* p, 
         if (rc != PL3D_OK) return rc;
         ctx->launches += 1;
     }
-    ctx->launches += normals_ready ? 2 : 1;
+    ctx->launches += n_launched;
     if (ctx->timing) ctx->timed_frames += 1;
     return PL3D_OK;
 }
@@ -387,7 +390,7 @@ int pl3d_read_timing(pl3d_ctx* ctx, double* ms_out, int64_t* launches_out, int n
     }
     ctx->pending.clear();
     if (cudaDeviceSynchronize() != cudaSuccess) return PL3D_ERR_CUDA;
-    unsigned long long ns[4] = {0, 0, 0, 0};
+    unsigned long long ns[kStageSlot + kBilStages];
     if (cudaMemcpy(ns, ctx->phase_ns(), sizeof(ns), cudaMemcpyDeviceToHost) != cudaSuccess) return PL3D_ERR_CUDA;
     double ms_all[PL3D_TIMING_SLOTS];
     int64_t n_all[PL3D_TIMING_SLOTS];
@@ -399,6 +402,10 @@ int pl3d_read_timing(pl3d_ctx* ctx, double* ms_out, int64_t* launches_out, int n
         ms_all[i] = (double)ns[i] * 1e-6;
         n_all[i] = ctx->timed_frames;
     }
+    for (int i = 0; i < kBilStages; ++i) {
+        ms_all[kSlotBilStage0 + i] = (double)ns[kStageSlot + i] * 1e-6;
+        n_all[kSlotBilStage0 + i] = ctx->timed_frames;
+    }
     for (int i = 0; i < n_slots && i < PL3D_TIMING_SLOTS; ++i) {
         if (ms_out) ms_out[i] = ms_all[i];
         if (launches_out) launches_out[i] = n_all[i];
@@ -409,6 +416,7 @@ int pl3d_read_timing(pl3d_ctx* ctx, double* ms_out, int64_t* launches_out, int n
             ctx->slot_n[i] = 0;
         }
         ctx->timed_frames = 0;
+        // the phase totals and the stage totals (the lap1 stamps between them are zero at rest)
         if (cudaMemset(ctx->phase_ns(), 0, sizeof(ns)) != cudaSuccess) return PL3D_ERR_CUDA;
         if (cudaDeviceSynchronize() != cudaSuccess) return PL3D_ERR_CUDA;
     }

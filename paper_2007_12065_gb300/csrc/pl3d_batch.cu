@@ -37,12 +37,13 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Byte offsets of the descriptor block for `cap` frames.
 struct DescLayout {
-    size_t lap, bil, merge, tris, frames, total;
+    size_t lap, bil, l1, merge, tris, frames, total;
     explicit DescLayout(int cap) {
         const size_t pre = (size_t)kMaxPasses * (cap + 1) * sizeof(int);
         lap = align_up(sizeof(BatchHeader), 128);
         bil = align_up(lap + pre, 128);
-        merge = align_up(bil + pre, 128);
+        l1 = align_up(bil + pre, 128);
+        merge = align_up(l1 + pre, 128);
         tris = align_up(merge + (cap + 1) * sizeof(long long), 128);
         frames = align_up(tris + (cap + 1) * sizeof(long long), 128);
         total = frames + (size_t)cap * sizeof(FrameArgs);
@@ -107,15 +108,32 @@ int grow_slab(pl3d_ctx* c, size_t need, cudaStream_t s) {
     return PL3D_OK;
 }
 
-// Graph with the batch kernel as its only (cooperative) node, for this launch shape.
-cudaGraphExec_t batch_graph(pl3d_ctx* c, const void* fn, size_t smem, int grid, const BatchArgs& args) {
+// Graph for this launch shape: n_l1 single-iteration Laplacian passes (lap1_kernel, one node each,
+// in pass order) and then the batch kernel as a cooperative node.
+cudaGraphExec_t batch_graph(pl3d_ctx* c, const void* fn, size_t smem, int grid, const BatchArgs& args, int n_l1,
+                            const Lap1Args* l1_args, const int* l1_grid) {
     for (auto& g : c->graphs)
-        if (g.fn == fn && g.smem == smem && g.grid == grid) return g.exec;
+        if (g.fn == fn && g.smem == smem && g.grid == grid && g.n_l1 == n_l1) return g.exec;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     if (cudaGraphCreate(&graph, 0) != cudaSuccess) {
         cudaGetLastError();
         return nullptr;
+    }
+    bool ok = true;
+    cudaGraphNode_t prev = nullptr;
+    for (int i = 0; i < n_l1 && ok; ++i) {
+        Lap1Args la = l1_args[i];
+        void* lparams[1] = {&la};
+        cudaKernelNodeParams lp;
+        memset(&lp, 0, sizeof(lp));
+        lp.func = const_cast<void*>(lap1_kernel_for(la.pass > 0));
+        lp.gridDim = dim3(l1_grid[i]);
+        lp.blockDim = dim3(kThreads);
+        lp.kernelParams = lparams;
+        cudaGraphNode_t node = nullptr;
+        ok = cudaGraphAddKernelNode(&node, graph, prev ? &prev : nullptr, prev ? 1 : 0, &lp) == cudaSuccess;
+        prev = node;
     }
     BatchArgs a = args;
     void* params[1] = {&a};
@@ -130,9 +148,9 @@ cudaGraphExec_t batch_graph(pl3d_ctx* c, const void* fn, size_t smem, int grid, 
     cudaLaunchAttributeValue coop;
     memset(&coop, 0, sizeof(coop));
     coop.cooperative = 1;
-    bool ok = cudaGraphAddKernelNode(&node, graph, nullptr, 0, &kp) == cudaSuccess &&
-              cudaGraphKernelNodeSetAttribute(node, cudaLaunchAttributeCooperative, &coop) == cudaSuccess &&
-              cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+    ok = ok && cudaGraphAddKernelNode(&node, graph, prev ? &prev : nullptr, prev ? 1 : 0, &kp) == cudaSuccess &&
+         cudaGraphKernelNodeSetAttribute(node, cudaLaunchAttributeCooperative, &coop) == cudaSuccess &&
+         cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
     cudaGraphDestroy(graph);
     if (!ok) {
         cudaGetLastError();
@@ -142,7 +160,7 @@ cudaGraphExec_t batch_graph(pl3d_ctx* c, const void* fn, size_t smem, int grid, 
         cudaGraphExecDestroy(c->graphs.front().exec);
         c->graphs.erase(c->graphs.begin());
     }
-    c->graphs.push_back({fn, smem, grid, exec});
+    c->graphs.push_back({fn, smem, grid, n_l1, exec});
     return exec;
 }
 
@@ -190,6 +208,7 @@ int run_batch(pl3d_ctx* c, const pl3d_frame* frames, int n, cudaStream_t s) {
     BatchHeader* hdr = reinterpret_cast<BatchHeader*>(st);
     int* lap_pre = reinterpret_cast<int*>(st + L.lap);
     int* bil_pre = reinterpret_cast<int*>(st + L.bil);
+    int* l1_pre = reinterpret_cast<int*>(st + L.l1);
     long long* merge_pre = reinterpret_cast<long long*>(st + L.merge);
     long long* tri_pre = reinterpret_cast<long long*>(st + L.tris);
     FrameArgs* fa = reinterpret_cast<FrameArgs*>(st + L.frames);
@@ -230,16 +249,24 @@ int run_batch(pl3d_ctx* c, const pl3d_frame* frames, int n, cudaStream_t s) {
         merge_pre[i + 1] = merge_pre[i] + plan.merge_items;
         tri_pre[i + 1] = tri_pre[i] + plan.tris;
     }
+    // every frame's Laplacian passes single-iteration with a 3 x 3 window: they run as lap1_kernel
+    // nodes of the graph, and the batch kernel starts at the bilateral
+    bool thin = rl == 1;
+    for (int i = 0; i < n && thin; ++i) thin = lap1_eligible(fa[i], 1);
+    const int n_l1 = thin ? n_lap : 0;
     long long most_tiles = 0;
     for (int pass = 0; pass < kMaxPasses; ++pass) {
         int* lp = lap_pre + pass * stride;
         int* bp = bil_pre + pass * stride;
+        int* l1p = l1_pre + pass * stride;
         for (int i = 0; i < n; ++i) {
-            lp[i + 1] = lp[i] + (pass < lap_passes[i] ? fa[i].lap[pass].tiles : 0);
+            lp[i + 1] = lp[i] + (pass < lap_passes[i] && !thin ? fa[i].lap[pass].tiles : 0);
             bp[i + 1] = bp[i] + (pass < bil_passes[i] ? bil_tiles[i] : 0);
+            l1p[i + 1] = l1p[i] + (pass < lap_passes[i] && thin ? lap1_tasks(fa[i].H, fa[i].W) : 0);
         }
         most_tiles = std::max(most_tiles, (long long)std::max(lp[n], bp[n]));
     }
+    if (thin) n_lap = 0;
     // per Laplacian pass: buffers sized for the largest box; staged ahead when some frame stages
     // by TMA, as many boxes as still fit two CTAs per SM
     for (int lp_pass = 0; lp_pass < n_lap; ++lp_pass) {
@@ -300,9 +327,24 @@ int run_batch(pl3d_ctx* c, const pl3d_frame* frames, int n, cudaStream_t s) {
     const int grid = persistent_grid(fn, smem, dev, t, most_tiles);
     if (grid <= 0) return PL3D_ERR_CUDA;
 
+    Lap1Args l1_args[kMaxPasses];
+    int l1_grid[kMaxPasses];
+    for (int pass = 0; pass < n_l1; ++pass) {
+        Lap1Args& la = l1_args[pass];
+        memset(&la, 0, sizeof(la));
+        la.hdr = args.hdr;
+        la.frames = args.frames;
+        la.task_pre = reinterpret_cast<const int*>(c->bdesc + L.l1) + pass * stride;
+        la.pass = pass;
+        la.stamp = c->phase_ns() + 4;
+        la.phase_ns = c->phase_ns();
+        l1_grid[pass] = lap1_grid(dev, pass > 0, -1);
+        if (l1_grid[pass] <= 0) return PL3D_ERR_CUDA;
+    }
+
     cudaEvent_t e0, e1;
     record_start(c, s, &e0, &e1);
-    cudaGraphExec_t exec = batch_graph(c, fn, smem, grid, args);
+    cudaGraphExec_t exec = batch_graph(c, fn, smem, grid, args, n_l1, l1_args, l1_grid);
     if (!exec) return PL3D_ERR_CUDA;
     if (cudaGraphLaunch(exec, s) != cudaSuccess) {
         cudaGetLastError();
@@ -310,17 +352,25 @@ int run_batch(pl3d_ctx* c, const pl3d_frame* frames, int n, cudaStream_t s) {
     }
     record_stop(c, s, kSlotKernel, e0, e1);
     c->graph_launches += 1;
-    c->launches += 1;
+    c->launches += 1 + n_l1;
     if (c->timing) c->timed_frames += 1;
     return PL3D_OK;
 }
 
-bool tuning_ok(const pl3d_tuning* t) { return t->lap_fuse >= 0 && t->bil_fuse >= 0 && t->ctas_per_sm >= 0; }
+bool tuning_ok(const pl3d_tuning* t) {
+    const bool lap_h = t->lap_tile_h == 0 ||
+                       (t->lap_tile_h % 8 == 0 && t->lap_tile_h >= kLapMinTileH && t->lap_tile_h <= kLapMaxTileH);
+    const bool bil_h = t->bil_tile_h == 0 ||
+                       (t->bil_tile_h % 8 == 0 && t->bil_tile_h >= kBilMinTileH && t->bil_tile_h <= kBilMaxTileH);
+    return t->lap_fuse >= 0 && t->bil_fuse >= 0 && t->ctas_per_sm >= 0 && lap_h && bil_h;
+}
 
 // Fused depths worth trying for `iters` iterations of a filter whose halo allows `max_fuse`:
-// everything in as few passes as possible, then two and three passes.
-std::vector<int> fuse_candidates(int iters, int max_fuse) {
+// everything in as few passes as possible, then two and three passes, and with `single` one
+// iteration per pass (the Laplacian with a 3 x 3 window, which then runs as lap1_kernel).
+std::vector<int> fuse_candidates(int iters, int max_fuse, bool single = false) {
     std::vector<int> v;
+    if (single && iters > 1 && iters <= kMaxPasses) v.push_back(1);
     for (int passes = 1; passes <= 3; ++passes) {
         int f = (iters + passes - 1) / passes;
         if (f > max_fuse) continue;
@@ -359,11 +409,11 @@ int pl3d_extract_planes_batched(pl3d_ctx* ctx, const pl3d_frame* frames, int n, 
 int pl3d_set_tuning(pl3d_ctx* ctx, const pl3d_tuning* t) {
     if (!ctx) return PL3D_ERR_INVALID_ARG;
     if (!t) {
-        ctx->tuning = Tuning{0, 0, 0};
+        ctx->tuning = Tuning{0, 0, 0, 0, 0};
         return PL3D_OK;
     }
     if (!tuning_ok(t)) return PL3D_ERR_INVALID_ARG;
-    ctx->tuning = Tuning{t->lap_fuse, t->bil_fuse, t->ctas_per_sm};
+    ctx->tuning = Tuning{t->lap_fuse, t->bil_fuse, t->ctas_per_sm, t->lap_tile_h, t->bil_tile_h};
     return PL3D_OK;
 }
 
@@ -372,6 +422,8 @@ int pl3d_get_tuning(const pl3d_ctx* ctx, pl3d_tuning* t) {
     t->lap_fuse = ctx->tuning.lap_fuse;
     t->bil_fuse = ctx->tuning.bil_fuse;
     t->ctas_per_sm = ctx->tuning.ctas_per_sm;
+    t->lap_tile_h = ctx->tuning.lap_tile_h;
+    t->bil_tile_h = ctx->tuning.bil_tile_h;
     return PL3D_OK;
 }
 
@@ -389,10 +441,10 @@ int pl3d_autotune_batched(pl3d_ctx* ctx, const pl3d_frame* frames, int n, void* 
         lap_iters = std::max(lap_iters, (int)frames[i].params->lap_iters);
         bil_iters = std::max(bil_iters, (int)frames[i].params->bil_iters);
     }
-    std::vector<Tuning> cands;
-    for (int lf : fuse_candidates(lap_iters, kLapMaxHalo / rl))
+    std::vector<Tuning> round1;
+    for (int lf : fuse_candidates(lap_iters, kLapMaxHalo / rl, rl == 1))
         for (int bf : fuse_candidates(bil_iters, kBilMaxHalo / rb))
-            for (int cps : {1, 2}) cands.push_back(Tuning{lf, bf, cps});
+            for (int cps : {1, 2}) round1.push_back(Tuning{lf, bf, cps, 0, 0});
 
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
@@ -406,26 +458,44 @@ int pl3d_autotune_batched(pl3d_ctx* ctx, const pl3d_frame* frames, int n, void* 
     double best_t = INFINITY;
     Tuning best_c = saved;
     std::vector<double> times;
-    for (const Tuning& cand : cands) {
-        ctx->tuning = cand;
-        if ((rc = run_batch(ctx, frames, n, s)) != PL3D_OK) break;
-        times.clear();
-        for (int r = 0; r < reps && rc == PL3D_OK; ++r) {
-            float ms = 0.f;
-            if (cudaEventRecord(e0, s) != cudaSuccess) rc = PL3D_ERR_CUDA;
-            if (rc == PL3D_OK) rc = run_batch(ctx, frames, n, s);
-            if (rc == PL3D_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-                                  cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
-                rc = PL3D_ERR_CUDA;
-            times.push_back(ms);
+    auto try_all = [&](const std::vector<Tuning>& cands) {
+        for (const Tuning& cand : cands) {
+            ctx->tuning = cand;
+            if ((rc = run_batch(ctx, frames, n, s)) != PL3D_OK) return;
+            times.clear();
+            for (int r = 0; r < reps && rc == PL3D_OK; ++r) {
+                float ms = 0.f;
+                if (cudaEventRecord(e0, s) != cudaSuccess) rc = PL3D_ERR_CUDA;
+                if (rc == PL3D_OK) rc = run_batch(ctx, frames, n, s);
+                if (rc == PL3D_OK && (cudaEventRecord(e1, s) != cudaSuccess ||
+                                      cudaEventSynchronize(e1) != cudaSuccess ||
+                                      cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                    rc = PL3D_ERR_CUDA;
+                times.push_back(ms);
+            }
+            if (rc != PL3D_OK) return;
+            std::sort(times.begin(), times.end());
+            const double med = times[times.size() / 2];
+            if (med < best_t) {
+                best_t = med;
+                best_c = cand;
+            }
         }
-        if (rc != PL3D_OK) break;
-        std::sort(times.begin(), times.end());
-        const double med = times[times.size() / 2];
-        if (med < best_t) {
-            best_t = med;
-            best_c = cand;
-        }
+    };
+    // round 1: fused depths and CTAs per SM at the default tile shapes; round 2: tile heights at
+    // the best of those (the default shape is round 1's own entry)
+    try_all(round1);
+    if (rc == PL3D_OK) {
+        std::vector<Tuning> round2;
+        for (int lh : {16, 32, 48, 64})
+            for (int bh : {16, 24, 32}) {
+                Tuning c = best_c;
+                c.lap_tile_h = lh;
+                c.bil_tile_h = bh == kTile ? 0 : bh;
+                if (c.lap_tile_h == kTile) c.lap_tile_h = 0;
+                if (c.lap_tile_h != 0 || c.bil_tile_h != 0) round2.push_back(c);
+            }
+        try_all(round2);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -442,6 +512,8 @@ int pl3d_autotune_batched(pl3d_ctx* ctx, const pl3d_frame* frames, int n, void* 
         best->lap_fuse = best_c.lap_fuse;
         best->bil_fuse = best_c.bil_fuse;
         best->ctas_per_sm = best_c.ctas_per_sm;
+        best->lap_tile_h = best_c.lap_tile_h;
+        best->bil_tile_h = best_c.bil_tile_h;
     }
     if (best_ms) *best_ms = best_t;
     return PL3D_OK;

@@ -15,23 +15,27 @@ namespace ctxutil {
 // Timing slots: four phases of the persistent kernels (device %globaltimer, accumulated by the
 // kernel), the kernel as a whole, the host copies, the explicit-mesh launch and the Gaussian
 // accumulator (CUDA events on the call's stream).
-enum Slot { kSlotLap = 0, kSlotBil, kSlotMerge, kSlotLabels, kSlotKernel, kSlotCopies, kSlotMesh, kSlotFastga };
+enum Slot { kSlotLap = 0, kSlotBil, kSlotMerge, kSlotLabels, kSlotKernel, kSlotCopies, kSlotMesh, kSlotFastga,
+            kSlotBilStage0 };   // then the kBilStages bilateral stage totals (CTA time)
 
 struct TimedRange {
     int slot;
     cudaEvent_t start, stop;
 };
 
-// One instantiated graph holding the batch kernel as a cooperative kernel node. Its arguments
-// point at the context's descriptor block, so the graph stays valid until that block moves.
+// One instantiated graph: n_l1 single-iteration Laplacian nodes, then the batch kernel as a
+// cooperative kernel node. Their arguments point at the context's descriptor block, so the graph
+// stays valid until that block moves.
 struct BatchGraph {
     const void* fn;
     size_t smem;
     int grid;
+    int n_l1;
     cudaGraphExec_t exec;
 };
 
-constexpr size_t kCtlBytes = 4 * sizeof(unsigned) + 4 * sizeof(unsigned long long);
+// barrier [2], error word, pad; phase totals [4]; lap1 timing stamps [3]; bilateral stage totals
+constexpr size_t kCtlBytes = 4 * sizeof(unsigned) + (kStageSlot + kBilStages) * sizeof(unsigned long long);
 
 }  // namespace ctxutil
 }  // namespace pl3d
@@ -46,7 +50,7 @@ struct pl3d_ctx {
     uint8_t* groups = nullptr;      // cap_tri
     int32_t* sizes = nullptr;       // cap_tri
     size_t cap_tri = 0;
-    unsigned* ctl = nullptr;        // barrier [2], error word, pad, phase totals [4] (u64)
+    unsigned* ctl = nullptr;        // barrier [2], error word, pad, phase totals [4] and lap1 stamps [3] (u64)
     uint8_t* seed_flags = nullptr;  // PL3D_FLAG_SEED_PTP: per-root flags, cap_seed
     size_t cap_seed = 0;
     float* seed_centroids = nullptr;   // PL3D_FLAG_SEED_PTP: 3 cap_seed_c floats

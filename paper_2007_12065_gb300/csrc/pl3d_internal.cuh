@@ -31,6 +31,10 @@ constexpr int kExactCap = 256;   // deferred exact-normal quads a bilateral tile
 constexpr int kTwoCtaSmem = 114048;
 constexpr int kLapMaxStages = 3;   // box buffers of a Laplacian pass: this tile's and up to 2 ahead
 constexpr int kLapThinTileH = 64;  // tile height of a single-iteration first Laplacian pass
+// Tile heights a tuning may ask for (tiles stay kTile wide): Laplacian 16..64 and bilateral
+// 8..32 rows, multiples of 8.
+constexpr int kLapMinTileH = 16, kLapMaxTileH = 64;
+constexpr int kBilMinTileH = 8, kBilMaxTileH = kTile;
 
 // Centroid given to a triangle without a normal: its bilateral weight underflows to
 // exactly 0 against any real triangle, so it drops out of every sum without a branch.
@@ -73,8 +77,8 @@ struct LapPhase {
     int use_tma;                   // points staged by TMA (tm_pts_lap), else plain loads
     int stages;                    // box buffers (1..kLapMaxStages): TMA loads of the next stages - 1
                                    // tiles overlap this tile
-    int tile_h;                    // tile height in points: 32, or kLapThinTileH for a single-iteration
-                                   // first pass (tiles are 32 points wide)
+    int tile_h;                    // tile height in points: the tuning's, else 32, or kLapThinTileH for a
+                                   // single-iteration first pass (tiles are 32 points wide)
     int tiles;                     // tiles of this pass
     int dbufs;                     // displacement buffers: 1 for a single-iteration first pass, else 2
     BoxGeom box;                   // rows = tile_h + 2 halo + 3 (spare rows), cols >= 3 (32 + 2 halo) + 3
@@ -87,13 +91,18 @@ struct BilPhase {
     int iters;
     int halo;
     int use_tma;                   // points and displacement staged by TMA (tm_pts_bil, tm_disp_bil)
-    BoxGeom box;                   // rows = 32 + 2 halo + 1, cols >= 3 (32 + 2 halo + 1) + 3
+    BoxGeom box;                   // rows = bil_th + 2 halo + 1, cols >= 3 (32 + 2 halo + 1) + 3
     int first, last;               // first pass builds the normals; last pass finishes the quads
     const float* carry_in;         // AoS [2Q][3] normals from the previous pass (not first)
     float* carry_out;              // AoS [2Q][3] normals for the next pass (not last)
 };
 
 constexpr int kMaxPasses = 8;
+
+// Timing words after the phase totals (phase_ns[0..3]): lap1 stamps at phase_ns + 4 .. + 6, the
+// bilateral tiles' stage totals at phase_ns + kStageSlot .. + kStageSlot + kBilStages - 1.
+constexpr int kStageSlot = 7;
+constexpr int kBilStages = 5;
 
 struct FrameArgs {
     CUtensorMap tm_pts_lap;        // points, Laplacian box (first pass)
@@ -106,6 +115,7 @@ struct FrameArgs {
     int n_lap;
     LapPhase lap[kMaxPasses];
     int n_bil;
+    int bil_th;                    // bilateral tile height in quads (tiles are kTile = 32 quads wide)
     BilPhase bil[kMaxPasses];
     uint8_t* out_mask;
     float* out_normals;
@@ -123,7 +133,8 @@ struct FrameArgs {
     int min_triangles;
     unsigned* barrier;             // [2] grid barrier state
     int* error;                    // device error word (sync.cuh bits)
-    unsigned long long* phase_ns;  // [4] accumulated phase times, or nullptr
+    unsigned long long* phase_ns;  // [4] accumulated phase times (then the lap1 stamps and the bilateral
+                                   // stage totals, see kStageSlot), or nullptr
     int part;                      // 0: the whole path; 1: smoothing and tile-local segments only
                                    // (mask, normals, groups final); 2: the segments across tiles only
     Dominant nd;
@@ -163,6 +174,37 @@ struct BatchArgs {
 template <int RL, int RB>
 __global__ void batch_kernel(const __grid_constant__ BatchArgs b);
 
+// The single-iteration Laplacian pass with a 3 x 3 window as a kernel of its own (lap1.cu): used
+// when every Laplacian pass of a frame (of every frame of a batch) runs at most one iteration,
+// before the persistent kernel, which then starts at the bilateral. Work unit: a warp task of
+// kLap1Cols columns x kLap1Rows rows of one frame.
+constexpr int kLap1Cols = 32;
+constexpr int kLap1Rows = 24;
+__host__ __device__ inline int lap1_tasks(int H, int W) { return div_up(H, kLap1Rows) * div_up(W, kLap1Cols); }
+
+struct Lap1Frame {
+    const float* points;
+    const float* d_in;             // previous pass's displacement, or nullptr (first pass)
+    float* d_out;
+    float* export_points;          // optional AoS export of v0 + d (last pass only)
+    int H, W;
+    int iters;                     // 0 (the displacement stays zero) or 1
+    float lambda;
+};
+
+struct Lap1Args {
+    Lap1Frame one;                 // the frame, when hdr == nullptr
+    const BatchHeader* hdr;        // batch: frame count and timing flag, or nullptr
+    const FrameArgs* frames;       // batch: pass `pass` of every frame
+    const int* task_pre;           // batch: [n + 1] prefix sums of the frames' warp tasks in this pass
+    int pass;
+    unsigned long long* stamp;     // [3]: latest ~start, latest end, CTAs done; or nullptr (no timing)
+    unsigned long long* phase_ns;  // the Laplacian span is added to phase_ns[0]
+};
+
+template <bool WITH_D>
+__global__ void lap1_kernel(const __grid_constant__ Lap1Args a);
+
 // --------------------------------------------------------------------------- host side
 
 // Device buffers one frame needs besides its inputs and outputs.
@@ -184,6 +226,10 @@ struct Tuning {
     int lap_fuse;                  // most Laplacian iterations per pass, 0 = as many as fit the halo
     int bil_fuse;                  // same for the bilateral
     int ctas_per_sm;               // 0 = as many as fit
+    int lap_tile_h;                // Laplacian tile height in points, 0 = 32 (64 for a single-iteration
+                                   // first pass); a height whose buffers would not fit two CTAs per SM
+                                   // falls back to 32
+    int bil_tile_h;                // bilateral tile height in quads, 0 = 32
 };
 
 // Number of bilateral passes the parameters need (> 1 needs the carry buffers).
@@ -233,13 +279,26 @@ int resident_ctas(const void* fn, size_t smem, int dev);
 // Sets the shared-memory opt-in of every frame kernel on the current device.
 cudaError_t frame_configure();
 
-// Enqueues the whole path for one frame on `s` (one cooperative launch). Returns a PL3D status.
+// lap1_kernel<WITH_D> (lap1.cu).
+const void* lap1_kernel_for(bool with_d);
+
+// Whether every Laplacian pass of these frame arguments runs at most one iteration with a 3 x 3
+// window, so that lap1_kernel takes them.
+bool lap1_eligible(const FrameArgs& a, int rl);
+
+// Grid of a lap1 launch over `tasks` warp tasks (all resident CTAs when tasks < 0).
+int lap1_grid(int dev, bool with_d, long long tasks);
+
+// Enqueues the whole path for one frame on `s`: one cooperative launch, after one lap1_kernel launch
+// per Laplacian pass when every pass runs at most one iteration with a 3 x 3 window. Returns a
+// PL3D status. The timing stamps of lap1 launches sit after the phase totals (phase_ns + 4).
 // With `normals_ready`, the path runs as two launches and the event is recorded between them,
 // once mask, normals and groups are final (the segments across tiles come after it).
+// *launches (optional) receives the number of kernels enqueued.
 int frame_launch(const FrameScratch& sc, const float* points, int H, int W, const pl3d_params* p, const float* nd_host,
                  int K, uint8_t* out_mask, float* out_normals, int32_t* out_labels, float* out_points,
                  uint8_t* out_groups, const Tuning& t, cudaStream_t s, int32_t* out_labels_copy = nullptr,
-                 cudaEvent_t normals_ready = nullptr);
+                 cudaEvent_t normals_ready = nullptr, int* launches = nullptr);
 
 // Device address of the allocation-free entry point's control words (barrier [2], error word,
 // pad) on the current device (pl3d_static.cu).

@@ -8,9 +8,14 @@
 // room for, up to max_batch_frames. Requests that arrive while a batch is on the GPU therefore
 // join the next batch, which runs beside it on the other slot.
 //
-// Two batches in flight must be resident on the GPU together (each is a cooperative kernel
-// whose CTAs wait for one another): every slot of a two-slot server launches one CTA per SM
-// and keeps its bilateral halo at 3 quads or less, so each CTA fits half an SM's shared memory.
+// Two batches in flight run side by side on the GPU (each is a cooperative kernel whose CTAs wait
+// for one another): every slot of a two-slot server keeps its bilateral halo at 3 quads or less,
+// so that each CTA fits half an SM's shared memory, and launches one CTA per SM while the other
+// slot has a batch on the GPU. A slot that launches while the other one is idle takes two CTAs per
+// SM, and a one-frame batch runs as a plain single-frame launch (no descriptor upload, no graph):
+// at low arrival rates that is the sequential path's own launch. A grid launched while the other
+// slot's grid fills the SMs waits for that grid's CTAs to finish; the other grid never waits for
+// it, so nothing can deadlock.
 #include <math.h>
 #include <string.h>
 
@@ -58,13 +63,13 @@ struct Request {
     int64_t t_launch;
 };
 
-// Launch shape of a batch whose bilateral radius is rb. With two slots both batches must be
-// resident together: one CTA per SM each, and a bilateral halo of at most 3 quads, so that a
-// CTA takes at most half of an SM's shared memory.
-Tuning slot_tuning(int max_inflight, int rb) {
+// Launch shape of a batch whose bilateral radius is rb. With two slots a batch that may run beside
+// the other slot's takes one CTA per SM and a bilateral halo of at most 3 quads, so that a CTA
+// takes at most half of an SM's shared memory; `alone` (the other slot idle) lifts the CTA limit.
+Tuning slot_tuning(int max_inflight, int rb, bool alone = false) {
     if (max_inflight == 1) return Tuning{0, 0, 0};
     const int r = rb > 0 ? rb : 1;
-    return Tuning{0, 3 / r > 0 ? 3 / r : 1, 1};
+    return Tuning{0, 3 / r > 0 ? 3 / r : 1, alone ? 0 : 1};
 }
 
 bool radii_match(int a, int b) { return a == 0 || b == 0 || a == b; }
@@ -149,7 +154,7 @@ int launch_slot(pl3d_server* S, ServeSlot* sl) {
             rc = PL3D_ERR_CUDA;
     }
     if (rc == PL3D_OK) {
-        if (S->cfg.max_batch_frames == 1) {
+        if (S->cfg.max_batch_frames == 1 || frames.size() == 1) {
             for (size_t i = 0; i < frames.size() && rc == PL3D_OK; ++i) {
                 const pl3d_frame& f = frames[i];
                 rc = pl3d_extract_planes(sl->ctx, f.points, f.H, f.W, f.params, f.dominant_normals, f.K,
@@ -237,7 +242,9 @@ void worker_main(pl3d_server* S) {
                 S->pending.pop_front();
             }
             if (sl->reqs.empty()) continue;
-            sl->ctx->tuning = slot_tuning(S->cfg.max_inflight, rb);
+            bool alone = true;
+            for (ServeSlot* o : S->slots) alone &= o == sl || !o->busy;
+            sl->ctx->tuning = slot_tuning(S->cfg.max_inflight, rb, alone);
             sl->busy = true;
             sl->t_done.store(0, std::memory_order_relaxed);
             const int64_t t = now_ns();
@@ -434,6 +441,156 @@ int pl3d_server_get_stats(const pl3d_server* S, pl3d_server_stats* out) {
     out->max_batch_frames = S->max_batch_seen;
     out->max_inflight = S->max_inflight_seen;
     out->slot_bytes = (int64_t)S->slot_bytes;
+    return PL3D_OK;
+}
+
+namespace {
+
+// Linear-interpolation percentile of sorted values (q in [0, 1]).
+double percentile_sorted(const std::vector<double>& v, double q) {
+    if (v.empty()) return 0.0;
+    const double pos = q * (double)(v.size() - 1);
+    const size_t lo = (size_t)pos;
+    const size_t hi = lo + 1 < v.size() ? lo + 1 : lo;
+    return v[lo] + (pos - (double)lo) * (v[hi] - v[lo]);
+}
+
+bool replay_args_ok(const pl3d_replay_source* src, int n_src, const double* arr, const int32_t* which, int64_t n) {
+    for (int s = 0; s < n_src; ++s) {
+        const pl3d_replay_source& r = src[s];
+        if (!r.host_points || r.n_variants < 1 || r.ring < 1 || r.reserved != 0 || !r.params || !r.dominant_normals ||
+            !r.host_mask || !r.host_normals || !r.host_labels)
+            return false;
+        for (int v = 0; v < r.n_variants; ++v)
+            if (!r.host_points[v]) return false;
+        for (int k = 0; k < r.ring; ++k)
+            if (!r.host_mask[k] || !r.host_normals[k] || !r.host_labels[k]) return false;
+    }
+    double prev = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (!(arr[i] >= prev) || !std::isfinite(arr[i]) || which[i] < 0 || which[i] >= n_src) return false;
+        prev = arr[i];
+    }
+    return true;
+}
+
+}  // namespace
+
+int pl3d_server_replay(pl3d_server* S, const pl3d_replay_source* src, int n_src, const double* arr,
+                       const int32_t* which, int64_t n, pl3d_replay_report* rep) {
+    if (!S || !src || n_src < 1 || !arr || !which || n < 1 || !rep) return PL3D_ERR_INVALID_ARG;
+    if (!replay_args_ok(src, n_src, arr, which, n)) return PL3D_ERR_INVALID_ARG;
+    memset(rep, 0, sizeof(*rep));
+    auto submit = [&](int s, int variant, int set, uint64_t* t) {
+        const pl3d_replay_source& r = src[s];
+        return pl3d_server_submit(S, r.host_points[variant], r.H, r.W, r.params, r.dominant_normals, r.K,
+                                  r.host_mask[set], r.host_normals[set], r.host_labels[set], t);
+    };
+    std::vector<pl3d_completion> buf(1024);
+    // warm-up: every frame of every source once, each on its own ring set in turn
+    for (int s = 0; s < n_src; ++s)
+        for (int v = 0; v < src[s].n_variants; ++v) {
+            int rc = submit(s, v, v % src[s].ring, nullptr);
+            if (rc == PL3D_OK && v % src[s].ring == src[s].ring - 1) rc = pl3d_server_drain(S);
+            if (rc != PL3D_OK) return rc;
+        }
+    pl3d_server_drain(S);
+    while (pl3d_server_poll(S, buf.data(), (int)buf.size(), 0) > 0) {
+    }
+    pl3d_server_stats st0;
+    pl3d_server_get_stats(S, &st0);
+
+    std::vector<int64_t> t_sched(n), t_call(n);
+    std::vector<double> latency(n, 0.0);
+    std::vector<int32_t> bframes(n, 0);
+    std::vector<char> done(n, 0);
+    std::vector<int32_t> status(n, PL3D_OK);
+    std::vector<std::vector<int64_t>> owner(n_src);
+    std::vector<int64_t> count(n_src, 0);
+    for (int s = 0; s < n_src; ++s) owner[s].assign(src[s].ring, -1);
+    uint64_t first = 0;
+    int64_t n_done = 0;
+    auto collect = [&](int wait_ms) {
+        const int got = pl3d_server_poll(S, buf.data(), (int)buf.size(), wait_ms);
+        if (got <= 0) return 0;
+        for (int j = 0; j < got; ++j) {
+            const pl3d_completion& c = buf[j];
+            if (c.ticket < first || c.ticket - first >= (uint64_t)n) continue;
+            const int64_t i = (int64_t)(c.ticket - first);
+            done[i] = 1;
+            status[i] = c.status;
+            bframes[i] = c.batch_frames;
+            // server latency runs from the submit call; add the time from the scheduled arrival
+            latency[i] = c.latency_ms + (double)(t_call[i] - t_sched[i]) * 1e-6;
+            ++n_done;
+        }
+        return got;
+    };
+    int rc = PL3D_OK;
+    const int64_t t0 = now_ns();
+    for (int64_t i = 0; i < n && rc == PL3D_OK; ++i) {
+        t_sched[i] = t0 + (int64_t)(arr[i] * 1e9);
+        for (;;) {
+            const int64_t left = t_sched[i] - now_ns();
+            if (left <= 0) break;
+            if (left > 300000) {
+                collect(0);
+                const int64_t nap = std::min<int64_t>(left - 200000, 1000000);
+                if (nap > 0) std::this_thread::sleep_for(std::chrono::nanoseconds(nap));
+            }
+        }
+        const int s = which[i];
+        const int64_t k = count[s]++;
+        const int set = (int)(k % src[s].ring);
+        const int64_t prev = owner[s][set];
+        while (prev >= 0 && !done[prev]) collect(1);   // its output buffers are still in use
+        t_call[i] = now_ns();
+        uint64_t ticket = 0;
+        rc = submit(s, (int)(k % src[s].n_variants), set, &ticket);
+        if (rc != PL3D_OK) break;
+        if (i == 0) first = ticket;
+        owner[s][set] = i;
+    }
+    pl3d_server_drain(S);   // every submitted request has completed
+    const int64_t t_end = now_ns();
+    while (collect(0) > 0) {
+    }
+    if (rc != PL3D_OK) return rc;
+    pl3d_server_stats st1;
+    pl3d_server_get_stats(S, &st1);
+    std::vector<double> lat;
+    lat.reserve(n);
+    double tris = 0.0, bsum = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (!done[i]) continue;
+        rep->completed += 1;
+        if (status[i] != PL3D_OK) rep->failed += 1;
+        lat.push_back(latency[i]);
+        const pl3d_replay_source& r = src[which[i]];
+        tris += 2.0 * (r.H - 1) * (double)(r.W - 1);
+        bsum += bframes[i];
+    }
+    std::vector<double> lags(n);
+    for (int64_t i = 0; i < n; ++i) lags[i] = (double)(t_call[i] - t_sched[i]) * 1e-6;
+    std::sort(lat.begin(), lat.end());
+    std::sort(lags.begin(), lags.end());
+    const double wall = (double)(t_end - t0) * 1e-9;
+    rep->requests = n;
+    rep->batches = st1.batches - st0.batches;
+    rep->max_batch_frames = st1.max_batch_frames;
+    rep->max_inflight = st1.max_inflight;
+    rep->seconds = wall;
+    rep->p50_ms = percentile_sorted(lat, 0.50);
+    rep->p90_ms = percentile_sorted(lat, 0.90);
+    rep->p99_ms = percentile_sorted(lat, 0.99);
+    rep->max_ms = lat.empty() ? 0.0 : lat.back();
+    double sum = 0.0;
+    for (double v : lat) sum += v;
+    rep->mean_ms = lat.empty() ? 0.0 : sum / (double)lat.size();
+    rep->mtri_s = wall > 0 ? tris / wall / 1e6 : 0.0;
+    rep->achieved_fps = wall > 0 ? (double)rep->completed / wall : 0.0;
+    rep->mean_batch_frames = rep->completed ? bsum / (double)rep->completed : 0.0;
+    rep->submit_lag_p99_ms = percentile_sorted(lags, 0.99);
     return PL3D_OK;
 }
 

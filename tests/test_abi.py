@@ -56,7 +56,8 @@ def test_status_strings(pl3d):
     assert pl3d.pl3d_version() >= 10000
     names = [pl3d.pl3d_timing_slot_name(i) for i in range(pl3d.PL3D_TIMING_SLOTS)]
     assert names == ["laplacian", "bilateral", "label_merge", "label_flatten", "frame_kernel", "host_copies",
-                     "mesh_kernel", "fastga_kernel"]
+                     "mesh_kernel", "fastga_kernel", "bil_staging_cta", "bil_geometry_cta", "bil_iterations_cta",
+                     "bil_finish_cta", "bil_labels_cta"]
 
 
 def test_default_params_are_paper_rgbd(pl3d):
@@ -154,7 +155,7 @@ def test_batch_and_tuning_structs(pl3d):
     assert ctypes.sizeof(pl3d.pl3d_frame) == 80
     assert pl3d.pl3d_frame.params.offset == 16 and pl3d.pl3d_frame.K.offset == 32
     assert pl3d.pl3d_frame.out_groups.offset == 72
-    assert ctypes.sizeof(pl3d.pl3d_tuning) == 12
+    assert ctypes.sizeof(pl3d.pl3d_tuning) == 20 and pl3d.pl3d_tuning.bil_tile_h.offset == 16
 
 
 def test_batch_and_tuning_null_arguments(pl3d):

@@ -166,7 +166,9 @@ def test_batch_on_side_stream_and_timing(env):
 
 
 @pytest.mark.parametrize("tun", [dict(lap_fuse=1), dict(bil_fuse=1), dict(lap_fuse=2, bil_fuse=2, ctas_per_sm=1),
-                                 dict(ctas_per_sm=1), dict(lap_fuse=3, bil_fuse=1, ctas_per_sm=2)])
+                                 dict(ctas_per_sm=1), dict(lap_fuse=3, bil_fuse=1, ctas_per_sm=2),
+                                 dict(lap_tile_h=16, bil_tile_h=16), dict(lap_tile_h=48, bil_tile_h=24),
+                                 dict(lap_tile_h=64, bil_tile_h=8, lap_fuse=2), dict(lap_fuse=1, lap_tile_h=40)])
 def test_tuning_never_changes_a_result(env, tun):
     pl3d, ctx, torch = env
     frames = _frames()
@@ -178,7 +180,8 @@ def test_tuning_never_changes_a_result(env, tun):
     single_ref = _single(env, pts[0], *frames[0])
     pl3d.pl3d_set_tuning(ctx, **tun)
     try:
-        assert pl3d.pl3d_get_tuning(ctx).as_dict() == dict(dict(lap_fuse=0, bil_fuse=0, ctas_per_sm=0), **tun)
+        assert pl3d.pl3d_get_tuning(ctx).as_dict() == dict(
+            dict(lap_fuse=0, bil_fuse=0, ctas_per_sm=0, lap_tile_h=0, bil_tile_h=0), **tun)
         b2, outs, _ = _batch(env, frames)
         pl3d.pl3d_extract_planes_batched(ctx, b2)
         single = _single(env, pts[0], *frames[0])
@@ -271,4 +274,26 @@ def test_batch_argument_errors(env):
     # an empty batch does nothing
     pl3d.pl3d_extract_planes_batched(ctx, pl3d.Batch())
     assert pl3d.pl3d_launch_count(ctx) == n0
+    pl3d.pl3d_sync(ctx)
+
+
+def test_single_iteration_batch_runs_lap1_nodes(env):
+    """Every frame at one Laplacian iteration (3 x 3): the Laplacian runs as a lap1_kernel node of
+    the graph before the batch kernel. Results equal single frames bit for bit, the launch count
+    includes the node, and the Laplacian phase time comes from the node's own stamps."""
+    pl3d, ctx, torch = env
+    frames = [(f, dict(p, lap_iters=1)) for f, p in _frames()]
+    frames[4] = (frames[4][0], dict(frames[4][1], lap_iters=0))   # a frame without smoothing beside them
+    b, outs, pts = _batch(env, frames)
+    n0 = pl3d.pl3d_launch_count(ctx)
+    pl3d.pl3d_set_timing(ctx, True)
+    pl3d.pl3d_read_timing(ctx, reset=True)
+    pl3d.pl3d_extract_planes_batched(ctx, b)
+    t = pl3d.pl3d_read_timing(ctx, reset=True)
+    pl3d.pl3d_set_timing(ctx, False)
+    assert pl3d.pl3d_launch_count(ctx) == n0 + 2
+    assert t["laplacian"][0] > 0 and t["bilateral"][0] > 0
+    assert t["laplacian"][0] + t["bilateral"][0] <= 1.05 * t["frame_kernel"][0]
+    for (f, params), o, p in zip(frames, outs, pts):
+        _same(o, _single(env, p, f, params))
     pl3d.pl3d_sync(ctx)

@@ -81,5 +81,7 @@ def test_one_iteration_work_by_hand():
     assert b == 24 * 307200 == 7372800 and f == 128 * 307200
     b, f = bench.one_iteration_work("bilateral", px, tri)
     assert b == 24 * 307200 + 18 * 612162 and f == 468 * 612162
+    b, f = bench.one_iteration_work("bilateral_iteration", px, tri)
+    assert b == 36 * 612162 and f == 468 * 612162
     with pytest.raises(ValueError):
         bench.one_iteration_work("merge", px, tri)

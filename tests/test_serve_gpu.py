@@ -184,3 +184,50 @@ def test_poll_semantics_and_unsupported_two_slot_frame(env):
     finally:
         pl3d.pl3d_server_destroy(srv)
     _equal(torch, o, _alone(env, f, dict(pl3d.make_params(bil_kernel=7, bil_iters=2).as_dict())))
+
+
+@pytest.mark.parametrize("max_inflight,max_batch", [(2, 64), (1, 1)])
+def test_native_trace_replay(env, max_inflight, max_batch):
+    """pl3d_server_replay submits a Poisson trace at its scheduled times from native code and
+    reports the latency from each scheduled arrival. Every request completes without error; after
+    the replay each ring set holds the result of the last request that used it, bit for bit the
+    single-frame result of that request's frame."""
+    pl3d, ctx, torch = env
+    sens = _sensors()
+    srv = pl3d.pl3d_server_create(0, max_inflight=max_inflight, max_batch_frames=max_batch, hbm_bytes=2 << 30)
+    ring = 3
+    sources = []
+    for f, params in sens:
+        H, W = f.points.shape[:2]
+        variants = [f.points, (f.points * np.float32(1.001))]
+        sources.append(dict(points=[torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for v in variants],
+                            params=pl3d.make_params(**params), dominant_normals=f.dominant_normals,
+                            outputs=[_host_out(torch, H, W) for _ in range(ring)]))
+    rng = np.random.default_rng(7)
+    n = 300
+    arr = np.cumsum(rng.exponential(1.0 / 1500.0, n))
+    which = rng.integers(0, len(sens), n)
+    try:
+        rep = pl3d.pl3d_server_replay(srv, sources, arr, which)
+    finally:
+        pl3d.pl3d_server_destroy(srv)
+    print(rep)
+    assert rep["requests"] == n and rep["completed"] == n and rep["failed"] == 0
+    assert 0 < rep["p50_ms"] <= rep["p90_ms"] <= rep["p99_ms"] <= rep["max_ms"]
+    assert rep["seconds"] >= arr[-1] and rep["achieved_fps"] > 0 and rep["mtri_s"] > 0
+    if max_batch == 1:
+        assert rep["max_batch_frames"] == 1
+    for s, (f, params) in enumerate(sens):
+        ks = np.nonzero(which == s)[0]
+        for k_set in range(ring):
+            uses = [k for k in range(len(ks)) if k % ring == k_set]
+            if not uses:
+                continue
+            variant = uses[-1] % 2
+            g = synth.Frame(points=sources[s]["points"][variant].numpy(), dominant_normals=f.dominant_normals,
+                            params=f.params, surface_id=f.surface_id, surface_normals=f.surface_normals,
+                            surface_group=f.surface_group, name=f.name, meta=f.meta)
+            want = _alone(env, g, params)
+            got = sources[s]["outputs"][k_set]
+            assert torch.equal(got[0], want[0]) and torch.equal(got[2], want[2])
+            assert torch.equal(got[1].nan_to_num(7.0), want[1].nan_to_num(7.0))
