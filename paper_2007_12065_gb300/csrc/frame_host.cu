@@ -225,8 +225,11 @@ cudaError_t frame_configure() {
     // the single-iteration Laplacian keeps its rings in static shared memory: all of it as shared
     // memory, so that its CTAs fit as many per SM as their registers allow
     for (bool with_d : {false, true}) {
-        const cudaError_t e = cudaFuncSetAttribute(lap1_kernel_for(with_d), cudaFuncAttributePreferredSharedMemoryCarveout,
-                                                   cudaSharedmemCarveoutMaxShared);
+        cudaError_t e = cudaFuncSetAttribute(lap1_kernel_for(with_d), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)lap1_smem_bytes(with_d));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(lap1_kernel_for(with_d), cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -364,7 +367,7 @@ bool lap1_eligible(const FrameArgs& a, int rl) {
 }
 
 int lap1_grid(int dev, bool with_d, long long tasks) {
-    const int resident = resident_ctas(lap1_kernel_for(with_d), 0, dev);
+    const int resident = resident_ctas(lap1_kernel_for(with_d), lap1_smem_bytes(with_d), dev);
     if (resident <= 0 || tasks < 0) return resident;
     const long long need = (tasks + kThreads / 32 - 1) / (kThreads / 32);
     return need < resident ? (int)(need > 0 ? need : 1) : resident;
@@ -400,7 +403,8 @@ int frame_launch(const FrameScratch& sc, const float* points, int H, int W, cons
             const int g = lap1_grid(dev, with_d, lap1_tasks(H, W));
             if (g <= 0) return PL3D_ERR_CUDA;
             void* largs[1] = {&la};
-            if (cudaLaunchKernel(lap1_kernel_for(with_d), dim3(g), dim3(kThreads), largs, 0, s) != cudaSuccess) {
+            if (cudaLaunchKernel(lap1_kernel_for(with_d), dim3(g), dim3(kThreads), largs, lap1_smem_bytes(with_d), s) !=
+                cudaSuccess) {
                 cudaGetLastError();
                 return PL3D_ERR_CUDA;
             }

@@ -2,20 +2,27 @@
 // window, as a kernel of its own.
 //
 // A single iteration reads every point once and writes its displacement once (24 bytes per point,
-// 36 with the previous pass's displacement), so the pass is bound by HBM, by instruction issue and
-// by how many loads are in flight, not by the halo trade-off that the fused tile passes of
-// frame_kernels.cuh make. A warp owns a task of 32 columns x 24 rows of one frame, each lane one
-// column, and walks down its rows. The rows come through a per-warp ring of kRing row slots in
-// shared memory, filled with cp.async (16-byte copies of the warp's 384-byte row chunk when the
-// rows are 16-byte aligned, 4-byte copies per point otherwise; lanes 0 and 31 also copy the point
-// just outside the chunk), so that kRing - 4 rows are in flight without holding registers. A lane
-// reads its point and its left and right neighbours of a row from the ring into a three-row
-// register window, where the point is computed.
+// 36 with the previous pass's displacement), so the pass is bound by HBM and by instruction issue,
+// not by the halo trade-off that the fused tile passes of frame_kernels.cuh make. A warp owns a task
+// of 64 columns x 24 rows of one frame, each lane a pair of adjacent columns, and walks down its
+// rows.
+//
+// Rows come through a per-warp ring of kRing row slots in shared memory, filled with cp.async:
+// one or two 16-byte copies per lane of the row's 800 bytes, from the point left of the chunk to
+// the point right of it, when the rows are 16-byte aligned; 4-byte copies per point otherwise.
+// So kRing - 4 rows are in flight without holding registers. A lane reads its pair and the points
+// on either side of it from the ring (64-bit shared loads, free of bank conflicts at a 24-byte
+// stride) into a three-row register window.
+//
+// A pair shares work that single columns would repeat: the edge between its two points (E of the
+// left one, W of the right one), the vertical edges (S of a row is N of the next), and the two
+// diagonals inside the pair (SE of the left point and SW of the right one become NW and NE of the
+// next row's pair). Only the weight of a shared diagonal is kept; its difference is formed again.
 //
 // Every point is the same arithmetic as in lap_iteration (frame_kernels.cuh): its window in
-// row-major order (NW, N, NE, W, E, SW, S, SE), the edge to the row below shared with that row's
-// point (w_ij = w_ji, opposite differences), the same rounding intrinsics. Passes of this kernel
-// and fused tile passes therefore give the same bits, and a batch the same bits as single frames.
+// row-major order (NW, N, NE, W, E, SW, S, SE), a shared edge entering with its difference negated
+// (w_ij = w_ji, opposite differences), the same rounding intrinsics. Passes of this kernel and fused
+// tile passes therefore give the same bits, and a batch the same bits as single frames.
 //
 // Invalid points (any coordinate non-finite or beyond kMaxCoord, and points outside the image)
 // become the finite sentinel kInvalidCoord with zero displacement, whose weight underflows to 0.
@@ -25,14 +32,16 @@ namespace pl3d {
 namespace frame {
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
 constexpr int kWarps = kThreads / 32;
 constexpr int kBlock = 3;      // rows per unrolled block: the register window's period
 constexpr int kRing = 8;       // row slots of a warp's ring: rows i + 3 .. i + 6 in flight at row i
-constexpr int kSlot = 104;     // floats per slot: pad, left point, 32 points (at float 4), right point, pad
-constexpr int kSlotPts = 4;    // float offset of the chunk's first point (16-byte aligned)
-static_assert(kLap1Rows % kBlock == 0, "warp tasks are whole blocks of rows");
-static_assert(kSlot % 4 == 0 && kSlotPts + 96 + 3 <= kSlot, "slot layout");
+// A slot: float 0 pad, floats 1-3 the point left of the chunk, floats 4 .. 195 the chunk's 64
+// points, floats 196-198 the point right of it, float 199 pad; kSlot / 4 pieces of 16 bytes.
+constexpr int kSlot = 200;
+constexpr int kSlotPts = 4;
+constexpr int kPieces = kSlot / 4;
+static_assert(kLap1Cols == 64 && kLap1Rows % kBlock == 0, "warp tasks: 64 columns, whole blocks of rows");
+static_assert(kSlotPts + 3 * kLap1Cols + 3 <= kSlot && kPieces <= 64, "slot layout");
 
 __device__ __forceinline__ void cp_async4(float* dst, const float* src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
@@ -46,91 +55,119 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// One row of the window: the lane's point and its left and right neighbours.
+// One row of the window: the point left of the lane's pair, the pair (a, b), the point right of it.
 struct L1Row {
-    LapPt l, c, r;
+    LapPt l, a, b, r;
 };
 
 struct L1Geom {
     int H, W, c0, lane;
-    int nvalid;   // points of the image in this warp's 32 columns
     bool vec;     // 16-byte copies: rows 16-byte aligned (W % 4 == 0, aligned arrays)
 };
 
-// Copies row `row` of the AoS array A (points or displacements) into a ring slot: the warp's 32
+// The edge from a point to the one below it: difference (below - point) and its weight.
+struct L1Edge {
+    float ex, ey, ez, w;
+};
+
+// Copies row `row` of the AoS array A (points or displacements) into a ring slot: the warp's 64
 // points and the one point on each side; points outside the image read as `fill`.
 __device__ __forceinline__ void l1_fill(float* slot, const float* A, const L1Geom& g, int row, float fill) {
     const int lane = g.lane;
+    const float4 f4 = make_float4(fill, fill, fill, fill);
     if (row < 0 || row >= g.H) {
-        slot[kSlotPts + 3 * lane] = fill;
-        slot[kSlotPts + 3 * lane + 1] = fill;
-        slot[kSlotPts + 3 * lane + 2] = fill;
-        if (lane == 0) slot[1] = slot[2] = slot[3] = fill;
-        if (lane == 31) slot[kSlotPts + 96] = slot[kSlotPts + 97] = slot[kSlotPts + 98] = fill;
+        *reinterpret_cast<float4*>(slot + 4 * lane) = f4;
+        if (lane + 32 < kPieces) *reinterpret_cast<float4*>(slot + 4 * (lane + 32)) = f4;
         return;
     }
-    const float* src = A + 3 * ((size_t)row * g.W + g.c0);
+    const float* rowp = A + 3 * (size_t)row * g.W;
     if (g.vec) {
-        // 3 nvalid floats, a multiple of 4 when W is: whole 16-byte pieces of the valid points
-        if (lane < 24 && 4 * lane < 3 * g.nvalid) cp_async16(slot + kSlotPts + 4 * lane, src + 4 * lane);
-    } else if (lane < g.nvalid) {
-        cp_async4(slot + kSlotPts + 3 * lane, src + 3 * lane);
-        cp_async4(slot + kSlotPts + 3 * lane + 1, src + 3 * lane + 1);
-        cp_async4(slot + kSlotPts + 3 * lane + 2, src + 3 * lane + 2);
+        // pieces of the floats 3 c0 - 4 .. 3 c0 + 195 of the row; with W % 4 == 0 a piece lies
+        // wholly inside the row or wholly outside it (then it reads as fill)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int p = lane + 32 * h;
+            if (p >= kPieces) break;
+            const int f0 = 3 * g.c0 - kSlotPts + 4 * p;
+            if (f0 >= 0 && f0 + 4 <= 3 * g.W) cp_async16(slot + 4 * p, rowp + f0);
+            else *reinterpret_cast<float4*>(slot + 4 * p) = f4;
+        }
+        return;
     }
-    if (lane >= g.nvalid) {
-        slot[kSlotPts + 3 * lane] = fill;
-        slot[kSlotPts + 3 * lane + 1] = fill;
-        slot[kSlotPts + 3 * lane + 2] = fill;
-    }
-    if (lane == 0) {
-        if (g.c0 > 0) {
-            cp_async4(slot + 1, src - 3);
-            cp_async4(slot + 2, src - 2);
-            cp_async4(slot + 3, src - 1);
+    // point by point: the lane's pair, and the point on each side for lanes 0 and 31
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int c = g.c0 + 2 * lane + k;
+        float* d = slot + kSlotPts + 3 * (2 * lane + k);
+        if (c < g.W) {
+            cp_async4(d, rowp + 3 * c);
+            cp_async4(d + 1, rowp + 3 * c + 1);
+            cp_async4(d + 2, rowp + 3 * c + 2);
         } else {
-            slot[1] = slot[2] = slot[3] = fill;
+            d[0] = d[1] = d[2] = fill;
         }
     }
-    if (lane == 31) {
-        if (g.nvalid == 32 && g.c0 + 32 < g.W) {
-            cp_async4(slot + kSlotPts + 96, src + 96);
-            cp_async4(slot + kSlotPts + 97, src + 97);
-            cp_async4(slot + kSlotPts + 98, src + 98);
+    if (lane == 0 || lane == 31) {
+        const int c = lane == 0 ? g.c0 - 1 : g.c0 + kLap1Cols;
+        float* d = lane == 0 ? slot + 1 : slot + kSlotPts + 3 * kLap1Cols;
+        if (c >= 0 && c < g.W) {
+            cp_async4(d, rowp + 3 * c);
+            cp_async4(d + 1, rowp + 3 * c + 1);
+            cp_async4(d + 2, rowp + 3 * c + 2);
         } else {
-            slot[kSlotPts + 96] = slot[kSlotPts + 97] = slot[kSlotPts + 98] = fill;
+            d[0] = d[1] = d[2] = fill;
         }
     }
 }
 
 // Invalid -> the sentinel with zero displacement.
 template <bool WITH_D>
-__device__ __forceinline__ LapPt l1_point(const float* p, const float* d) {
+__device__ __forceinline__ LapPt l1_point(float x, float y, float z, float dx, float dy, float dz) {
     LapPt q;
-    const float x = p[0], y = p[1], z = p[2];
     const bool ok = point_valid(x, y, z);
     q.x = ok ? x : kInvalidCoord;
     q.y = ok ? y : kInvalidCoord;
     q.z = ok ? z : kInvalidCoord;
-    q.dx = (WITH_D && ok) ? d[0] : 0.f;
-    q.dy = (WITH_D && ok) ? d[1] : 0.f;
-    q.dz = (WITH_D && ok) ? d[2] : 0.f;
+    q.dx = (WITH_D && ok) ? dx : 0.f;
+    q.dy = (WITH_D && ok) ? dy : 0.f;
+    q.dz = (WITH_D && ok) ? dz : 0.f;
     return q;
 }
 
-// The lane's left point, own point and right point of a ring slot into a window row.
-template <bool WITH_D>
-__device__ __forceinline__ void l1_take(const float* sp, const float* sd, int lane, L1Row& w) {
-    const int o = kSlotPts + 3 * lane;
-    w.l = l1_point<WITH_D>(sp + o - 3, sd + o - 3);
-    w.c = l1_point<WITH_D>(sp + o, sd + o);
-    w.r = l1_point<WITH_D>(sp + o + 3, sd + o + 3);
+// The 12 floats of a lane's window row: the left point at slot float 1 + 6 lane, the pair at
+// 4 + 6 lane, the right point at 10 + 6 lane (64-bit loads at the even offsets).
+struct L1Floats {
+    float v[12];
+};
+
+__device__ __forceinline__ void l1_read(const float* s, int lane, L1Floats& f) {
+    const int o = 6 * lane;
+    f.v[0] = s[o + 1];
+    const float2 p0 = *reinterpret_cast<const float2*>(s + o + 2);
+    const float2 p1 = *reinterpret_cast<const float2*>(s + o + 4);
+    const float2 p2 = *reinterpret_cast<const float2*>(s + o + 6);
+    const float2 p3 = *reinterpret_cast<const float2*>(s + o + 8);
+    const float2 p4 = *reinterpret_cast<const float2*>(s + o + 10);
+    f.v[1] = p0.x, f.v[2] = p0.y, f.v[3] = p1.x, f.v[4] = p1.y, f.v[5] = p2.x, f.v[6] = p2.y;
+    f.v[7] = p3.x, f.v[8] = p3.y, f.v[9] = p4.x, f.v[10] = p4.y;
+    f.v[11] = s[o + 12];
 }
 
-// The shared edge to the row below: difference (below - centre) and its weight.
-struct L1Edge {
-    float ex, ey, ez, w;
-};
+template <bool WITH_D>
+__device__ __forceinline__ void l1_take(const float* sp, const float* sd, int lane, L1Row& w) {
+    L1Floats p, d;
+    l1_read(sp, lane, p);
+    if (WITH_D) {
+        l1_read(sd, lane, d);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) d.v[k] = 0.f;
+    }
+    w.l = l1_point<WITH_D>(p.v[0], p.v[1], p.v[2], d.v[0], d.v[1], d.v[2]);
+    w.a = l1_point<WITH_D>(p.v[3], p.v[4], p.v[5], d.v[3], d.v[4], d.v[5]);
+    w.b = l1_point<WITH_D>(p.v[6], p.v[7], p.v[8], d.v[6], d.v[7], d.v[8]);
+    w.r = l1_point<WITH_D>(p.v[9], p.v[10], p.v[11], d.v[9], d.v[10], d.v[11]);
+}
 
 // Frame f of warp task t: the largest f < n with pre[f] <= t (pre[0] = 0 <= t < pre[n]). The
 // lanes probe 32 positions at once.
@@ -140,7 +177,7 @@ __device__ __forceinline__ int l1_find_frame(const int* pre, int n, int t, int l
         const int step = (hi - lo + 31) >> 5;
         const int pos = lo + lane * step;
         const bool le = pos < hi && __ldg(pre + pos) <= t;
-        const unsigned m = __ballot_sync(kFull, le);   // lanes 0 .. k (lane 0: pos = lo)
+        const unsigned m = __ballot_sync(0xffffffffu, le);   // lanes 0 .. k (lane 0: pos = lo)
         const int k = 31 - __clz((int)m);
         lo += k * step;
         hi = min(hi, lo + step);
@@ -148,11 +185,62 @@ __device__ __forceinline__ int l1_find_frame(const int* pre, int n, int t, int l
     return lo;
 }
 
-// One warp task: columns cb * 32 + lane, rows rb * kLap1Rows .. + kLap1Rows - 1 of frame fr. `ring`
-// (and `dring` with WITH_D) hold kRing slots; `stage` one output row.
+// Sums of one point's Eq. 1 terms.
+struct L1Sum {
+    float sx, sy, sz, ws;
+};
+
+// A neighbour term with a fresh difference q - p and its weight.
 template <bool WITH_D>
-__device__ __forceinline__ void l1_task(const Lap1Frame& fr, int task, int lane, float* ring, float* dring,
-                                        float* stage) {
+__device__ __forceinline__ void l1_add(L1Sum& s, const LapPt& p, const LapPt& q) {
+    float ex, ey, ez;
+    lap_diff<WITH_D>(p, q, ex, ey, ez);
+    lap_accumulate(s.sx, s.sy, s.sz, s.ws, lap_weight(ex, ey, ez), ex, ey, ez);
+}
+
+// A neighbour term with a fresh difference q - p and a known weight (of the same pair of points).
+template <bool WITH_D>
+__device__ __forceinline__ void l1_add_w(L1Sum& s, const LapPt& p, const LapPt& q, float w) {
+    float ex, ey, ez;
+    lap_diff<WITH_D>(p, q, ex, ey, ez);
+    lap_accumulate(s.sx, s.sy, s.sz, s.ws, w, ex, ey, ez);
+}
+
+// A neighbour term whose difference is the negation of a known edge's (the edge from q to p).
+__device__ __forceinline__ void l1_add_neg(L1Sum& s, const L1Edge& e) {
+    lap_accumulate(s.sx, s.sy, s.sz, s.ws, e.w, -e.ex, -e.ey, -e.ez);
+}
+
+// A neighbour term that also keeps its edge (difference q - p and weight).
+template <bool WITH_D>
+__device__ __forceinline__ void l1_add_keep(L1Sum& s, const LapPt& p, const LapPt& q, L1Edge& e) {
+    lap_diff<WITH_D>(p, q, e.ex, e.ey, e.ez);
+    e.w = lap_weight(e.ex, e.ey, e.ez);
+    lap_accumulate(s.sx, s.sy, s.sz, s.ws, e.w, e.ex, e.ey, e.ez);
+}
+
+// Eq. 1 for one point: its new displacement (or the kept one), and its export.
+__device__ __forceinline__ void l1_out(const LapPt& p, const L1Sum& s, bool pin, float lambda, bool zero, float& ox,
+                                       float& oy, float& oz) {
+    const bool keep = pin || p.x == kInvalidCoord || !(s.ws > 0.f);
+    const float k = lap_scale(keep, lambda, s.ws);
+    ox = fmaf(k, s.sx, p.dx);
+    oy = fmaf(k, s.sy, p.dy);
+    oz = fmaf(k, s.sz, p.dz);
+    if (zero) ox = oy = oz = 0.f;
+}
+
+__device__ __forceinline__ void l1_export(float* e, const LapPt& p, float ox, float oy, float oz) {
+    const bool valid = p.x != kInvalidCoord;
+    e[0] = valid ? __fadd_rn(p.x, ox) : NAN;
+    e[1] = valid ? __fadd_rn(p.y, oy) : NAN;
+    e[2] = valid ? __fadd_rn(p.z, oz) : NAN;
+}
+
+// One warp task: columns cb * 64 + 2 lane and + 1, rows rb * kLap1Rows .. + kLap1Rows - 1 of frame
+// fr. `ring` (and `dring` with WITH_D) hold kRing slots of this warp.
+template <bool WITH_D>
+__device__ __forceinline__ void l1_task(const Lap1Frame& fr, int task, int lane, float* ring, float* dring) {
     const int H = fr.H, W = fr.W;
     const int ncb = div_up(W, kLap1Cols);
     const int rb = task / ncb, cb = task - rb * ncb;
@@ -162,24 +250,22 @@ __device__ __forceinline__ void l1_task(const Lap1Frame& fr, int task, int lane,
     g.W = W;
     g.c0 = cb * kLap1Cols;
     g.lane = lane;
-    g.nvalid = min(32, W - g.c0);
     g.vec = (W & 3) == 0 && ((uintptr_t)fr.points & 15u) == 0 && (!WITH_D || ((uintptr_t)fr.d_in & 15u) == 0);
-    const int c = g.c0 + lane;
-    const bool col_out = c < W;
+    const int ca = g.c0 + 2 * lane;   // the pair's columns: ca, ca + 1
+    const bool out_a = ca < W, out_b = ca + 1 < W;
+    const bool pin_a = ca < 1 || ca >= W - 1, pin_b = ca + 1 >= W - 1;
     const float lambda = fr.lambda;
     const bool zero = fr.iters == 0;
     float* const d_out = fr.d_out;
     float* const exp_pts = fr.export_points;
-    // rows go out as float4 through the staging row when they are 16-byte aligned
-    const bool vec_out = (W & 3) == 0 && ((uintptr_t)d_out & 15u) == 0;
-    const bool colpin = c < 1 || c >= W - 1;
+    // the pair's six floats start 8-byte aligned in every row when W is even
+    const bool st64 = (W & 1) == 0 && ((uintptr_t)d_out & 7u) == 0;
     // rows r0 - 1 .. r0 + kLap1Rows are needed (row H, the one below the image, read as invalid);
     // ring index i holds row r0 - 1 + i in slot i % kRing
     const int last_index = min(kLap1Rows + 1, H - r0 + 1);
     auto fill = [&](int i) {
         if (i <= last_index) {
-            float* sl = ring + (i % kRing) * kSlot;
-            l1_fill(sl, fr.points, g, r0 - 1 + i, NAN);
+            l1_fill(ring + (i % kRing) * kSlot, fr.points, g, r0 - 1 + i, NAN);
             if (WITH_D) l1_fill(dring + (i % kRing) * kSlot, fr.d_in, g, r0 - 1 + i, 0.f);
         }
         cp_async_commit();   // one group per index, empty or not: the wait counts stay constant
@@ -197,60 +283,90 @@ __device__ __forceinline__ void l1_task(const Lap1Frame& fr, int task, int lane,
     take(0, win[2]);
     take(1, win[0]);
     take(2, win[1]);
-    L1Edge es;   // edge from row r - 1 down to row r of this column
-    lap_diff<WITH_D>(win[2].c, win[0].c, es.ex, es.ey, es.ez);
-    es.w = lap_weight(es.ex, es.ey, es.ez);
+    // edges carried from row r - 1 to row r: the verticals of a and b, and the weights of the
+    // diagonals inside the pair (a above to b below, b above to a below)
+    L1Edge na, nb;
+    float w_se, w_sw;
+    {
+        const L1Row& up = win[2];
+        const L1Row& mid = win[0];
+        lap_diff<WITH_D>(up.a, mid.a, na.ex, na.ey, na.ez);
+        na.w = lap_weight(na.ex, na.ey, na.ez);
+        lap_diff<WITH_D>(up.b, mid.b, nb.ex, nb.ey, nb.ez);
+        nb.w = lap_weight(nb.ex, nb.ey, nb.ez);
+        float ex, ey, ez;
+        lap_diff<WITH_D>(up.a, mid.b, ex, ey, ez);
+        w_se = lap_weight(ex, ey, ez);
+        lap_diff<WITH_D>(up.b, mid.a, ex, ey, ez);
+        w_sw = lap_weight(ex, ey, ez);
+    }
 
-    for (int b = 0; b < kLap1Rows; b += kBlock) {
-        if (r0 + b >= H) break;   // warp-uniform
+    for (int bk = 0; bk < kLap1Rows; bk += kBlock) {
+        if (r0 + bk >= H) break;   // warp-uniform
 #pragma unroll
         for (int j = 0; j < kBlock; ++j) {
-            const int r = r0 + b + j;
-            const int i = b + j + 1;   // ring index of row r
+            const int r = r0 + bk + j;
+            const int i = bk + j + 1;   // ring index of row r
             L1Row& up = win[(j + 2) % 3];
             L1Row& mid = win[j % 3];
             L1Row& dn = win[(j + 1) % 3];
             fill(i + kRing - 2);   // into the slot of index i - 2, read before the last __syncwarp
 
-            LapAcc A;
-            A.c = mid.c;
-            A.sx = A.sy = A.sz = A.ws = 0.f;
-            lap_add<WITH_D>(A, up.l);                                                   // NW
-            lap_accumulate(A.sx, A.sy, A.sz, A.ws, es.w, -es.ex, -es.ey, -es.ez);      // N (shared)
-            lap_add<WITH_D>(A, up.r);                                                   // NE
-            lap_add<WITH_D>(A, mid.l);                                                  // W
-            lap_add<WITH_D>(A, mid.r);                                                  // E
-            lap_add<WITH_D>(A, dn.l);                                                   // SW
-            lap_diff<WITH_D>(A.c, dn.c, es.ex, es.ey, es.ez);                           // S (kept)
-            es.w = lap_weight(es.ex, es.ey, es.ez);
-            lap_accumulate(A.sx, A.sy, A.sz, A.ws, es.w, es.ex, es.ey, es.ez);
-            lap_add<WITH_D>(A, dn.r);                                                   // SE
+            const LapPt& pa = mid.a;
+            const LapPt& pb = mid.b;
+            L1Sum A = {0.f, 0.f, 0.f, 0.f}, B = {0.f, 0.f, 0.f, 0.f};
+            // a: NW, N (carried), NE (weight carried), W
+            l1_add<WITH_D>(A, pa, up.l);
+            l1_add_neg(A, na);
+            l1_add_w<WITH_D>(A, pa, up.b, w_sw);
+            l1_add<WITH_D>(A, pa, mid.l);
+            // b: NW (weight carried), N (carried), NE
+            l1_add_w<WITH_D>(B, pb, up.a, w_se);
+            l1_add_neg(B, nb);
+            l1_add<WITH_D>(B, pb, up.r);
+            // the edge inside the pair: E of a, W of b
+            L1Edge ab;
+            l1_add_keep<WITH_D>(A, pa, pb, ab);
+            l1_add_neg(B, ab);
+            // a: SW, S (kept for the next row), SE (weight kept)
+            l1_add<WITH_D>(A, pa, dn.l);
+            l1_add_keep<WITH_D>(A, pa, dn.a, na);
+            L1Edge dg;
+            l1_add_keep<WITH_D>(A, pa, dn.b, dg);
+            w_se = dg.w;
+            // b: E, SW (weight kept), S (kept), SE
+            l1_add<WITH_D>(B, pb, mid.r);
+            l1_add_keep<WITH_D>(B, pb, dn.a, dg);
+            w_sw = dg.w;
+            l1_add_keep<WITH_D>(B, pb, dn.b, nb);
+            l1_add<WITH_D>(B, pb, dn.r);
 
-            const bool keep = colpin || r < 1 || r >= H - 1 || A.c.x == kInvalidCoord || !(A.ws > 0.f);
-            const float s = lap_scale(keep, lambda, A.ws);
-            float ox = fmaf(s, A.sx, A.c.dx), oy = fmaf(s, A.sy, A.c.dy), oz = fmaf(s, A.sz, A.c.dz);
-            if (zero) ox = oy = oz = 0.f;
+            const bool row_pin = r < 1 || r >= H - 1;
+            float ax, ay, az, bx, by, bz;
+            l1_out(pa, A, pin_a || row_pin, lambda, zero, ax, ay, az);
+            l1_out(pb, B, pin_b || row_pin, lambda, zero, bx, by, bz);
             if (r < H) {   // warp-uniform
-                const size_t gi = 3 * ((size_t)r * W + c);
-                if (vec_out) {
-                    stage[3 * lane] = ox;
-                    stage[3 * lane + 1] = oy;
-                    stage[3 * lane + 2] = oz;
-                    __syncwarp();
-                    if (lane < 24 && 4 * lane < 3 * g.nvalid)
-                        *reinterpret_cast<float4*>(d_out + 3 * ((size_t)r * W + g.c0) + 4 * lane) =
-                            reinterpret_cast<const float4*>(stage)[lane];
-                    __syncwarp();
-                } else if (col_out) {
-                    d_out[gi] = ox;
-                    d_out[gi + 1] = oy;
-                    d_out[gi + 2] = oz;
+                const size_t gi = 3 * ((size_t)r * W + ca);
+                if (st64 && out_b) {
+                    float2* o = reinterpret_cast<float2*>(d_out + gi);
+                    o[0] = make_float2(ax, ay);
+                    o[1] = make_float2(az, bx);
+                    o[2] = make_float2(by, bz);
+                } else {
+                    if (out_a) {
+                        d_out[gi] = ax;
+                        d_out[gi + 1] = ay;
+                        d_out[gi + 2] = az;
+                    }
+                    if (out_b) {
+                        d_out[gi + 3] = bx;
+                        d_out[gi + 4] = by;
+                        d_out[gi + 5] = bz;
+                    }
                 }
-                if (exp_pts && col_out) {
-                    const bool valid = A.c.x != kInvalidCoord;
-                    exp_pts[gi] = valid ? __fadd_rn(A.c.x, ox) : NAN;
-                    exp_pts[gi + 1] = valid ? __fadd_rn(A.c.y, oy) : NAN;
-                    exp_pts[gi + 2] = valid ? __fadd_rn(A.c.z, oz) : NAN;
+                if (exp_pts) {
+                    if (out_a) l1_export(exp_pts + gi, pa, ax, ay, az);
+                    if (out_b) l1_export(exp_pts + gi + 3, pb, bx, by, bz);
                 }
             }
             // row r + 2 (index i + 2) takes the window slot of row r - 1
@@ -267,12 +383,19 @@ __device__ __forceinline__ void l1_task(const Lap1Frame& fr, int task, int lane,
 }  // namespace
 }  // namespace frame
 
+size_t lap1_smem_bytes(bool with_d) {
+    return (size_t)(with_d ? 2 : 1) * frame::kWarps * frame::kRing * frame::kSlot * sizeof(float);
+}
+
+// Dynamic shared memory: kWarps rings of points, then (WITH_D) kWarps rings of displacements.
+// Two CTAs per SM: 128 registers hold the three-row window of a pair without spilling.
 template <bool WITH_D>
-__global__ void __launch_bounds__(kThreads, WITH_D ? 2 : 4) lap1_kernel(const __grid_constant__ Lap1Args a) {
-    __shared__ __align__(16) float stage[kThreads / 32][3 * 32];
-    __shared__ __align__(16) float ring[kThreads / 32][frame::kRing * frame::kSlot];
-    __shared__ __align__(16) float dring[WITH_D ? kThreads / 32 : 1][WITH_D ? frame::kRing * frame::kSlot : 4];
+__global__ void __launch_bounds__(kThreads, 2) lap1_kernel(const __grid_constant__ Lap1Args a) {
+    extern __shared__ __align__(16) float l1_smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int kWarpFloats = frame::kRing * frame::kSlot;
+    float* const ring = l1_smem + warp * kWarpFloats;
+    float* const dring = WITH_D ? l1_smem + (frame::kWarps + warp) * kWarpFloats : ring;
     bool timed = false;
     if (a.stamp) timed = a.hdr ? __ldg(&a.hdr->timing) != 0 : true;
     if (timed && threadIdx.x == 0) atomicMax(a.stamp, ~(unsigned long long)global_ns());
@@ -293,10 +416,9 @@ __global__ void __launch_bounds__(kThreads, WITH_D ? 2 : 4) lap1_kernel(const __
             fr.W = __ldg(&fa->W);
             fr.iters = __ldg(&ph->iters);
             fr.lambda = __ldg(&fa->lambda);
-            frame::l1_task<WITH_D>(fr, t - __ldg(a.task_pre + f), lane, ring[warp], dring[WITH_D ? warp : 0],
-                                   stage[warp]);
+            frame::l1_task<WITH_D>(fr, t - __ldg(a.task_pre + f), lane, ring, dring);
         } else {
-            frame::l1_task<WITH_D>(a.one, t, lane, ring[warp], dring[WITH_D ? warp : 0], stage[warp]);
+            frame::l1_task<WITH_D>(a.one, t, lane, ring, dring);
         }
     }
     if (timed) {

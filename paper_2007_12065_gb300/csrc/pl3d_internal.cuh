@@ -177,8 +177,8 @@ __global__ void batch_kernel(const __grid_constant__ BatchArgs b);
 // The single-iteration Laplacian pass with a 3 x 3 window as a kernel of its own (lap1.cu): used
 // when every Laplacian pass of a frame (of every frame of a batch) runs at most one iteration,
 // before the persistent kernel, which then starts at the bilateral. Work unit: a warp task of
-// kLap1Cols columns x kLap1Rows rows of one frame.
-constexpr int kLap1Cols = 32;
+// kLap1Cols columns x kLap1Rows rows of one frame (a pair of columns per lane).
+constexpr int kLap1Cols = 64;
 constexpr int kLap1Rows = 24;
 __host__ __device__ inline int lap1_tasks(int H, int W) { return div_up(H, kLap1Rows) * div_up(W, kLap1Cols); }
 
@@ -279,8 +279,9 @@ int resident_ctas(const void* fn, size_t smem, int dev);
 // Sets the shared-memory opt-in of every frame kernel on the current device.
 cudaError_t frame_configure();
 
-// lap1_kernel<WITH_D> (lap1.cu).
+// lap1_kernel<WITH_D> (lap1.cu) and its dynamic shared memory.
 const void* lap1_kernel_for(bool with_d);
+size_t lap1_smem_bytes(bool with_d);
 
 // Whether every Laplacian pass of these frame arguments runs at most one iteration with a 3 x 3
 // window, so that lap1_kernel takes them.
