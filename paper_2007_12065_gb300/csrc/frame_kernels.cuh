@@ -607,21 +607,36 @@ __device__ __forceinline__ void quad_neighbour(QuadAcc& A, f2 a2, f2 cx, f2 cy, 
 // geometry, `ph.iters` fused iterations (Eq. 3-6), then either
 // the carry for the next chunk or mask, normals, groups (Algorithm 4) and the tile-local
 // segments (Algorithm 5).
-// With timing on (sns != nullptr), thread 0 adds the tile's time in each stage -- staging,
-// geometry, iterations, finish (groups and outputs, or the carry), tile labels -- to sns[0..4]
-// (%globaltimer nanoseconds summed over tiles: CTA time, not wall time).
+// Shared-memory header of the persistent kernels (128 bytes before the tiles' buffers): the staging
+// mbarriers from byte 0, the bilateral tile's deferred-normal count at byte 64, and for the stage
+// timing the last stamp at byte 72 and the stage totals' address (or nullptr) at byte 80.
+constexpr int kHdrExact = 64, kHdrStamp = 72, kHdrStages = 80;
+
+__device__ __forceinline__ void set_stage_timing(uint64_t* bar, unsigned long long* sns) {
+    if (threadIdx.x == 0) *reinterpret_cast<unsigned long long**>(reinterpret_cast<unsigned char*>(bar) + kHdrStages) = sns;
+}
+
+// With stage timing on (set_stage_timing), thread 0 adds the tile's time in each stage -- staging,
+// geometry, iterations, finish (groups and outputs, or the carry), tile labels -- to the totals
+// (%globaltimer nanoseconds summed over tiles: CTA time, not wall time). The state lives in the
+// shared-memory header, so that it holds no register across the tile.
+__device__ __forceinline__ void stage_mark(uint64_t* bar, int k) {
+    if (threadIdx.x == 0) {
+        unsigned char* hdr = reinterpret_cast<unsigned char*>(bar);
+        unsigned long long* sns = *reinterpret_cast<unsigned long long**>(hdr + kHdrStages);
+        if (sns) {
+            unsigned long long* last = reinterpret_cast<unsigned long long*>(hdr + kHdrStamp);
+            const unsigned long long t = global_ns();
+            if (k >= 0) atomicAdd(sns + k, t - *last);
+            *last = t;
+        }
+    }
+}
+
 template <int R>
 __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float* smem, uint64_t* bar,
-                         unsigned& parity, unsigned long long* sns = nullptr) {
-    uint64_t t_stage = 0;
-    auto stage_mark = [&](int k) {
-        if (sns && threadIdx.x == 0) {
-            const uint64_t t = global_ns();
-            if (k >= 0) atomicAdd(sns + k, (unsigned long long)(t - t_stage));
-            t_stage = t;
-        }
-    };
-    stage_mark(-1);
+                         unsigned& parity) {
+    stage_mark(bar, -1);
     // the frame's arguments, read once (the batch kernel keeps them in global memory, where every
     // barrier and every global store would make the compiler load them again)
     const int H = a.H, W = a.W, Hq = H - 1, Wq = W - 1;
@@ -664,7 +679,7 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
         parity ^= 1u;
     }
     __syncthreads();
-    int* n_exact = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(bar) + 64);   // in the smem header
+    int* n_exact = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(bar) + kHdrExact);   // in the smem header
     if (threadIdx.x == 0) *n_exact = 0;
     {
         // (row, column) of point i = threadIdx.x + k blockDim.x, stepped without a division; four
@@ -704,7 +719,7 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
         }
     }
     __syncthreads();
-    stage_mark(0);
+    stage_mark(bar, 0);
 
     // Centroids and normals of every staged triangle; masks of the tile's own quads. A normal
     // whose FP32 error bound fails is deferred: its quad goes on a short list that a second
@@ -830,7 +845,7 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
         }
     }
     __syncthreads();   // the staged boxes are dead from here on; Nb reuses their space
-    stage_mark(1);
+    stage_mark(bar, 1);
 
     // Fused bilateral iterations: each work item is a vertical pair of quads.
     float* cur = Na;
@@ -871,7 +886,7 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
         cur = nxt;
         nxt = tmp;
     }
-    stage_mark(2);
+    stage_mark(bar, 2);
 
     if (!last) {
         for (int i = threadIdx.x; i < TH * T; i += blockDim.x) {
@@ -891,7 +906,7 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
             }
         }
         __syncthreads();
-        stage_mark(3);
+        stage_mark(bar, 3);
         return;
     }
 
@@ -911,6 +926,10 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
     float nd[3 * kRegGroups];
 #pragma unroll
     for (int j = 0; j < 3 * kRegGroups; ++j) nd[j] = j < 3 * K ? ndv[j] : 0.f;
+    // quads' outputs as 2-byte and 8-byte stores when the arrays allow (a quad starts at an even
+    // GID; sizes, when present, are scratch of this library and 8-byte aligned)
+    const bool vec_out = ((uintptr_t)out_mask & 1u) == 0 && ((uintptr_t)out_groups & 1u) == 0 &&
+                         ((uintptr_t)out_normals & 7u) == 0;
     for (int i = threadIdx.x; i < TH * T; i += blockDim.x) {
         const int r = i / T, c = i - r * T;
         const int gu = ty * TH + r, gv = tx * T + c;
@@ -918,6 +937,8 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
         V3 n[2];
         load_quad(cur, (r + h) * RQW + (c + h), n[0], n[1]);
         const size_t gid0 = exists ? 2 * ((size_t)gu * Wq + gv) : 0;
+        int gk[2];
+        bool kk[2];
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
             const int t = 2 * i + k;
@@ -947,21 +968,36 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
                 }
                 if (best < min_dot) g = PL3D_NO_GROUP;
             }
-            if (exists) {
-                const size_t gid = gid0 + k;
-                out_mask[gid] = kept ? 1 : 0;
-                float* o = out_normals + 3 * gid;
-                o[0] = has ? n[k].x : NAN;
-                o[1] = has ? n[k].y : NAN;
-                o[2] = has ? n[k].z : NAN;
-                out_groups[gid] = (uint8_t)g;
-                if (sizes) sizes[gid] = 0;
-            }
+            gk[k] = g;
+            kk[k] = kept;
+            if (!has) n[k] = {NAN, NAN, NAN};
             Gs[t] = exists ? (uint8_t)g : (uint8_t)PL3D_NO_GROUP;
+        }
+        if (exists) {
+            // the quad's two triangles are consecutive GIDs: one store per array when aligned
+            if (vec_out) {
+                *reinterpret_cast<uint16_t*>(out_mask + gid0) = (uint16_t)((kk[0] ? 1 : 0) | (kk[1] ? 256 : 0));
+                *reinterpret_cast<uint16_t*>(out_groups + gid0) = (uint16_t)(gk[0] | (gk[1] << 8));
+                float2* o = reinterpret_cast<float2*>(out_normals + 3 * gid0);
+                o[0] = make_float2(n[0].x, n[0].y);
+                o[1] = make_float2(n[0].z, n[1].x);
+                o[2] = make_float2(n[1].y, n[1].z);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    out_mask[gid0 + k] = kk[k] ? 1 : 0;
+                    out_groups[gid0 + k] = (uint8_t)gk[k];
+                    float* o = out_normals + 3 * (gid0 + k);
+                    o[0] = n[k].x;
+                    o[1] = n[k].y;
+                    o[2] = n[k].z;
+                }
+            }
+            if (sizes) *reinterpret_cast<int2*>(sizes + gid0) = make_int2(0, 0);
         }
     }
     __syncthreads();
-    stage_mark(3);
+    stage_mark(bar, 3);
 
     // Connected components inside the tile (twins of Algorithm 2 that stay in the tile).
     const bool offs = a.max_offset_scaled > 0.f;
@@ -1054,7 +1090,7 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
         }
     }
     __syncthreads();
-    stage_mark(4);
+    stage_mark(bar, 4);
 }
 
 // ------------------------------------------------------------------------- segments (Alg. 5)
@@ -1214,6 +1250,7 @@ __global__ void __launch_bounds__(kThreads, 2) frame_kernel(const __grid_constan
     float* smem = reinterpret_cast<float*>(smem_raw + 128);
     if (threadIdx.x == 0)
         for (int i = 0; i < kLapMaxStages; ++i) mbar_init(bar + i, 1);
+    frame::set_stage_timing(bar, a.phase_ns ? a.phase_ns + kStageSlot : nullptr);
     __syncthreads();
     unsigned par = 0;   // mbarrier parities of the staging slots, one bit each
     uint64_t t_prev = 0;
@@ -1255,8 +1292,7 @@ __global__ void __launch_bounds__(kThreads, 2) frame_kernel(const __grid_constan
         const int tiles_bil = div_up(a.H - 1, a.bil_th) * div_up(a.W - 1, kTile);
         unsigned par0 = par & 1u;   // the bilateral stages through slot 0
         for (int c = 0; c < a.n_bil; ++c) {
-            for (int t = blockIdx.x; t < tiles_bil; t += gridDim.x)
-                frame::bil_tile<RB>(a, a.bil[c], t, smem, bar, par0, a.phase_ns ? a.phase_ns + kStageSlot : nullptr);
+            for (int t = blockIdx.x; t < tiles_bil; t += gridDim.x) frame::bil_tile<RB>(a, a.bil[c], t, smem, bar, par0);
             if (a.part == 0 || c + 1 < a.n_bil) grid_barrier(a.barrier, a.error);
         }
         frame::phase_mark(a, 1, t_prev);
@@ -1310,6 +1346,7 @@ __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const __grid_constan
     float* smem = reinterpret_cast<float*>(smem_raw + 128);
     if (threadIdx.x == 0)
         for (int i = 0; i < kLapMaxStages; ++i) mbar_init(bar + i, 1);
+    frame::set_stage_timing(bar, b.hdr->timing ? b.phase_ns + kStageSlot : nullptr);
     __syncthreads();
     unsigned par = 0;   // mbarrier parities of the staging slots, one bit each
     const int n = b.hdr->n, n_lap = b.hdr->n_lap, n_bil = b.hdr->n_bil;
@@ -1403,7 +1440,7 @@ __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const __grid_constan
                 }
                 acquired = f;
             }
-            frame::bil_tile<RB>(a, a.bil[c], t - __ldg(pre + f), smem, bar, par0, pns ? pns + kStageSlot : nullptr);
+            frame::bil_tile<RB>(a, a.bil[c], t - __ldg(pre + f), smem, bar, par0);
         }
         grid_barrier(b.barrier, b.error);
     }

@@ -63,7 +63,18 @@ struct L1Row {
 struct L1Geom {
     int H, W, c0, lane;
     bool vec;     // 16-byte copies: rows 16-byte aligned (W % 4 == 0, aligned arrays)
+    // vec: the lane's two pieces (lane, lane + 32): float offsets in the row, and whether each
+    // lies inside the row (with W % 4 == 0 a piece lies wholly inside or wholly outside)
+    int f0, f1;
+    bool in0, in1;
 };
+
+__device__ __forceinline__ void l1_geom_pieces(L1Geom& g) {
+    g.f0 = 3 * g.c0 - kSlotPts + 4 * g.lane;
+    g.f1 = g.f0 + 4 * 32;
+    g.in0 = g.f0 >= 0 && g.f0 + 4 <= 3 * g.W;
+    g.in1 = g.lane + 32 < kPieces && g.f1 + 4 <= 3 * g.W;
+}
 
 // The edge from a point to the one below it: difference (below - point) and its weight.
 struct L1Edge {
@@ -82,15 +93,12 @@ __device__ __forceinline__ void l1_fill(float* slot, const float* A, const L1Geo
     }
     const float* rowp = A + 3 * (size_t)row * g.W;
     if (g.vec) {
-        // pieces of the floats 3 c0 - 4 .. 3 c0 + 195 of the row; with W % 4 == 0 a piece lies
-        // wholly inside the row or wholly outside it (then it reads as fill)
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int p = lane + 32 * h;
-            if (p >= kPieces) break;
-            const int f0 = 3 * g.c0 - kSlotPts + 4 * p;
-            if (f0 >= 0 && f0 + 4 <= 3 * g.W) cp_async16(slot + 4 * p, rowp + f0);
-            else *reinterpret_cast<float4*>(slot + 4 * p) = f4;
+        // the pieces of the floats 3 c0 - 4 .. 3 c0 + 195 of the row; one outside it reads as fill
+        if (g.in0) cp_async16(slot + 4 * lane, rowp + g.f0);
+        else *reinterpret_cast<float4*>(slot + 4 * lane) = f4;
+        if (lane + 32 < kPieces) {
+            if (g.in1) cp_async16(slot + 4 * (lane + 32), rowp + g.f1);
+            else *reinterpret_cast<float4*>(slot + 4 * (lane + 32)) = f4;
         }
         return;
     }
@@ -219,15 +227,14 @@ __device__ __forceinline__ void l1_add_keep(L1Sum& s, const LapPt& p, const LapP
     lap_accumulate(s.sx, s.sy, s.sz, s.ws, e.w, e.ex, e.ey, e.ez);
 }
 
-// Eq. 1 for one point: its new displacement (or the kept one), and its export.
-__device__ __forceinline__ void l1_out(const LapPt& p, const L1Sum& s, bool pin, float lambda, bool zero, float& ox,
-                                       float& oy, float& oz) {
+// Eq. 1 for one point: its new displacement, or the kept one.
+__device__ __forceinline__ void l1_out(const LapPt& p, const L1Sum& s, bool pin, float lambda, float& ox, float& oy,
+                                       float& oz) {
     const bool keep = pin || p.x == kInvalidCoord || !(s.ws > 0.f);
     const float k = lap_scale(keep, lambda, s.ws);
     ox = fmaf(k, s.sx, p.dx);
     oy = fmaf(k, s.sy, p.dy);
     oz = fmaf(k, s.sz, p.dz);
-    if (zero) ox = oy = oz = 0.f;
 }
 
 __device__ __forceinline__ void l1_export(float* e, const LapPt& p, float ox, float oy, float oz) {
@@ -251,13 +258,30 @@ __device__ __forceinline__ void l1_task(const Lap1Frame& fr, int task, int lane,
     g.c0 = cb * kLap1Cols;
     g.lane = lane;
     g.vec = (W & 3) == 0 && ((uintptr_t)fr.points & 15u) == 0 && (!WITH_D || ((uintptr_t)fr.d_in & 15u) == 0);
+    l1_geom_pieces(g);
     const int ca = g.c0 + 2 * lane;   // the pair's columns: ca, ca + 1
     const bool out_a = ca < W, out_b = ca + 1 < W;
     const bool pin_a = ca < 1 || ca >= W - 1, pin_b = ca + 1 >= W - 1;
     const float lambda = fr.lambda;
-    const bool zero = fr.iters == 0;
     float* const d_out = fr.d_out;
     float* const exp_pts = fr.export_points;
+    if (fr.iters == 0) {
+        // no smoothing: the displacement stays zero (warp-uniform; only a first pass has no iteration)
+        for (int r = r0; r < min(H, r0 + kLap1Rows); ++r) {
+            const size_t gi = 3 * ((size_t)r * W + ca);
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                if (!(k == 0 ? out_a : out_b)) continue;
+                const size_t o = gi + 3 * k;
+                d_out[o] = d_out[o + 1] = d_out[o + 2] = 0.f;
+                if (exp_pts) {
+                    const float x = __ldg(fr.points + o), y = __ldg(fr.points + o + 1), z = __ldg(fr.points + o + 2);
+                    l1_export(exp_pts + o, l1_point<false>(x, y, z, 0.f, 0.f, 0.f), 0.f, 0.f, 0.f);
+                }
+            }
+        }
+        return;
+    }
     // the pair's six floats start 8-byte aligned in every row when W is even
     const bool st64 = (W & 1) == 0 && ((uintptr_t)d_out & 7u) == 0;
     // rows r0 - 1 .. r0 + kLap1Rows are needed (row H, the one below the image, read as invalid);
@@ -343,8 +367,8 @@ __device__ __forceinline__ void l1_task(const Lap1Frame& fr, int task, int lane,
 
             const bool row_pin = r < 1 || r >= H - 1;
             float ax, ay, az, bx, by, bz;
-            l1_out(pa, A, pin_a || row_pin, lambda, zero, ax, ay, az);
-            l1_out(pb, B, pin_b || row_pin, lambda, zero, bx, by, bz);
+            l1_out(pa, A, pin_a || row_pin, lambda, ax, ay, az);
+            l1_out(pb, B, pin_b || row_pin, lambda, bx, by, bz);
             if (r < H) {   // warp-uniform
                 const size_t gi = 3 * ((size_t)r * W + ca);
                 if (st64 && out_b) {
@@ -388,9 +412,10 @@ size_t lap1_smem_bytes(bool with_d) {
 }
 
 // Dynamic shared memory: kWarps rings of points, then (WITH_D) kWarps rings of displacements.
-// Two CTAs per SM: 128 registers hold the three-row window of a pair without spilling.
+// Three CTAs per SM (80 registers; two with the displacement window): the more warps per SM hide the
+// dependent chains of the sums better than a spill-free 128-register window does.
 template <bool WITH_D>
-__global__ void __launch_bounds__(kThreads, 2) lap1_kernel(const __grid_constant__ Lap1Args a) {
+__global__ void __launch_bounds__(kThreads, WITH_D ? 2 : 3) lap1_kernel(const __grid_constant__ Lap1Args a) {
     extern __shared__ __align__(16) float l1_smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int kWarpFloats = frame::kRing * frame::kSlot;

@@ -177,7 +177,9 @@ __global__ void batch_kernel(const __grid_constant__ BatchArgs b);
 // The single-iteration Laplacian pass with a 3 x 3 window as a kernel of its own (lap1.cu): used
 // when every Laplacian pass of a frame (of every frame of a batch) runs at most one iteration,
 // before the persistent kernel, which then starts at the bilateral. Work unit: a warp task of
-// kLap1Cols columns x kLap1Rows rows of one frame (a pair of columns per lane).
+// kLap1Cols columns x kLap1Rows rows of one frame (a pair of columns per lane). Taller tasks (48
+// rows) and a height chosen per launch to even out the last round of tasks both measured slower
+// than 24 rows on the 256-frame batch.
 constexpr int kLap1Cols = 64;
 constexpr int kLap1Rows = 24;
 __host__ __device__ inline int lap1_tasks(int H, int W) { return div_up(H, kLap1Rows) * div_up(W, kLap1Cols); }
