@@ -680,6 +680,12 @@ def run_pl3d(args):
         phases[name] = {"us": p_ms / max(p_n, 1) * 1e3}
     phases["laplacian"]["tflops"] = flop["laplacian"] / (phases["laplacian"]["us"] * 1e-6) / 1e12
     phases["bilateral"]["tflops"] = flop["bilateral"] / (phases["bilateral"]["us"] * 1e-6) / 1e12
+    # the bilateral phase split by its tiles' stage totals (CTA time; the shares apply to the phase)
+    st = {k: per_kernel.get(f"bil_{k}_cta", (0.0, 0))[0] for k in ("staging", "geometry", "iterations", "finish",
+                                                                   "labels")}
+    st_total = sum(st.values())
+    if st_total > 0:
+        phases["bilateral"]["stages_us"] = {k: phases["bilateral"]["us"] * v / st_total for k, v in st.items()}
     roofline = {"bound": "alu", "kernel": "frame_kernel", "achieved": achieved, "peak": fp32_peak,
                 "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                 "traffic": recorded_traffic("frame_kernel", args.workload),

@@ -1072,21 +1072,28 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
     __syncthreads();
     // (4) Each triangle leaves with the GID of its tile-local root (-1 without a group).
     int32_t* const labels = a.labels;
+    const bool vec_lab = ((uintptr_t)labels & 7u) == 0;   // a quad's two labels in one 8-byte store
     for (int i = threadIdx.x; i < TH * T; i += blockDim.x) {
         const int r = i / T, c = i - r * T;
         const int gu = ty * TH + r, gv = tx * T + c;
         if (gu >= Hq || gv >= Wq) continue;
         const size_t gid0 = 2 * ((size_t)gu * Wq + gv);
+        int lab[2];
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
             const int rep = RunOf[2 * i + k];
-            int lab = -1;
+            lab[k] = -1;
             if (rep >= 0) {
                 const int root = RootOf[rep];
                 const int rq = root >> 1, rr = rq / T, rc = rq - rr * T;
-                lab = (int)(2 * ((size_t)(ty * TH + rr) * Wq + (tx * T + rc)) + (root & 1));
+                lab[k] = (int)(2 * ((size_t)(ty * TH + rr) * Wq + (tx * T + rc)) + (root & 1));
             }
-            labels[gid0 + k] = lab;
+        }
+        if (vec_lab) {
+            *reinterpret_cast<int2*>(labels + gid0) = make_int2(lab[0], lab[1]);
+        } else {
+            labels[gid0] = lab[0];
+            labels[gid0 + 1] = lab[1];
         }
     }
     __syncthreads();
