@@ -399,6 +399,7 @@ int frame_launch(const FrameScratch& sc, const float* points, int H, int W, cons
             la.pass = c;
             la.stamp = sc.phase_ns ? sc.phase_ns + 4 : nullptr;
             la.phase_ns = sc.phase_ns;
+            la.sched = sc.lap1_sched;
             const bool with_d = ph.d_in != nullptr;
             const int g = lap1_grid(dev, with_d, lap1_tasks(H, W));
             if (g <= 0) return PL3D_ERR_CUDA;

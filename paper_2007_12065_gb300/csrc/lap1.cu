@@ -5,7 +5,8 @@
 // 36 with the previous pass's displacement), so the pass is bound by HBM and by instruction issue,
 // not by the halo trade-off that the fused tile passes of frame_kernels.cuh make. A warp owns a task
 // of 64 columns x 24 rows of one frame, each lane a pair of adjacent columns, and walks down its
-// rows.
+// rows. Tasks after the first round are handed out by a counter in global memory (a batch mixes
+// frames whose ragged tasks differ in size, and a static split leaves a tail of idle warps).
 //
 // Rows come through a per-warp ring of kRing row slots in shared memory, filled with cp.async:
 // one or two 16-byte copies per lane of the row's 800 bytes, from the point left of the chunk to
@@ -426,7 +427,14 @@ __global__ void __launch_bounds__(kThreads, WITH_D ? 2 : 3) lap1_kernel(const __
     if (timed && threadIdx.x == 0) atomicMax(a.stamp, ~(unsigned long long)global_ns());
     const int n = a.hdr ? __ldg(&a.hdr->n) : 1;
     const int tasks = a.hdr ? __ldg(a.task_pre + n) : lap1_tasks(a.one.H, a.one.W);
-    for (int t = blockIdx.x * frame::kWarps + warp; t < tasks; t += gridDim.x * frame::kWarps) {
+    // The first round of tasks goes one per warp by index; after it, a warp takes the next task
+    // from the counter, asked for when it starts a task, so that the warps end within about one
+    // task of each other however the frames' ragged tasks fall.
+    const int warps = gridDim.x * frame::kWarps;
+    int t = blockIdx.x * frame::kWarps + warp;
+    while (t < tasks) {
+        unsigned next = 0;
+        if (lane == 0) next = atomicAdd(a.sched, 1u);
         if (a.hdr) {
             const int f = frame::l1_find_frame(a.task_pre, n, t, lane);
             const FrameArgs* fa = a.frames + f;
@@ -444,6 +452,16 @@ __global__ void __launch_bounds__(kThreads, WITH_D ? 2 : 3) lap1_kernel(const __
             frame::l1_task<WITH_D>(fr, t - __ldg(a.task_pre + f), lane, ring, dring);
         } else {
             frame::l1_task<WITH_D>(a.one, t, lane, ring, dring);
+        }
+        t = warps + (int)__shfl_sync(0xffffffffu, next, 0);
+    }
+    // every warp of every CTA has taken its last index before the last CTA puts the counter back
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(a.sched + 1, 1u) + 1 == gridDim.x) {
+            atomicExch(a.sched, 0u);
+            atomicExch(a.sched + 1, 0u);
         }
     }
     if (timed) {

@@ -78,6 +78,7 @@ int run(pl3d_ctx* ctx, const float* points, int H, int W, const pl3d_params* p, 
     sc.barrier = ctx->barrier();
     sc.error = ctx->error();
     sc.phase_ns = ctx->timing ? ctx->phase_ns() : nullptr;
+    sc.lap1_sched = ctx->lap1_sched();
     sc.seed_flags = nullptr;
     sc.seed_centroids = nullptr;
 

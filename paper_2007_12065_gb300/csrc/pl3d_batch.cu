@@ -236,6 +236,7 @@ int run_batch(pl3d_ctx* c, const pl3d_frame* frames, int n, cudaStream_t s) {
         sc.barrier = c->barrier();
         sc.error = c->error();
         sc.phase_ns = nullptr;
+        sc.lap1_sched = c->lap1_sched();
         FramePlan plan;
         rc = frame_build(fa[i], plan, sc, f.points, f.H, f.W, f.params, f.dominant_normals, f.K, f.out_tri_mask,
                          f.out_normals, f.out_labels, f.out_points, f.out_groups, t);
@@ -339,6 +340,7 @@ int run_batch(pl3d_ctx* c, const pl3d_frame* frames, int n, cudaStream_t s) {
         la.pass = pass;
         la.stamp = c->phase_ns() + 4;
         la.phase_ns = c->phase_ns();
+        la.sched = c->lap1_sched();
         l1_grid[pass] = lap1_grid(dev, pass > 0, -1);
         if (l1_grid[pass] <= 0) return PL3D_ERR_CUDA;
     }

@@ -35,7 +35,9 @@ struct BatchGraph {
 };
 
 // barrier [2], error word, pad; phase totals [4]; lap1 timing stamps [3]; bilateral stage totals
-constexpr size_t kCtlBytes = 4 * sizeof(unsigned) + (kStageSlot + kBilStages) * sizeof(unsigned long long);
+// [5] (u64); lap1 task counter [2]
+constexpr size_t kCtlBytes =
+    4 * sizeof(unsigned) + (kStageSlot + kBilStages) * sizeof(unsigned long long) + 2 * sizeof(unsigned);
 
 }  // namespace ctxutil
 }  // namespace pl3d
@@ -50,7 +52,7 @@ struct pl3d_ctx {
     uint8_t* groups = nullptr;      // cap_tri
     int32_t* sizes = nullptr;       // cap_tri
     size_t cap_tri = 0;
-    unsigned* ctl = nullptr;        // barrier [2], error word, pad, phase totals [4] and lap1 stamps [3] (u64)
+    unsigned* ctl = nullptr;        // control words (ctxutil::kCtlBytes): barrier, error, timing, lap1 counter
     uint8_t* seed_flags = nullptr;  // PL3D_FLAG_SEED_PTP: per-root flags, cap_seed
     size_t cap_seed = 0;
     float* seed_centroids = nullptr;   // PL3D_FLAG_SEED_PTP: 3 cap_seed_c floats
@@ -99,6 +101,7 @@ struct pl3d_ctx {
     unsigned* barrier() const { return ctl; }
     int* error() const { return reinterpret_cast<int*>(ctl + 2); }
     unsigned long long* phase_ns() const { return reinterpret_cast<unsigned long long*>(ctl + 4); }
+    unsigned* lap1_sched() const { return ctl + 4 + 2 * (pl3d::kStageSlot + pl3d::kBilStages); }
 };
 
 namespace pl3d {

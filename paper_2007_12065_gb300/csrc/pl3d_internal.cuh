@@ -202,6 +202,8 @@ struct Lap1Args {
     int pass;
     unsigned long long* stamp;     // [3]: latest ~start, latest end, CTAs done; or nullptr (no timing)
     unsigned long long* phase_ns;  // the Laplacian span is added to phase_ns[0]
+    unsigned* sched;               // [2], zero at rest: tasks handed out after the first round, CTAs
+                                   // done (the last CTA puts both back to zero)
 };
 
 template <bool WITH_D>
@@ -218,6 +220,7 @@ struct FrameScratch {
     unsigned* barrier;             // [2], zero before the first use
     int* error;                    // [1]
     unsigned long long* phase_ns;  // [4] or nullptr
+    unsigned* lap1_sched;          // [2], zero at rest: the single-iteration Laplacian's task counter
     uint8_t* seed_flags;           // >= 2 Q, PL3D_FLAG_SEED_PTP only
     float* seed_centroids;         // >= 6 Q, PL3D_FLAG_SEED_PTP only
 };

@@ -40,7 +40,8 @@ constexpr size_t kMaxTri = 2 * kMaxPoints;                       // 2(H-1)(W-1) 
 constexpr size_t kDispBytes = 6 * kMaxPoints * sizeof(float);    // displacement ping-pong, AoS
 constexpr size_t kGroupBytes = (kMaxTri + 255) / 256 * 256;
 constexpr size_t kSizeBytes = kMaxTri * sizeof(int32_t);
-constexpr size_t kCtlBytes = 256;                                // barrier [2], error word
+constexpr size_t kCtlBytes = 256;                                // barrier [2], error word, pad,
+                                                                 // lap1 task counter [2]
 constexpr size_t kScratchBytes = kDispBytes + kGroupBytes + kSizeBytes + kCtlBytes;
 
 static __device__ __align__(256) unsigned char g_static_scratch[kScratchBytes];
@@ -150,6 +151,7 @@ extern "C" int pl3d_extract_planes_static(const float* points, int H, int W, con
     sc.barrier = ctl;
     sc.error = reinterpret_cast<int*>(ctl + 2);
     sc.phase_ns = nullptr;
+    sc.lap1_sched = ctl + 4;
     return frame_launch(sc, points, H, W, p, nd_host, K, out_mask, out_normals, out_labels, nullptr, nullptr,
                         Tuning{0, 0, 0}, (cudaStream_t)stream);
 }
