@@ -87,12 +87,12 @@ struct L1Edge {
 __device__ __forceinline__ void l1_fill(float* slot, const float* A, const L1Geom& g, int row, float fill) {
     const int lane = g.lane;
     const float4 f4 = make_float4(fill, fill, fill, fill);
-    if (row < 0 || row >= g.H) {
+    if ((unsigned)row >= (unsigned)g.H) {
         *reinterpret_cast<float4*>(slot + 4 * lane) = f4;
         if (lane + 32 < kPieces) *reinterpret_cast<float4*>(slot + 4 * (lane + 32)) = f4;
         return;
     }
-    const float* rowp = A + 3 * (size_t)row * g.W;
+    const float* rowp = A + (long long)row * (3 * g.W);   // 3 H W < 2^31 floats (pl3d_validate)
     if (g.vec) {
         // the pieces of the floats 3 c0 - 4 .. 3 c0 + 195 of the row; one outside it reads as fill
         if (g.in0) cp_async16(slot + 4 * lane, rowp + g.f0);
@@ -371,7 +371,7 @@ __device__ __forceinline__ void l1_task(const Lap1Frame& fr, int task, int lane,
             l1_out(pa, A, pin_a || row_pin, lambda, ax, ay, az);
             l1_out(pb, B, pin_b || row_pin, lambda, bx, by, bz);
             if (r < H) {   // warp-uniform
-                const size_t gi = 3 * ((size_t)r * W + ca);
+                const long long gi = (long long)r * (3 * W) + 3 * ca;
                 if (st64 && out_b) {
                     float2* o = reinterpret_cast<float2*>(d_out + gi);
                     o[0] = make_float2(ax, ay);
