@@ -119,12 +119,12 @@ int g_occ_vals[64];
 int g_occ_n = 0;
 }  // namespace
 
-int resident_ctas(const void* fn, size_t smem, int dev) {
+int resident_ctas(const void* fn, size_t smem, int dev, int threads) {
     std::lock_guard<std::mutex> lock(g_occ_mutex);
     for (int i = 0; i < g_occ_n; ++i)
         if (g_occ_keys[i].fn == fn && g_occ_keys[i].smem == smem && g_occ_keys[i].dev == dev) return g_occ_vals[i];
     int per_sm = 0, sms = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
         cudaGetLastError();
         return 0;
@@ -367,9 +367,9 @@ bool lap1_eligible(const FrameArgs& a, int rl) {
 }
 
 int lap1_grid(int dev, bool with_d, long long tasks) {
-    const int resident = resident_ctas(lap1_kernel_for(with_d), lap1_smem_bytes(with_d), dev);
+    const int resident = resident_ctas(lap1_kernel_for(with_d), lap1_smem_bytes(with_d), dev, kLap1Threads);
     if (resident <= 0 || tasks < 0) return resident;
-    const long long need = (tasks + kThreads / 32 - 1) / (kThreads / 32);
+    const long long need = (tasks + kLap1Threads / 32 - 1) / (kLap1Threads / 32);
     return need < resident ? (int)(need > 0 ? need : 1) : resident;
 }
 
@@ -404,7 +404,8 @@ int frame_launch(const FrameScratch& sc, const float* points, int H, int W, cons
             const int g = lap1_grid(dev, with_d, lap1_tasks(H, W));
             if (g <= 0) return PL3D_ERR_CUDA;
             void* largs[1] = {&la};
-            if (cudaLaunchKernel(lap1_kernel_for(with_d), dim3(g), dim3(kThreads), largs, lap1_smem_bytes(with_d), s) !=
+            if (cudaLaunchKernel(lap1_kernel_for(with_d), dim3(g), dim3(kLap1Threads), largs, lap1_smem_bytes(with_d),
+                                 s) !=
                 cudaSuccess) {
                 cudaGetLastError();
                 return PL3D_ERR_CUDA;

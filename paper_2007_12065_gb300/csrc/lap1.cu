@@ -33,9 +33,13 @@ namespace pl3d {
 namespace frame {
 namespace {
 
-constexpr int kWarps = kThreads / 32;
+constexpr int kWarps = kLap1Threads / 32;
 constexpr int kBlock = 3;      // rows per unrolled block: the register window's period
-constexpr int kRing = 8;       // row slots of a warp's ring: rows i + 3 .. i + 6 in flight at row i
+// Row slots of a warp's ring: rows i + 3 .. i + kRing - 2 in flight at row i.
+template <bool WITH_D>
+struct L1Ring {
+    static constexpr int n = WITH_D ? 8 : 8;
+};
 // A slot: float 0 pad, floats 1-3 the point left of the chunk, floats 4 .. 195 the chunk's 64
 // points, floats 196-198 the point right of it, float 199 pad; kSlot / 4 pieces of 16 bytes.
 constexpr int kSlot = 200;
@@ -249,6 +253,7 @@ __device__ __forceinline__ void l1_export(float* e, const LapPt& p, float ox, fl
 // fr. `ring` (and `dring` with WITH_D) hold kRing slots of this warp.
 template <bool WITH_D>
 __device__ __forceinline__ void l1_task(const Lap1Frame& fr, int task, int lane, float* ring, float* dring) {
+    constexpr int kRing = L1Ring<WITH_D>::n;
     const int H = fr.H, W = fr.W;
     const int ncb = div_up(W, kLap1Cols);
     const int rb = task / ncb, cb = task - rb * ncb;
@@ -409,17 +414,18 @@ __device__ __forceinline__ void l1_task(const Lap1Frame& fr, int task, int lane,
 }  // namespace frame
 
 size_t lap1_smem_bytes(bool with_d) {
-    return (size_t)(with_d ? 2 : 1) * frame::kWarps * frame::kRing * frame::kSlot * sizeof(float);
+    const int slots = with_d ? 2 * frame::L1Ring<true>::n : frame::L1Ring<false>::n;
+    return (size_t)slots * frame::kWarps * frame::kSlot * sizeof(float);
 }
 
 // Dynamic shared memory: kWarps rings of points, then (WITH_D) kWarps rings of displacements.
-// Three CTAs per SM (80 registers; two with the displacement window): the more warps per SM hide the
-// dependent chains of the sums better than a spill-free 128-register window does.
+// Four-warp CTAs, five per SM (96 registers, no spills; four with the displacement window at 128):
+// 20 warps per SM measured faster than 24 at 80 registers with spills, and than 16 at 128.
 template <bool WITH_D>
-__global__ void __launch_bounds__(kThreads, WITH_D ? 2 : 3) lap1_kernel(const __grid_constant__ Lap1Args a) {
+__global__ void __launch_bounds__(kLap1Threads, WITH_D ? kLap1CtasD : kLap1Ctas) lap1_kernel(const __grid_constant__ Lap1Args a) {
     extern __shared__ __align__(16) float l1_smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    constexpr int kWarpFloats = frame::kRing * frame::kSlot;
+    constexpr int kWarpFloats = frame::L1Ring<WITH_D>::n * frame::kSlot;
     float* const ring = l1_smem + warp * kWarpFloats;
     float* const dring = WITH_D ? l1_smem + (frame::kWarps + warp) * kWarpFloats : ring;
     bool timed = false;

@@ -129,7 +129,7 @@ cudaGraphExec_t batch_graph(pl3d_ctx* c, const void* fn, size_t smem, int grid, 
         memset(&lp, 0, sizeof(lp));
         lp.func = const_cast<void*>(lap1_kernel_for(la.pass > 0));
         lp.gridDim = dim3(l1_grid[i]);
-        lp.blockDim = dim3(kThreads);
+        lp.blockDim = dim3(kLap1Threads);
         lp.sharedMemBytes = (unsigned)lap1_smem_bytes(la.pass > 0);
         lp.kernelParams = lparams;
         cudaGraphNode_t node = nullptr;

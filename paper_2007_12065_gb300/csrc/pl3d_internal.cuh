@@ -182,6 +182,11 @@ __global__ void batch_kernel(const __grid_constant__ BatchArgs b);
 // than 24 rows on the 256-frame batch.
 constexpr int kLap1Cols = 64;
 constexpr int kLap1Rows = 24;
+// Threads per CTA, and CTAs per SM the register budget is set for (without, with the previous
+// pass's displacement).
+constexpr int kLap1Threads = 128;
+constexpr int kLap1Ctas = 5;
+constexpr int kLap1CtasD = 4;
 __host__ __device__ inline int lap1_tasks(int H, int W) { return div_up(H, kLap1Rows) * div_up(W, kLap1Cols); }
 
 struct Lap1Frame {
@@ -279,7 +284,7 @@ int frame_build(FrameArgs& a, FramePlan& plan, const FrameScratch& sc, const flo
 const void* batch_kernel_for_radii(int rl, int rb);
 
 // Resident CTAs of a kernel over the whole device for a shared-memory size (cached).
-int resident_ctas(const void* fn, size_t smem, int dev);
+int resident_ctas(const void* fn, size_t smem, int dev, int threads = kThreads);
 
 // Sets the shared-memory opt-in of every frame kernel on the current device.
 cudaError_t frame_configure();
