@@ -7,6 +7,7 @@ streams).
 """
 from __future__ import annotations
 
+import fcntl
 import os
 import shutil
 import subprocess
@@ -47,11 +48,23 @@ def up_to_date() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None) -> str:
-    """Compile and link libpl3d.so; returns its path. Skips the work when nothing changed."""
+    """Compile and link libpl3d.so; returns its path. Skips the work when nothing changed. Builds in
+    several processes at once (parallel test workers) take turns on a lock file."""
     if not force and not extra_flags and up_to_date():
         return LIB
-    nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
+    with open(os.path.join(BUILD, ".lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            if not force and not extra_flags and up_to_date():
+                return LIB
+            return _build_locked(verbose, extra_flags)
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
+def _build_locked(verbose: bool, extra_flags: list[str] | None) -> str:
+    nvcc = _nvcc()
     flags = NVCC_FLAGS + list(extra_flags or [])
 
     def compile_one(src: str) -> str:
