@@ -7,9 +7,10 @@ frame already resident in HBM. The frame (3.7 MB) is smaller than L2, so L2 is f
 writing a 256 MB buffer before every timed step, outside the step's CUDA events.
 
 Prints one JSON line. `value` is Mtri/s over all ranks (triangles = 2(H-1)(W-1) per frame),
-`e2e` repeats the measurement through pl3d_extract_planes_host with pinned host buffers (the
-points copied in, the normals copied out beside the segment launch, the mask and labels written
-by the kernel into the pinned buffers; all of it inside the timed region), `roofline` describes
+`e2e` repeats the measurement from page-locked host buffers through the pipelined entry point
+(pl3d_pipeline_*: every frame's points copied in and its mask, normals and labels copied out
+inside the timed region, the copies of one frame beside the kernels of the next; the synchronous
+one-frame call pl3d_extract_planes_host is reported beside it as `e2e.sync_call`), `roofline` describes
 the kernel with the largest share of
 device time, `cpu_baseline` times the FP64 oracle on the host cores on a bounded sample.
 
@@ -39,6 +40,8 @@ if ROOT not in sys.path:
 import synth  # noqa: E402
 
 METRIC = "Mtri/s smoothed+segmented and HBM roofline fraction; served p50/p99 frame latency"
+E2E_DEPTH = 3          # frames in flight in the end-to-end pipeline
+E2E_HOST_SETS = 8      # page-locked host input/output sets the end-to-end frames rotate through
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -562,24 +565,53 @@ def run_pl3d(args):
     ms = max_over_ranks(sum(step_ms) / len(step_ms), world, dev)
     value = aggregate_mtri_s(ntri, world, ms)
 
-    # ---------------- end to end through the host-buffer entry point
-    h_pts = torch.from_numpy(frame.points).pin_memory()
-    h_mask = torch.empty(ntri, dtype=torch.uint8).pin_memory()
-    h_normals = torch.empty((ntri, 3), dtype=torch.float32).pin_memory()
-    h_labels = torch.empty(ntri, dtype=torch.int32).pin_memory()
-    e2e_steps = max(args.steps // 2, 10)
-    for _ in range(3):
-        pl3d.pl3d_extract_planes_host(ctx, h_pts, H, W, params, nd, K, h_mask, h_normals, h_labels, stream)
-    barrier()
+    # ---------------- end to end: host buffers through the pipelined entry point
+    # A stream of frames, each copied in from page-locked host memory, run, and copied back out;
+    # the copies of one frame overlap the kernels of the others (pl3d_pipeline_*). The host
+    # timer runs from the first submit to the last frame's outputs in host memory.
+    step()
     torch.cuda.synchronize()
-    e2e_s = []
-    for k in range(e2e_steps):
+    ref = (mask.cpu(), normals.cpu(), labels.cpu())
+    h_pts = [torch.from_numpy(frame.points).pin_memory() for _ in range(E2E_HOST_SETS)]
+    h_out = [(torch.empty(ntri, dtype=torch.uint8).pin_memory(), torch.empty((ntri, 3), dtype=torch.float32).pin_memory(),
+              torch.empty(ntri, dtype=torch.int32).pin_memory()) for _ in range(E2E_HOST_SETS)]
+    e2e_steps = max(10 * args.steps, 200)
+    pipe = pl3d.pl3d_pipeline_create(local, max_points=H * W, depth=E2E_DEPTH)
+
+    def e2e_run(n):
+        tickets = []
+        for k in range(n):
+            b = k % E2E_HOST_SETS
+            if k >= E2E_HOST_SETS:
+                pl3d.pl3d_pipeline_wait(pipe, tickets[k - E2E_HOST_SETS])   # host set b free again
+            tickets.append(pl3d.pl3d_pipeline_submit(pipe, h_pts[b], H, W, params, nd, K, *h_out[b]))
+        for t in tickets[-E2E_HOST_SETS:]:
+            pl3d.pl3d_pipeline_wait(pipe, t)
+        return (n - 1) % E2E_HOST_SETS
+
+    e2e_run(max(args.warmup, 3) * E2E_HOST_SETS)
+    barrier()
+    t_a = time.perf_counter()
+    last = e2e_run(e2e_steps)
+    e2e_s = time.perf_counter() - t_a
+    barrier()
+    e2e_match = all(torch.equal(a.view(torch.uint8), b.view(torch.uint8)) for a, b in zip(h_out[last], ref))
+    pl3d.pl3d_pipeline_destroy(pipe)
+    e2e_ms = max_over_ranks(1e3 * e2e_s / e2e_steps, world, dev)
+
+    # the synchronous host-buffer call, one frame at a time (latency of a lone frame)
+    hs_pts, (hs_mask, hs_normals, hs_labels) = h_pts[0], h_out[0]
+    for _ in range(3):
+        pl3d.pl3d_extract_planes_host(ctx, hs_pts, H, W, params, nd, K, hs_mask, hs_normals, hs_labels, stream)
+    torch.cuda.synchronize()
+    sync_s = []
+    for k in range(max(args.steps // 2, 10)):
         flush.fill_(float(k))
         torch.cuda.synchronize()
-        t_a = time.perf_counter()
-        pl3d.pl3d_extract_planes_host(ctx, h_pts, H, W, params, nd, K, h_mask, h_normals, h_labels, stream)
-        e2e_s.append(time.perf_counter() - t_a)
-    e2e_ms = max_over_ranks(1e3 * sum(e2e_s) / len(e2e_s), world, dev)
+        t_s = time.perf_counter()
+        pl3d.pl3d_extract_planes_host(ctx, hs_pts, H, W, params, nd, K, hs_mask, hs_normals, hs_labels, stream)
+        sync_s.append(time.perf_counter() - t_s)
+    sync_ms = max_over_ranks(1e3 * sum(sync_s) / len(sync_s), world, dev)
     sampler.stop()
     clocks = sampler.summary(t0, t1)
 
@@ -721,10 +753,15 @@ def run_pl3d(args):
                    "parallelism": f"replicas x{world}"},
         "clocks": clocks,
         "e2e": {"value": aggregate_mtri_s(ntri, world, e2e_ms), "unit": "Mtri/s", "ms_per_step": e2e_ms,
-                "h2d_bytes_per_step": int(h_pts.numel() * 4),
-                "d2h_bytes_per_step": int(h_mask.numel() + h_normals.numel() * 4 + h_labels.numel() * 4),
-                "d2h": "normals by copy once they are final (beside the second launch, which joins the segments "
-                       "across tiles); mask and labels written by the kernel into the pinned host buffers"},
+                "h2d_bytes_per_step": int(h_pts[0].numel() * 4),
+                "d2h_bytes_per_step": int(sum(t.numel() * t.element_size() for t in h_out[0])),
+                "api": f"pl3d_pipeline_submit / pl3d_pipeline_wait, depth {E2E_DEPTH}: {e2e_steps} frames back to "
+                       f"back from {E2E_HOST_SETS} page-locked host buffer sets; points copied in, mask, normals and "
+                       "labels copied out, every frame, inside the host-timed region",
+                "l2": "not flushed: every frame's points arrive over the host link inside the step",
+                "outputs_match_device_path": bool(e2e_match),
+                "sync_call": {"api": "pl3d_extract_planes_host (synchronous; L2 flushed before each call)",
+                              "ms_per_frame": sync_ms, "mtri_s": aggregate_mtri_s(ntri, world, sync_ms)}},
         "gpu_launches": int(launches),
         "roofline": roofline,
         "cpu_baseline": cpu,

@@ -164,6 +164,49 @@ int pl3d_extract_planes_host(pl3d_ctx* ctx, const float* host_points, int H, int
                              const float* dominant_normals, int K, uint8_t* host_tri_mask, float* host_normals,
                              int32_t* host_labels, void* stream);
 
+/*
+ * Pipelined host-buffer frames (no counterpart in the paper): a stream of frames from host
+ * memory, each through the same path as pl3d_extract_planes, with the copies of one frame
+ * overlapping the kernels of the others. A pipeline owns a context, three CUDA streams (input
+ * copies, kernels, output copies) and `depth` sets of device buffers for frames of up to
+ * max_points points. The kernels run one frame at a time in submission order on the kernel
+ * stream (they share the context's scratch); a frame's input copy runs while the frames before
+ * it are in their kernels, and its output copy while the frames after it are.
+ *
+ * pl3d_pipeline_create   device: CUDA device; max_points: largest H * W submitted (>= 4);
+ *                        depth: frames in flight, 1 .. 16. Allocates everything up front
+ *                        (PL3D_ERR_OUT_OF_MEMORY when that fails); *out NULL on failure.
+ * pl3d_pipeline_submit   enqueues one frame and returns its ticket (1, 2, 3, ...) without
+ *                        waiting for it. Arguments as pl3d_extract_planes_host; the host
+ *                        buffers should be page-locked (pageable ones make the copies
+ *                        synchronous), must stay valid and untouched until the frame is waited
+ *                        for, and must not overlap. When `depth` frames are in flight it first
+ *                        waits for the oldest (its status is kept for pl3d_pipeline_wait).
+ *                        PL3D_FLAG_SEED_PTP is not supported (PL3D_ERR_UNSUPPORTED); H * W
+ *                        above max_points is PL3D_ERR_INVALID_ARG. A failed submit issues no
+ *                        ticket (an input copy it enqueued lands in a free buffer set).
+ * pl3d_pipeline_wait     waits until the frame's three outputs are in host memory and returns
+ *                        its status: PL3D_OK, or PL3D_ERR_TIMEOUT when a bounded device wait gave
+ *                        up during it or during a frame whose kernels overlapped its output copy
+ *                        (their results are void; the context's error word and grid-barrier
+ *                        state are cleared after every stream has drained). Frames complete in
+ *                        submission order. A ticket waited for before returns its kept status
+ *                        while it is among the last 1024 issued; an unknown or older ticket is
+ *                        PL3D_ERR_INVALID_ARG.
+ * pl3d_pipeline_destroy  waits for every frame in flight and frees everything (NULL is a no-op).
+ */
+typedef struct pl3d_pipeline pl3d_pipeline;
+int pl3d_pipeline_create(int device, int64_t max_points, int depth, pl3d_pipeline** out);
+int pl3d_pipeline_submit(pl3d_pipeline* pl, const float* host_points, int H, int W, const pl3d_params* params,
+                         const float* dominant_normals, int K, uint8_t* host_tri_mask, float* host_normals,
+                         int32_t* host_labels, uint64_t* ticket);
+int pl3d_pipeline_wait(pl3d_pipeline* pl, uint64_t ticket);
+int pl3d_pipeline_destroy(pl3d_pipeline* pl);
+/* The pipeline's context, owned by the pipeline (NULL for NULL): for pl3d_set_timing,
+ * pl3d_read_timing, pl3d_launch_count and pl3d_selftest_wait_timeout while no frame is in flight.
+ * An error word set between frames is reported by the next frame submitted. */
+pl3d_ctx* pl3d_pipeline_context(pl3d_pipeline* pl);
+
 /* Waits for `stream` and reports any pending CUDA error as PL3D_ERR_CUDA. Then reads the
  * context's device error word: when a bounded device wait of an earlier call gave up (a grid
  * barrier or a TMA copy not completing within 1 s), the results of the calls since the last

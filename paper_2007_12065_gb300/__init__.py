@@ -205,6 +205,13 @@ def lib():
     L.pl3d_server_destroy.restype = None
     L.pl3d_server_replay.argtypes = [_vp, ctypes.POINTER(pl3d_replay_source), ctypes.c_int, _vp, _vp, ctypes.c_int64,
                                      ctypes.POINTER(pl3d_replay_report)]
+    L.pl3d_pipeline_create.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(_vp)]
+    L.pl3d_pipeline_submit.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, P, _vp, ctypes.c_int, _vp, _vp, _vp,
+                                       ctypes.POINTER(ctypes.c_uint64)]
+    L.pl3d_pipeline_wait.argtypes = [_vp, ctypes.c_uint64]
+    L.pl3d_pipeline_destroy.argtypes = [_vp]
+    L.pl3d_pipeline_context.argtypes = [_vp]
+    L.pl3d_pipeline_context.restype = _vp
     _lib = L
     return L
 
@@ -545,6 +552,50 @@ def pl3d_fastga_peaks(level, counts, v_min: float, d_peak: float, max_peaks: int
     if k < 0:
         raise PL3DError(k, "pl3d_fastga_peaks")
     return out[:k].copy(), w[:k].copy()
+
+
+def pl3d_pipeline_create(device: int = 0, max_points: int = 480 * 640, depth: int = 3) -> int:
+    """A pipeline of host-buffer frames; returns its handle (see include/pl3d.h)."""
+    h = _vp()
+    _check(lib().pl3d_pipeline_create(int(device), int(max_points), int(depth), ctypes.byref(h)),
+           "pl3d_pipeline_create")
+    return int(h.value)
+
+
+def pl3d_pipeline_submit(pl, points, H, W, params, dominant_normals, K, out_tri_mask, out_normals,
+                         out_labels) -> int:
+    """Enqueues one frame (host buffers: pinned CPU tensors that stay alive and untouched until the
+    ticket is waited for); returns its ticket."""
+    n_tri = 2 * (H - 1) * (W - 1)
+    _check_tensor(points, "points", "torch.float32", H * W * 3, "cpu")
+    _check_tensor(out_tri_mask, "out_tri_mask", "torch.uint8", n_tri, "cpu")
+    _check_tensor(out_normals, "out_normals", "torch.float32", n_tri * 3, "cpu")
+    _check_tensor(out_labels, "out_labels", "torch.int32", n_tri, "cpu")
+    nd = _nd_host(dominant_normals, K)
+    t = ctypes.c_uint64()
+    _check(lib().pl3d_pipeline_submit(pl, _ptr(points), int(H), int(W), ctypes.byref(params), _ptr(nd), int(K),
+                                      _ptr(out_tri_mask), _ptr(out_normals), _ptr(out_labels), ctypes.byref(t)),
+           "pl3d_pipeline_submit")
+    return int(t.value)
+
+
+def pl3d_pipeline_wait(pl, ticket: int) -> int:
+    """Waits for a frame's outputs in host memory; raises PL3DError on a failed frame."""
+    return _check(lib().pl3d_pipeline_wait(pl, int(ticket)), "pl3d_pipeline_wait")
+
+
+def pl3d_pipeline_status(pl, ticket: int) -> int:
+    """As pl3d_pipeline_wait, returning the status code instead of raising."""
+    return int(lib().pl3d_pipeline_wait(pl, int(ticket)))
+
+
+def pl3d_pipeline_context(pl) -> int:
+    """The pipeline's own context handle (timing, launch counts, the timeout self-test)."""
+    return int(lib().pl3d_pipeline_context(pl) or 0)
+
+
+def pl3d_pipeline_destroy(pl) -> None:
+    lib().pl3d_pipeline_destroy(pl)
 
 
 def pl3d_server_create(device: int = 0, max_inflight: int = 2, max_batch_frames: int = 64, hbm_bytes: int = 0) -> int:

@@ -21,7 +21,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpl3d.so")
 
-SOURCES = ["pl3d_api.cu", "frame_host.cu", "frame_r1.cu", "frame_r2.cu", "frame_r3.cu", "pl3d_static.cu", "pl3d_batch.cu", "pl3d_serve.cu", "pl3d_mesh.cu", "pl3d_fastga.cu", "pl3d_seeded.cu", "pl3d_selftest.cu", "lap1.cu"]
+SOURCES = ["pl3d_api.cu", "frame_host.cu", "frame_r1.cu", "frame_r2.cu", "frame_r3.cu", "pl3d_static.cu", "pl3d_batch.cu", "pl3d_serve.cu", "pl3d_mesh.cu", "pl3d_fastga.cu", "pl3d_seeded.cu", "pl3d_selftest.cu", "lap1.cu", "pl3d_pipeline.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-I", INCLUDE, "-I", CSRC,
                      "--expt-relaxed-constexpr"]

@@ -115,6 +115,23 @@ int run(pl3d_ctx* ctx, const float* points, int H, int W, const pl3d_params* p, 
 
 }  // namespace
 
+namespace pl3d {
+namespace ctxutil {
+
+int ctx_run(pl3d_ctx* ctx, const float* points, int H, int W, const pl3d_params* p, const float* nd_host, int K,
+            uint8_t* out_mask, float* out_normals, int32_t* out_labels, cudaStream_t s) {
+    return run(ctx, points, H, W, p, nd_host, K, out_mask, out_normals, out_labels, nullptr, nullptr, s);
+}
+
+int ctx_reserve(pl3d_ctx* ctx, size_t points, cudaStream_t s) {
+    int rc = grow(&ctx->disp, &ctx->cap_points, points, 6, s);
+    if (rc == PL3D_OK) rc = grow_tri(ctx, 2 * points, s);
+    return rc;
+}
+
+}  // namespace ctxutil
+}  // namespace pl3d
+
 extern "C" {
 
 int pl3d_version(void) { return kVersion; }

@@ -180,5 +180,13 @@ size_t batch_scratch_bytes(const pl3d_frame& f, const Tuning& t);
 // that later batches within those limits allocate nothing.
 int batch_reserve(pl3d_ctx* c, size_t slab_bytes, int frames, cudaStream_t s);
 
+// The single-frame path on device buffers, enqueued on `s` (pl3d_api.cu): the arguments checked
+// as pl3d_extract_planes checks them; grows the context's scratch when a frame needs more.
+int ctx_run(pl3d_ctx* ctx, const float* points, int H, int W, const pl3d_params* p, const float* nd_host, int K,
+            uint8_t* out_mask, float* out_normals, int32_t* out_labels, cudaStream_t s);
+
+// Sizes the context's scratch for frames of up to `points` points now (pl3d_api.cu).
+int ctx_reserve(pl3d_ctx* ctx, size_t points, cudaStream_t s);
+
 }  // namespace ctxutil
 }  // namespace pl3d
