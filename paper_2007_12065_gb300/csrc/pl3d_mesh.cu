@@ -25,8 +25,8 @@
 namespace pl3d {
 namespace mesh {
 
-constexpr int kChunk = 2048;
-constexpr int kPer = kChunk / kThreads;   // 8 consecutive entries per thread
+constexpr int kChunk = 1024;
+constexpr int kPer = kChunk / kThreads;   // 4 consecutive entries per thread
 constexpr int kBins = 256;
 constexpr int kWarps = kThreads / 32;
 
@@ -172,11 +172,13 @@ __global__ void __launch_bounds__(kThreads, 4) mesh_kernel(const __grid_constant
     // C: T, T_map, T labels, segment roots (GID order). A GID's place among the chunk's entries
     // is the count of (round, warp) blocks before its own plus its lane's rank in its warp's
     // ballot; the per-block counts live in sh_wc (free until the sort).
-    static_assert(kPer * kWarps == 64, "one (round, warp) count per lane pair of warp 0");
+    constexpr int kBlocks = kPer * kWarps;   // (round, warp) blocks of a chunk
+    constexpr int kPerLane = kBlocks / 32;   // blocks per lane of warp 0 in their prefix
+    static_assert(kBlocks % 32 == 0 && kPerLane <= 2 && 4 * kBlocks <= kWarps * kBins, "block counts");
     int* const cntT = &sh_wc[0][0];
-    int* const cntR = cntT + 64;
-    int* const preT = cntT + 128;
-    int* const preR = cntT + 192;
+    int* const cntR = cntT + kBlocks;
+    int* const preT = cntT + 2 * kBlocks;
+    int* const preR = cntT + 3 * kBlocks;
     for (int c = blockIdx.x; c < C; c += gridDim.x) {
         const long long c0 = (long long)c * kChunk;
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -203,9 +205,10 @@ __global__ void __launch_bounds__(kThreads, 4) mesh_kernel(const __grid_constant
         int ct, cr;
         block_exclusive((int)bt, sh_scan, &ct);   // (its barriers also publish the counts above)
         block_exclusive((int)br, sh_scan, &cr);
-        if (warp == 0) {   // exclusive prefix over the 64 (round, warp) blocks, two per lane
-            const int k0 = 2 * lane;
-            const int t0 = cntT[k0], t1 = cntT[k0 + 1], r0 = cntR[k0], r1 = cntR[k0 + 1];
+        if (warp == 0) {   // exclusive prefix over the (round, warp) blocks, kPerLane per lane
+            const int k0 = kPerLane * lane;
+            const int t0 = cntT[k0], t1 = kPerLane > 1 ? cntT[k0 + 1] : 0;
+            const int r0 = cntR[k0], r1 = kPerLane > 1 ? cntR[k0 + 1] : 0;
             int st = t0 + t1, sr = r0 + r1;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -216,9 +219,11 @@ __global__ void __launch_bounds__(kThreads, 4) mesh_kernel(const __grid_constant
                 }
             }
             preT[k0] = st - (t0 + t1);
-            preT[k0 + 1] = st - t1;
             preR[k0] = sr - (r0 + r1);
-            preR[k0 + 1] = sr - r1;
+            if (kPerLane > 1) {
+                preT[k0 + 1] = st - t1;
+                preR[k0 + 1] = sr - r1;
+            }
         }
         __syncthreads();
         const unsigned below = (1u << lane) - 1u;
