@@ -44,6 +44,7 @@ struct MeshArgs {
     uint8_t* border;             // [|T|]
     int n_chunks;                // chunks of GIDs
     int32_t* cnt;                // [2][n_chunks]: T entries and roots per chunk -> exclusive offsets
+    unsigned* bits;              // [2][n_chunks kChunk / 32]: valid triangles, segment roots, one bit per GID
     int32_t* root_idx;           // [2Q]
     int32_t* tlab;               // [2Q] label of each T entry
     int32_t* keys[2];            // [2Q]
@@ -61,9 +62,9 @@ __device__ __forceinline__ bool vertex_valid(const float* P, long long i) {
 // Vertex (point) indices of triangle gid in the order of Algorithm 1:
 // first = {p3, p2, p1}, second = {p1, p4, p3}.
 __device__ __forceinline__ void tri_vertices(long long gid, int W, int Wq, long long v[3]) {
-    const long long q = gid >> 1;
-    const long long u = q / Wq, c = q - u * Wq;
-    const long long p1 = u * W + c, p2 = p1 + 1, p3 = p1 + W + 1, p4 = p1 + W;
+    const int q = (int)(gid >> 1);   // 2 (H - 1)(W - 1) < 2^31
+    const int u = q / Wq, c = q - u * Wq;
+    const long long p1 = (long long)u * W + c, p2 = p1 + 1, p3 = p1 + W + 1, p4 = p1 + W;
     if ((gid & 1) == 0) {
         v[0] = p3, v[1] = p2, v[2] = p1;
     } else {
@@ -136,6 +137,13 @@ __global__ void __launch_bounds__(kThreads, 4) mesh_kernel(const __grid_constant
             nt += f.valid;
             nr += f.root;
             if (a.labels && g < n) a.root_idx[g] = -1;
+            // the flags as bits, one word per warp and round (kept for phase C)
+            const unsigned bv = __ballot_sync(0xffffffffu, f.valid), br = __ballot_sync(0xffffffffu, f.root);
+            if ((threadIdx.x & 31) == 0) {
+                const long long w = (c0 + j * kThreads + threadIdx.x) >> 5;
+                a.bits[w] = bv;
+                a.bits[(long long)C * (kChunk / 32) + w] = br;
+            }
         }
         int tt, tr;
         block_exclusive(nt, sh_scan, &tt);
@@ -173,8 +181,7 @@ __global__ void __launch_bounds__(kThreads, 4) mesh_kernel(const __grid_constant
     // is the count of (round, warp) blocks before its own plus its lane's rank in its warp's
     // ballot; the per-block counts live in sh_wc (free until the sort).
     constexpr int kBlocks = kPer * kWarps;   // (round, warp) blocks of a chunk
-    constexpr int kPerLane = kBlocks / 32;   // blocks per lane of warp 0 in their prefix
-    static_assert(kBlocks % 32 == 0 && kPerLane <= 2 && 4 * kBlocks <= kWarps * kBins, "block counts");
+    static_assert(kBlocks <= 64 && 4 * kBlocks <= kWarps * kBins, "block counts: two per lane of warp 0");
     int* const cntT = &sh_wc[0][0];
     int* const cntR = cntT + kBlocks;
     int* const preT = cntT + 2 * kBlocks;
@@ -186,9 +193,11 @@ __global__ void __launch_bounds__(kThreads, 4) mesh_kernel(const __grid_constant
         unsigned bv[kPer], brt[kPer];
 #pragma unroll
         for (int j = 0; j < kPer; ++j) {
-            f[j] = gid_flags(a, c0 + j * kThreads + threadIdx.x, n);
-            bv[j] = __ballot_sync(0xffffffffu, f[j].valid);
-            brt[j] = __ballot_sync(0xffffffffu, f[j].root);
+            const long long w = (c0 + j * kThreads) / 32 + warp;
+            bv[j] = __ldcg(a.bits + w);
+            brt[j] = __ldcg(a.bits + (long long)C * (kChunk / 32) + w);
+            f[j].valid = (bv[j] >> lane) & 1u;
+            f[j].root = (brt[j] >> lane) & 1u;
         }
         if (lane == 0) {
 #pragma unroll
@@ -205,10 +214,10 @@ __global__ void __launch_bounds__(kThreads, 4) mesh_kernel(const __grid_constant
         int ct, cr;
         block_exclusive((int)bt, sh_scan, &ct);   // (its barriers also publish the counts above)
         block_exclusive((int)br, sh_scan, &cr);
-        if (warp == 0) {   // exclusive prefix over the (round, warp) blocks, kPerLane per lane
-            const int k0 = kPerLane * lane;
-            const int t0 = cntT[k0], t1 = kPerLane > 1 ? cntT[k0 + 1] : 0;
-            const int r0 = cntR[k0], r1 = kPerLane > 1 ? cntR[k0 + 1] : 0;
+        if (warp == 0) {   // exclusive prefix over the (round, warp) blocks, two per lane
+            const int k0 = 2 * lane;
+            const int t0 = k0 < kBlocks ? cntT[k0] : 0, t1 = k0 + 1 < kBlocks ? cntT[k0 + 1] : 0;
+            const int r0 = k0 < kBlocks ? cntR[k0] : 0, r1 = k0 + 1 < kBlocks ? cntR[k0 + 1] : 0;
             int st = t0 + t1, sr = r0 + r1;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -218,9 +227,11 @@ __global__ void __launch_bounds__(kThreads, 4) mesh_kernel(const __grid_constant
                     sr += yr;
                 }
             }
-            preT[k0] = st - (t0 + t1);
-            preR[k0] = sr - (r0 + r1);
-            if (kPerLane > 1) {
+            if (k0 < kBlocks) {
+                preT[k0] = st - (t0 + t1);
+                preR[k0] = sr - (r0 + r1);
+            }
+            if (k0 + 1 < kBlocks) {
                 preT[k0 + 1] = st - t1;
                 preR[k0 + 1] = sr - r1;
             }
@@ -462,10 +473,12 @@ extern "C" int pl3d_extract_mesh(pl3d_ctx* ctx, const float* points, const int32
     cudaStream_t s = (cudaStream_t)stream;
     const size_t ntri = 2 * (size_t)(H - 1) * (W - 1);
     const int C = (int)((ntri + mesh::kChunk - 1) / mesh::kChunk);
-    // scratch: chunk counts, root index, T labels, keys and values (double buffered), histograms
+    // scratch: chunk counts, root index, T labels, keys and values (double buffered), histograms,
+    // digit totals, flag bits
     const size_t b_cnt = align_up(2 * (size_t)C * 4, 256), b_tri = align_up(ntri * 4, 256);
     const size_t b_hist = align_up((size_t)mesh::kBins * C * 4, 256), b_bins = align_up(mesh::kBins * 4, 256);
-    int rc = grow_mesh(ctx, b_cnt + 6 * b_tri + b_hist + b_bins, s);
+    const size_t b_bits = align_up(2 * (size_t)C * (mesh::kChunk / 32) * 4, 256);
+    int rc = grow_mesh(ctx, b_cnt + 6 * b_tri + b_hist + b_bins + b_bits, s);
     if (rc != PL3D_OK) return rc;
     mesh::MeshArgs a;
     memset(&a, 0, sizeof(a));
@@ -498,6 +511,8 @@ extern "C" int pl3d_extract_mesh(pl3d_ctx* ctx, const float* points, const int32
     a.hist = reinterpret_cast<int32_t*>(p);
     p += b_hist;
     a.bin_tot = reinterpret_cast<int32_t*>(p);
+    p += b_bins;
+    a.bits = reinterpret_cast<unsigned*>(p);
     a.barrier = ctx->barrier();
     a.error = ctx->error();
     int dev = 0;
