@@ -2,18 +2,20 @@
 // HE) and the triangle lists and boundary half-edges of its planar segments (the inputs of the
 // polygon extraction of Section 7.2), in one cooperative launch (pl3d_extract_mesh).
 //
-// Phases, one grid barrier apart, all over chunks of 2048 consecutive entries (8 per thread:
+// Phases, one grid barrier apart, all over chunks of 1024 consecutive entries (4 per thread:
 // consecutive ones in the sort, one per round of 256 consecutive GIDs in A and C):
 //   A  per chunk of GIDs: valid triangles (all three points valid, Algorithm 1) and segment
-//      roots (a label is the smallest GID of its segment, so a root is labelled with itself)
-//      (no scan phase: each CTA sums the counts of the chunks before its own when it needs them)
+//      roots (a label is the smallest GID of its segment, so a root is labelled with itself),
+//      kept as ballot words (no scan phase: each CTA sums the counts of the chunks before its own
+//      when it needs them)
 //   C  T, T_map, the label of each T entry, and the segment index of each root, in GID order
-//   D  HE from the neighbours' T_map (the twin rules of Algorithm 2); sort keys: the segment
-//      index of each T entry (the segment count for an unlabelled one, so it sorts last)
-//   R  a stable LSD radix sort of (segment index, T index), 8 bits per pass: per-chunk digit
-//      histograms; per-digit exclusive scans over the chunks; a stable scatter that ranks equal
-//      digits inside a warp with __match_any_sync and across warps with per-warp counters
-//   G  the segments' CSR (offsets where the key changes) and the boundary half-edges
+//   D  HE from the neighbours' T_map (the twin rules of Algorithm 2) and the boundary half-edges
+//      (no twin, or a twin of another label); sort keys: the segment index of each T entry (the
+//      segment count for an unlabelled one, so it sorts last)
+//   R  a stable LSD radix sort of (segment index, T index) with digits of up to 8 bits: per-chunk
+//      digit histograms; per-digit exclusive scans over the chunks; a stable scatter that ranks
+//      equal digits inside a warp with __match_any_sync and across warps with per-warp counters
+//   G  the segments' CSR (offsets where the key changes)
 // Data written by one CTA and read by another after a barrier is loaded with __ldcg (L2), never
 // through the non-coherent read-only path.
 // Everything in T order keeps GID order, so the lists come out sorted by (label, T index).
@@ -27,7 +29,9 @@ namespace mesh {
 
 constexpr int kChunk = 1024;
 constexpr int kPer = kChunk / kThreads;   // 4 consecutive entries per thread
-constexpr int kBins = 256;
+constexpr int kMaxDigitBits = 8;   // radix digits of up to 8 bits (11-bit digits, one pass below 2048 segments, measured slower)
+constexpr int kMaxBins = 1 << kMaxDigitBits;
+constexpr size_t kSmemBytes = 2 * kMaxBins * sizeof(int) + (size_t)(kThreads / 32) * kMaxBins * sizeof(uint16_t);
 constexpr int kWarps = kThreads / 32;
 
 struct MeshArgs {
@@ -49,8 +53,8 @@ struct MeshArgs {
     int32_t* tlab;               // [2Q] label of each T entry
     int32_t* keys[2];            // [2Q]
     int32_t* vals[2];            // [2Q]
-    int32_t* hist;               // [kBins][n_chunks]
-    int32_t* bin_tot;            // [kBins]
+    int32_t* hist;               // [kMaxBins][n_chunks]
+    int32_t* bin_tot;            // [kMaxBins]
     unsigned* barrier;
     int* error;
 };
@@ -115,9 +119,12 @@ __device__ __forceinline__ Flags gid_flags(const MeshArgs& a, long long g, long 
 
 __global__ void __launch_bounds__(kThreads, 4) mesh_kernel(const __grid_constant__ MeshArgs a) {
     __shared__ int sh_scan[kWarps + 1];
-    __shared__ int sh_bins[kBins];
-    __shared__ int sh_base[kBins];
-    __shared__ int sh_wc[kWarps][kBins];
+    // dynamic: digit counts [kMaxBins], digit bases [kMaxBins], per-warp digit counts
+    // [kWarps][kMaxBins] (16-bit: at most kChunk / kWarps entries per warp)
+    extern __shared__ int mesh_smem[];
+    int* const sh_bins = mesh_smem;
+    int* const sh_base = mesh_smem + kMaxBins;
+    uint16_t* const sh_wc = reinterpret_cast<uint16_t*>(mesh_smem + 2 * kMaxBins);
     const int Wq = a.W - 1, Hq = a.H - 1;
     const long long n = 2LL * Hq * Wq;
     const int C = a.n_chunks;
@@ -181,8 +188,8 @@ __global__ void __launch_bounds__(kThreads, 4) mesh_kernel(const __grid_constant
     // is the count of (round, warp) blocks before its own plus its lane's rank in its warp's
     // ballot; the per-block counts live in sh_wc (free until the sort).
     constexpr int kBlocks = kPer * kWarps;   // (round, warp) blocks of a chunk
-    static_assert(kBlocks <= 64 && 4 * kBlocks <= kWarps * kBins, "block counts: two per lane of warp 0");
-    int* const cntT = &sh_wc[0][0];
+    static_assert(kBlocks <= 64 && 4 * kBlocks <= kWarps * kMaxBins / 2, "block counts: two per lane of warp 0");
+    int* const cntT = reinterpret_cast<int*>(sh_wc);
     int* const cntR = cntT + kBlocks;
     int* const preT = cntT + 2 * kBlocks;
     int* const preR = cntT + 3 * kBlocks;
@@ -286,6 +293,38 @@ __global__ void __launch_bounds__(kThreads, 4) mesh_kernel(const __grid_constant
                 a.HE[3LL * second + 1] = bottom >= 0 ? 3 * bottom + 1 : -1;
                 a.HE[3LL * second + 2] = first >= 0 ? 3 * first + 2 : -1;
             }
+            if (a.border) {
+                // a half-edge is on a segment's boundary when it has no twin or the twin's label
+                // differs; unlabelled triangles have no boundary
+                const long long g1 = 2 * q, g2 = 2 * q + 1;
+                const int l1 = a.labels ? __ldg(a.labels + g1) : -1, l2 = a.labels ? __ldg(a.labels + g2) : -1;
+                if (first >= 0) {
+                    unsigned bits = 0;
+                    if (l1 >= 0) {
+                        const int lr = v + 1 < Wq ? __ldg(a.labels + 2 * (q + 1) + 1) : -1;
+                        const int lt = u > 0 ? __ldg(a.labels + 2 * (q - Wq) + 1) : -1;
+                        const bool hr = v + 1 < Wq && __ldcg(tm + 2 * (q + 1) + 1) >= 0;
+                        const bool ht = u > 0 && __ldcg(tm + 2 * (q - Wq) + 1) >= 0;
+                        bits |= (!hr || lr != l1) ? 1u : 0u;
+                        bits |= (!ht || lt != l1) ? 2u : 0u;
+                        bits |= (second < 0 || l2 != l1) ? 4u : 0u;
+                    }
+                    a.border[first] = (uint8_t)bits;
+                }
+                if (second >= 0) {
+                    unsigned bits = 0;
+                    if (l2 >= 0) {
+                        const int ll = v > 0 ? __ldg(a.labels + 2 * (q - 1)) : -1;
+                        const int lb = u + 1 < Hq ? __ldg(a.labels + 2 * (q + Wq)) : -1;
+                        const bool hl = v > 0 && __ldcg(tm + 2 * (q - 1)) >= 0;
+                        const bool hb = u + 1 < Hq && __ldcg(tm + 2 * (q + Wq)) >= 0;
+                        bits |= (!hl || ll != l2) ? 1u : 0u;
+                        bits |= (!hb || lb != l2) ? 2u : 0u;
+                        bits |= (first < 0 || l1 != l2) ? 4u : 0u;
+                    }
+                    a.border[second] = (uint8_t)bits;
+                }
+            }
             if (a.labels && nS > 0) {
                 for (int side = 0; side < 2; ++side) {
                     const int t = side == 0 ? first : second;
@@ -301,10 +340,7 @@ __global__ void __launch_bounds__(kThreads, 4) mesh_kernel(const __grid_constant
         }
     }
     if (!a.labels || nS == 0) {
-        // no segments: no lists; every boundary flag is 0
-        const long long stride = (long long)gridDim.x * blockDim.x;
-        for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nT; t += stride)
-            if (a.border) a.border[t] = 0;
+        // no segments: no lists (the boundary flags are all 0)
         if (a.labels && blockIdx.x == 0 && threadIdx.x == 0) a.seg_offsets[0] = 0;
         return;
     }
@@ -313,29 +349,31 @@ __global__ void __launch_bounds__(kThreads, 4) mesh_kernel(const __grid_constant
     // R: stable LSD radix sort of (segment index, T index) over the T entries
     const int Ct = (int)((nT + kChunk - 1) / kChunk);
     const int key_bits = 32 - __clz(nS);   // keys run over 0..nS
-    const int passes = (key_bits + 7) / 8;
+    const int passes = (key_bits + kMaxDigitBits - 1) / kMaxDigitBits;
+    const int dbits = (key_bits + passes - 1) / passes;
+    const int bins = 1 << dbits;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int pass = 0; pass < passes; ++pass) {
-        const int shift = 8 * pass;
+        const int shift = dbits * pass;
         const int32_t* ks = a.keys[pass & 1];
         const int32_t* vs = a.vals[pass & 1];
         int32_t* kd = a.keys[(pass + 1) & 1];
         int32_t* vd = a.vals[(pass + 1) & 1];
         // R1: digit histogram of every chunk
         for (int c = blockIdx.x; c < Ct; c += gridDim.x) {
-            sh_bins[threadIdx.x] = 0;
+            for (int d = threadIdx.x; d < bins; d += kThreads) sh_bins[d] = 0;
             __syncthreads();
             const long long i0 = (long long)c * kChunk + threadIdx.x * kPer;
 #pragma unroll
             for (int j = 0; j < kPer; ++j)
-                if (i0 + j < nT) atomicAdd(&sh_bins[(__ldcg(ks + i0 + j) >> shift) & (kBins - 1)], 1);
+                if (i0 + j < nT) atomicAdd(&sh_bins[(__ldcg(ks + i0 + j) >> shift) & (bins - 1)], 1);
             __syncthreads();
-            a.hist[(long long)threadIdx.x * Ct + c] = sh_bins[threadIdx.x];
+            for (int d = threadIdx.x; d < bins; d += kThreads) a.hist[(long long)d * Ct + c] = sh_bins[d];
             __syncthreads();
         }
         grid_barrier(a.barrier, a.error);
         // R2: per digit, exclusive offsets over the chunks, and the digit's total
-        for (int d = blockIdx.x; d < kBins; d += gridDim.x) {
+        for (int d = blockIdx.x; d < bins; d += gridDim.x) {
             int32_t* h = a.hist + (long long)d * Ct;
             long long carry = 0;
             for (int base = 0; base < Ct; base += kThreads) {
@@ -352,10 +390,21 @@ __global__ void __launch_bounds__(kThreads, 4) mesh_kernel(const __grid_constant
         // R3: stable scatter
         {
             int tot;
-            sh_base[threadIdx.x] = block_exclusive(__ldcg(a.bin_tot + threadIdx.x), sh_scan, &tot);
+            // the digits' bases: thread t scans its run of consecutive digits
+            const int per = (bins + kThreads - 1) / kThreads, d0 = threadIdx.x * per;
+            int local = 0;
+            for (int d = d0; d < d0 + per && d < bins; ++d) local += __ldcg(a.bin_tot + d);
+            int run = block_exclusive(local, sh_scan, &tot);
+            for (int d = d0; d < d0 + per && d < bins; ++d) {
+                sh_base[d] = run;
+                run += __ldcg(a.bin_tot + d);
+            }
         }
         for (int c = blockIdx.x; c < Ct; c += gridDim.x) {
-            for (int d = threadIdx.x; d < kWarps * kBins; d += kThreads) (&sh_wc[0][0])[d] = 0;
+            for (int d = threadIdx.x; d < kWarps * bins / 2; d += kThreads) {
+                const int w = d / (bins / 2), e = d - w * (bins / 2);
+                reinterpret_cast<unsigned*>(sh_wc + w * kMaxBins)[e] = 0u;
+            }
             __syncthreads();
             // warp w owns the 256 consecutive entries [c kChunk + 256 w, + 256), in 8 rounds of 32
             const long long w0 = (long long)c * kChunk + warp * (kChunk / kWarps);
@@ -363,25 +412,24 @@ __global__ void __launch_bounds__(kThreads, 4) mesh_kernel(const __grid_constant
 #pragma unroll
             for (int r = 0; r < kPer; ++r) {
                 const long long i = w0 + r * 32 + lane;
-                const int d = i < nT ? (__ldcg(ks + i) >> shift) & (kBins - 1) : -1;
+                const int d = i < nT ? (__ldcg(ks + i) >> shift) & (bins - 1) : -1;
                 const unsigned peers = __match_any_sync(0xffffffffu, d);
                 const unsigned lower = peers & ((1u << lane) - 1u);
                 int base = 0;
-                if (d >= 0) base = sh_wc[warp][d];
+                if (d >= 0) base = sh_wc[warp * kMaxBins + d];
                 __syncwarp();
-                if (d >= 0 && lower == 0) sh_wc[warp][d] = base + __popc(peers);
+                if (d >= 0 && lower == 0) sh_wc[warp * kMaxBins + d] = (uint16_t)(base + __popc(peers));
                 __syncwarp();
                 rank[r] = base + __popc(lower);
                 dig[r] = d;
             }
             __syncthreads();
             // per digit: offsets of the warps (warp order = entry order)
-            {
-                const int d = threadIdx.x;
+            for (int d = threadIdx.x; d < bins; d += kThreads) {
                 int run = 0;
                 for (int w = 0; w < kWarps; ++w) {
-                    const int t = sh_wc[w][d];
-                    sh_wc[w][d] = run;
+                    const int t = sh_wc[w * kMaxBins + d];
+                    sh_wc[w * kMaxBins + d] = (uint16_t)run;
                     run += t;
                 }
             }
@@ -392,7 +440,7 @@ __global__ void __launch_bounds__(kThreads, 4) mesh_kernel(const __grid_constant
                 if (d < 0) continue;
                 const long long i = w0 + r * 32 + lane;
                 const long long pos =
-                    (long long)sh_base[d] + __ldcg(a.hist + (long long)d * Ct + c) + sh_wc[warp][d] + rank[r];
+                    (long long)sh_base[d] + __ldcg(a.hist + (long long)d * Ct + c) + sh_wc[warp * kMaxBins + d] + rank[r];
                 kd[pos] = __ldcg(ks + i);
                 vd[pos] = __ldcg(vs + i);
             }
@@ -401,7 +449,7 @@ __global__ void __launch_bounds__(kThreads, 4) mesh_kernel(const __grid_constant
         grid_barrier(a.barrier, a.error);
     }
 
-    // G: CSR of the segments and their boundary half-edges
+    // G: CSR of the segments (their boundary half-edges came with HE in D)
     // keys below nS are the triangles in segments, sorted first
     const int32_t* K = a.keys[passes & 1];
     const int32_t* V = a.vals[passes & 1];
@@ -414,20 +462,6 @@ __global__ void __launch_bounds__(kThreads, 4) mesh_kernel(const __grid_constant
         if (p + 1 == nT || __ldcg(K + p + 1) >= nS) {   // the last triangle in a segment
             a.seg_offsets[nS] = (int32_t)(p + 1);
             a.counts[2] = p + 1;
-        }
-    }
-    if (a.border) {
-        for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nT; t += stride) {
-            const int l = __ldcg(a.tlab + t);
-            unsigned bits = 0;
-            if (l >= 0) {
-#pragma unroll
-                for (int e = 0; e < 3; ++e) {
-                    const int tw = __ldcg(a.HE + 3 * t + e);
-                    if (tw < 0 || __ldcg(a.tlab + tw / 3) != l) bits |= 1u << e;
-                }
-            }
-            a.border[t] = (uint8_t)bits;
         }
     }
 }
@@ -476,7 +510,7 @@ extern "C" int pl3d_extract_mesh(pl3d_ctx* ctx, const float* points, const int32
     // scratch: chunk counts, root index, T labels, keys and values (double buffered), histograms,
     // digit totals, flag bits
     const size_t b_cnt = align_up(2 * (size_t)C * 4, 256), b_tri = align_up(ntri * 4, 256);
-    const size_t b_hist = align_up((size_t)mesh::kBins * C * 4, 256), b_bins = align_up(mesh::kBins * 4, 256);
+    const size_t b_hist = align_up((size_t)mesh::kMaxBins * C * 4, 256), b_bins = align_up(mesh::kMaxBins * 4, 256);
     const size_t b_bits = align_up(2 * (size_t)C * (mesh::kChunk / 32) * 4, 256);
     int rc = grow_mesh(ctx, b_cnt + 6 * b_tri + b_hist + b_bins + b_bits, s);
     if (rc != PL3D_OK) return rc;
@@ -519,13 +553,17 @@ extern "C" int pl3d_extract_mesh(pl3d_ctx* ctx, const float* points, const int32
     if (cudaGetDevice(&dev) != cudaSuccess) return PL3D_ERR_CUDA;
     const void* fn = reinterpret_cast<const void*>(&mesh::mesh_kernel);
     // one CTA per chunk (at least one per digit of the radix scans), as many as are resident
-    const int want = C > mesh::kBins ? C : mesh::kBins;
-    const int grid = persistent_grid(fn, 0, dev, Tuning{0, 0, 0}, want);
+    const int want = C > mesh::kMaxBins ? C : mesh::kMaxBins;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mesh::kSmemBytes) != cudaSuccess) {
+        cudaGetLastError();
+        return PL3D_ERR_CUDA;
+    }
+    const int grid = persistent_grid(fn, mesh::kSmemBytes, dev, Tuning{0, 0, 0}, want);
     if (grid <= 0) return PL3D_ERR_CUDA;
     void* args[1] = {&a};
     cudaEvent_t e0, e1;
     record_start(ctx, s, &e0, &e1);
-    if (cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kThreads), args, 0, s) != cudaSuccess) {
+    if (cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kThreads), args, mesh::kSmemBytes, s) != cudaSuccess) {
         cudaGetLastError();
         return PL3D_ERR_CUDA;
     }

@@ -74,9 +74,9 @@ def test_tri_min_and_offset_labels(env):
     _check(env, f.points, _oracle_labels(f, max_offset=0.02))
 
 
-def test_three_radix_passes(env):
+def test_many_segments_three_radix_passes(env):
     """One segment per quad (label = the quad's first GID when both triangles are valid): about
-    300,000 segments, so the sort runs three 8-bit passes."""
+    300,000 segments, so the sort runs three passes of 7-bit digits."""
     f = synth.rgbd_480x640()
     H, W = f.points.shape[:2]
     valid = np.isfinite(f.points).all(-1)
