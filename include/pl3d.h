@@ -539,7 +539,13 @@ int pl3d_extract_mesh(pl3d_ctx* ctx, const float* points, const int32_t* labels,
  * `mask` (device, n bytes) is given, whose mask byte is non-zero: each goes to the cell whose
  * surface normal is closest (Section 6.1.3, Algorithm 3). out_counts (device, cells int32) receives
  * the histogram; out_cells (device, n int32, or NULL) the cell of every triangle, -1 where not
- * integrated. The first call for a level on a context uploads the level's tables (synchronously).
+ * integrated (up to near ties of FP32 dot products: a cell whose surface normal is within 1e-6 of
+ * the closest one's dot product may be chosen instead). The first call for a level in a process
+ * builds the level's tables on the host (about 0.1 s at level 4, 1 s at level 5) and the first
+ * call on a context uploads them (synchronously). One cooperative launch; it uses the context's
+ * grid barrier, so a device wait that gives up is reported by pl3d_sync as for the path itself.
+ * Returns PL3D_ERR_UNSUPPORTED if the level's tables fail their own construction check (not
+ * expected for levels 0 .. 5).
  *
  * pl3d_fastga_peaks (host only) detects peaks in a histogram (host, cells int32): a cell whose
  * count is above v_min and not below any 1-ring neighbour's (a plateau keeps its lowest index),
