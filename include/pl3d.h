@@ -532,7 +532,9 @@ int pl3d_extract_mesh(pl3d_ctx* ctx, const float* points, const int32_t* labels,
  *
  * pl3d_fastga_cells (host only) writes the level's surface normals (host, cells * 3 floats) and
  * 1-ring neighbours (host, cells * 12 int32, ascending, -1 padded; either pointer may be NULL)
- * and returns the number of cells.
+ * and returns the number of cells. It builds the level's tables, the device search's included,
+ * and returns PL3D_ERR_UNSUPPORTED if they fail their construction check (every rotated cell
+ * normal of face 0's neighbourhood on a cell normal, child numbers kept).
  *
  * pl3d_fastga integrates every stride-th triangle of `normals` (device, n * 3 FP32, e.g. the
  * out_normals of pl3d_extract_planes; Section 6.3's sampling) whose normal is finite and, when

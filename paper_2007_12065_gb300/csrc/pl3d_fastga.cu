@@ -552,6 +552,7 @@ extern "C" {
 int pl3d_fastga_cells(int level, float* out_normals, int32_t* out_neighbors) {
     if (level < 0 || level > fastga::kMaxLevel) return PL3D_ERR_INVALID_ARG;
     const fastga::Tables& t = fastga::tables(level);
+    if (!t.canonical_ok) return PL3D_ERR_UNSUPPORTED;   // the tables failed their own check
     if (out_normals) memcpy(out_normals, t.normals.data(), t.normals.size() * sizeof(float));
     if (out_neighbors) memcpy(out_neighbors, t.nbrs.data(), t.nbrs.size() * sizeof(int32_t));
     return t.cells;

@@ -29,6 +29,14 @@ def test_cell_tables_match_oracle(pl3d, level):
         assert all(x == -1 for x in nbrs[i][len(row):])
 
 
+@pytest.mark.parametrize("level", [0, 1, 2, 3, 4, 5])
+def test_search_tables_pass_their_check(pl3d, level):
+    """The device search treats every level-0 face as a rotated copy of face 0; the library checks
+    on the host, for every cell of face 0's neighbourhood, that the rotation lands on a cell normal
+    with the same child number, and reports a failure from pl3d_fastga_cells."""
+    assert pl3d.lib().pl3d_fastga_cells(level, None, None) == 20 * 4 ** level
+
+
 def test_invalid_level_rejected(pl3d):
     assert pl3d.lib().pl3d_fastga_cells(6, None, None) == pl3d.PL3D_ERR_INVALID_ARG
     assert pl3d.lib().pl3d_fastga_cells(-1, None, None) == pl3d.PL3D_ERR_INVALID_ARG
