@@ -88,6 +88,7 @@ struct pl3d_ctx {
     // Gaussian accumulator tables of one refinement level (pl3d_fastga.cu)
     unsigned char* ga_tables = nullptr;
     int ga_level = -1;
+    size_t ga_smem_optin = 0;       // dynamic shared memory the accumulator kernel is opted in to
     size_t ga_off[3] = {0, 0, 0};
     // timing
     bool timing = false;

@@ -620,9 +620,13 @@ int pl3d_fastga(pl3d_ctx* ctx, const float* normals, const uint8_t* mask, int64_
     a.error = ctx->error();
     const size_t smem = (size_t)t.cells * sizeof(int);
     const void* fn = reinterpret_cast<const void*>(&fastga::fastga_kernel);
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
-        cudaGetLastError();
-        return PL3D_ERR_CUDA;
+    // above the default 48 KB (level 5) the kernel needs the opt-in; set once per level, not per call
+    if (smem > 48 * 1024 && ctx->ga_smem_optin < smem) {
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+            cudaGetLastError();
+            return PL3D_ERR_CUDA;
+        }
+        ctx->ga_smem_optin = smem;
     }
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return PL3D_ERR_CUDA;

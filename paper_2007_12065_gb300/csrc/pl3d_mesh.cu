@@ -554,10 +554,7 @@ extern "C" int pl3d_extract_mesh(pl3d_ctx* ctx, const float* points, const int32
     const void* fn = reinterpret_cast<const void*>(&mesh::mesh_kernel);
     // one CTA per chunk (at least one per digit of the radix scans), as many as are resident
     const int want = C > mesh::kMaxBins ? C : mesh::kMaxBins;
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mesh::kSmemBytes) != cudaSuccess) {
-        cudaGetLastError();
-        return PL3D_ERR_CUDA;
-    }
+    static_assert(mesh::kSmemBytes <= 48 * 1024, "within the default dynamic shared memory: no opt-in per call");
     const int grid = persistent_grid(fn, mesh::kSmemBytes, dev, Tuning{0, 0, 0}, want);
     if (grid <= 0) return PL3D_ERR_CUDA;
     void* args[1] = {&a};
