@@ -114,8 +114,8 @@ class ClockSampler:
 
 # FLOP per unit of work, from the operation lists of the method's arithmetic (Eq. 1-6, Algorithm 4)
 # counted the way the FP32 peak counts them: an add, sub or mul is 1 FLOP, an FMA 2, an exp or
-# rsqrt 1 (the survey's per-unit lists write "3 FMA" for a squared norm and count each listed
-# operation once; the table below spells every one out at FMA = 2, the unit of the peak).
+# rsqrt 1 (a count of one per listed operation, with "3 FMA" for a squared norm, gives smaller
+# totals; the table below spells every operation out at FMA = 2, the unit of the peak).
 FLOP_PER_UNIT = {
     # per point, iteration and window neighbour: difference 3 sub (3), squared norm 1 mul + 2 FMA
     # (5), 1/sqrt (1), weighted sum 3 FMA (6), weight sum 1 add (1)
