@@ -351,7 +351,7 @@ int pl3d_get_tuning(const pl3d_ctx* ctx, pl3d_tuning* tuning);
 /*
  * Autotuner: times the batch under launch shapes, `reps` timed runs each after one untimed run,
  * on `stream` with CUDA events, and keeps the fastest median as the context's tuning. It searches
- * in two rounds: first the fused depths (1, 2 or 3 passes per filter, and one iteration per
+ * in two stages: first the fused depths (1, 2 or 3 passes per filter, and one iteration per
  * Laplacian pass when its window is 3 x 3) x 1 or 2 CTAs per SM at the default tile shapes, then,
  * at the best of those, the tile heights (Laplacian 16, 32, 48, 64 points; bilateral 16, 24, 32
  * quads; 32 wide). Writes the choice to *best and its median milliseconds to *best_ms (either may be

@@ -485,8 +485,8 @@ int pl3d_autotune_batched(pl3d_ctx* ctx, const pl3d_frame* frames, int n, void* 
             }
         }
     };
-    // round 1: fused depths and CTAs per SM at the default tile shapes; round 2: tile heights at
-    // the best of those (the default shape is round 1's own entry)
+    // stage 1: fused depths and CTAs per SM at the default tile shapes; stage 2: tile heights at
+    // the best of those (the default shape is stage 1's own entry)
     try_all(round1);
     if (rc == PL3D_OK) {
         std::vector<Tuning> round2;
