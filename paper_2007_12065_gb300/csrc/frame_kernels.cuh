@@ -1048,8 +1048,12 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
     }
     __syncthreads();
     // (2) Rows joined across horizontal edges: first(r, v) with second(r-1, v); one union per
-    // run pair (a lane skips the pair its left neighbour already joined).
-    for (int r = 1 + warp; r < TH; r += kThreads / 32) {
+    // run pair (a lane skips the pair its left neighbour already joined). Each warp takes a block
+    // of consecutive edges, top down, so that a union finds the row above already joined and the
+    // trees stay shallow (rows dealt to the warps in turn left chains as long as the tile is high;
+    // the tile's label stage took 9.6 us instead of 7.5 us on the 480x640 frame).
+    const int per_w = (TH - 1 + kThreads / 32 - 1) / (kThreads / 32);
+    for (int r = 1 + warp * per_w, r_end = min(TH, 1 + (warp + 1) * per_w); r < r_end; ++r) {
         const int tf = 2 * (r * T + lane), tu = 2 * ((r - 1) * T + lane) + 1;
         const int gf = Gs[tf];
         bool link = gf != PL3D_NO_GROUP && Gs[tu] == gf;
