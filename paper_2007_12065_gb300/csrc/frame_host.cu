@@ -179,6 +179,11 @@ static int lap_tile_h(int iters, bool first, int halo, int requested) {
 
 static int bil_tile_h(const Tuning& t) { return t.bil_tile_h > 0 ? t.bil_tile_h : kTile; }
 
+size_t border_counters(int H, int W, const Tuning& t) {
+    if (H < 2 || W < 2) return 0;
+    return 2 * (size_t)div_up(H - 1, bil_tile_h(t)) * (size_t)div_up(W - 1, kTile);
+}
+
 const float* final_disp(const FrameScratch& sc, const pl3d_params* p, const Tuning& t) {
     const int rl = p->lap_iters > 0 ? p->lap_kernel / 2 : 1;
     const int lf = fused_iters(p->lap_iters, kLapMaxHalo / rl, t.lap_fuse);
@@ -322,6 +327,7 @@ int frame_build(FrameArgs& a, FramePlan& plan, const FrameScratch& sc, const flo
     a.min_triangles = p->min_triangles;
     a.barrier = sc.barrier;
     a.error = sc.error;
+    a.border = sc.border && sc.cap_border >= border_counters(H, W, t) ? sc.border : nullptr;
     a.phase_ns = sc.phase_ns;
     a.nd.K = K;
     for (int j = 0; j < K; ++j) {
@@ -414,9 +420,11 @@ int frame_launch(const FrameScratch& sc, const float* points, int H, int W, cons
         }
         a.n_lap = 0;
     }
-    void* args[1] = {&a};
     // one launch, or two with the event between them: the first ends once mask, normals and
-    // groups are final, the second joins the segments across tiles (the same arguments)
+    // groups are final, the second joins the segments across tiles (the same arguments; the
+    // merge phase joins the tile borders there, so that the first launch ends sooner)
+    if (normals_ready) a.border = nullptr;
+    void* args[1] = {&a};
     for (int part = normals_ready ? 1 : 0; part <= (normals_ready ? 2 : 0); ++part) {
         a.part = part;
         if (cudaLaunchCooperativeKernel(plan.frame_fn, dim3(grid), dim3(kThreads), args, plan.smem, s) != cudaSuccess) {

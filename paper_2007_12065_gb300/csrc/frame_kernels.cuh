@@ -606,11 +606,15 @@ __device__ __forceinline__ void quad_neighbour(QuadAcc& A, f2 a2, f2 cx, f2 cy, 
 // One bilateral tile: TH x T quads (TH = a.bil_th rows of T = 32, so that a warp spans a tile row);
 // geometry, `ph.iters` fused iterations (Eq. 3-6), then either
 // the carry for the next chunk or mask, normals, groups (Algorithm 4) and the tile-local
-// segments (Algorithm 5).
+// segments (Algorithm 5); with JOIN (the single-frame kernel) also the joins across the tile's
+// borders with finished neighbours.
 // Shared-memory header of the persistent kernels (128 bytes before the tiles' buffers): the staging
 // mbarriers from byte 0, the bilateral tile's deferred-normal count at byte 64, and for the stage
 // timing the last stamp at byte 72 and the stage totals' address (or nullptr) at byte 80.
 constexpr int kHdrExact = 64, kHdrStamp = 72, kHdrStages = 80;
+
+// The borders of a finished tile's segments with its neighbours' (defined with the merge phase).
+__device__ __forceinline__ void join_tile_borders(const FrameArgs& a, int tile);
 
 __device__ __forceinline__ void set_stage_timing(uint64_t* bar, unsigned long long* sns) {
     if (threadIdx.x == 0) *reinterpret_cast<unsigned long long**>(reinterpret_cast<unsigned char*>(bar) + kHdrStages) = sns;
@@ -633,7 +637,7 @@ __device__ __forceinline__ void stage_mark(uint64_t* bar, int k) {
     }
 }
 
-template <int R>
+template <int R, bool JOIN>
 __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float* smem, uint64_t* bar,
                          unsigned& parity) {
     stage_mark(bar, -1);
@@ -1101,6 +1105,9 @@ __device__ void bil_tile(const FrameArgs& a, const BilPhase& ph, int tile, float
         }
     }
     __syncthreads();
+    // (5) The borders with the neighbouring tiles, when this launch joins them here (the
+    // single-frame kernel; the batch kernel joins them in its merge phase).
+    if (JOIN && a.border) join_tile_borders(a, tile);
     stage_mark(bar, 4);
 }
 
@@ -1154,6 +1161,38 @@ __device__ __forceinline__ bool merge_pair(const FrameArgs& a, long long w, int&
     return true;
 }
 
+// merge_pair with the item's two groups and two labels loaded together (one round trip to L2
+// instead of two; the labels are read whether or not the item joins).
+__device__ __forceinline__ bool merge_pair_eager(const FrameArgs& a, long long w, int& ra, int& rb) {
+    const int Wq = a.W - 1, Hq = a.H - 1, TH = a.bil_th;
+    const long long n_row_items = (long long)(div_up(Hq, TH) - 1) * Wq;
+    int u, v, uj, vj;
+    if (w < n_row_items) {
+        u = (int)(w / Wq + 1) * TH;
+        v = (int)(w % Wq);
+        uj = u - 1;
+        vj = v;
+    } else {
+        const long long x = w - n_row_items;
+        v = (int)(x / Hq + 1) * T - 1;
+        u = (int)(x % Hq);
+        uj = u;
+        vj = v + 1;
+    }
+    const int i = 2 * (u * Wq + v);
+    const int j = 2 * (uj * Wq + vj) + 1;
+    const int g = __ldcg(a.groups + i), gj = __ldcg(a.groups + j);
+    ra = __ldcg(a.labels + i);
+    rb = __ldcg(a.labels + j);
+    if (g == PL3D_NO_GROUP || gj != g) return false;
+    if (a.max_offset > 0.f) {
+        const V3 ci = centroid_global(a, u, v, 0), cj = centroid_global(a, uj, vj, 1);
+        const float* nd = a.nd.v + 3 * g;
+        if (fabsf(nd[0] * (ci.x - cj.x) + nd[1] * (ci.y - cj.y) + nd[2] * (ci.z - cj.z)) > a.max_offset) return false;
+    }
+    return true;
+}
+
 // One union per distinct pair in a warp: consecutive lanes walk one border, where long runs
 // of twins join the same two tile segments; a lane whose pair (and frame) equals its left
 // neighbour's leaves the union to that lane. Called by whole warps.
@@ -1163,6 +1202,47 @@ __device__ __forceinline__ void merge_unite(int32_t* labels, bool link, int ra, 
     const int pf = __shfl_up_sync(0xffffffffu, frame, 1);
     const bool dup = (threadIdx.x & 31) > 0 && pa == ra && pb == rb && pf == frame;
     if (link && !dup) uf_unite(labels, ra, rb);
+}
+
+// Joins a finished tile's segments with its neighbours' across the tile's borders, in the
+// bilateral pass instead of a merge phase of its own. Each border is joined by the second of its
+// two tiles to finish: both add 1 to the border's counter (an acquire-release atomic, after the
+// barrier that ends the tile's label stores), and the one that reads an odd count joins it, so
+// that no tile waits for another. Every launch adds 2 to each counter, so the counters are even
+// between launches. Counter 2t is tile t's top border, 2t + 1 its left border. Warp k of the CTA
+// takes side k (top, left, bottom, right), its lanes along the border (merge_pair's items); the
+// other warps go on. Each item's groups and labels are loaded together; the unions halve the
+// paths they walk, which keeps the trees shallow for the flatten phase (walking both paths side by
+// side without halving measured 6 us slower per 480x640 frame, most of it in the flatten).
+__device__ __forceinline__ void join_tile_borders(const FrameArgs& a, int tile) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp >= 4) return;
+    const int Wq = a.W - 1, Hq = a.H - 1, TH = a.bil_th;
+    const int tiles_x = div_up(Wq, T), tiles_y = div_up(Hq, TH);
+    const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
+    const bool has = warp == 0 ? ty > 0 : warp == 1 ? tx > 0 : warp == 2 ? ty + 1 < tiles_y : tx + 1 < tiles_x;
+    if (!has) return;
+    const int c = warp == 0 ? 2 * tile : warp == 1 ? 2 * tile + 1 : warp == 2 ? 2 * (tile + tiles_x) : 2 * (tile + 1) + 1;
+    unsigned n = 0;
+    if (lane == 0) n = atom_add_acq_rel_gpu(a.border + c, 1u);
+    __syncwarp();   // the lanes' loads below ordered after lane 0's acquire
+    if (!(__shfl_sync(0xffffffffu, n, 0) & 1u)) return;   // the neighbour joins it when it finishes
+    // row borders first among the items, then columns
+    const long long n_row_items = (long long)(tiles_y - 1) * Wq;
+    const int len = (warp & 1) ? min(TH, Hq - ty * TH) : min(T, Wq - tx * T);
+    const long long w0 = warp == 0   ? (long long)(ty - 1) * Wq + tx * T
+                         : warp == 1 ? n_row_items + (long long)(tx - 1) * Hq + ty * TH
+                         : warp == 2 ? (long long)ty * Wq + tx * T
+                                     : n_row_items + (long long)tx * Hq + ty * TH;
+    int32_t* const L = a.labels;
+    for (int i0 = 0; i0 < len; i0 += 32) {   // the same trip count in every lane
+        int ra = -1, rb = -1;
+        const bool link = i0 + lane < len && merge_pair_eager(a, w0 + i0 + lane, ra, rb);
+        if (!link) ra = rb = -1;
+        const int pa = __shfl_up_sync(0xffffffffu, ra, 1), pb = __shfl_up_sync(0xffffffffu, rb, 1);
+        const bool dup = lane > 0 && pa == ra && pb == rb;   // one union per distinct pair
+        if (link && !dup) uf_unite(L, ra, rb);
+    }
 }
 
 __device__ __forceinline__ void merge_phase(const FrameArgs& a) {
@@ -1303,14 +1383,16 @@ __global__ void __launch_bounds__(kThreads, 2) frame_kernel(const __grid_constan
         const int tiles_bil = div_up(a.H - 1, a.bil_th) * div_up(a.W - 1, kTile);
         unsigned par0 = par & 1u;   // the bilateral stages through slot 0
         for (int c = 0; c < a.n_bil; ++c) {
-            for (int t = blockIdx.x; t < tiles_bil; t += gridDim.x) frame::bil_tile<RB>(a, a.bil[c], t, smem, bar, par0);
+            for (int t = blockIdx.x; t < tiles_bil; t += gridDim.x) frame::bil_tile<RB, true>(a, a.bil[c], t, smem, bar, par0);
             if (a.part == 0 || c + 1 < a.n_bil) grid_barrier(a.barrier, a.error);
         }
         frame::phase_mark(a, 1, t_prev);
     }
     if (a.part == 1) return;
-    frame::merge_phase(a);
-    grid_barrier(a.barrier, a.error);
+    if (!a.border) {   // else the bilateral tiles joined their borders
+        frame::merge_phase(a);
+        grid_barrier(a.barrier, a.error);
+    }
     frame::phase_mark(a, 2, t_prev);
     frame::flatten_phase(a);
     if (a.min_triangles > 0) {
@@ -1451,7 +1533,7 @@ __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const __grid_constan
                 }
                 acquired = f;
             }
-            frame::bil_tile<RB>(a, a.bil[c], t - __ldg(pre + f), smem, bar, par0);
+            frame::bil_tile<RB, false>(a, a.bil[c], t - __ldg(pre + f), smem, bar, par0);
         }
         grid_barrier(b.barrier, b.error);
     }

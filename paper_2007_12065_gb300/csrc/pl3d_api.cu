@@ -47,6 +47,15 @@ int grow_tri(pl3d_ctx* ctx, size_t need, cudaStream_t s) {
     return PL3D_OK;
 }
 
+// The tile-border counters start at zero (even: every launch adds two to each one it uses).
+int grow_border(pl3d_ctx* ctx, size_t need, cudaStream_t s) {
+    if (ctx->cap_border >= need) return PL3D_OK;
+    int rc = grow(&ctx->border, &ctx->cap_border, need, 1, s);
+    if (rc != PL3D_OK) return rc;
+    return cudaMemsetAsync(ctx->border, 0, ctx->cap_border * sizeof(unsigned), s) == cudaSuccess ? PL3D_OK
+                                                                                                : PL3D_ERR_CUDA;
+}
+
 // The device address of a page-locked (cudaHostAlloc'd or registered) host buffer, or nullptr
 // for memory the device cannot address directly (pageable memory, device memory).
 void* device_view(void* host) {
@@ -66,6 +75,7 @@ int run(pl3d_ctx* ctx, const float* points, int H, int W, const pl3d_params* p, 
     int rc;
     if ((rc = grow(&ctx->disp, &ctx->cap_points, npts, 6, s)) != PL3D_OK) return rc;
     if ((rc = grow_tri(ctx, ntri, s)) != PL3D_OK) return rc;
+    if ((rc = grow_border(ctx, border_counters(H, W, ctx->tuning), s)) != PL3D_OK) return rc;
     if (bilateral_passes(p, ctx->tuning) > 1 && (rc = grow(&ctx->carry, &ctx->cap_carry, ntri, 6, s)) != PL3D_OK) return rc;
 
     FrameScratch sc;
@@ -79,6 +89,8 @@ int run(pl3d_ctx* ctx, const float* points, int H, int W, const pl3d_params* p, 
     sc.error = ctx->error();
     sc.phase_ns = ctx->timing ? ctx->phase_ns() : nullptr;
     sc.lap1_sched = ctx->lap1_sched();
+    sc.border = ctx->border;
+    sc.cap_border = ctx->cap_border;
     sc.seed_flags = nullptr;
     sc.seed_centroids = nullptr;
 
@@ -126,6 +138,9 @@ int ctx_run(pl3d_ctx* ctx, const float* points, int H, int W, const pl3d_params*
 int ctx_reserve(pl3d_ctx* ctx, size_t points, cudaStream_t s) {
     int rc = grow(&ctx->disp, &ctx->cap_points, points, 6, s);
     if (rc == PL3D_OK) rc = grow_tri(ctx, 2 * points, s);
+    // tiles of 8 x 32 quads at the smallest height: at most about points / 16 of them, whatever
+    // the frame's shape, and two counters each
+    if (rc == PL3D_OK) rc = grow_border(ctx, points / 4 + 8, s);
     return rc;
 }
 
@@ -242,6 +257,7 @@ void pl3d_destroy(pl3d_ctx* c) {
         cudaFree(c->groups);
         cudaFree(c->sizes);
         cudaFree(c->ctl);
+        cudaFree(c->border);
         cudaFree(c->st_points);
         cudaFree(c->st_mask);
         cudaFree(c->st_normals);

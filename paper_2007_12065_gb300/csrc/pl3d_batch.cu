@@ -237,6 +237,8 @@ int run_batch(pl3d_ctx* c, const pl3d_frame* frames, int n, cudaStream_t s) {
         sc.error = c->error();
         sc.phase_ns = nullptr;
         sc.lap1_sched = c->lap1_sched();
+        sc.border = nullptr;   // the batch kernel joins the tile borders in its merge phase
+        sc.cap_border = 0;
         FramePlan plan;
         rc = frame_build(fa[i], plan, sc, f.points, f.H, f.W, f.params, f.dominant_normals, f.K, f.out_tri_mask,
                          f.out_normals, f.out_labels, f.out_points, f.out_groups, t);

@@ -53,6 +53,8 @@ struct pl3d_ctx {
     int32_t* sizes = nullptr;       // cap_tri
     size_t cap_tri = 0;
     unsigned* ctl = nullptr;        // control words (ctxutil::kCtlBytes): barrier, error, timing, lap1 counter
+    unsigned* border = nullptr;     // cap_border tile-border counters of the single-frame kernel, even at rest
+    size_t cap_border = 0;
     uint8_t* seed_flags = nullptr;  // PL3D_FLAG_SEED_PTP: per-root flags, cap_seed
     size_t cap_seed = 0;
     float* seed_centroids = nullptr;   // PL3D_FLAG_SEED_PTP: 3 cap_seed_c floats

@@ -133,6 +133,9 @@ struct FrameArgs {
     int min_triangles;
     unsigned* barrier;             // [2] grid barrier state
     int* error;                    // device error word (sync.cuh bits)
+    unsigned* border;              // [2 x bilateral tiles], even between launches: counters of the tile
+                                   // borders that the bilateral tiles join themselves; nullptr: the
+                                   // merge phase joins them
     unsigned long long* phase_ns;  // [4] accumulated phase times (then the lap1 stamps and the bilateral
                                    // stage totals, see kStageSlot), or nullptr
     int part;                      // 0: the whole path; 1: smoothing and tile-local segments only
@@ -226,6 +229,8 @@ struct FrameScratch {
     int* error;                    // [1]
     unsigned long long* phase_ns;  // [4] or nullptr
     unsigned* lap1_sched;          // [2], zero at rest: the single-iteration Laplacian's task counter
+    unsigned* border;              // cap_border counters, zeroed when allocated, or nullptr
+    size_t cap_border;
     uint8_t* seed_flags;           // >= 2 Q, PL3D_FLAG_SEED_PTP only
     float* seed_centroids;         // >= 6 Q, PL3D_FLAG_SEED_PTP only
 };
@@ -241,6 +246,9 @@ struct Tuning {
                                    // falls back to 32
     int bil_tile_h;                // bilateral tile height in quads, 0 = 32
 };
+
+// Tile-border counters a frame's bilateral tiles use under tuning t (FrameArgs::border).
+size_t border_counters(int H, int W, const Tuning& t);
 
 // Number of bilateral passes the parameters need (> 1 needs the carry buffers).
 int bilateral_passes(const pl3d_params* p, const Tuning& t);

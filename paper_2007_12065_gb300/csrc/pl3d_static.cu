@@ -152,6 +152,8 @@ extern "C" int pl3d_extract_planes_static(const float* points, int H, int W, con
     sc.error = reinterpret_cast<int*>(ctl + 2);
     sc.phase_ns = nullptr;
     sc.lap1_sched = ctl + 4;
+    sc.border = nullptr;   // the tile borders joined by the merge phase (no counters in the fixed scratch)
+    sc.cap_border = 0;
     return frame_launch(sc, points, H, W, p, nd_host, K, out_mask, out_normals, out_labels, nullptr, nullptr,
                         Tuning{0, 0, 0}, (cudaStream_t)stream);
 }
