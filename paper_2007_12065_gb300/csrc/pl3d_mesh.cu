@@ -12,6 +12,15 @@
 //   D  HE from the neighbours' T_map (the twin rules of Algorithm 2) and the boundary half-edges
 //      (no twin, or a twin of another label); sort keys: the segment index of each T entry (the
 //      segment count for an unlabelled one, so it sorts last)
+//   With at most kMaxOnePass segments, the lists come from one counting pass instead of a sort:
+//   D also counts the entries of each (segment, chunk of T) pair into a segments x chunks matrix
+//   (zeroed in C; warp-aggregated atomics), then
+//   S  each segment's row becomes its exclusive prefix over the chunks, and the row total its size
+//   P  a stable scatter straight into the segment lists: an entry's place is its segment's start,
+//      plus its row's prefix at its chunk, plus the entries of its segment in the chunk's earlier
+//      warps and its rank among equal segments in its warp (__match_any_sync); the CSR offsets
+//      are the segment starts
+//   With more segments:
 //   R  a stable LSD radix sort of (segment index, T index) with digits of up to 8 bits: per-chunk
 //      digit histograms; per-digit exclusive scans over the chunks; a stable scatter that ranks
 //      equal digits inside a warp with __match_any_sync and across warps with per-warp counters
@@ -20,6 +29,8 @@
 // through the non-coherent read-only path.
 // Everything in T order keeps GID order, so the lists come out sorted by (label, T index).
 #include <string.h>
+
+#include <algorithm>
 
 #include "pl3d_ctx.cuh"
 #include "sync.cuh"
@@ -31,8 +42,13 @@ constexpr int kChunk = 1024;
 constexpr int kPer = kChunk / kThreads;   // 4 consecutive entries per thread
 constexpr int kMaxDigitBits = 8;   // radix digits of up to 8 bits (11-bit digits, one pass below 2048 segments, measured slower)
 constexpr int kMaxBins = 1 << kMaxDigitBits;
-constexpr size_t kSmemBytes = 2 * kMaxBins * sizeof(int) + (size_t)(kThreads / 32) * kMaxBins * sizeof(uint16_t);
 constexpr int kWarps = kThreads / 32;
+// one counting pass up to this many segments: their starts and per-warp counts in shared memory
+constexpr int kMaxOnePass = 2048;
+constexpr size_t kSmemRadix = 2 * kMaxBins * sizeof(int) + (size_t)kWarps * kMaxBins * sizeof(uint16_t);
+constexpr size_t kSmemOnePass = kMaxOnePass * sizeof(int) + (size_t)kWarps * kMaxOnePass * sizeof(uint16_t);
+constexpr size_t kSmemBytes = kSmemRadix > kSmemOnePass ? kSmemRadix : kSmemOnePass;
+static_assert(kMaxOnePass % kThreads == 0, "segment starts: the same count per thread");
 
 struct MeshArgs {
     const float* points;
@@ -55,6 +71,9 @@ struct MeshArgs {
     int32_t* vals[2];            // [2Q]
     int32_t* hist;               // [kMaxBins][n_chunks]
     int32_t* bin_tot;            // [kMaxBins]
+    int32_t* seg_chunk;          // [kMaxOnePass][n_chunks]: entries per (segment, chunk of T) -> row prefixes
+    int32_t* seg_cnt;            // [kMaxOnePass]: entries per segment
+    long long seg_chunk_cap;     // entries of seg_chunk
     unsigned* barrier;
     int* error;
 };
@@ -183,6 +202,9 @@ __global__ void __launch_bounds__(kThreads, 4) mesh_kernel(const __grid_constant
         }
     }
     const int nS = (int)nS_l;
+    const int Ct = (int)((nT + kChunk - 1) / kChunk);   // chunks of T entries
+    // the lists from one counting pass (S, P) instead of the radix sort (R, G)
+    const bool one = a.labels && a.seg_chunk && nS > 0 && nS <= kMaxOnePass && (long long)nS * Ct <= a.seg_chunk_cap;
 
     // C: T, T_map, T labels, segment roots (GID order). A GID's place among the chunk's entries
     // is the count of (round, warp) blocks before its own plus its lane's rank in its warp's
@@ -270,6 +292,11 @@ __global__ void __launch_bounds__(kThreads, 4) mesh_kernel(const __grid_constant
         }
         __syncthreads();   // the next chunk rewrites the block counts
     }
+    if (one) {   // the (segment, chunk) counts start at zero
+        const long long nz = (long long)nS * Ct;
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nz; i += (long long)gridDim.x * blockDim.x)
+            a.seg_chunk[i] = 0;
+    }
     grid_barrier(a.barrier, a.error);
 
     // D: HE (Algorithm 2) and the sort keys
@@ -328,13 +355,24 @@ __global__ void __launch_bounds__(kThreads, 4) mesh_kernel(const __grid_constant
             if (a.labels && nS > 0) {
                 for (int side = 0; side < 2; ++side) {
                     const int t = side == 0 ? first : second;
-                    if (t < 0) continue;
-                    // the segment index of the label's root; a label that names no root (only
-                    // possible for labels not made by pl3d_extract_planes) sorts with the rest
-                    const int l = __ldcg(a.tlab + t);
-                    const int k = (l >= 0 && l < n) ? __ldcg(a.root_idx + l) : -1;
-                    a.keys[0][t] = k >= 0 ? k : nS;
-                    a.vals[0][t] = t;
+                    int key = nS;
+                    if (t >= 0) {
+                        // the segment index of the label's root; a label that names no root (only
+                        // possible for labels not made by pl3d_extract_planes) sorts with the rest
+                        const int l = __ldcg(a.tlab + t);
+                        const int k = (l >= 0 && l < n) ? __ldcg(a.root_idx + l) : -1;
+                        key = k >= 0 ? k : nS;
+                        a.keys[0][t] = key;
+                        if (!one) a.vals[0][t] = t;
+                    }
+                    if (one) {
+                        // entries per (segment, chunk of T): one atomic per group of equal cells
+                        // among the warp's active lanes
+                        const int cell = (t >= 0 && key < nS) ? key * Ct + t / kChunk : -1;
+                        const unsigned peers = __match_any_sync(__activemask(), cell);
+                        if (cell >= 0 && (int)(threadIdx.x & 31) == __ffs(peers) - 1)
+                            atomicAdd(a.seg_chunk + cell, __popc(peers));
+                    }
                 }
             }
         }
@@ -346,8 +384,110 @@ __global__ void __launch_bounds__(kThreads, 4) mesh_kernel(const __grid_constant
     }
     grid_barrier(a.barrier, a.error);
 
+    if (one) {
+        const int ln = threadIdx.x & 31, wp = threadIdx.x >> 5;
+        // S: each segment's row of chunk counts becomes its exclusive prefix, and the row total
+        // the segment's size: a warp per row, in spans of 256 chunks whose loads (coalesced: lane
+        // l takes chunks l, l + 32, ...) are in flight together, scanned 32 at a time
+        {
+            constexpr int kSpan = 8;
+            for (int k = blockIdx.x * kWarps + wp; k < nS; k += gridDim.x * kWarps) {
+                int32_t* const row = a.seg_chunk + (long long)k * Ct;
+                int carry = 0;
+                for (int base = 0; base < Ct; base += 32 * kSpan) {
+                    int v[kSpan];
+#pragma unroll
+                    for (int j = 0; j < kSpan; ++j) {
+                        const int c = base + 32 * j + ln;
+                        v[j] = c < Ct ? __ldcg(row + c) : 0;
+                    }
+#pragma unroll
+                    for (int j = 0; j < kSpan; ++j) {
+                        int x = v[j];
+#pragma unroll
+                        for (int o = 1; o < 32; o <<= 1) {
+                            const int y = __shfl_up_sync(0xffffffffu, x, o);
+                            if (ln >= o) x += y;
+                        }
+                        const int c = base + 32 * j + ln;
+                        if (c < Ct) row[c] = carry + x - v[j];
+                        carry += __shfl_sync(0xffffffffu, x, 31);
+                    }
+                }
+                if (ln == 0) a.seg_cnt[k] = carry;
+            }
+        }
+        grid_barrier(a.barrier, a.error);
+        // P: stable scatter into the segment lists; the CSR offsets are the segment starts
+        int* const sh_start = mesh_smem;                                                  // [kMaxOnePass]
+        uint16_t* const wc = reinterpret_cast<uint16_t*>(mesh_smem + kMaxOnePass);       // [kWarps][kMaxOnePass]
+        for (int i = threadIdx.x; i < kWarps * kMaxOnePass / 2; i += kThreads) reinterpret_cast<unsigned*>(wc)[i] = 0u;
+        {
+            // segment starts: thread t scans its run of kPerT consecutive sizes, loaded together
+            constexpr int kPerT = kMaxOnePass / kThreads;
+            const int d0 = threadIdx.x * kPerT;
+            int v[kPerT];
+            int local = 0;
+#pragma unroll
+            for (int j = 0; j < kPerT; ++j) {
+                v[j] = d0 + j < nS ? __ldcg(a.seg_cnt + d0 + j) : 0;
+                local += v[j];
+            }
+            int tot;
+            int run = block_exclusive(local, sh_scan, &tot);
+#pragma unroll
+            for (int j = 0; j < kPerT; ++j) {
+                if (d0 + j < nS) {
+                    sh_start[d0 + j] = run;
+                    if (blockIdx.x == 0) a.seg_offsets[d0 + j] = run;
+                }
+                run += v[j];
+            }
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                a.seg_offsets[nS] = tot;
+                a.counts[2] = tot;
+            }
+        }
+        __syncthreads();
+        for (int c = blockIdx.x; c < Ct; c += gridDim.x) {
+            // warp w owns the 128 consecutive entries [c kChunk + 128 w, + 128), in 4 rounds of 32
+            const long long w0 = (long long)c * kChunk + wp * (kChunk / kWarps);
+            int rank[kPer], seg[kPer];
+#pragma unroll
+            for (int r = 0; r < kPer; ++r) {
+                const long long i = w0 + r * 32 + ln;
+                int k = i < nT ? __ldcg(a.keys[0] + i) : -1;
+                if (k >= nS) k = -1;   // in no segment
+                const unsigned peers = __match_any_sync(0xffffffffu, k);
+                const unsigned lower = peers & ((1u << ln) - 1u);
+                int base = 0;
+                if (k >= 0) base = wc[wp * kMaxOnePass + k];
+                __syncwarp();
+                if (k >= 0 && lower == 0) wc[wp * kMaxOnePass + k] = (uint16_t)(base + __popc(peers));
+                __syncwarp();
+                rank[r] = base + __popc(lower);
+                seg[r] = k;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < kPer; ++r) {
+                const int k = seg[r];
+                if (k < 0) continue;
+                int pre = 0;   // the segment's entries in the chunk's earlier warps
+                for (int w = 0; w < wp; ++w) pre += wc[w * kMaxOnePass + k];
+                const long long pos = (long long)sh_start[k] + __ldcg(a.seg_chunk + (long long)k * Ct + c) + pre + rank[r];
+                a.seg_tris[pos] = (int32_t)(w0 + r * 32 + ln);
+            }
+            __syncthreads();   // every warp has read the counts before any clears its own
+#pragma unroll
+            for (int r = 0; r < kPer; ++r)
+                if (seg[r] >= 0) wc[wp * kMaxOnePass + seg[r]] = 0;
+            __syncwarp();
+        }
+        return;
+    }
+
     // R: stable LSD radix sort of (segment index, T index) over the T entries
-    const int Ct = (int)((nT + kChunk - 1) / kChunk);
     const int key_bits = 32 - __clz(nS);   // keys run over 0..nS
     const int passes = (key_bits + kMaxDigitBits - 1) / kMaxDigitBits;
     const int dbits = (key_bits + passes - 1) / passes;
@@ -508,11 +648,15 @@ extern "C" int pl3d_extract_mesh(pl3d_ctx* ctx, const float* points, const int32
     const size_t ntri = 2 * (size_t)(H - 1) * (W - 1);
     const int C = (int)((ntri + mesh::kChunk - 1) / mesh::kChunk);
     // scratch: chunk counts, root index, T labels, keys and values (double buffered), histograms,
-    // digit totals, flag bits
+    // digit totals, flag bits, and the (segment, chunk) counts and segment sizes of the one-pass
+    // lists (up to kMaxOnePass segments x C chunks, at most 2^24 entries: 8 B per triangle below
+    // that; a frame whose segments need more takes the radix sort)
     const size_t b_cnt = align_up(2 * (size_t)C * 4, 256), b_tri = align_up(ntri * 4, 256);
     const size_t b_hist = align_up((size_t)mesh::kMaxBins * C * 4, 256), b_bins = align_up(mesh::kMaxBins * 4, 256);
     const size_t b_bits = align_up(2 * (size_t)C * (mesh::kChunk / 32) * 4, 256);
-    int rc = grow_mesh(ctx, b_cnt + 6 * b_tri + b_hist + b_bins + b_bits, s);
+    const long long seg_cap = labels ? std::min((long long)mesh::kMaxOnePass * C, 1LL << 24) : 0;
+    const size_t b_segc = align_up((size_t)seg_cap * 4, 256), b_segn = align_up(mesh::kMaxOnePass * 4, 256);
+    int rc = grow_mesh(ctx, b_cnt + 6 * b_tri + b_hist + b_bins + b_bits + b_segc + b_segn, s);
     if (rc != PL3D_OK) return rc;
     mesh::MeshArgs a;
     memset(&a, 0, sizeof(a));
@@ -547,6 +691,11 @@ extern "C" int pl3d_extract_mesh(pl3d_ctx* ctx, const float* points, const int32
     a.bin_tot = reinterpret_cast<int32_t*>(p);
     p += b_bins;
     a.bits = reinterpret_cast<unsigned*>(p);
+    p += b_bits;
+    a.seg_chunk = seg_cap > 0 ? reinterpret_cast<int32_t*>(p) : nullptr;
+    a.seg_chunk_cap = seg_cap;
+    p += b_segc;
+    a.seg_cnt = reinterpret_cast<int32_t*>(p);
     a.barrier = ctx->barrier();
     a.error = ctx->error();
     int dev = 0;
