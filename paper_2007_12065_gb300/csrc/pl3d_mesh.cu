@@ -8,7 +8,7 @@
 //      roots (a label is the smallest GID of its segment, so a root is labelled with itself),
 //      kept as ballot words (no scan phase: each CTA sums the counts of the chunks before its own
 //      when it needs them)
-//   C  T, T_map, the label of each T entry, and the segment index of each root, in GID order
+//   C  T, T_map and the segment index of each root, in GID order
 //   D  HE from the neighbours' T_map (the twin rules of Algorithm 2) and the boundary half-edges
 //      (no twin, or a twin of another label); sort keys: the segment index of each T entry (the
 //      segment count for an unlabelled one, so it sorts last)
@@ -66,12 +66,11 @@ struct MeshArgs {
     int32_t* cnt;                // [2][n_chunks]: T entries and roots per chunk -> exclusive offsets
     unsigned* bits;              // [2][n_chunks kChunk / 32]: valid triangles, segment roots, one bit per GID
     int32_t* root_idx;           // [2Q]
-    int32_t* tlab;               // [2Q] label of each T entry
     int32_t* keys[2];            // [2Q]
     int32_t* vals[2];            // [2Q]
     int32_t* hist;               // [kMaxBins][n_chunks]
     int32_t* bin_tot;            // [kMaxBins]
-    int32_t* seg_chunk;          // [kMaxOnePass][n_chunks]: entries per (segment, chunk of T) -> row prefixes
+    int32_t* seg_chunk;          // [segments][chunks of T, padded to 8]: entries per (segment, chunk) -> row prefixes
     int32_t* seg_cnt;            // [kMaxOnePass]: entries per segment
     long long seg_chunk_cap;     // entries of seg_chunk
     unsigned* barrier;
@@ -203,10 +202,11 @@ __global__ void __launch_bounds__(kThreads, 4) mesh_kernel(const __grid_constant
     }
     const int nS = (int)nS_l;
     const int Ct = (int)((nT + kChunk - 1) / kChunk);   // chunks of T entries
+    const int Ctp = (Ct + 7) & ~7;   // the matrix's row stride: rows start on 32-byte boundaries
     // the lists from one counting pass (S, P) instead of the radix sort (R, G)
-    const bool one = a.labels && a.seg_chunk && nS > 0 && nS <= kMaxOnePass && (long long)nS * Ct <= a.seg_chunk_cap;
+    const bool one = a.labels && a.seg_chunk && nS > 0 && nS <= kMaxOnePass && (long long)nS * Ctp <= a.seg_chunk_cap;
 
-    // C: T, T_map, T labels, segment roots (GID order). A GID's place among the chunk's entries
+    // C: T, T_map, segment roots (GID order). A GID's place among the chunk's entries
     // is the count of (round, warp) blocks before its own plus its lane's rank in its warp's
     // ballot; the per-block counts live in sh_wc (free until the sort).
     constexpr int kBlocks = kPer * kWarps;   // (round, warp) blocks of a chunk
@@ -279,7 +279,6 @@ __global__ void __launch_bounds__(kThreads, 4) mesh_kernel(const __grid_constant
                 a.T[3LL * pt] = (int32_t)v[0];
                 a.T[3LL * pt + 1] = (int32_t)v[1];
                 a.T[3LL * pt + 2] = (int32_t)v[2];
-                a.tlab[pt] = a.labels ? __ldg(a.labels + g) : -1;
                 a.Tmap[g] = pt;
             } else {
                 a.Tmap[g] = -1;
@@ -292,8 +291,8 @@ __global__ void __launch_bounds__(kThreads, 4) mesh_kernel(const __grid_constant
         }
         __syncthreads();   // the next chunk rewrites the block counts
     }
-    if (one) {   // the (segment, chunk) counts start at zero
-        const long long nz = (long long)nS * Ct;
+    if (one) {   // the (segment, chunk) counts start at zero, the rows' padding included
+        const long long nz = (long long)nS * Ctp;
         for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nz; i += (long long)gridDim.x * blockDim.x)
             a.seg_chunk[i] = 0;
     }
@@ -306,6 +305,8 @@ __global__ void __launch_bounds__(kThreads, 4) mesh_kernel(const __grid_constant
             const int u = (int)(q / Wq), v = (int)(q - (long long)u * Wq);
             const int32_t* tm = a.Tmap;
             const int first = __ldcg(tm + 2 * q), second = __ldcg(tm + 2 * q + 1);
+            // the labels of the quad's two triangles (GIDs 2q, 2q + 1), loaded beside T_map
+            const int l1 = a.labels ? __ldg(a.labels + 2 * q) : -1, l2 = a.labels ? __ldg(a.labels + 2 * q + 1) : -1;
             if (first >= 0) {
                 const int right = v + 1 < Wq ? __ldcg(tm + 2 * (q + 1) + 1) : -1;
                 const int top = u > 0 ? __ldcg(tm + 2 * (q - Wq) + 1) : -1;
@@ -323,8 +324,6 @@ __global__ void __launch_bounds__(kThreads, 4) mesh_kernel(const __grid_constant
             if (a.border) {
                 // a half-edge is on a segment's boundary when it has no twin or the twin's label
                 // differs; unlabelled triangles have no boundary
-                const long long g1 = 2 * q, g2 = 2 * q + 1;
-                const int l1 = a.labels ? __ldg(a.labels + g1) : -1, l2 = a.labels ? __ldg(a.labels + g2) : -1;
                 if (first >= 0) {
                     unsigned bits = 0;
                     if (l1 >= 0) {
@@ -359,7 +358,7 @@ __global__ void __launch_bounds__(kThreads, 4) mesh_kernel(const __grid_constant
                     if (t >= 0) {
                         // the segment index of the label's root; a label that names no root (only
                         // possible for labels not made by pl3d_extract_planes) sorts with the rest
-                        const int l = __ldcg(a.tlab + t);
+                        const int l = side == 0 ? l1 : l2;
                         const int k = (l >= 0 && l < n) ? __ldcg(a.root_idx + l) : -1;
                         key = k >= 0 ? k : nS;
                         a.keys[0][t] = key;
@@ -368,7 +367,7 @@ __global__ void __launch_bounds__(kThreads, 4) mesh_kernel(const __grid_constant
                     if (one) {
                         // entries per (segment, chunk of T): one atomic per group of equal cells
                         // among the warp's active lanes
-                        const int cell = (t >= 0 && key < nS) ? key * Ct + t / kChunk : -1;
+                        const int cell = (t >= 0 && key < nS) ? key * Ctp + t / kChunk : -1;
                         const unsigned peers = __match_any_sync(__activemask(), cell);
                         if (cell >= 0 && (int)(threadIdx.x & 31) == __ffs(peers) - 1)
                             atomicAdd(a.seg_chunk + cell, __popc(peers));
@@ -387,32 +386,34 @@ __global__ void __launch_bounds__(kThreads, 4) mesh_kernel(const __grid_constant
     if (one) {
         const int ln = threadIdx.x & 31, wp = threadIdx.x >> 5;
         // S: each segment's row of chunk counts becomes its exclusive prefix, and the row total
-        // the segment's size: a warp per row, in spans of 256 chunks whose loads (coalesced: lane
-        // l takes chunks l, l + 32, ...) are in flight together, scanned 32 at a time
+        // the segment's size: a warp per row, in spans of 256 chunks, 8 consecutive per lane (two
+        // 16-byte loads; the padding past Ct is zero), scanned in registers and then across the
+        // lanes, carried from span to span
         {
-            constexpr int kSpan = 8;
             for (int k = blockIdx.x * kWarps + wp; k < nS; k += gridDim.x * kWarps) {
-                int32_t* const row = a.seg_chunk + (long long)k * Ct;
+                int32_t* const row = a.seg_chunk + (long long)k * Ctp;
                 int carry = 0;
-                for (int base = 0; base < Ct; base += 32 * kSpan) {
-                    int v[kSpan];
-#pragma unroll
-                    for (int j = 0; j < kSpan; ++j) {
-                        const int c = base + 32 * j + ln;
-                        v[j] = c < Ct ? __ldcg(row + c) : 0;
+                for (int base = 0; base < Ctp; base += 32 * 8) {
+                    const int c0 = base + 8 * ln;
+                    int4 u = make_int4(0, 0, 0, 0), w = u;
+                    if (c0 < Ctp) {
+                        u = __ldcg(reinterpret_cast<const int4*>(row + c0));
+                        w = __ldcg(reinterpret_cast<const int4*>(row + c0 + 4));
                     }
+                    const int e1 = u.x, e2 = e1 + u.y, e3 = e2 + u.z, e4 = e3 + u.w;   // exclusive in the lane
+                    const int e5 = e4 + w.x, e6 = e5 + w.y, e7 = e6 + w.z, local = e7 + w.w;
+                    int x = local;
 #pragma unroll
-                    for (int j = 0; j < kSpan; ++j) {
-                        int x = v[j];
-#pragma unroll
-                        for (int o = 1; o < 32; o <<= 1) {
-                            const int y = __shfl_up_sync(0xffffffffu, x, o);
-                            if (ln >= o) x += y;
-                        }
-                        const int c = base + 32 * j + ln;
-                        if (c < Ct) row[c] = carry + x - v[j];
-                        carry += __shfl_sync(0xffffffffu, x, 31);
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int y = __shfl_up_sync(0xffffffffu, x, o);
+                        if (ln >= o) x += y;
                     }
+                    const int r0 = carry + x - local;
+                    if (c0 < Ctp) {
+                        *reinterpret_cast<int4*>(row + c0) = make_int4(r0, r0 + e1, r0 + e2, r0 + e3);
+                        *reinterpret_cast<int4*>(row + c0 + 4) = make_int4(r0 + e4, r0 + e5, r0 + e6, r0 + e7);
+                    }
+                    carry += __shfl_sync(0xffffffffu, x, 31);
                 }
                 if (ln == 0) a.seg_cnt[k] = carry;
             }
@@ -475,7 +476,7 @@ __global__ void __launch_bounds__(kThreads, 4) mesh_kernel(const __grid_constant
                 if (k < 0) continue;
                 int pre = 0;   // the segment's entries in the chunk's earlier warps
                 for (int w = 0; w < wp; ++w) pre += wc[w * kMaxOnePass + k];
-                const long long pos = (long long)sh_start[k] + __ldcg(a.seg_chunk + (long long)k * Ct + c) + pre + rank[r];
+                const long long pos = (long long)sh_start[k] + __ldcg(a.seg_chunk + (long long)k * Ctp + c) + pre + rank[r];
                 a.seg_tris[pos] = (int32_t)(w0 + r * 32 + ln);
             }
             __syncthreads();   // every warp has read the counts before any clears its own
@@ -647,16 +648,16 @@ extern "C" int pl3d_extract_mesh(pl3d_ctx* ctx, const float* points, const int32
     cudaStream_t s = (cudaStream_t)stream;
     const size_t ntri = 2 * (size_t)(H - 1) * (W - 1);
     const int C = (int)((ntri + mesh::kChunk - 1) / mesh::kChunk);
-    // scratch: chunk counts, root index, T labels, keys and values (double buffered), histograms,
+    // scratch: chunk counts, root index, keys and values (double buffered), histograms,
     // digit totals, flag bits, and the (segment, chunk) counts and segment sizes of the one-pass
     // lists (up to kMaxOnePass segments x C chunks, at most 2^24 entries: 8 B per triangle below
     // that; a frame whose segments need more takes the radix sort)
     const size_t b_cnt = align_up(2 * (size_t)C * 4, 256), b_tri = align_up(ntri * 4, 256);
     const size_t b_hist = align_up((size_t)mesh::kMaxBins * C * 4, 256), b_bins = align_up(mesh::kMaxBins * 4, 256);
     const size_t b_bits = align_up(2 * (size_t)C * (mesh::kChunk / 32) * 4, 256);
-    const long long seg_cap = labels ? std::min((long long)mesh::kMaxOnePass * C, 1LL << 24) : 0;
+    const long long seg_cap = labels ? std::min((long long)mesh::kMaxOnePass * (C + 8), 1LL << 24) : 0;
     const size_t b_segc = align_up((size_t)seg_cap * 4, 256), b_segn = align_up(mesh::kMaxOnePass * 4, 256);
-    int rc = grow_mesh(ctx, b_cnt + 6 * b_tri + b_hist + b_bins + b_bits + b_segc + b_segn, s);
+    int rc = grow_mesh(ctx, b_cnt + 5 * b_tri + b_hist + b_bins + b_bits + b_segc + b_segn, s);
     if (rc != PL3D_OK) return rc;
     mesh::MeshArgs a;
     memset(&a, 0, sizeof(a));
@@ -677,8 +678,6 @@ extern "C" int pl3d_extract_mesh(pl3d_ctx* ctx, const float* points, const int32
     a.cnt = reinterpret_cast<int32_t*>(p);
     p += b_cnt;
     a.root_idx = reinterpret_cast<int32_t*>(p);
-    p += b_tri;
-    a.tlab = reinterpret_cast<int32_t*>(p);
     p += b_tri;
     for (int i = 0; i < 2; ++i) {
         a.keys[i] = reinterpret_cast<int32_t*>(p);
