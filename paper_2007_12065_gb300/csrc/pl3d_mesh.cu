@@ -130,8 +130,11 @@ __device__ __forceinline__ Flags gid_flags(const MeshArgs& a, long long g, long 
     if (g >= n) return f;
     long long v[3];
     tri_vertices(g, a.W, a.W - 1, v);
-    f.valid = vertex_valid(a.points, v[0]) && vertex_valid(a.points, v[1]) && vertex_valid(a.points, v[2]);
-    if (f.valid && a.labels) f.root = __ldg(a.labels + g) == (int)g;
+    // the three points and the label loaded together (no short circuit between them)
+    const bool v0 = vertex_valid(a.points, v[0]), v1 = vertex_valid(a.points, v[1]), v2 = vertex_valid(a.points, v[2]);
+    const int lab = a.labels ? __ldg(a.labels + g) : -1;
+    f.valid = v0 & v1 & v2;
+    f.root = f.valid && lab == (int)g;
     return f;
 }
 
@@ -304,19 +307,28 @@ __global__ void __launch_bounds__(kThreads, 4) mesh_kernel(const __grid_constant
         for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < (long long)Hq * Wq; q += stride) {
             const int u = (int)(q / Wq), v = (int)(q - (long long)u * Wq);
             const int32_t* tm = a.Tmap;
+            // every load of the quad issued up front (none waits on another's value): its two
+            // T_map entries and its neighbours' across its four outer edges, and the labels of
+            // the same triangles (GIDs 2q, 2q + 1 and the neighbours')
+            const bool hasr = v + 1 < Wq, hast = u > 0, hasl = v > 0, hasb = u + 1 < Hq;
             const int first = __ldcg(tm + 2 * q), second = __ldcg(tm + 2 * q + 1);
-            // the labels of the quad's two triangles (GIDs 2q, 2q + 1), loaded beside T_map
-            const int l1 = a.labels ? __ldg(a.labels + 2 * q) : -1, l2 = a.labels ? __ldg(a.labels + 2 * q + 1) : -1;
+            const int right = hasr ? __ldcg(tm + 2 * (q + 1) + 1) : -1;
+            const int top = hast ? __ldcg(tm + 2 * (q - Wq) + 1) : -1;
+            const int left = hasl ? __ldcg(tm + 2 * (q - 1)) : -1;
+            const int bottom = hasb ? __ldcg(tm + 2 * (q + Wq)) : -1;
+            const int32_t* const L = a.labels;
+            const int l1 = L ? __ldg(L + 2 * q) : -1, l2 = L ? __ldg(L + 2 * q + 1) : -1;
+            const bool bd = a.border && L;
+            const int lr = bd && hasr ? __ldg(L + 2 * (q + 1) + 1) : -1;
+            const int lt = bd && hast ? __ldg(L + 2 * (q - Wq) + 1) : -1;
+            const int ll = bd && hasl ? __ldg(L + 2 * (q - 1)) : -1;
+            const int lb = bd && hasb ? __ldg(L + 2 * (q + Wq)) : -1;
             if (first >= 0) {
-                const int right = v + 1 < Wq ? __ldcg(tm + 2 * (q + 1) + 1) : -1;
-                const int top = u > 0 ? __ldcg(tm + 2 * (q - Wq) + 1) : -1;
                 a.HE[3LL * first] = right >= 0 ? 3 * right : -1;
                 a.HE[3LL * first + 1] = top >= 0 ? 3 * top + 1 : -1;
                 a.HE[3LL * first + 2] = second >= 0 ? 3 * second + 2 : -1;
             }
             if (second >= 0) {
-                const int left = v > 0 ? __ldcg(tm + 2 * (q - 1)) : -1;
-                const int bottom = u + 1 < Hq ? __ldcg(tm + 2 * (q + Wq)) : -1;
                 a.HE[3LL * second] = left >= 0 ? 3 * left : -1;
                 a.HE[3LL * second + 1] = bottom >= 0 ? 3 * bottom + 1 : -1;
                 a.HE[3LL * second + 2] = first >= 0 ? 3 * first + 2 : -1;
@@ -327,12 +339,8 @@ __global__ void __launch_bounds__(kThreads, 4) mesh_kernel(const __grid_constant
                 if (first >= 0) {
                     unsigned bits = 0;
                     if (l1 >= 0) {
-                        const int lr = v + 1 < Wq ? __ldg(a.labels + 2 * (q + 1) + 1) : -1;
-                        const int lt = u > 0 ? __ldg(a.labels + 2 * (q - Wq) + 1) : -1;
-                        const bool hr = v + 1 < Wq && __ldcg(tm + 2 * (q + 1) + 1) >= 0;
-                        const bool ht = u > 0 && __ldcg(tm + 2 * (q - Wq) + 1) >= 0;
-                        bits |= (!hr || lr != l1) ? 1u : 0u;
-                        bits |= (!ht || lt != l1) ? 2u : 0u;
+                        bits |= (right < 0 || lr != l1) ? 1u : 0u;
+                        bits |= (top < 0 || lt != l1) ? 2u : 0u;
                         bits |= (second < 0 || l2 != l1) ? 4u : 0u;
                     }
                     a.border[first] = (uint8_t)bits;
@@ -340,12 +348,8 @@ __global__ void __launch_bounds__(kThreads, 4) mesh_kernel(const __grid_constant
                 if (second >= 0) {
                     unsigned bits = 0;
                     if (l2 >= 0) {
-                        const int ll = v > 0 ? __ldg(a.labels + 2 * (q - 1)) : -1;
-                        const int lb = u + 1 < Hq ? __ldg(a.labels + 2 * (q + Wq)) : -1;
-                        const bool hl = v > 0 && __ldcg(tm + 2 * (q - 1)) >= 0;
-                        const bool hb = u + 1 < Hq && __ldcg(tm + 2 * (q + Wq)) >= 0;
-                        bits |= (!hl || ll != l2) ? 1u : 0u;
-                        bits |= (!hb || lb != l2) ? 2u : 0u;
+                        bits |= (left < 0 || ll != l2) ? 1u : 0u;
+                        bits |= (bottom < 0 || lb != l2) ? 2u : 0u;
                         bits |= (first < 0 || l1 != l2) ? 4u : 0u;
                     }
                     a.border[second] = (uint8_t)bits;
