@@ -121,6 +121,27 @@ __device__ __forceinline__ int block_exclusive(int v, int* sh, int* total) {
     return r;
 }
 
+// Sums of a and b over the CTA, in every thread (one barrier to publish, one before sh is reused).
+// Uses sh[2 kWarps].
+__device__ __forceinline__ void block_sum2(int a, int b, int* sh, int* ta, int* tb) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int wa = (int)__reduce_add_sync(0xffffffffu, (unsigned)a), wb = (int)__reduce_add_sync(0xffffffffu, (unsigned)b);
+    if (lane == 0) {
+        sh[warp] = wa;
+        sh[kWarps + warp] = wb;
+    }
+    __syncthreads();
+    int sa = 0, sb = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+        sa += sh[w];
+        sb += sh[kWarps + w];
+    }
+    *ta = sa;
+    *tb = sb;
+    __syncthreads();
+}
+
 struct Flags {
     bool valid, root;
 };
@@ -140,6 +161,7 @@ __device__ __forceinline__ Flags gid_flags(const MeshArgs& a, long long g, long 
 
 __global__ void __launch_bounds__(kThreads, 4) mesh_kernel(const __grid_constant__ MeshArgs a) {
     __shared__ int sh_scan[kWarps + 1];
+    __shared__ int sh_sum[2 * kWarps];
     // dynamic: digit counts [kMaxBins], digit bases [kMaxBins], per-warp digit counts
     // [kWarps][kMaxBins] (16-bit: at most kChunk / kWarps entries per warp)
     extern __shared__ int mesh_smem[];
@@ -158,10 +180,13 @@ __global__ void __launch_bounds__(kThreads, 4) mesh_kernel(const __grid_constant
     for (int c = blockIdx.x; c < C; c += gridDim.x) {
         const long long c0 = (long long)c * kChunk;
         int nt = 0, nr = 0;
+        Flags fl[kPer];
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) fl[j] = gid_flags(a, c0 + j * kThreads + threadIdx.x, n);   // loads in flight together
 #pragma unroll
         for (int j = 0; j < kPer; ++j) {
             const long long g = c0 + j * kThreads + threadIdx.x;
-            const Flags f = gid_flags(a, g, n);
+            const Flags f = fl[j];
             nt += f.valid;
             nr += f.root;
             if (a.labels && g < n) a.root_idx[g] = -1;
@@ -174,8 +199,7 @@ __global__ void __launch_bounds__(kThreads, 4) mesh_kernel(const __grid_constant
             }
         }
         int tt, tr;
-        block_exclusive(nt, sh_scan, &tt);
-        block_exclusive(nr, sh_scan, &tr);
+        block_sum2(nt, nr, sh_sum, &tt, &tr);
         if (threadIdx.x == 0) {
             cT[c] = tt;
             cR[c] = tr;
@@ -193,8 +217,7 @@ __global__ void __launch_bounds__(kThreads, 4) mesh_kernel(const __grid_constant
             sr += __ldcg(cR + i);
         }
         int tt, tr;
-        block_exclusive((int)st, sh_scan, &tt);
-        block_exclusive((int)sr, sh_scan, &tr);
+        block_sum2((int)st, (int)sr, sh_sum, &tt, &tr);
         nT = tt;
         nS_l = tr;
         if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -244,8 +267,7 @@ __global__ void __launch_bounds__(kThreads, 4) mesh_kernel(const __grid_constant
             br += __ldcg(cR + i);
         }
         int ct, cr;
-        block_exclusive((int)bt, sh_scan, &ct);   // (its barriers also publish the counts above)
-        block_exclusive((int)br, sh_scan, &cr);
+        block_sum2((int)bt, (int)br, sh_sum, &ct, &cr);   // (its barriers also publish the counts above)
         if (warp == 0) {   // exclusive prefix over the (round, warp) blocks, two per lane
             const int k0 = 2 * lane;
             const int t0 = k0 < kBlocks ? cntT[k0] : 0, t1 = k0 + 1 < kBlocks ? cntT[k0 + 1] : 0;
@@ -457,11 +479,15 @@ __global__ void __launch_bounds__(kThreads, 4) mesh_kernel(const __grid_constant
         for (int c = blockIdx.x; c < Ct; c += gridDim.x) {
             // warp w owns the 128 consecutive entries [c kChunk + 128 w, + 128), in 4 rounds of 32
             const long long w0 = (long long)c * kChunk + wp * (kChunk / kWarps);
-            int rank[kPer], seg[kPer];
+            int rank[kPer], seg[kPer], kk[kPer];
+#pragma unroll
+            for (int r = 0; r < kPer; ++r) {   // the keys' loads in flight together
+                const long long i = w0 + r * 32 + ln;
+                kk[r] = i < nT ? __ldcg(a.keys[0] + i) : -1;
+            }
 #pragma unroll
             for (int r = 0; r < kPer; ++r) {
-                const long long i = w0 + r * 32 + ln;
-                int k = i < nT ? __ldcg(a.keys[0] + i) : -1;
+                int k = kk[r];
                 if (k >= nS) k = -1;   // in no segment
                 const unsigned peers = __match_any_sync(0xffffffffu, k);
                 const unsigned lower = peers & ((1u << ln) - 1u);
