@@ -91,6 +91,23 @@ def test_many_segments_three_radix_passes(env):
     assert dev["counts"][1] > 65536
 
 
+@pytest.mark.parametrize("n_seg", [1, 2, 255, 256, 2047, 2048, 2049, 4097])
+def test_segment_counts_around_the_counting_pass(env, n_seg):
+    """Up to 2048 segments the lists come from one counting pass, beyond it from the radix sort:
+    n_seg - 1 segments of a single valid triangle, spread over the frame, and one segment of all
+    other valid triangles (its label the smallest of their GIDs), on both sides of that limit."""
+    f = synth.rgbd_120x160()
+    _, Tmap = oracle.extract_triangles(oracle.widen(f.points))
+    valid = np.nonzero(np.asarray(Tmap) >= 0)[0]
+    single = valid[np.linspace(0, len(valid) - 1, n_seg - 1).astype(np.int64)] if n_seg > 1 else valid[:0]
+    labels = np.full(len(Tmap), -1, np.int32)
+    rest = np.setdiff1d(valid, single)
+    labels[rest] = rest.min()
+    labels[single] = single
+    dev, ref = _check(env, f.points, labels)
+    assert dev["counts"][1] == n_seg
+
+
 def test_argument_checks(env):
     pl3d, ctx, torch = env
     import ctypes
