@@ -117,8 +117,11 @@ int pl3d_validate(const pl3d_params* params, int H, int W, const float* dominant
 
 /* Creates a context bound to CUDA device `cuda_device` (the device must be sm_103-class,
  * else PL3D_ERR_UNSUPPORTED). The context owns scratch memory that grows to the largest
- * frame seen (growth synchronises the stream of the call that grows it). *out receives the
- * context; on error *out is NULL. */
+ * frame seen (growth synchronises the stream of the call that grows it): displacements,
+ * groups, the grid-barrier and error words, and the counters with which the tiles of one
+ * launch decide which of two neighbours joins their shared border. Calls on one context run
+ * one after another: enqueue them on one stream (or order their streams), and use a context
+ * per concurrent stream or thread. *out receives the context; on error *out is NULL. */
 int pl3d_create(pl3d_ctx** out, int cuda_device);
 
 /* Releases the context and its scratch memory after synchronising its device.
